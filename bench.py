@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of the Laplacian-preconditioned Schur solve inside one full
+one-way SIMPLE-IBM time step on GB300.
+
+Workload (default): 256^3 MAC grid on the unit cube, eight spheres with radii
+uniform in [0.05, 0.1] at seeded non-overlapping positions, 60000 Fibonacci
+markers split by area, random rigid marker velocities in [-1, 1], a smooth
+random body force (8 sine modes), Re 200, dt 1e-3, first step from rest,
+FGMRES to a relative residual of 1e-8.
+
+A step = marker binning (ibm_set_markers) + ibm_step (predictor, correction
+right-hand sides, Schur solve, force recovery, update, diagnostics): every
+row of the hot path, one Schur solve per step, so steps/s = Schur solves/s.
+The headline `value` uses the mixed form (FP64 FGMRES, FP32 V-cycle); the FP64
+form and the solve alone are reported beside it.
+
+Multi-GPU: replicas only (one independent workload per rank, no collective on
+the data path); `value` sums the ranks' step rates over the slowest rank's
+time.  `--impl reference` times the CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Schur solves/s at 256^3 to 1e-8 residual, FP32-precond vs FP64; HBM fraction"
+UNIT = "solves/s"
+SAMPLE_ITERS = 3           # FGMRES iterations in the CPU oracle's bounded sample
+
+# DRAM bytes (read + write) per launch of the dominant kernels from one ncu
+# capture (profiles/*.md), null once the kernel has changed since.
+NCU_TRAFFIC = {}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_sample(W, n_iters_full):
+    """Bounded CPU sample of one oracle step: setup, predictor and right-hand
+    sides, SAMPLE_ITERS FGMRES iterations (exact L^+ by DCT), force recovery
+    and update.  Returns (estimated seconds per full step, detail)."""
+    import numpy as np
+    from oracle import helmholtz, mac, schur
+    workers = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    g = mac.Grid(W.n)
+    sysm = schur.SchurSystem(g, W.X)
+    a = 1.5 / W.dt
+    rhs = W.f_body * g.interior_face_mask_packed()
+    us = helmholtz.solve(g, rhs, a, 1.0 / W.Re, workers=workers)
+    rhs_F = a * (sysm.R.T @ us - W.U_gamma.ravel())
+    b = sysm.rhs_scalar(a * mac.apply_GT(g, us), rhs_F)
+    t1 = time.perf_counter()
+    x, it, rel, _ = schur.fgmres(sysm.apply_S_tilde, b,
+                                 lambda r: mac.laplacian_pinv(g, r, workers=workers),
+                                 rtol=1e-8, restart=60, maxit=SAMPLE_ITERS)
+    t2 = time.perf_counter()
+    Fc = sysm.force_scalar(x, rhs_F)
+    u = us + (2.0 * W.dt / 3.0) * (-mac.apply_G(g, x) + sysm.R @ Fc)
+    t3 = time.perf_counter()
+    est = (t1 - t0) + (t2 - t1) / SAMPLE_ITERS * n_iters_full + (t3 - t2)
+    return est, dict(setup_predictor_s=t1 - t0, sample_iters=SAMPLE_ITERS,
+                     sample_solve_s=t2 - t1, update_s=t3 - t2, sample_wall_s=t3 - t0,
+                     workers=workers, est_step_s=est, iters_full=n_iters_full, _u=float(u[0]))
+
+
+def oracle_iterations(cfg):
+    p = ROOT / "oracle" / "iteration_counts.json"
+    d = json.loads(p.read_text())
+    return int(d[f"config{cfg}_stated_markers_rtol1e-8"])
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def workload_config(W):
+    return {"workload": f"{W.name}: {W.n}^3 MAC grid, {len(W.radii)} spheres r in "
+                        f"[0.05,0.1], {W.n_markers} markers (spacing ratio "
+                        f"{W.info['spacing_ratio']:.2f}), Re {W.Re:g}, dt {W.dt:g}, first "
+                        f"step from rest, FGMRES rtol 1e-8",
+            "grid": [W.n, W.n, W.n], "markers": W.n_markers, "bodies": len(W.radii),
+            "Re": W.Re, "dt": W.dt, "rtol": 1e-8,
+            "l2": "no flush: every field (>= 134 MB) exceeds the 129 MB L2",
+            "parallelism": "replicas"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_2501_15314_gb300 import workloads as wl
+    W = wl.config(args.config, secondary=True)
+    n_it = oracle_iterations(args.config)
+    for _ in range(args.warmup):
+        oracle_sample(W, n_it)
+    ests, details = [], []
+    for _ in range(args.steps):
+        e, d = oracle_sample(W, n_it)
+        ests.append(e)
+        details.append(d)
+    value = len(ests) / sum(ests)
+    cores = details[-1]["workers"]
+    sample = (f"per step: oracle setup + predictor + RHS, {SAMPLE_ITERS} of {n_it} FGMRES "
+              f"iterations (exact L^+ by DCT), force recovery and update at the full workload; "
+              f"solve time scaled by {n_it}/{SAMPLE_ITERS}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(W),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+
+    W = wl.config(args.config, secondary=True)
+    n = W.n
+    s = IBMSolver(n, Re=W.Re, dt=W.dt)
+    lib = s.lib
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    X = dev(W.X)
+    U = dev(W.U_gamma.ravel())
+    f = dev(W.f_body)
+    nf, m, k = s.nf, s.m, 3 * W.n_markers
+    zf, zc, zk = (torch.zeros(nf, dtype=torch.float64, device="cuda"),
+                  torch.zeros(m, dtype=torch.float64, device="cuda"),
+                  torch.zeros(k, dtype=torch.float64, device="cuda"))
+    out = dict(u=torch.empty_like(zf), p=torch.empty_like(zc), F=torch.empty_like(zk))
+    stream = s.stream
+
+    def step(prec):
+        s.set_markers(X)
+        _, st = s.step(zf, zf, zc, zk, U, f, out=out, precond_prec=prec, rtol=1e-8)
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, K):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = [fn() for _ in range(K)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats
+
+    # ---- mixed form (headline) ----
+    for _ in range(args.warmup):
+        step(_lib.IBM_PREC_FP32)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = lib.ibm_kernel_launches()
+    s.profile_enable(True)
+    ms_mixed, st_mixed = timed(lambda: step(_lib.IBM_PREC_FP32), args.steps)
+    prof = s.profile_read()
+    launches = lib.ibm_kernel_launches() - l0
+    s.profile_enable(False)
+    clk = clocks.stop()
+
+    # ---- FP64 form ----
+    k64 = max(1, args.steps // 2)
+    step(_lib.IBM_PREC_FP64)
+    ms_fp64, st_fp64 = timed(lambda: step(_lib.IBM_PREC_FP64), k64)
+
+    # ---- the solve alone, on a right-hand side of the step's form ----
+    a = 1.5 / W.dt
+    s.set_markers(X)
+    rhs_F = a * (s.interp(f) - U)
+    b = a * s.gradient_t(f) + 2.0 * s.gradient_t(s.spread(rhs_F))
+    solve_only = {}
+    for name, prec in (("fp32_vcycle", _lib.IBM_PREC_FP32), ("fp64_vcycle", _lib.IBM_PREC_FP64)):
+        s.solve_schur(b, precond_prec=prec, rtol=1e-8)
+        msq, stq = timed(lambda: s.solve_schur(b, precond_prec=prec, rtol=1e-8)[1], k64)
+        solve_only[name] = {"solves_per_s": world * 1000.0 / msq, "ms": msq,
+                            "iters": stq[-1]["iters"], "relres": stq[-1]["relres_true"]}
+
+    # ---- end to end through the public API with host buffers ----
+    pin = lambda t: t.cpu().pin_memory()
+    h_in = dict(X=pin(X), U=pin(U), f=pin(f), u_n=pin(zf), u_nm1=pin(zf), p_n=pin(zc),
+                F_n=pin(zk))
+    d_in = {kk: torch.empty_like(v, device="cuda") for kk, v in h_in.items()}
+    h_out = {kk: torch.empty(v.shape, dtype=v.dtype).pin_memory() for kk, v in out.items()}
+    h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+
+    def e2e_step():
+        for kk in h_in:
+            d_in[kk].copy_(h_in[kk], non_blocking=True)
+        s.set_markers(d_in["X"])
+        _, st = s.step(d_in["u_n"], d_in["u_nm1"], d_in["p_n"], d_in["F_n"], d_in["U"],
+                       d_in["f"], out=out, precond_prec=_lib.IBM_PREC_FP32, rtol=1e-8)
+        for kk in h_out:
+            h_out[kk].copy_(out[kk], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return st
+
+    e2e_step()
+    ms_e2e, _ = timed(e2e_step, args.steps)
+
+    # ---- roofline of the dominant kernel class ----
+    hbm, peak_kind = measured_peaks()
+    it_avg = statistics.mean(st["iters"] for st in st_mixed)
+    kern = {
+        # name: (profile class, algorithmic bytes per launch)
+        "k_cheb_sweep<float> (finest V-cycle smoothing sweep, FP32)":
+            ("mg_smooth_fine", 12.0 * m),
+        "k_laplacian<double> (7-point FP64 Laplacian in S~ v)": ("laplacian_f64", 16.0 * m),
+        "k_multidot (Gram-Schmidt multi-dot, FP64)":
+            ("multidot", 8.0 * m * ((it_avg + 1) / 2.0 + 1.0)),
+        "k_axpy_norm (Gram-Schmidt axpy+norm, FP64)":
+            ("axpy_norm", 8.0 * m * ((it_avg + 1) / 2.0 + 2.0)),
+    }
+    best = max(kern, key=lambda kk: prof[kern[kk][0]]["ms"])
+    cls, bytes_per = kern[best]
+    avg_ms = prof[cls]["ms"] / max(1, prof[cls]["launches"])
+    achieved = bytes_per / (avg_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+            "traffic": NCU_TRAFFIC.get(best), "avg_launch_ms": avg_ms,
+            "bytes_per_launch": bytes_per}
+    breakdown = {kk: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
+                 for kk, v in prof.items() if v["launches"]}
+
+    value = world * 1000.0 / ms_mixed
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FGMRES, Schur products) + f32 (V-cycle)", "data": "synthetic",
+            "config": workload_config(W),
+            "fp64_form": {"value": world * 1000.0 / ms_fp64, "unit": UNIT, "ms_per_step": ms_fp64,
+                          "iters": st_fp64[-1]["iters"]},
+            "solve_only": solve_only,
+            "iters": st_mixed[-1]["iters"], "relres_true": st_mixed[-1]["relres_true"],
+            "helm_iters": st_mixed[-1]["helm_iters"],
+            "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
+            "roofline": roof, "breakdown": breakdown, "gpu_launches": int(launches),
+            "clocks": clk,
+            "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, det = oracle_sample(W, oracle_iterations(args.config))
+        line["cpu_baseline"] = {
+            "value": 1.0 / est, "unit": UNIT, "cores": det["workers"], "kind": "oracle",
+            "sample": (f"one oracle step at the full workload with {SAMPLE_ITERS} of "
+                       f"{det['iters_full']} FGMRES iterations run (scipy.fft workers = "
+                       f"{det['workers']}, sparse products single-threaded), solve time "
+                       f"scaled to the full count; {det['sample_wall_s']:.1f} s of CPU work"),
+            "cpu": cpu_model()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,251 @@
+/*
+ * ibm_schur.h -- C ABI of the GB300 (sm_103a) Laplacian-preconditioned Schur
+ * solver for the SIMPLE-based direct-forcing immersed boundary method
+ * (Yovel, Treister & Feldman, arXiv 2501.15314).
+ *
+ * Problem (Sec. 3.1, Eq. (Saddle)): on a staggered MAC grid with pressure at
+ * cell centres and velocity components on faces, with Lagrangian markers X_k
+ * carrying forces F_k, the pressure / force-density corrections solve
+ *
+ *     [ L  B^T ] [p']   [RHS_p]      L = G^T G,  B = R^T G,  C = R^T R,
+ *     [ B  -C  ] [F'] = [RHS_F],
+ *
+ * G the central-difference gradient (cells -> interior faces), G^T = -div,
+ * R the regularisation (Eq. (regularization)) built from Roma's 3-point delta
+ * (Eq. (delta)) and R^T the interpolation (Eq. (interpolation)).  With the
+ * scalar approximation C^{-1} ~ 2I (Eq. (tildeSp)) the primal Schur complement
+ * S~ = L + 2 B^T B is solved by a Krylov method preconditioned with the
+ * Laplacian (Sec. 4.1-4.2): here right-preconditioned flexible GMRES in FP64
+ * with one geometric-multigrid V-cycle (FP32 or FP64) standing in for L^{-1}.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: nx*ny*nz cells of width h; domain [0,nx h]x[0,ny h]x[0,nz h]; all six
+ *   walls no-slip.
+ * Layout (C order, x fastest):
+ *   cell field   [nz][ny][nx]                                 (m = nx ny nz)
+ *   face vector  u_x [nz][ny][nx+1] ++ u_y [nz][ny+1][nx] ++ u_z [nz+1][ny][nx]
+ *                packed contiguously in that order (n_faces values); the
+ *                wall-normal faces on the walls are not unknowns, inputs there
+ *                are ignored and outputs there are written as 0.
+ *   marker data  structure-of-arrays [3][n_markers]: all x, then all y, then
+ *                all z (positions, velocities, forces alike).
+ * Memory: every field pointer is caller-owned DEVICE memory holding FP64
+ *   (int32 where stated), contiguous, 8-byte aligned; the library never frees
+ *   it.  The library owns only the workspace it allocates in ibm_create /
+ *   ibm_set_markers and frees in ibm_destroy.
+ * Streams: all work is enqueued on the stream given to ibm_create.  Entry
+ *   points that return statistics or detect errors on the device synchronise
+ *   that stream before returning (stated per call); the others are
+ *   asynchronous.
+ * Errors: every call returns an ibm_status; ibm_last_error gives a message.
+ *   No exception crosses the ABI and no kernel traps or asserts.  Arguments are
+ *   validated before any work is enqueued.
+ * Singular pressure: L (Neumann) and S~ have the constants as null space.  The
+ *   solver returns the mean-zero solution (the paper pins a Dirichlet point
+ *   instead, Sec. 5; a mean-zero projection keeps L = G^T G symmetric).
+ */
+#ifndef IBM_SCHUR_H
+#define IBM_SCHUR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibm_ctx ibm_ctx;
+
+typedef enum {
+  IBM_OK = 0,
+  IBM_ERR_ARG = 1,            /* invalid argument (null pointer, bad size)   */
+  IBM_ERR_CUDA = 2,           /* a CUDA runtime call failed                  */
+  IBM_ERR_NOMEM = 3,          /* device allocation failed                    */
+  IBM_ERR_NOT_CONVERGED = 4,  /* maxit reached; best iterate is returned     */
+  IBM_ERR_BREAKDOWN = 5,      /* Krylov breakdown without convergence        */
+  IBM_ERR_NAN = 6,            /* non-finite value in a residual or norm      */
+  IBM_ERR_MARKER_DOMAIN = 7,  /* a marker's delta support leaves the interior */
+  IBM_ERR_STATE = 8           /* call out of order (e.g. no markers set)     */
+} ibm_status;
+
+typedef enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32 = 1 } ibm_precision;
+
+/* Grid description: cell counts, cell width, Reynolds number and time step
+ * (a = 3/(2 dt) and nu = 1/Re enter the BDF2 predictor, Eq. (ustar), and the
+ * correction right-hand sides below Eq. (Saddle)). */
+typedef struct {
+  int32_t nx, ny, nz;
+  double h;
+  double Re;
+  double dt;
+} ibm_grid_desc;
+
+/* Solver options (defaults from ibm_default_opts). */
+typedef struct {
+  int32_t precond_prec;  /* IBM_PREC_FP32: V-cycle stored and accumulated in
+                            FP32 (mixed mode); IBM_PREC_FP64: V-cycle in FP64 */
+  double rtol;           /* stop when ||b - S x|| / ||b|| <= rtol (FP64)     */
+  int32_t maxit;         /* total FGMRES iterations over all restarts        */
+  int32_t restart;       /* Krylov basis size (<= 64)                        */
+  int32_t mg_pre;        /* Chebyshev degree of the pre-smoother  (0..4)     */
+  int32_t mg_post;       /* Chebyshev degree of the post-smoother (0..4)     */
+  int32_t reorth;        /* 1: classical Gram-Schmidt applied twice          */
+  double helm_rtol;      /* predictor (Helmholtz) relative residual target   */
+  int32_t helm_maxit;    /* predictor outer (FP64 defect) iterations         */
+  int32_t with_advection;/* 1: include the explicit convective term of
+                            Eq. (ustar) in the predictor                     */
+} ibm_solve_opts;
+
+#define IBM_HIST_MAX 256
+
+/* Solve statistics (host memory, filled by the call). */
+typedef struct {
+  int32_t iters;          /* FGMRES iterations (preconditioner applications) */
+  int32_t restarts;       /* completed restart cycles                        */
+  double relres_true;     /* ||b - S x|| / ||b|| recomputed in FP64 at exit  */
+  double relres_hist[IBM_HIST_MAX]; /* Arnoldi residual estimate per iter   */
+  int32_t helm_iters;     /* predictor outer iterations (ibm_step only)      */
+  double helm_relres;     /* predictor relative residual (ibm_step only)     */
+  double div_l2;          /* ||G^T u^{n+1}||_2            (ibm_step only)    */
+  double slip_l2;         /* ||R^T u^{n+1} - U^Gamma||_2  (ibm_step only)    */
+} ibm_solve_stats;
+
+/* Fills *opts with defaults: FP32 V-cycle, rtol 1e-8, maxit 200, restart 40,
+ * Chebyshev (2,2), single Gram-Schmidt pass, helm_rtol 1e-10, helm_maxit 8,
+ * advection on. */
+void ibm_default_opts(ibm_solve_opts* opts);
+
+/* Creates a context for one grid and allocates the grid-sized workspace
+ * (multigrid hierarchy, Krylov bases for restart <= 64, temporaries).
+ * stream: a cudaStream_t (may be NULL for the legacy default stream).
+ * Requires nx, ny, nz >= 4 and h > 0, Re > 0, dt > 0.  Synchronises. */
+ibm_status ibm_create(const ibm_grid_desc* grid, void* stream, ibm_ctx** out);
+
+/* Frees the context and all workspace.  Safe on NULL. */
+void ibm_destroy(ibm_ctx* ctx);
+
+/* Message for the last error on this context ("" if none).  Valid until the
+ * next call on the context. */
+const char* ibm_last_error(const ibm_ctx* ctx);
+
+/* Number of cells and packed faces of the context's grid. */
+int64_t ibm_num_cells(const ibm_ctx* ctx);
+int64_t ibm_num_faces(const ibm_ctx* ctx);
+
+/* Sets the Lagrangian markers (Sec. 2.3): X is device [3][n_markers] FP64
+ * positions.  Builds the per-marker Roma weights of Eq. (delta) for the three
+ * velocity components and a cell-sorted marker list used by the deterministic
+ * (atomic-free) spread.  n_markers == 0 is valid (then S~ = L).  Returns
+ * IBM_ERR_MARKER_DOMAIN if a marker's 3x3x3 support for some component
+ * touches a wall-normal boundary face or leaves the grid (Appendix B: the
+ * support must lie on grid points that exist).  Synchronises. */
+ibm_status ibm_set_markers(ibm_ctx* ctx, int64_t n_markers, const double* X);
+
+/* out = L v = G^T G v (cells -> cells), the Neumann 7-point Laplacian of
+ * Eq. (Saddle).  v and out must not alias.  Asynchronous. */
+ibm_status ibm_apply_laplacian(ibm_ctx* ctx, const double* v, double* out);
+
+/* out = S~ v = L v + 2 B^T B v, Eq. (tildeSp) (cells -> cells).  v and out
+ * must not alias.  Asynchronous. */
+ibm_status ibm_apply_schur(ibm_ctx* ctx, const double* v, double* out);
+
+/* z = M^{-1} r: one multigrid V-cycle for the Neumann Laplacian (Chebyshev
+ * smoothing, full-weighting restriction, trilinear prolongation, dense
+ * pseudo-inverse on the coarsest level), the preconditioner of Sec. 4.1 (the
+ * paper's own suggested replacement for its direct solver, Sec. 7).  prec
+ * selects FP32 or FP64 storage/arithmetic inside the cycle; r and z are FP64.
+ * The result is not mean-projected.  r and z must not alias.  Asynchronous. */
+ibm_status ibm_apply_laplacian_precond(ibm_ctx* ctx, const double* r, double* z,
+                                       int32_t prec, int32_t pre, int32_t post);
+
+/* U = R^T u (faces -> markers, [3][n_markers]), Eq. (interpolation).
+ * Asynchronous. */
+ibm_status ibm_interp(ibm_ctx* ctx, const double* u, double* U);
+
+/* u = R F (markers -> faces), Eq. (regularization); every face is written
+ * (0 away from the markers).  Deterministic: each face sums its markers in a
+ * fixed order, no atomics.  Asynchronous. */
+ibm_status ibm_spread(ibm_ctx* ctx, const double* F, double* u);
+
+/* u = G p (cells -> faces, 0 on wall faces) and out = G^T u (faces -> cells,
+ * = -div u).  Asynchronous. */
+ibm_status ibm_gradient(ibm_ctx* ctx, const double* p, double* u);
+ibm_status ibm_gradient_t(ibm_ctx* ctx, const double* u, double* out);
+
+/* Solves S~ p = b for the mean-zero p (Eq. (ApproxSchurPrimalP)) by
+ * right-preconditioned FGMRES(restart) with one V-cycle per iteration.
+ * p: in = initial guess x0, out = solution.  b must be orthogonal to the
+ * constants (every b built from G^T(.) is).  stats may be NULL.  Synchronises
+ * once per iteration (convergence test) and at exit.  Returns
+ * IBM_ERR_NOT_CONVERGED if rtol is not met within maxit (p holds the last
+ * iterate), IBM_ERR_NAN on a non-finite residual. */
+ibm_status ibm_solve_schur(ibm_ctx* ctx, const double* b, double* p,
+                           const ibm_solve_opts* opts, ibm_solve_stats* stats);
+
+/* F' = 2 (B p - RHS_F), Eq. (ApproxSchurPrimalF) ([3][n_markers]).
+ * Asynchronous. */
+ibm_status ibm_force_correction(ibm_ctx* ctx, const double* p,
+                                const double* rhs_F, double* F_corr);
+
+/* One one-way SIMPLE-IBM time step (Sec. 3.1) with the markers last set:
+ *   1. predictor (Eq. (ustar)): (3/(2dt) - Lap/Re) u* = (4u^n - u^{n-1})/(2dt)
+ *      - G p^n + R F^n - (u.grad u)^n + f_body, solved by FP64 defect
+ *      correction around FP32 Chebyshev sweeps to helm_rtol;
+ *   2. RHS_p = (3/(2dt)) G^T u*, RHS_F = (3/(2dt)) (R^T u* - U_gamma);
+ *   3. ibm_solve_schur on b = RHS_p + 2 B^T RHS_F;
+ *   4. F' = 2 (B p' - RHS_F);
+ *   5. u^{n+1} = u* + (2dt/3)(-G p' + R F'), p^{n+1} = p^n + p',
+ *      F^{n+1} = F^n + F'  (Eq. (u_n_plus_1) and the correction step);
+ *   6. diagnostics ||G^T u^{n+1}||, ||R^T u^{n+1} - U_gamma|| into stats.
+ * Inputs u_n, u_nm1 (faces), p_n (cells), F_n, U_gamma ([3][n_markers]),
+ * f_body (faces; may be NULL for none).  Outputs u_np1, p_np1, F_np1 must not
+ * alias the inputs.  Synchronises like ibm_solve_schur. */
+ibm_status ibm_step(ibm_ctx* ctx, const double* u_n, const double* u_nm1,
+                    const double* p_n, const double* F_n, const double* U_gamma,
+                    const double* f_body, double* u_np1, double* p_np1,
+                    double* F_np1, const ibm_solve_opts* opts,
+                    ibm_solve_stats* stats);
+
+/* Per body b in [0, n_bodies): out[6b+0..2] = h^3 sum_{k in b} F_k (the IB
+ * force sum of Eq. (IBM_force)) and out[6b+3..5] = h^3 sum (X_k - c_b) x F_k.
+ * F, X: device [3][n_markers]; body_id: device int32 [n_markers] (values in
+ * [0, n_bodies)); centers: host [n_bodies][3]; out: host [n_bodies][6].
+ * Deterministic fixed-order reduction.  Synchronises. */
+ibm_status ibm_body_forces(ibm_ctx* ctx, const double* F, const double* X,
+                           const int32_t* body_id, int32_t n_bodies,
+                           const double* centers, double* out);
+
+/* Optional timing of kernel classes with CUDA events recorded on the
+ * context's stream around the launches of each class (no effect on results).
+ * ibm_profile_enable(ctx, 1) resets the counters and starts recording;
+ * ibm_profile_read synchronises the stream and returns, per class, the summed
+ * event-measured milliseconds and the number of timed launches. */
+enum {
+  IBM_PROF_LAPLACIAN_F64 = 0,  /* 7-point FP64 Laplacian inside S~ v        */
+  IBM_PROF_SCHUR_MARKERS = 1,  /* B v gather + B^T t shell gather in S~ v   */
+  IBM_PROF_VCYCLE = 2,         /* one whole V-cycle (all levels)            */
+  IBM_PROF_MULTIDOT = 3,       /* Gram-Schmidt multi-dot (+ final reduce)   */
+  IBM_PROF_AXPY_NORM = 4,      /* Gram-Schmidt axpy + norm + normalisation  */
+  IBM_PROF_PREDICTOR = 5,      /* whole predictor (Helmholtz) solve         */
+  IBM_PROF_SOLVE = 6,          /* whole ibm_solve_schur / step solve        */
+  IBM_PROF_STEP = 7,           /* whole ibm_step                            */
+  IBM_PROF_MARKER_BUILD = 8,   /* ibm_set_markers                           */
+  IBM_PROF_MG_SMOOTH_FINE = 9, /* one finest-level smoothing sweep kernel   */
+  IBM_PROF_NCLASS = 16
+};
+typedef struct {
+  double ms[IBM_PROF_NCLASS];
+  int64_t launches[IBM_PROF_NCLASS];
+} ibm_profile;
+
+ibm_status ibm_profile_enable(ibm_ctx* ctx, int32_t on);
+/* Number of kernels this library has launched in the process so far (all
+ * contexts); a difference of two reads counts the launches in between. */
+int64_t ibm_kernel_launches(void);
+ibm_status ibm_profile_read(ibm_ctx* ctx, ibm_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_SCHUR_H */

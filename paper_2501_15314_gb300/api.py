@@ -1,0 +1,205 @@
+"""Torch-facing wrapper of the C ABI (include/ibm_schur.h).
+
+PyTorch provides device memory and the stream; every operation is one call
+into libibmschur.  Tensors must be contiguous CUDA float64 (int32 for body
+ids) in the layouts of the header: cells [nz][ny][nx] flattened, packed faces
+u_x|u_y|u_z, marker arrays [3][N].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import IBM_PREC_FP32, IBM_PREC_FP64, check
+
+__all__ = ["IBMSolver", "IBM_PREC_FP32", "IBM_PREC_FP64"]
+
+
+def _ptr(t: torch.Tensor, dtype=torch.float64, numel=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cuda" or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+def _stats_dict(st: _lib.ibm_solve_stats) -> dict:
+    n = min(st.iters, _lib.HIST_MAX)
+    return dict(iters=st.iters, restarts=st.restarts, relres_true=st.relres_true,
+                relres_hist=list(st.relres_hist[:n]), helm_iters=st.helm_iters,
+                helm_relres=st.helm_relres, div_l2=st.div_l2, slip_l2=st.slip_l2)
+
+
+class IBMSolver:
+    """One MAC grid (nx, ny, nz, h) with its workspace on the current device
+    and stream."""
+
+    def __init__(self, nx: int, ny: int | None = None, nz: int | None = None,
+                 h: float | None = None, Re: float = 100.0, dt: float = 0.01,
+                 stream: torch.cuda.Stream | None = None):
+        self.lib = _lib.load()
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        h = 1.0 / nx if h is None else h
+        self.nx, self.ny, self.nz, self.h, self.Re, self.dt = nx, ny, nz, h, Re, dt
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = _lib.ibm_grid_desc(nx, ny, nz, h, Re, dt)
+        ctx = C.c_void_p()
+        st = self.lib.ibm_create(C.byref(g), C.c_void_p(self.stream.cuda_stream), C.byref(ctx))
+        if st != _lib.IBM_OK:
+            raise _lib.IBMError(st, "ibm_create failed")
+        self.ctx = ctx
+        self.m = self.lib.ibm_num_cells(ctx)
+        self.nf = self.lib.ibm_num_faces(ctx)
+        self.n_markers = 0
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ibm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _cells(self, **kw):
+        return torch.empty(self.m, dtype=torch.float64, device="cuda", **kw)
+
+    def _faces(self):
+        return torch.empty(self.nf, dtype=torch.float64, device="cuda")
+
+    # -- setup ------------------------------------------------------------
+    def set_markers(self, X: torch.Tensor):
+        X = X.reshape(3, -1) if X.numel() else X
+        n = X.shape[1] if X.numel() else 0
+        check(self.lib.ibm_set_markers(self.ctx, n, _ptr(X, name="X") if n else None), self.ctx)
+        self.n_markers = n
+        self._X = X
+
+    # -- operators --------------------------------------------------------
+    def apply_laplacian(self, v, out=None):
+        out = self._cells() if out is None else out
+        check(self.lib.ibm_apply_laplacian(self.ctx, _ptr(v, numel=self.m, name="v"),
+                                           _ptr(out, numel=self.m, name="out")), self.ctx)
+        return out
+
+    def apply_schur(self, v, out=None):
+        out = self._cells() if out is None else out
+        check(self.lib.ibm_apply_schur(self.ctx, _ptr(v, numel=self.m, name="v"),
+                                       _ptr(out, numel=self.m, name="out")), self.ctx)
+        return out
+
+    def precond(self, r, prec=IBM_PREC_FP32, pre=2, post=2, out=None):
+        out = self._cells() if out is None else out
+        check(self.lib.ibm_apply_laplacian_precond(
+            self.ctx, _ptr(r, numel=self.m, name="r"), _ptr(out, numel=self.m, name="z"),
+            prec, pre, post), self.ctx)
+        return out
+
+    def interp(self, u, out=None):
+        out = torch.zeros(3 * self.n_markers, dtype=torch.float64, device="cuda") \
+            if out is None else out
+        if self.n_markers:
+            check(self.lib.ibm_interp(self.ctx, _ptr(u, numel=self.nf, name="u"),
+                                      _ptr(out, name="U")), self.ctx)
+        return out
+
+    def spread(self, F, out=None):
+        out = self._faces() if out is None else out
+        check(self.lib.ibm_spread(self.ctx, _ptr(F, name="F") if self.n_markers else None,
+                                  _ptr(out, numel=self.nf, name="u")), self.ctx)
+        return out
+
+    def gradient(self, p, out=None):
+        out = self._faces() if out is None else out
+        check(self.lib.ibm_gradient(self.ctx, _ptr(p, numel=self.m, name="p"),
+                                    _ptr(out, numel=self.nf, name="u")), self.ctx)
+        return out
+
+    def gradient_t(self, u, out=None):
+        out = self._cells() if out is None else out
+        check(self.lib.ibm_gradient_t(self.ctx, _ptr(u, numel=self.nf, name="u"),
+                                      _ptr(out, numel=self.m, name="out")), self.ctx)
+        return out
+
+    def force_correction(self, p, rhs_F, out=None):
+        out = torch.zeros(3 * self.n_markers, dtype=torch.float64, device="cuda") \
+            if out is None else out
+        if self.n_markers:
+            check(self.lib.ibm_force_correction(self.ctx, _ptr(p, numel=self.m, name="p"),
+                                                _ptr(rhs_F, name="rhs_F"),
+                                                _ptr(out, name="F")), self.ctx)
+        return out
+
+    # -- solves -------------------------------------------------------------
+    def opts(self, **kw) -> _lib.ibm_solve_opts:
+        o = _lib.default_opts()
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        return o
+
+    def solve_schur(self, b, x0=None, raise_on_error=True, **kw):
+        p = torch.zeros(self.m, dtype=torch.float64, device="cuda") if x0 is None \
+            else x0.clone()
+        o = self.opts(**kw)
+        st = _lib.ibm_solve_stats()
+        status = self.lib.ibm_solve_schur(self.ctx, _ptr(b, numel=self.m, name="b"),
+                                          _ptr(p, numel=self.m, name="p"), C.byref(o),
+                                          C.byref(st))
+        if raise_on_error:
+            check(status, self.ctx)
+        d = _stats_dict(st)
+        d["status"] = status
+        return p, d
+
+    def step(self, u_n, u_nm1, p_n, F_n, U_gamma, f_body=None, out=None,
+             raise_on_error=True, **kw):
+        nmk = 3 * self.n_markers
+        if out is None:
+            out = dict(u=self._faces(), p=self._cells(),
+                       F=torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda"))
+        o = self.opts(**kw)
+        st = _lib.ibm_solve_stats()
+        status = self.lib.ibm_step(
+            self.ctx, _ptr(u_n, numel=self.nf, name="u_n"),
+            _ptr(u_nm1, numel=self.nf, name="u_nm1"), _ptr(p_n, numel=self.m, name="p_n"),
+            _ptr(F_n, name="F_n") if nmk else None,
+            _ptr(U_gamma, name="U_gamma") if nmk else None,
+            _ptr(f_body, numel=self.nf, name="f_body") if f_body is not None else None,
+            _ptr(out["u"], numel=self.nf, name="u_np1"), _ptr(out["p"], numel=self.m, name="p_np1"),
+            _ptr(out["F"], name="F_np1") if nmk else None, C.byref(o), C.byref(st))
+        if raise_on_error:
+            check(status, self.ctx)
+        d = _stats_dict(st)
+        d["status"] = status
+        return out, d
+
+    def profile_enable(self, on=True):
+        check(self.lib.ibm_profile_enable(self.ctx, 1 if on else 0), self.ctx)
+
+    def profile_read(self) -> dict:
+        p = _lib.ibm_profile()
+        check(self.lib.ibm_profile_read(self.ctx, C.byref(p)), self.ctx)
+        return {name: dict(ms=p.ms[i], launches=p.launches[i])
+                for i, name in enumerate(_lib.PROF_NAMES)}
+
+    def body_forces(self, F, X, body_id, centers):
+        import numpy as np
+        centers = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, 3))
+        nb = centers.shape[0]
+        out = np.zeros((nb, 6))
+        check(self.lib.ibm_body_forces(
+            self.ctx, _ptr(F, name="F"), _ptr(X, name="X"),
+            _ptr(body_id, dtype=torch.int32, name="body_id"), nb,
+            centers.ctypes.data_as(C.POINTER(C.c_double)),
+            out.ctypes.data_as(C.POINTER(C.c_double))), self.ctx)
+        return out

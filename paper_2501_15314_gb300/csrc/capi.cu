@@ -1,0 +1,586 @@
+// C ABI of libibmschur (include/ibm_schur.h): context lifetime, argument
+// validation, and the one-way SIMPLE-IBM time step of Sec. 3.1 composed from
+// the stencil, marker, multigrid and Krylov kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+ibm_status set_err(ibm_ctx* c, ibm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+ibm_status cuda_err(ibm_ctx* c, cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "CUDA error %s (%d) at %s", cudaGetErrorString(e), (int)e, where);
+  return set_err(c, e == cudaErrorMemoryAllocation ? IBM_ERR_NOMEM : IBM_ERR_CUDA, buf);
+}
+
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int prof_begin(ibm_ctx* c, int cls) {
+  if (!c->prof_on) return -1;
+  if (c->prof_used == c->prof.size()) {
+    ibm_ctx::ProfRec r;
+    r.cls = cls;
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    c->prof.push_back(r);
+  }
+  const int h = (int)c->prof_used++;
+  c->prof[h].cls = cls;
+  cudaEventRecord(c->prof[h].a, c->stream);
+  return h;
+}
+
+void prof_end(ibm_ctx* c, int h) {
+  if (h < 0) return;
+  cudaEventRecord(c->prof[h].b, c->stream);
+}
+
+namespace {
+
+constexpr int TPB = 256;
+
+__global__ void k_body_forces(const double* __restrict__ F, const double* __restrict__ X,
+                              const int32_t* __restrict__ bid, int64_t n, double cx, double cy,
+                              double cz, int body, double h3, double* __restrict__ out) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    if (bid[k] != body) continue;
+    const double fx = F[k], fy = F[n + k], fz = F[2 * n + k];
+    const double rx = X[k] - cx, ry = X[n + k] - cy, rz = X[2 * n + k] - cz;
+    acc[0] += fx; acc[1] += fy; acc[2] += fz;
+    acc[3] += ry * fz - rz * fy;
+    acc[4] += rz * fx - rx * fz;
+    acc[5] += rx * fy - ry * fx;
+  }
+  __shared__ double sh[6][TPB];
+  for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[threadIdx.x] = h3 * sh[threadIdx.x][0];
+}
+
+__global__ void k_axpby_small(const double* __restrict__ x, double a, const double* __restrict__ y,
+                              double b, double* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_d2f_scaled(const double* __restrict__ x, float* __restrict__ y, int64_t n,
+                             double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(s * x[i]);
+}
+
+__global__ void k_f2d_add_scaled(const float* __restrict__ e, double* __restrict__ u, int64_t n,
+                                 double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += s * (double)e[i];
+}
+
+bool bad_ptr(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 7) != 0; }
+
+ibm_status check_ctx(ibm_ctx* c) {
+  if (!c) return IBM_ERR_ARG;
+  c->err.clear();
+  return IBM_OK;
+}
+
+ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o) {
+  if (!o) return set_err(c, IBM_ERR_ARG, "opts is null");
+  if (o->precond_prec != IBM_PREC_FP32 && o->precond_prec != IBM_PREC_FP64)
+    return set_err(c, IBM_ERR_ARG, "precond_prec must be IBM_PREC_FP32 or IBM_PREC_FP64");
+  if (!(o->rtol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > kMaxRestart)
+    return set_err(c, IBM_ERR_ARG, "need rtol > 0, maxit >= 1, 1 <= restart <= 64");
+  if (o->mg_pre < 0 || o->mg_pre > 4 || o->mg_post < 0 || o->mg_post > 4 ||
+      o->mg_pre + o->mg_post == 0)
+    return set_err(c, IBM_ERR_ARG, "mg_pre, mg_post in 0..4, not both 0");
+  if (!(o->helm_rtol > 0.0) || o->helm_maxit < 1)
+    return set_err(c, IBM_ERR_ARG, "need helm_rtol > 0 and helm_maxit >= 1");
+  return IBM_OK;
+}
+
+ibm_status ensure_krylov(ibm_ctx* c, int restart) {
+  if (restart <= c->restart_cap) return IBM_OK;
+  cudaFree(c->V);
+  cudaFree(c->Z);
+  c->V = c->Z = nullptr;
+  c->restart_cap = 0;
+  if (cudaMalloc(&c->V, sizeof(double) * (restart + 1) * c->m) != cudaSuccess ||
+      cudaMalloc(&c->Z, sizeof(double) * restart * c->m) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->V);
+    cudaFree(c->Z);
+    c->V = c->Z = nullptr;
+    return set_err(c, IBM_ERR_NOMEM, "Krylov basis allocation failed");
+  }
+  c->restart_cap = restart;
+  return IBM_OK;
+}
+
+ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out) {
+  launch_dot(x, x, n, c->red_part, c->red_out + 3 * (kMaxRestart + 2) + 8, c->stream);
+  IBM_LAUNCH_CHECK(c);
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, c->red_out + 3 * (kMaxRestart + 2) + 8,
+                              sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = std::sqrt(c->host_red[0]);
+  return IBM_OK;
+}
+
+void free_all(ibm_ctx* c) {
+  cudaFree(c->cell_count); cudaFree(c->cell_start); cudaFree(c->cell_flag); cudaFree(c->scan_tmp);
+  cudaFree(c->dev_flag); cudaFreeHost(c->host_flag);
+  cudaFree(c->c1); cudaFree(c->c2); cudaFree(c->c3);
+  cudaFree(c->f1); cudaFree(c->f2); cudaFree(c->f3); cudaFree(c->f4);
+  cudaFree(c->g1); cudaFree(c->g2); cudaFree(c->g3); cudaFree(c->g4);
+  cudaFree(c->red_part); cudaFree(c->red_out); cudaFreeHost(c->host_red);
+  cudaFree(c->V); cudaFree(c->Z);
+  for (int l = 0; l < c->n_levels; ++l) {
+    MGLevel& L = c->lv[l];
+    cudaFree(L.x32); cudaFree(L.b32); cudaFree(L.t32);
+    cudaFree(L.x64); cudaFree(L.b64); cudaFree(L.t64);
+  }
+  cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
+  MarkerData& m = c->mk;
+  cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
+  cudaFree(m.t); cudaFree(m.t2);
+  cudaFree(m.entry_key); cudaFree(m.entry_coef); cudaFree(m.shell_cell); cudaFree(m.shell_off);
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->prof.clear();
+}
+
+// Predictor of Eq. (ustar): (a - nu Lap) u = rhs by FP64 defect correction;
+// each correction solves A e = r approximately with K Chebyshev steps in FP32
+// on the exact spectral bounds [a, a + 12 nu / h^2] of the operator.
+ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
+                           int* iters, double* relres) {
+  cudaStream_t s = c->stream;
+  const int64_t nf = c->nf;
+  const double a = 1.5 / c->dt;
+  const double nu = 1.0 / c->Re;
+  const double nu_h2 = nu / (c->h * c->h);
+  const double lmin = a, lmax = a + 12.0 * nu_h2;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  // steps for a 1e-6 error reduction: T_K(sigma) >= 1e6
+  int K = (int)std::ceil(std::acosh(1e6) / std::acosh(sigma));
+  K = K < 4 ? 4 : (K > 60 ? 60 : K);
+  double rnorm0;
+  ibm_status st = norm2_host(c, rhs, nf, &rnorm0);
+  if (st != IBM_OK) return st;
+  if (!std::isfinite(rnorm0)) return set_err(c, IBM_ERR_NAN, "non-finite predictor RHS");
+  IBM_CUDA(c, cudaMemsetAsync(u, 0, sizeof(double) * nf, s));
+  *iters = 0;
+  *relres = 0.0;
+  if (rnorm0 == 0.0) return IBM_OK;
+  double* res = c->f3;
+  const double* rcur = rhs;   // residual of the zero iterate is rhs itself
+  for (int it = 0; it < o->helm_maxit; ++it) {
+    double rn = rnorm0;
+    if (it > 0) {
+      launch_helm_apply(c->d, u, a, nu_h2, rhs, res, s);
+      IBM_LAUNCH_CHECK(c);
+      if ((st = norm2_host(c, res, nf, &rn)) != IBM_OK) return st;
+      if (!std::isfinite(rn)) return set_err(c, IBM_ERR_NAN, "non-finite predictor residual");
+      rcur = res;
+    }
+    *relres = rn / rnorm0;
+    if (*relres <= o->helm_rtol) return IBM_OK;
+    // scale the residual to O(1) before rounding to FP32
+    const double sc = 1.0 / rn;
+    count_launch();
+    k_d2f_scaled<<<kRedBlocks, TPB, 0, s>>>(rcur, c->g1, nf, sc);
+    float* eo = c->g2;
+    float* e = c->g3;
+    float* en = c->g4;
+    double rho_prev = 1.0 / sigma;
+    launch_helm_cheb(c->d, nullptr, nullptr, c->g1, (float)a, (float)nu_h2, (float)(1.0 / theta),
+                     0.f, e, 1, s);
+    IBM_CUDA(c, cudaMemsetAsync(eo, 0, sizeof(float) * nf, s));
+    for (int q = 1; q < K; ++q) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      launch_helm_cheb(c->d, e, eo, c->g1, (float)a, (float)nu_h2, (float)(2.0 * rho / delta),
+                       (float)(rho * rho_prev), en, 0, s);
+      rho_prev = rho;
+      float* t = eo; eo = e; e = en; en = t;
+    }
+    count_launch();
+    k_f2d_add_scaled<<<kRedBlocks, TPB, 0, s>>>(e, u, nf, rn);
+    IBM_LAUNCH_CHECK(c);
+    *iters = it + 1;
+  }
+  double rn;
+  launch_helm_apply(c->d, u, a, nu_h2, rhs, res, s);
+  IBM_LAUNCH_CHECK(c);
+  if ((st = norm2_host(c, res, nf, &rn)) != IBM_OK) return st;
+  *relres = rn / rnorm0;
+  if (*relres > o->helm_rtol) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "predictor did not reach helm_rtol %.3g (relres %.3g)", o->helm_rtol,
+             *relres);
+    return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
+  }
+  return IBM_OK;
+}
+
+}  // namespace
+}  // namespace ibm
+
+using namespace ibm;
+
+extern "C" {
+
+void ibm_default_opts(ibm_solve_opts* o) {
+  if (!o) return;
+  o->precond_prec = IBM_PREC_FP32;
+  o->rtol = 1e-8;
+  o->maxit = 200;
+  o->restart = 40;
+  o->mg_pre = 2;
+  o->mg_post = 2;
+  o->reorth = 0;
+  o->helm_rtol = 1e-10;
+  o->helm_maxit = 8;
+  o->with_advection = 1;
+}
+
+ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
+  if (!out) return IBM_ERR_ARG;
+  *out = nullptr;
+  if (!g || g->nx < 4 || g->ny < 4 || g->nz < 4 || !(g->h > 0.0) || !(g->Re > 0.0) ||
+      !(g->dt > 0.0))
+    return IBM_ERR_ARG;
+  if ((int64_t)g->nx * g->ny * g->nz * 4 > (int64_t)0x7fffffff) return IBM_ERR_ARG;
+  ibm_ctx* c = new (std::nothrow) ibm_ctx();
+  if (!c) return IBM_ERR_NOMEM;
+  c->d = Dims{g->nx, g->ny, g->nz};
+  c->h = g->h;
+  c->Re = g->Re;
+  c->dt = g->dt;
+  c->m = cells_of(c->d);
+  c->fd = face_dims(c->d);
+  c->nf = c->fd.nfx + c->fd.nfy + c->fd.nfz;
+  c->stream = static_cast<cudaStream_t>(stream);
+  const int64_t m = c->m, nf = c->nf;
+  const int64_t nscan = (m + 4095) / 4096 + 2;
+  bool ok = cudaMalloc(&c->cell_count, sizeof(int32_t) * m) == cudaSuccess &&
+            cudaMalloc(&c->cell_start, sizeof(int32_t) * (m + 1)) == cudaSuccess &&
+            cudaMalloc(&c->cell_flag, sizeof(int32_t) * (m + 1)) == cudaSuccess &&
+            cudaMalloc(&c->scan_tmp, sizeof(int32_t) * nscan) == cudaSuccess &&
+            cudaMalloc(&c->dev_flag, sizeof(int32_t) * 4) == cudaSuccess &&
+            cudaMallocHost(&c->host_flag, sizeof(int32_t) * 4) == cudaSuccess &&
+            cudaMalloc(&c->c1, sizeof(double) * m) == cudaSuccess &&
+            cudaMalloc(&c->c2, sizeof(double) * m) == cudaSuccess &&
+            cudaMalloc(&c->c3, sizeof(double) * (m + 1)) == cudaSuccess &&
+            cudaMalloc(&c->f1, sizeof(double) * nf) == cudaSuccess &&
+            cudaMalloc(&c->f2, sizeof(double) * nf) == cudaSuccess &&
+            cudaMalloc(&c->f3, sizeof(double) * nf) == cudaSuccess &&
+            cudaMalloc(&c->f4, sizeof(double) * nf) == cudaSuccess &&
+            cudaMalloc(&c->g1, sizeof(float) * nf) == cudaSuccess &&
+            cudaMalloc(&c->g2, sizeof(float) * nf) == cudaSuccess &&
+            cudaMalloc(&c->g3, sizeof(float) * nf) == cudaSuccess &&
+            cudaMalloc(&c->g4, sizeof(float) * nf) == cudaSuccess &&
+            cudaMalloc(&c->red_part, sizeof(double) * kRedBlocks * (kMaxRestart + 2)) ==
+                cudaSuccess &&
+            cudaMalloc(&c->red_out, sizeof(double) * 4 * (kMaxRestart + 2) + 64 * sizeof(double)) ==
+                cudaSuccess &&
+            cudaMallocHost(&c->host_red, sizeof(double) * 4 * (kMaxRestart + 2)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return IBM_ERR_NOMEM;
+  }
+  ibm_status st = mg_setup(c);
+  if (st == IBM_OK) st = ensure_krylov(c, 40);
+  if (st == IBM_OK && cudaDeviceSynchronize() != cudaSuccess) st = IBM_ERR_CUDA;
+  if (st != IBM_OK) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return st;
+  }
+  c->markers_set = true;   // zero markers until ibm_set_markers
+  *out = c;
+  return IBM_OK;
+}
+
+void ibm_destroy(ibm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+const char* ibm_last_error(const ibm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t ibm_num_cells(const ibm_ctx* c) { return c ? c->m : 0; }
+int64_t ibm_num_faces(const ibm_ctx* c) { return c ? c->nf : 0; }
+
+ibm_status ibm_set_markers(ibm_ctx* c, int64_t n, const double* X) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (n < 0 || n > (int64_t)1 << 24) return set_err(c, IBM_ERR_ARG, "n_markers out of range");
+  if (n > 0 && bad_ptr(X)) return set_err(c, IBM_ERR_ARG, "X is null or misaligned");
+  const int ph = prof_begin(c, IBM_PROF_MARKER_BUILD);
+  const ibm_status st = markers_build(c, n, X);
+  prof_end(c, ph);
+  return st;
+}
+
+ibm_status ibm_apply_laplacian(ibm_ctx* c, const double* v, double* out) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(v) || bad_ptr(out) || v == out) return set_err(c, IBM_ERR_ARG, "bad v/out");
+  launch_laplacian<double>(c->d, v, out, 1.0 / (c->h * c->h), c->stream);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status ibm_apply_schur(ibm_ctx* c, const double* v, double* out) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(v) || bad_ptr(out) || v == out) return set_err(c, IBM_ERR_ARG, "bad v/out");
+  return schur_apply(c, v, out);
+}
+
+ibm_status ibm_apply_laplacian_precond(ibm_ctx* c, const double* r, double* z, int32_t prec,
+                                       int32_t pre, int32_t post) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(r) || bad_ptr(z) || r == z) return set_err(c, IBM_ERR_ARG, "bad r/z");
+  if ((prec != IBM_PREC_FP32 && prec != IBM_PREC_FP64) || pre < 0 || pre > 4 || post < 0 ||
+      post > 4 || pre + post == 0)
+    return set_err(c, IBM_ERR_ARG, "bad precision or smoothing degrees");
+  return mg_vcycle(c, r, z, prec, pre, post);
+}
+
+ibm_status ibm_interp(ibm_ctx* c, const double* u, double* U) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (c->mk.n == 0) return IBM_OK;
+  if (bad_ptr(u) || bad_ptr(U)) return set_err(c, IBM_ERR_ARG, "bad u/U");
+  launch_interp(c, u, U);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status ibm_spread(ibm_ctx* c, const double* F, double* u) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(u) || (c->mk.n > 0 && bad_ptr(F))) return set_err(c, IBM_ERR_ARG, "bad F/u");
+  IBM_CUDA(c, cudaMemsetAsync(u, 0, sizeof(double) * c->nf, c->stream));
+  launch_shell_spread_faces(c, F, 1.0, u);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status ibm_gradient(ibm_ctx* c, const double* p, double* u) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(p) || bad_ptr(u)) return set_err(c, IBM_ERR_ARG, "bad p/u");
+  launch_gradient(c->d, p, u, 1.0 / c->h, c->stream);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status ibm_gradient_t(ibm_ctx* c, const double* u, double* out) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(u) || bad_ptr(out)) return set_err(c, IBM_ERR_ARG, "bad u/out");
+  launch_gradient_t(c->d, u, out, 1.0 / c->h, c->stream);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status ibm_solve_schur(ibm_ctx* c, const double* b, double* p, const ibm_solve_opts* o,
+                           ibm_solve_stats* st) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(b) || bad_ptr(p) || b == p) return set_err(c, IBM_ERR_ARG, "bad b/p");
+  ibm_status s = check_opts(c, o);
+  if (s != IBM_OK) return s;
+  if ((s = ensure_krylov(c, o->restart)) != IBM_OK) return s;
+  if (st) memset(st, 0, sizeof(*st));
+  const int ph = prof_begin(c, IBM_PROF_SOLVE);
+  s = fgmres_solve(c, b, p, o, st);
+  prof_end(c, ph);
+  return s;
+}
+
+ibm_status ibm_force_correction(ibm_ctx* c, const double* p, const double* rhs_F, double* Fc) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  const int64_t n = c->mk.n;
+  if (n == 0) return IBM_OK;
+  if (bad_ptr(p) || bad_ptr(rhs_F) || bad_ptr(Fc)) return set_err(c, IBM_ERR_ARG, "bad args");
+  launch_marker_grad_interp(c, p, 1.0, c->mk.t);
+  count_launch();
+  k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, c->stream>>>(c->mk.t, 2.0, rhs_F, -2.0, Fc, 3 * n);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, const double* p_n,
+                    const double* F_n, const double* U_gamma, const double* f_body,
+                    double* u_np1, double* p_np1, double* F_np1, const ibm_solve_opts* o,
+                    ibm_solve_stats* st) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  const int64_t n = c->mk.n;
+  if (bad_ptr(u_n) || bad_ptr(u_nm1) || bad_ptr(p_n) || bad_ptr(u_np1) || bad_ptr(p_np1) ||
+      (f_body && bad_ptr(f_body)))
+    return set_err(c, IBM_ERR_ARG, "bad field pointer");
+  if (n > 0 && (bad_ptr(F_n) || bad_ptr(U_gamma) || bad_ptr(F_np1)))
+    return set_err(c, IBM_ERR_ARG, "bad marker pointer");
+  if (u_np1 == u_n || u_np1 == u_nm1 || p_np1 == p_n || (n > 0 && F_np1 == F_n))
+    return set_err(c, IBM_ERR_ARG, "outputs must not alias inputs");
+  ibm_status s = check_opts(c, o);
+  if (s != IBM_OK) return s;
+  if ((s = ensure_krylov(c, o->restart)) != IBM_OK) return s;
+  ibm_solve_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  cudaStream_t str = c->stream;
+  const double a = 1.5 / c->dt;
+  const double inv_h = 1.0 / c->h;
+  MarkerData& mk = c->mk;
+
+  // 1. predictor (Eq. (ustar))
+  const double* adv = nullptr;
+  if (o->with_advection) {
+    launch_advection(c->d, u_n, inv_h, c->f4, str);
+    adv = c->f4;
+  }
+  launch_predictor_rhs(c->d, u_n, u_nm1, p_n, f_body, adv, 1.0 / (2.0 * c->dt), inv_h, c->f1,
+                       str);
+  if (n > 0) launch_shell_spread_faces(c, F_n, 1.0, c->f1);
+  IBM_LAUNCH_CHECK(c);
+  double* u_star = c->f2;
+  int ph = prof_begin(c, IBM_PROF_PREDICTOR);
+  s = helmholtz_solve(c, c->f1, u_star, o, &st->helm_iters, &st->helm_relres);
+  prof_end(c, ph);
+  if (s != IBM_OK) return s;
+
+  // 2. RHS_p = a G^T u*, RHS_F = a (R^T u* - U), b = RHS_p + 2 B^T RHS_F
+  launch_gradt_axpby(c->d, u_star, a * inv_h, nullptr, 0.0, c->c1, str);
+  IBM_CUDA(c, cudaMemcpyAsync(c->c2, c->c1, sizeof(double) * c->m, cudaMemcpyDeviceToDevice, str));
+  if (n > 0) {
+    launch_interp(c, u_star, mk.t2);
+    count_launch();
+    k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t2, a, U_gamma, -a, mk.t2, 3 * n);
+    launch_shell_gradt_spread(c, mk.t2, 2.0, c->c2);
+  }
+  IBM_LAUNCH_CHECK(c);
+
+  // 3. Schur solve for p' (into c3, zero initial guess)
+  double* pc = c->c3;
+  IBM_CUDA(c, cudaMemsetAsync(pc, 0, sizeof(double) * c->m, str));
+  ph = prof_begin(c, IBM_PROF_SOLVE);
+  s = fgmres_solve(c, c->c2, pc, o, st);
+  prof_end(c, ph);
+  if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
+  const ibm_status solve_status = s;
+
+  // 4.-5. F' = 2 (B p' - RHS_F); updates
+  launch_axpby(p_n, 1.0, pc, 1.0, p_np1, c->m, str);
+  launch_grad_axpy(c->d, u_star, pc, -(2.0 * c->dt / 3.0) * inv_h, u_np1, str);
+  if (n > 0) {
+    launch_marker_grad_interp(c, pc, 1.0, mk.t);
+    count_launch();
+    k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t, 2.0, mk.t2, -2.0, mk.t, 3 * n);
+    count_launch();
+    k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(F_n, 1.0, mk.t, 1.0, F_np1, 3 * n);
+    launch_shell_spread_faces(c, mk.t, 2.0 * c->dt / 3.0, u_np1);
+  }
+  IBM_LAUNCH_CHECK(c);
+
+  // 6. diagnostics
+  launch_gradient_t(c->d, u_np1, c->c1, inv_h, str);
+  IBM_LAUNCH_CHECK(c);
+  if ((s = norm2_host(c, c->c1, c->m, &st->div_l2)) != IBM_OK) return s;
+  if (n > 0) {
+    launch_interp(c, u_np1, mk.t2);
+    count_launch();
+    k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t2, 1.0, U_gamma, -1.0, mk.t2, 3 * n);
+    IBM_LAUNCH_CHECK(c);
+    if ((s = norm2_host(c, mk.t2, 3 * n, &st->slip_l2)) != IBM_OK) return s;
+  }
+  return solve_status;
+}
+
+ibm_status ibm_step(ibm_ctx* c, const double* u_n, const double* u_nm1, const double* p_n,
+                    const double* F_n, const double* U_gamma, const double* f_body,
+                    double* u_np1, double* p_np1, double* F_np1, const ibm_solve_opts* o,
+                    ibm_solve_stats* st) {
+  const int ph = c ? prof_begin(c, IBM_PROF_STEP) : -1;
+  const ibm_status s = step_impl(c, u_n, u_nm1, p_n, F_n, U_gamma, f_body, u_np1, p_np1, F_np1,
+                                 o, st);
+  if (c) prof_end(c, ph);
+  return s;
+}
+
+int64_t ibm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+ibm_status ibm_profile_enable(ibm_ctx* c, int32_t on) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->prof_on = on != 0;
+  c->prof_used = 0;
+  return IBM_OK;
+}
+
+ibm_status ibm_profile_read(ibm_ctx* c, ibm_profile* out) {
+  if (check_ctx(c) != IBM_OK || !out) return IBM_ERR_ARG;
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof(*out));
+  for (size_t i = 0; i < c->prof_used; ++i) {
+    float ms = 0.f;
+    IBM_CUDA(c, cudaEventElapsedTime(&ms, c->prof[i].a, c->prof[i].b));
+    const int k = c->prof[i].cls;
+    if (k >= 0 && k < IBM_PROF_NCLASS) {
+      out->ms[k] += ms;
+      out->launches[k] += 1;
+    }
+  }
+  return IBM_OK;
+}
+
+ibm_status ibm_body_forces(ibm_ctx* c, const double* F, const double* X, const int32_t* body_id,
+                           int32_t n_bodies, const double* centers, double* out) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  const int64_t n = c->mk.n;
+  if (n_bodies < 1 || n_bodies > 4096 || !centers || !out)
+    return set_err(c, IBM_ERR_ARG, "bad body arguments");
+  if (n > 0 && (bad_ptr(F) || bad_ptr(X) || body_id == nullptr))
+    return set_err(c, IBM_ERR_ARG, "bad marker pointers");
+  double* dout = c->red_part;   // n_bodies * 6 <= kRedBlocks * (kMaxRestart + 2)
+  const double h3 = c->h * c->h * c->h;
+  if (n == 0) {
+    for (int q = 0; q < 6 * n_bodies; ++q) out[q] = 0.0;
+    return IBM_OK;
+  }
+  for (int b = 0; b < n_bodies; ++b) {
+    count_launch();
+    k_body_forces<<<1, TPB, 0, c->stream>>>(F, X, body_id, n, centers[3 * b], centers[3 * b + 1],
+                                             centers[3 * b + 2], b, h3, dout + 6 * b);
+  }
+  IBM_LAUNCH_CHECK(c);
+  IBM_CUDA(c, cudaMemcpyAsync(out, dout, sizeof(double) * 6 * n_bodies, cudaMemcpyDeviceToHost,
+                              c->stream));
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+}  // extern "C"

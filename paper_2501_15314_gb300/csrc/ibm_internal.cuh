@@ -1,0 +1,229 @@
+// Internal declarations shared by the CUDA translation units of libibmschur.
+// Layout conventions are those of include/ibm_schur.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ibm_schur.h"
+
+namespace ibm {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxRestart = 64;
+constexpr int kMaxCoarse = 512;     // cells on the coarsest level (dense pinv)
+constexpr int kRedBlocks = 1216;    // fixed grid of the two-stage reductions
+constexpr int kRedThreads = 256;
+
+struct Dims {
+  int nx, ny, nz;
+};
+
+__host__ __device__ inline int64_t cells_of(Dims d) {
+  return (int64_t)d.nx * d.ny * d.nz;
+}
+
+// Face-grid sizes of the packed face vector.
+struct FaceDims {
+  int64_t nfx, nfy, nfz;
+};
+
+__host__ __device__ inline FaceDims face_dims(Dims d) {
+  FaceDims f;
+  f.nfx = (int64_t)d.nz * d.ny * (d.nx + 1);
+  f.nfy = (int64_t)d.nz * (d.ny + 1) * d.nx;
+  f.nfz = (int64_t)(d.nz + 1) * d.ny * d.nx;
+  return f;
+}
+
+// One multigrid level: cell counts, width, and FP32/FP64 buffers.
+struct MGLevel {
+  Dims d;
+  double h;
+  int64_t m;
+  float* x32 = nullptr;
+  float* b32 = nullptr;
+  float* t32 = nullptr;   // ping-pong buffer for smoothing sweeps
+  double* x64 = nullptr;
+  double* b64 = nullptr;
+  double* t64 = nullptr;
+};
+
+// Per-marker Roma data (Eq. (delta)).  For axis e: bf[e] is the first of the
+// three face-type taps (positions i*h), bc[e] the first of the three
+// centre-type taps (positions (i+1/2)h); wf/wc the 1-D weights; org[e] the
+// origin of the 4x4x4 cell box covering every component's G^T R stencil.
+struct MarkerData {
+  int64_t n = 0, cap = 0;
+  int32_t* bf = nullptr;    // [3][n]
+  int32_t* bc = nullptr;    // [3][n]
+  int32_t* org = nullptr;   // [3][n]
+  double* wf = nullptr;     // [3 axes][3 taps][n]
+  double* wc = nullptr;     // [3 axes][3 taps][n]
+  // cell-sorted (marker, slot) list for the atomic-free gathers
+  int64_t n_entries = 0, entries_cap = 0;
+  int32_t* entry_key = nullptr;   // marker * 64 + slot, sorted within a cell
+  double* entry_coef = nullptr;   // [3][n_entries] G^T R coefficients
+  int64_t n_shell = 0;
+  int32_t* shell_cell = nullptr;  // [n_shell] cells touched by any marker
+  int32_t* shell_off = nullptr;   // [n_shell + 1] segment offsets
+  double* t = nullptr;            // [3][n] per-marker scratch
+  double* t2 = nullptr;           // [3][n] per-marker scratch
+};
+
+}  // namespace ibm
+
+struct ibm_ctx {
+  ibm::Dims d;
+  double h, Re, dt;
+  int64_t m, nf;
+  ibm::FaceDims fd;
+  cudaStream_t stream;
+  std::string err;
+
+  // grid-sized scratch (FP64)
+  int32_t* cell_count = nullptr;   // [m]
+  int32_t* cell_start = nullptr;   // [m + 1]
+  int32_t* cell_flag = nullptr;    // [m + 1]
+  int32_t* scan_tmp = nullptr;     // block sums of the scans
+  int32_t* dev_flag = nullptr;     // device error word(s)
+  int32_t* host_flag = nullptr;    // pinned mirror
+  double* c1 = nullptr;            // [m] cell temporaries
+  double* c2 = nullptr;
+  double* c3 = nullptr;
+  double* f1 = nullptr;            // [nf] face temporaries
+  double* f2 = nullptr;
+  double* f3 = nullptr;
+  double* f4 = nullptr;
+  float* g1 = nullptr;             // [nf] FP32 face temporaries (predictor)
+  float* g2 = nullptr;
+  float* g3 = nullptr;
+  float* g4 = nullptr;
+  double* red_part = nullptr;      // [kRedBlocks][kMaxRestart + 2] partials
+  double* red_out = nullptr;       // [kMaxRestart + 2] reduced values
+  double* host_red = nullptr;      // pinned mirror of red_out
+
+  // Krylov bases
+  double* V = nullptr;             // [(kMaxRestart + 1)][m]
+  double* Z = nullptr;             // [kMaxRestart][m]
+  int restart_cap = 0;
+
+  // multigrid hierarchy
+  int n_levels = 0;
+  ibm::MGLevel lv[ibm::kMaxLevels];
+  double* coarse_pinv64 = nullptr; // dense [mc][mc]
+  float* coarse_pinv32 = nullptr;
+  int coarse_m = 0;
+
+  ibm::MarkerData mk;
+  bool markers_set = false;
+
+  // event timing of kernel classes (ibm_profile_enable)
+  bool prof_on = false;
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof;
+  size_t prof_used = 0;
+};
+
+namespace ibm {
+
+// ---- error helpers (host) ----
+ibm_status set_err(ibm_ctx* c, ibm_status s, const std::string& msg);
+ibm_status cuda_err(ibm_ctx* c, cudaError_t e, const char* where);
+
+#define IBM_CUDA(ctx, call)                                           \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return ::ibm::cuda_err((ctx), e_, #call);  \
+  } while (0)
+
+#define IBM_LAUNCH_CHECK(ctx)                                              \
+  do {                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                   \
+    if (e_ != cudaSuccess) return ::ibm::cuda_err((ctx), e_, "kernel launch"); \
+  } while (0)
+
+// ---- stencils (stencil.cu) ----
+// out = scale * L v  (Neumann 7-point, L = G^T G with h folded into scale)
+template <typename T>
+void launch_laplacian(Dims d, const T* v, T* out, double inv_h2, cudaStream_t s);
+void launch_gradient(Dims d, const double* p, double* u, double inv_h, cudaStream_t s);
+void launch_gradient_t(Dims d, const double* u, double* out, double inv_h, cudaStream_t s);
+// u_out = u_in + alpha * G p   (interior faces; wall faces 0)
+void launch_grad_axpy(Dims d, const double* u_in, const double* p, double alpha,
+                      double* u_out, cudaStream_t s);
+// out = alpha * G^T u + beta * c   (c may be null)
+void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c,
+                        double beta, double* out, cudaStream_t s);
+// predictor helpers
+void launch_helm_apply(Dims d, const double* u, double a, double nu_h2,
+                       const double* rhs, double* res, cudaStream_t s);
+void launch_helm_cheb(Dims d, const float* e, const float* e_old, const float* r,
+                      float a, float nu_h2, float alpha, float beta, float* e_new,
+                      int first, cudaStream_t s);
+void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s);
+void launch_predictor_rhs(Dims d, const double* u_n, const double* u_nm1,
+                          const double* p_n, const double* f_body, const double* adv,
+                          double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
+
+// ---- markers (markers.cu) ----
+ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);
+// t[d][k] = scale * (B v)_{k,d} = scale * (R^T G v)_{k,d}
+void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t);
+// out[cell] += scale * (G^T R t)[cell] on the shell cells
+void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);
+// U[d][k] = (R^T u)_{k,d}
+void launch_interp(ibm_ctx* c, const double* u, double* U);
+// u[face] = beta * u[face] + scale * (R F)[face] on shell faces only
+void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double* u);
+
+// ---- reductions and vector kernels (krylov.cu) ----
+// red_out[q] = <w, V_q>, q < nq (two-stage, fixed order)
+void launch_multidot(const double* w, const double* V, int64_t ld, int nq, int64_t n,
+                     double* part, double* out, cudaStream_t s);
+// w -= sum_q coef[q] V_q  (coef on device), out = ||w||^2 (two-stage)
+void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const double* coef,
+                      int64_t n, double* part, double* out, cudaStream_t s);
+void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out,
+                cudaStream_t s);
+void launch_scale(double* x, int64_t n, const double* inv, double scale, cudaStream_t s);
+void launch_scale_to(const double* x, int64_t n, double a, double* y, cudaStream_t s);
+void launch_axpby(const double* x, double a, const double* y, double b, double* out,
+                  int64_t n, cudaStream_t s);
+void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const double* y,
+                     int64_t n, cudaStream_t s);
+void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s);
+void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
+                           cudaStream_t s);
+void launch_copy_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+void launch_copy_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t s);
+
+// ---- scans (markers.cu) ----
+ibm_status exclusive_scan(ibm_ctx* c, const int32_t* in, int32_t* out, int64_t n);
+
+// ---- multigrid (multigrid.cu) ----
+ibm_status mg_setup(ibm_ctx* c);
+ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, int post);
+
+// ---- solver (krylov.cu) ----
+ibm_status schur_apply(ibm_ctx* c, const double* v, double* out);
+ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
+                        ibm_solve_stats* st);
+
+// Counts one kernel launch (process-wide counter, ibm_kernel_launches).
+void count_launch();
+
+// Records a start event for class cls (returns a handle, -1 when off) and the
+// matching end event.
+int prof_begin(ibm_ctx* c, int cls);
+void prof_end(ibm_ctx* c, int handle);
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ibm

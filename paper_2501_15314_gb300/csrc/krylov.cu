@@ -1,0 +1,391 @@
+// Schur-complement operator S~ = L + 2 B^T B (Eq. (tildeSp)) and its
+// Laplacian-preconditioned Krylov solve (Sec. 4.1-4.2): right-preconditioned
+// flexible GMRES in FP64 with classical Gram-Schmidt done as one fused
+// multi-dot pass and one fused axpy+norm pass per iteration.  The paper's own
+// solver is left-preconditioned (BiCGStab/GMRES with an exact L^{-1}); the
+// flexible right-preconditioned form is used here because the preconditioner
+// (one FP32 V-cycle) is not an exact fixed linear map, and it measures the
+// unpreconditioned residual directly.
+//
+// Reductions are two-stage with a fixed grid (kRedBlocks blocks, fixed-order
+// tree inside each block, then one fixed-order tree per output): results are
+// bitwise reproducible run to run.
+#include <cmath>
+#include <vector>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+namespace {
+
+constexpr int RT = kRedThreads;
+constexpr int kOutStride = kMaxRestart + 2;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduces NQ per-thread values across the block; thread q < nq of the block
+// writes part[blockIdx.x * kOutStride + q].
+template <int NQ>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NQ], int nq, double* part) {
+  __shared__ double sh[RT / 32][NQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) sh[wid][q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nq; q += RT) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) s += sh[w][q];
+    part[(int64_t)blockIdx.x * kOutStride + q] = s;
+  }
+}
+
+// part[b][q] = sum over this block's elements of w_i * V_q[i], q < nq <= NQ
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ w,
+                                                 const double* __restrict__ V, int64_t ld, int nq,
+                                                 int64_t n, double* __restrict__ part) {
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    const double wi = __ldg(w + i);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) acc[q] = fma(wi, __ldg(V + q * ld + i), acc[q]);
+  }
+  block_reduce_store<NQ>(acc, nq, part);
+}
+
+// w -= sum_q coef[q] V_q ; part[b][0] = sum of w_i^2 over this block
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_axpy_norm(double* __restrict__ w,
+                                                  const double* __restrict__ V, int64_t ld,
+                                                  int nq, const double* __restrict__ coef,
+                                                  int64_t n, double* __restrict__ part) {
+  double cf[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) cf[q] = q < nq ? coef[q] : 0.0;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) wi = fma(-cf[q], __ldg(V + q * ld + i), wi);
+    w[i] = wi;
+    acc[0] = fma(wi, wi, acc[0]);
+  }
+  block_reduce_store<1>(acc, 1, part);
+}
+
+// out[q] = sum_b part[b][q], fixed-order tree (one block per q)
+__global__ void __launch_bounds__(RT) k_final_reduce(const double* __restrict__ part, int nb,
+                                                     double* __restrict__ out) {
+  const int q = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * kOutStride + q];
+  __shared__ double sh[RT / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < RT / 32; ++w) t += sh[w];
+    out[q] = t;
+  }
+}
+
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                      double* __restrict__ part) {
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT)
+    acc[0] = fma(__ldg(a + i), b ? __ldg(b + i) : 1.0, acc[0]);
+  block_reduce_store<1>(acc, 1, part);
+}
+
+// x *= scale / sqrt(*inv) when inv != null, else x *= scale
+__global__ void k_scale(double* __restrict__ x, int64_t n, const double* __restrict__ nrm2,
+                        double scale) {
+  const double f = nrm2 ? scale / sqrt(*nrm2) : scale;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+
+__global__ void k_scale_to(const double* __restrict__ x, int64_t n, double a,
+                           double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+__global__ void k_axpby(const double* __restrict__ x, double a, const double* __restrict__ y,
+                        double b, double* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = fma(a, x[i], b * y[i]);
+}
+
+// x += sum_q y[q] Z_q  (y on device)
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_gemv_acc(double* __restrict__ x,
+                                                 const double* __restrict__ Z, int64_t ld, int nq,
+                                                 const double* __restrict__ y, int64_t n) {
+  double cf[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) cf[q] = q < nq ? y[q] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    double xi = x[i];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) xi = fma(cf[q], __ldg(Z + q * ld + i), xi);
+    x[i] = xi;
+  }
+}
+
+__global__ void k_add_scalar(double* __restrict__ x, int64_t n, const double* __restrict__ val,
+                             double scale) {
+  const double v = scale * (*val);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += v;
+}
+
+#define IBM_NQ_DISPATCH(nq, KERNEL, ...)                          \
+  do {                                                            \
+    count_launch();                                               \
+    if ((nq) <= 2) KERNEL<2><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);        \
+    else if ((nq) <= 4) KERNEL<4><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
+    else if ((nq) <= 8) KERNEL<8><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
+    else if ((nq) <= 12) KERNEL<12><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 16) KERNEL<16><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 24) KERNEL<24><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 32) KERNEL<32><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 48) KERNEL<48><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else KERNEL<kMaxRestart + 1><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);    \
+  } while (0)
+
+}  // namespace
+
+void launch_multidot(const double* w, const double* V, int64_t ld, int nq, int64_t n,
+                     double* part, double* out, cudaStream_t s) {
+  IBM_NQ_DISPATCH(nq, k_multidot, w, V, ld, nq, n, part);
+  count_launch();
+  k_final_reduce<<<nq, RT, 0, s>>>(part, kRedBlocks, out);
+}
+
+void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const double* coef,
+                      int64_t n, double* part, double* out, cudaStream_t s) {
+  IBM_NQ_DISPATCH(nq, k_axpy_norm, w, V, ld, nq, coef, n, part);
+  count_launch();
+  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out);
+}
+
+void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out,
+                cudaStream_t s) {
+  count_launch();
+  k_dot<<<kRedBlocks, RT, 0, s>>>(a, b, n, part);
+  count_launch();
+  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out);
+}
+
+void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s) {
+  launch_dot(x, nullptr, n, part, out, s);
+}
+
+void launch_scale(double* x, int64_t n, const double* nrm2, double scale, cudaStream_t s) {
+  count_launch();
+  k_scale<<<kRedBlocks, RT, 0, s>>>(x, n, nrm2, scale);
+}
+
+void launch_scale_to(const double* x, int64_t n, double a, double* y, cudaStream_t s) {
+  count_launch();
+  k_scale_to<<<kRedBlocks, RT, 0, s>>>(x, n, a, y);
+}
+
+void launch_axpby(const double* x, double a, const double* y, double b, double* out, int64_t n,
+                  cudaStream_t s) {
+  count_launch();
+  k_axpby<<<kRedBlocks, RT, 0, s>>>(x, a, y, b, out, n);
+}
+
+void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const double* y, int64_t n,
+                     cudaStream_t s) {
+  IBM_NQ_DISPATCH(nq, k_gemv_acc, x, Z, ld, nq, y, n);
+}
+
+void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
+                           cudaStream_t s) {
+  count_launch();
+  k_add_scalar<<<kRedBlocks, RT, 0, s>>>(x, n, val, scale);
+}
+
+// ---------------------------------------------------------------------------
+ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
+  // out = L v + 2 B^T (B v): t = 2 R^T G v per marker, out = L v, then the
+  // shell cells gather G^T R t.
+  int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
+  launch_laplacian<double>(c->d, v, out, 1.0 / (c->h * c->h), c->stream);
+  prof_end(c, ph);
+  ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
+  launch_marker_grad_interp(c, v, 2.0, c->mk.t);
+  launch_shell_gradt_spread(c, c->mk.t, 1.0, out);
+  prof_end(c, ph);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+namespace {
+
+ibm_status fetch(ibm_ctx* c, const double* dev, int n) {
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, dev, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                              c->stream));
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+}  // namespace
+
+ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
+                        ibm_solve_stats* st) {
+  cudaStream_t s = c->stream;
+  const int64_t m = c->m;
+  const int restart = o->restart;
+  double* part = c->red_part;
+  double* hdev = c->red_out;                    // h column (and norm^2 at [j+1])
+  double* hdev2 = c->red_out + kOutStride;      // second Gram-Schmidt pass
+  double* ydev = c->red_out + 2 * kOutStride;   // solution coefficients
+  double* sdev = c->red_out + 3 * kOutStride;   // scalars
+  ibm_status stt;
+
+  // ||b||
+  launch_dot(b, b, m, part, sdev, s);
+  IBM_LAUNCH_CHECK(c);
+  if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
+  const double bnorm = std::sqrt(c->host_red[0]);
+  if (!std::isfinite(bnorm)) return set_err(c, IBM_ERR_NAN, "non-finite right-hand side");
+  int total = 0, cycles = 0;
+  double relres = 0.0;
+  if (bnorm == 0.0) {
+    IBM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * m, s));
+    if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; }
+    return IBM_OK;
+  }
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart),
+      g(restart + 1), y(restart);
+  auto Hm = [&](int i, int j) -> double& { return H[(size_t)i * restart + j]; };
+  double* V = c->V;
+  double* Z = c->Z;
+  bool converged = false;
+  ibm_status final_status = IBM_OK;
+  while (true) {
+    // r0 = b - S x  into V_0
+    if ((stt = schur_apply(c, x, V)) != IBM_OK) return stt;
+    launch_axpby(b, 1.0, V, -1.0, V, m, s);
+    launch_dot(V, V, m, part, sdev, s);
+    IBM_LAUNCH_CHECK(c);
+    if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
+    const double beta = std::sqrt(c->host_red[0]);
+    if (!std::isfinite(beta)) return set_err(c, IBM_ERR_NAN, "non-finite residual");
+    relres = beta / bnorm;
+    if (relres <= o->rtol) { converged = true; break; }
+    if (total >= o->maxit) break;
+    launch_scale(V, m, nullptr, 1.0 / beta, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jused = 0;
+    bool breakdown = false;
+    for (int j = 0; j < restart && total < o->maxit; ++j) {
+      double* vj = V + (int64_t)j * m;
+      double* zj = Z + (int64_t)j * m;
+      double* w = V + (int64_t)(j + 1) * m;
+      int ph = prof_begin(c, IBM_PROF_VCYCLE);
+      if ((stt = mg_vcycle(c, vj, zj, o->precond_prec, o->mg_pre, o->mg_post)) != IBM_OK)
+        return stt;
+      prof_end(c, ph);
+      if ((stt = schur_apply(c, zj, w)) != IBM_OK) return stt;
+      ph = prof_begin(c, IBM_PROF_MULTIDOT);
+      launch_multidot(w, V, m, j + 1, m, part, hdev, s);
+      prof_end(c, ph);
+      ph = prof_begin(c, IBM_PROF_AXPY_NORM);
+      launch_axpy_norm(w, V, m, j + 1, hdev, m, part, hdev + j + 1, s);
+      prof_end(c, ph);
+      if (o->reorth) {
+        launch_multidot(w, V, m, j + 1, m, part, hdev2, s);
+        launch_axpy_norm(w, V, m, j + 1, hdev2, m, part, hdev + j + 1, s);
+      }
+      IBM_LAUNCH_CHECK(c);
+      IBM_CUDA(c, cudaMemcpyAsync(c->host_red, hdev, sizeof(double) * (j + 2),
+                                  cudaMemcpyDeviceToHost, s));
+      if (o->reorth)
+        IBM_CUDA(c, cudaMemcpyAsync(c->host_red + kOutStride, hdev2, sizeof(double) * (j + 1),
+                                    cudaMemcpyDeviceToHost, s));
+      IBM_CUDA(c, cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i)
+        Hm(i, j) = c->host_red[i] + (o->reorth ? c->host_red[kOutStride + i] : 0.0);
+      const double hn = std::sqrt(c->host_red[j + 1]);
+      if (!std::isfinite(hn)) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
+      Hm(j + 1, j) = hn;
+      if (hn > 0.0) launch_scale(w, m, nullptr, 1.0 / hn, s);
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
+        Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
+        Hm(i, j) = t;
+      }
+      const double den = std::hypot(Hm(j, j), Hm(j + 1, j));
+      if (den == 0.0) { breakdown = true; break; }
+      cs[j] = Hm(j, j) / den;
+      sn[j] = Hm(j + 1, j) / den;
+      Hm(j, j) = den;
+      Hm(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      jused = j + 1;
+      if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = std::fabs(g[j + 1]) / bnorm;
+      if (std::fabs(g[j + 1]) / bnorm <= o->rtol || hn == 0.0) break;
+    }
+    if (jused > 0) {
+      for (int i = jused - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int q = i + 1; q < jused; ++q) acc -= Hm(i, q) * y[q];
+        y[i] = acc / Hm(i, i);
+      }
+      IBM_CUDA(c, cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jused, cudaMemcpyHostToDevice,
+                                  s));
+      IBM_CUDA(c, cudaStreamSynchronize(s));   // y is a stack buffer
+      launch_gemv_acc(x, Z, m, jused, ydev, m, s);
+      IBM_LAUNCH_CHECK(c);
+    }
+    ++cycles;
+    if (breakdown && jused == 0) { final_status = IBM_ERR_BREAKDOWN; break; }
+  }
+  // mean-zero projection (S~ annihilates constants)
+  launch_sum(x, m, part, sdev, s);
+  launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
+  IBM_LAUNCH_CHECK(c);
+  if (st) {
+    st->iters = total;
+    st->restarts = cycles;
+    st->relres_true = relres;
+  }
+  if (final_status != IBM_OK) return set_err(c, final_status, "FGMRES breakdown");
+  if (!converged) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "FGMRES did not reach rtol %.3g in %d iterations (relres %.3g)",
+             o->rtol, total, relres);
+    return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
+  }
+  return IBM_OK;
+}
+
+}  // namespace ibm

@@ -1,0 +1,541 @@
+// Lagrangian-marker transfer operators (Sec. 2.3): Roma's discrete delta
+// (Eq. (delta)), interpolation R^T (Eq. (interpolation)), regularisation R
+// (Eq. (regularization)) and the Schur-complement terms B = R^T G and
+// B^T = G^T R of Eq. (Saddle), all matrix-free.
+//
+// Per marker and axis e only two tap bases exist: bf (positions i h, used by
+// the component normal to e) and bc (positions (i+1/2) h, used by the other
+// two components), each with three 1-D weights.  The cell footprint of
+// G^T R e_{k,d} is 4 x 3 x 3 cells; the union over the three components is a
+// 4 x 4 x 4 box with origin org.  A cell-sorted list of (marker, box slot)
+// entries, each with its three G^T R coefficients, lets every shell cell (and
+// every shell face) gather its markers in a fixed order: the spreads are
+// deterministic and use no atomics.  The list is built once per marker set by
+// a counting sort (atomics only in the counting, followed by a per-segment
+// sort so that the final order does not depend on scheduling).
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+namespace {
+
+constexpr int TPB = 256;
+
+// Eq. (delta) times the cell width, r in cell widths.
+__device__ __forceinline__ double roma_phi(double r) {
+  r = fabs(r);
+  if (r <= 0.5) return (1.0 + sqrt(fmax(1.0 - 3.0 * r * r, 0.0))) * (1.0 / 3.0);
+  if (r <= 1.5) {
+    const double q = 1.0 - r;
+    return (5.0 - 3.0 * r - sqrt(fmax(1.0 - 3.0 * q * q, 0.0))) * (1.0 / 6.0);
+  }
+  return 0.0;
+}
+
+struct MkView {
+  int64_t n;
+  const int32_t* bf;
+  const int32_t* bc;
+  const int32_t* org;
+  const double* wf;
+  const double* wc;
+};
+
+MkView view(const MarkerData& m) { return MkView{m.n, m.bf, m.bc, m.org, m.wf, m.wc}; }
+
+__global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __restrict__ X,
+                               int32_t* bf, int32_t* bc, int32_t* org, double* wf, double* wc,
+                               int32_t* err) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int ncell[3] = {d.nx, d.ny, d.nz};
+  bool bad = false;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const double s = X[e * n + k] * inv_h;
+    const double fs = floor(s + 0.5);
+    const double fc = floor(s);
+    // guard the conversions against non-finite or huge inputs
+    if (!(fs > -1e9 && fs < 1e9 && fc > -1e9 && fc < 1e9)) {
+      bad = true;
+      bf[e * n + k] = 1; bc[e * n + k] = 0; org[e * n + k] = 0;
+      for (int q = 0; q < 3; ++q) { wf[(e * 3 + q) * n + k] = 0.0; wc[(e * 3 + q) * n + k] = 0.0; }
+      continue;
+    }
+    const int b_f = (int)fs - 1;   // face taps b_f .. b_f+2 at positions i h
+    const int b_c = (int)fc - 1;   // centre taps b_c .. b_c+2 at (i+1/2) h
+    if (b_f < 1 || b_f + 2 > ncell[e] - 1) bad = true;
+    if (b_c < 0 || b_c + 2 > ncell[e] - 1) bad = true;
+    bf[e * n + k] = b_f;
+    bc[e * n + k] = b_c;
+    org[e * n + k] = min(b_f - 1, b_c);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      wf[(e * 3 + q) * n + k] = roma_phi((double)(b_f + q) - s);
+      wc[(e * 3 + q) * n + k] = roma_phi((double)(b_c + q) + 0.5 - s);
+    }
+  }
+  if (bad) atomicOr(err, 1);
+}
+
+__device__ __forceinline__ int64_t cell_of(Dims d, int i, int j, int k) {
+  return ((int64_t)k * d.ny + j) * d.nx + i;
+}
+
+__global__ void k_count(Dims d, MkView mk, int32_t* count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= mk.n * 64) return;
+  const int64_t k = t >> 6;
+  const int s = (int)(t & 63);
+  const int i = mk.org[k] + (s & 3), j = mk.org[mk.n + k] + ((s >> 2) & 3),
+            l = mk.org[2 * mk.n + k] + (s >> 4);
+  atomicAdd(count + cell_of(d, i, j, l), 1);
+}
+
+__global__ void k_flag(const int32_t* __restrict__ count, int64_t m, int32_t* flag) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c < m) flag[c] = count[c] > 0 ? 1 : 0;
+}
+
+__global__ void k_shell_list(const int32_t* __restrict__ count, const int32_t* __restrict__ start,
+                             const int32_t* __restrict__ fpos, int64_t m, int32_t* shell_cell,
+                             int32_t* shell_off) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  if (count[c] > 0) {
+    const int32_t q = fpos[c];
+    shell_cell[q] = (int32_t)c;
+    shell_off[q] = start[c];
+  }
+}
+
+__global__ void k_fill(Dims d, MkView mk, const int32_t* __restrict__ start, int32_t* fillc,
+                       int32_t* key) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= mk.n * 64) return;
+  const int64_t k = t >> 6;
+  const int s = (int)(t & 63);
+  const int i = mk.org[k] + (s & 3), j = mk.org[mk.n + k] + ((s >> 2) & 3),
+            l = mk.org[2 * mk.n + k] + (s >> 4);
+  const int64_t c = cell_of(d, i, j, l);
+  const int32_t pos = start[c] + atomicAdd(fillc + c, 1);
+  key[pos] = (int32_t)(k * 64 + s);
+}
+
+// Insertion sort of each shell cell's segment (segments hold <= a few hundred
+// keys); makes the entry order independent of atomic scheduling.
+__global__ void k_sort_segments(int64_t n_shell, const int32_t* __restrict__ off, int32_t* key) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n_shell) return;
+  const int32_t a = off[q], b = off[q + 1];
+  for (int32_t x = a + 1; x < b; ++x) {
+    const int32_t v = key[x];
+    int32_t y = x - 1;
+    while (y >= a && key[y] > v) { key[y + 1] = key[y]; --y; }
+    key[y + 1] = v;
+  }
+}
+
+// Coefficient of G^T R e_{k,d} at global cell (g0, g1, g2).  Along d the cell
+// weight is (w_i - w_{i+1})/h with w the face-tap weights (cell i lies between
+// faces i and i+1); along the other axes it is the centre-tap weight.
+__device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcomp, const int g[3],
+                                           double inv_h) {
+  double c = 1.0;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (e == dcomp) {
+      const int q = g[e] - mk.bf[e * mk.n + k];   // face index i - b_f, cell i
+      const double wi = (q >= 0 && q <= 2) ? mk.wf[(e * 3 + q) * mk.n + k] : 0.0;
+      const double wn = (q + 1 >= 0 && q + 1 <= 2) ? mk.wf[(e * 3 + q + 1) * mk.n + k] : 0.0;
+      c *= (wi - wn) * inv_h;
+    } else {
+      const int q = g[e] - mk.bc[e * mk.n + k];
+      c *= (q >= 0 && q <= 2) ? mk.wc[(e * 3 + q) * mk.n + k] : 0.0;
+    }
+  }
+  return c;
+}
+
+__global__ void k_entry_coef(Dims d, MkView mk, int64_t n_entries, const int32_t* __restrict__ key,
+                             double inv_h, double* coef) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_entries) return;
+  const int32_t kk = key[t];
+  const int64_t k = kk >> 6;
+  const int s = kk & 63;
+  const int g[3] = {mk.org[k] + (s & 3), mk.org[mk.n + k] + ((s >> 2) & 3),
+                    mk.org[2 * mk.n + k] + (s >> 4)};
+#pragma unroll
+  for (int dc = 0; dc < 3; ++dc) coef[dc * n_entries + t] = gtr_coef(mk, k, dc, g, inv_h);
+}
+
+// t[d][k] = scale * sum_cells gtr_coef * v  (= scale * (R^T G v)_{k,d}).  One
+// thread per (marker, component); the coefficients are the same products as
+// the stored entry coefficients, so B and B^T are exact transposes.
+__global__ void k_marker_grad_interp(Dims d, MkView mk, const double* __restrict__ v,
+                                     double inv_h, double scale, double* __restrict__ t) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= 3 * mk.n) return;
+  const int dc = (int)(tid / mk.n);
+  const int64_t k = tid - dc * mk.n;
+  // stencil extent: 4 cells along dc starting at b_f - 1, 3 cells elsewhere
+  int lo[3], len[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (e == dc) { lo[e] = mk.bf[e * mk.n + k] - 1; len[e] = 4; }
+    else { lo[e] = mk.bc[e * mk.n + k]; len[e] = 3; }
+  }
+  double acc = 0.0;
+  for (int c2 = 0; c2 < len[2]; ++c2)
+    for (int c1 = 0; c1 < len[1]; ++c1)
+      for (int c0 = 0; c0 < len[0]; ++c0) {
+        const int g[3] = {lo[0] + c0, lo[1] + c1, lo[2] + c2};
+        const double cf = gtr_coef(mk, k, dc, g, inv_h);
+        acc = fma(cf, __ldg(v + cell_of(d, g[0], g[1], g[2])), acc);
+      }
+  t[dc * mk.n + k] = scale * acc;
+}
+
+// out[c] += scale * sum_{entries of c} sum_d coef_d t[d][k]   (shell cells)
+__global__ void k_shell_gradt(int64_t n_shell, const int32_t* __restrict__ shell_cell,
+                              const int32_t* __restrict__ off, const int32_t* __restrict__ key,
+                              const double* __restrict__ coef, int64_t n_entries, int64_t nmk,
+                              const double* __restrict__ t, double scale,
+                              double* __restrict__ out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n_shell) return;
+  const int32_t a = off[q], b = off[q + 1];
+  double acc = 0.0;
+  for (int32_t x = a; x < b; ++x) {
+    const int64_t k = key[x] >> 6;
+    acc = fma(coef[x], t[k], acc);
+    acc = fma(coef[n_entries + x], t[nmk + k], acc);
+    acc = fma(coef[2 * n_entries + x], t[2 * nmk + k], acc);
+  }
+  const int64_t c = shell_cell[q];
+  out[c] = fma(scale, acc, out[c]);
+}
+
+// U[d][k] = sum over the 27 taps of component d of w * u_d  (R^T u)
+__global__ void k_interp(Dims d, MkView mk, const double* __restrict__ u, double* __restrict__ U) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= 3 * mk.n) return;
+  const int dc = (int)(tid / mk.n);
+  const int64_t k = tid - dc * mk.n;
+  const FaceDims fd = face_dims(d);
+  const int64_t off = dc == 0 ? 0 : (dc == 1 ? fd.nfx : fd.nfx + fd.nfy);
+  const int sx = 1;
+  const int64_t sy = d.nx + (dc == 0 ? 1 : 0);
+  const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
+  int b[3];
+  const double* w[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    b[e] = (e == dc) ? mk.bf[e * mk.n + k] : mk.bc[e * mk.n + k];
+    w[e] = (e == dc) ? (mk.wf + e * 3 * mk.n + k) : (mk.wc + e * 3 * mk.n + k);
+  }
+  double acc = 0.0;
+  for (int c2 = 0; c2 < 3; ++c2) {
+    double acc1 = 0.0;
+    for (int c1 = 0; c1 < 3; ++c1) {
+      double acc0 = 0.0;
+      const int64_t base = off + (int64_t)(b[2] + c2) * sz + (int64_t)(b[1] + c1) * sy + b[0];
+      for (int c0 = 0; c0 < 3; ++c0) acc0 = fma(w[0][c0 * mk.n], __ldg(u + base + c0 * sx), acc0);
+      acc1 = fma(w[1][c1 * mk.n], acc0, acc1);
+    }
+    acc = fma(w[2][c2 * mk.n], acc1, acc);
+  }
+  U[dc * mk.n + k] = acc;
+}
+
+// Face spread R F on the shell: every tap face of a marker is the lower face
+// (along its own normal) of a cell of the marker's box, so one thread per
+// (shell cell, component) owns that face and gathers its markers in order.
+__global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
+                                     const int32_t* __restrict__ shell_cell,
+                                     const int32_t* __restrict__ off,
+                                     const int32_t* __restrict__ key,
+                                     const double* __restrict__ F, double scale,
+                                     double* __restrict__ u) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= 3 * n_shell) return;
+  const int dc = (int)(tid / n_shell);
+  const int64_t q = tid - dc * n_shell;
+  const int64_t c = shell_cell[q];
+  const int ci = (int)(c % d.nx);
+  const int cj = (int)((c / d.nx) % d.ny);
+  const int ck = (int)(c / ((int64_t)d.nx * d.ny));
+  const int g[3] = {ci, cj, ck};
+  const int32_t a = off[q], b = off[q + 1];
+  double acc = 0.0;
+  bool any = false;
+  for (int32_t x = a; x < b; ++x) {
+    const int64_t k = key[x] >> 6;
+    double w = 1.0;
+    bool in = true;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int base = (e == dc) ? mk.bf[e * mk.n + k] : mk.bc[e * mk.n + k];
+      const int r = g[e] - base;
+      if (r < 0 || r > 2) { in = false; break; }
+      w *= (e == dc) ? mk.wf[(e * 3 + r) * mk.n + k] : mk.wc[(e * 3 + r) * mk.n + k];
+    }
+    if (in) { acc = fma(w, F[dc * mk.n + k], acc); any = true; }
+  }
+  if (!any) return;
+  const FaceDims fd = face_dims(d);
+  const int64_t foff = dc == 0 ? 0 : (dc == 1 ? fd.nfx : fd.nfx + fd.nfy);
+  const int64_t sy = d.nx + (dc == 0 ? 1 : 0);
+  const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
+  const int64_t f = foff + ck * sz + cj * sy + ci;
+  u[f] = fma(scale, acc, u[f]);
+}
+
+// ---- exclusive scan of int32 (three phases, 4096 elements per block) ----
+constexpr int SCAN_T = 1024, SCAN_E = 4;
+
+__device__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+  // warp-level inclusive scan then scan of warp totals
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  const int32_t wprefix = wid > 0 ? sh[wid - 1] : 0;
+  if (total) *total = sh[31];
+  return wprefix + x - v;
+}
+
+__global__ void k_scan_blocks(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ out,
+                              int32_t* __restrict__ block_sums) {
+  __shared__ int32_t sh[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_T * SCAN_E + (int64_t)threadIdx.x * SCAN_E;
+  int32_t v[SCAN_E];
+  int32_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < SCAN_E; ++q) {
+    v[q] = (base + q < n) ? in[base + q] : 0;
+    sum += v[q];
+  }
+  int32_t total;
+  int32_t ex = block_excl_scan(sum, sh, &total);
+#pragma unroll
+  for (int q = 0; q < SCAN_E; ++q) {
+    if (base + q < n) out[base + q] = ex;
+    ex += v[q];
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// scans block_sums (nb entries) in place with a single block; writes the grand
+// total to *total.
+__global__ void k_scan_sums(int32_t* sums, int64_t nb, int32_t* total) {
+  __shared__ int32_t sh[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += SCAN_T) {
+    const int64_t i = base + threadIdx.x;
+    const int32_t v = i < nb ? sums[i] : 0;
+    int32_t tot;
+    const int32_t ex = block_excl_scan(v, sh, &tot);
+    const int32_t c0 = carry;
+    if (i < nb) sums[i] = ex + c0;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c0 + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int32_t* out, int64_t n, const int32_t* __restrict__ sums,
+                           const int32_t* __restrict__ total) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_T * SCAN_E;
+  const int32_t add = sums[blockIdx.x];
+  for (int q = threadIdx.x; q < SCAN_T * SCAN_E; q += SCAN_T) {
+    const int64_t i = base + q;
+    if (i < n) out[i] += add;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
+}
+
+}  // namespace
+
+// out[0..n] = exclusive scan of in[0..n-1] with out[n] = total.
+ibm_status exclusive_scan(ibm_ctx* c, const int32_t* in, int32_t* out, int64_t n) {
+  const int64_t nb = (n + SCAN_T * SCAN_E - 1) / (SCAN_T * SCAN_E);
+  if (nb == 0) {
+    IBM_CUDA(c, cudaMemsetAsync(out, 0, sizeof(int32_t), c->stream));
+    return IBM_OK;
+  }
+  int32_t* sums = c->scan_tmp;
+  int32_t* total = c->scan_tmp + nb;
+  count_launch();
+  k_scan_blocks<<<(unsigned)nb, SCAN_T, 0, c->stream>>>(in, n, out, sums);
+  count_launch();
+  k_scan_sums<<<1, SCAN_T, 0, c->stream>>>(sums, nb, total);
+  count_launch();
+  k_scan_add<<<(unsigned)nb, SCAN_T, 0, c->stream>>>(out, n, sums, total);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
+  MarkerData& m = c->mk;
+  if (n <= m.cap) return IBM_OK;
+  cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
+  cudaFree(m.t); cudaFree(m.t2);
+  m.bf = m.bc = m.org = nullptr; m.wf = m.wc = m.t = m.t2 = nullptr; m.cap = 0;
+  const size_t ni = sizeof(int32_t) * 3 * n, nd = sizeof(double) * 9 * n;
+  if (cudaMalloc(&m.bf, ni) != cudaSuccess || cudaMalloc(&m.bc, ni) != cudaSuccess ||
+      cudaMalloc(&m.org, ni) != cudaSuccess || cudaMalloc(&m.wf, nd) != cudaSuccess ||
+      cudaMalloc(&m.wc, nd) != cudaSuccess ||
+      cudaMalloc(&m.t, sizeof(double) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, IBM_ERR_NOMEM, "marker workspace allocation failed");
+  }
+  m.cap = n;
+  return IBM_OK;
+}
+
+static ibm_status grow_entries(ibm_ctx* c, int64_t ne) {
+  // shell cells never outnumber entries (each shell cell holds >= 1 entry)
+  MarkerData& m = c->mk;
+  if (ne <= m.entries_cap && m.entry_key) return IBM_OK;
+  cudaFree(m.entry_key); cudaFree(m.entry_coef); cudaFree(m.shell_cell); cudaFree(m.shell_off);
+  m.entry_key = nullptr; m.entry_coef = nullptr; m.shell_cell = nullptr; m.shell_off = nullptr;
+  m.entries_cap = 0;
+  const int64_t cap = ne > 0 ? ne : 1;
+  if (cudaMalloc(&m.entry_key, sizeof(int32_t) * cap) != cudaSuccess ||
+      cudaMalloc(&m.entry_coef, sizeof(double) * 3 * cap) != cudaSuccess ||
+      cudaMalloc(&m.shell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
+      cudaMalloc(&m.shell_off, sizeof(int32_t) * (cap + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, IBM_ERR_NOMEM, "marker entry list allocation failed");
+  }
+  m.entries_cap = cap;
+  return IBM_OK;
+}
+
+ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
+  MarkerData& m = c->mk;
+  c->markers_set = false;
+  m.n = 0;
+  m.n_entries = 0;
+  m.n_shell = 0;
+  if (n == 0) {
+    c->markers_set = true;
+    return IBM_OK;
+  }
+  ibm_status st = grow_markers(c, n);
+  if (st != IBM_OK) return st;
+  cudaStream_t s = c->stream;
+  IBM_CUDA(c, cudaMemsetAsync(c->dev_flag, 0, sizeof(int32_t), s));
+  count_launch();
+  k_marker_setup<<<div_up(n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org, m.wf,
+                                                 m.wc, c->dev_flag);
+  IBM_LAUNCH_CHECK(c);
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->dev_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  IBM_CUDA(c, cudaStreamSynchronize(s));
+  if (c->host_flag[0] != 0)
+    return set_err(c, IBM_ERR_MARKER_DOMAIN,
+                   "a marker's delta support touches a wall face or leaves the grid");
+  m.n = n;
+  const MkView mv = view(m);
+  // counting sort of (marker, slot) pairs by cell
+  IBM_CUDA(c, cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->m, s));
+  count_launch();
+  k_count<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_count);
+  IBM_LAUNCH_CHECK(c);
+  st = exclusive_scan(c, c->cell_count, c->cell_start, c->m);
+  if (st != IBM_OK) return st;
+  count_launch();
+  k_flag<<<div_up(c->m, TPB), TPB, 0, s>>>(c->cell_count, c->m, c->cell_flag);
+  IBM_LAUNCH_CHECK(c);
+  // compact positions of the shell cells (scan of the flags); the cell
+  // temporary c3 (m doubles) holds the m + 1 ints
+  int32_t* fpos = reinterpret_cast<int32_t*>(c->c3);   // m + 1 ints fit in m doubles
+  st = exclusive_scan(c, c->cell_flag, fpos, c->m);
+  if (st != IBM_OK) return st;
+  int32_t tot[2];
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->cell_start + c->m, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, s));
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag + 1, fpos + c->m, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, s));
+  IBM_CUDA(c, cudaStreamSynchronize(s));
+  tot[0] = c->host_flag[0];
+  tot[1] = c->host_flag[1];
+  const int64_t ne = tot[0], ns = tot[1];
+  st = grow_entries(c, ne);
+  if (st != IBM_OK) return st;
+  count_launch();
+  k_shell_list<<<div_up(c->m, TPB), TPB, 0, s>>>(c->cell_count, c->cell_start, fpos, c->m,
+                                                 m.shell_cell, m.shell_off);
+  IBM_LAUNCH_CHECK(c);
+  IBM_CUDA(c, cudaMemcpyAsync(m.shell_off + ns, c->cell_start + c->m, sizeof(int32_t),
+                              cudaMemcpyDeviceToDevice, s));
+  IBM_CUDA(c, cudaMemsetAsync(c->cell_flag, 0, sizeof(int32_t) * c->m, s));
+  count_launch();
+  k_fill<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_start, c->cell_flag, m.entry_key);
+  IBM_LAUNCH_CHECK(c);
+  count_launch();
+  k_sort_segments<<<div_up(ns, TPB), TPB, 0, s>>>(ns, m.shell_off, m.entry_key);
+  count_launch();
+  k_entry_coef<<<div_up(ne, TPB), TPB, 0, s>>>(c->d, mv, ne, m.entry_key, 1.0 / c->h,
+                                               m.entry_coef);
+  IBM_LAUNCH_CHECK(c);
+  m.n_entries = ne;
+  m.n_shell = ns;
+  c->markers_set = true;
+  return IBM_OK;
+}
+
+void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0) return;
+  count_launch();
+  k_marker_grad_interp<<<div_up(3 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v, 1.0 / c->h,
+                                                                     scale, t);
+}
+
+void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0 || m.n_shell == 0) return;
+  count_launch();
+  k_shell_gradt<<<div_up(m.n_shell, TPB), TPB, 0, c->stream>>>(
+      m.n_shell, m.shell_cell, m.shell_off, m.entry_key, m.entry_coef, m.n_entries, m.n, t, scale,
+      out);
+}
+
+void launch_interp(ibm_ctx* c, const double* u, double* U) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0) return;
+  count_launch();
+  k_interp<<<div_up(3 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), u, U);
+}
+
+void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double* u) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0 || m.n_shell == 0) return;
+  count_launch();
+  k_shell_spread_faces<<<div_up(3 * m.n_shell, TPB), TPB, 0, c->stream>>>(
+      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, scale, u);
+}
+
+}  // namespace ibm

@@ -1,0 +1,115 @@
+"""Parity of the GPU Schur solve (FGMRES + V-cycle, FP64 and mixed FP32
+preconditioner) with the oracle's solve, plus the solver's edge cases."""
+import numpy as np
+import pytest
+
+import gpu_cases as gc
+from gpu_cases import dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+PARITY = 1e-10      # FP64 path vs FP64 oracle, both solved to 1e-13
+
+
+@pytest.fixture(scope="module", params=[gc.sphere16, gc.ragged_multi,
+                                        lambda: gc.config_case(1)],
+                ids=["sphere16", "ragged48x40x32", "config1_32"])
+def setup(request, cuda_device):
+    import torch
+    from oracle import schur
+    from paper_2501_15314_gb300.api import IBMSolver
+    case = request.param()
+    g = case.grid()
+    s = IBMSolver(case.nx, case.ny, case.nz, case.h, Re=case.Re, dt=case.dt)
+    s.set_markers(dev(case.X))
+    sysm = schur.SchurSystem(g, case.X)
+    # a right-hand side of the form the step builds: RHS_p + 2 B^T RHS_F
+    from oracle import mac
+    u = case.rng.standard_normal(g.n_faces) * g.interior_face_mask_packed()
+    b = sysm.rhs_scalar(mac.apply_GT(g, u), case.rng.standard_normal(sysm.k))
+    ref, it_ref, rel_ref, _ = schur.solve_schur(sysm, b, rtol=1e-13)
+    yield case, g, s, sysm, b, ref
+    s.close()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_solve_parity(setup, prec):
+    case, g, s, sysm, b, ref = setup
+    p, st = s.solve_schur(dev(b), rtol=1e-13, precond_prec=prec, maxit=300)
+    assert st["relres_true"] <= 1e-13
+    ph = host(p)
+    assert abs(ph.mean()) < 1e-12 * np.abs(ph).max()
+    assert rel(ph, ref) < PARITY, rel(ph, ref)
+    # independent residual check with the oracle operator
+    assert rel(sysm.apply_S_tilde(ph), b) < 2e-13
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_solve_throughput_setting(setup, prec):
+    case, g, s, sysm, b, ref = setup
+    p, st = s.solve_schur(dev(b), rtol=1e-8, precond_prec=prec)
+    ph = host(p)
+    assert rel(sysm.apply_S_tilde(ph), b) <= 1e-8 * 1.001
+    assert rel(ph, ref) < 1e-6
+    assert st["iters"] <= 20, st["iters"]
+
+
+def test_deterministic_and_restart_and_reorth(setup):
+    import torch
+    case, g, s, sysm, b, ref = setup
+    bd = dev(b)
+    p1, st1 = s.solve_schur(bd, rtol=1e-10)
+    p2, st2 = s.solve_schur(bd, rtol=1e-10)
+    assert torch.equal(p1, p2) and st1["iters"] == st2["iters"]
+    p3, st3 = s.solve_schur(bd, rtol=1e-13, restart=4, maxit=400, precond_prec=0)
+    assert st3["restarts"] > 1 and rel(host(p3), ref) < PARITY
+    p4, st4 = s.solve_schur(bd, rtol=1e-13, reorth=1, precond_prec=0)
+    assert rel(host(p4), ref) < PARITY
+
+
+def test_initial_guess(setup):
+    case, g, s, sysm, b, ref = setup
+    x0 = dev(ref + 1e-3 * case.rng.standard_normal(g.m))
+    p, st = s.solve_schur(dev(b), x0=x0, rtol=1e-13, precond_prec=0)
+    assert rel(host(p), ref) < PARITY
+
+
+def test_edge_cases(cuda_device):
+    import torch
+    from oracle import mac
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300.api import IBMSolver
+    s = IBMSolver(16)
+    g = mac.Grid(16)
+    # no markers: S~ = L and the solution is L^+ b
+    b = mac.remove_mean(np.random.default_rng(0).standard_normal(g.m))
+    p, st = s.solve_schur(dev(b), rtol=1e-13, precond_prec=0)
+    assert rel(host(p), mac.laplacian_pinv(g, b)) < PARITY
+    # zero right-hand side gives zero
+    p, st = s.solve_schur(dev(np.zeros(g.m)))
+    assert st["iters"] == 0 and torch.count_nonzero(p) == 0
+    # NaN right-hand side is reported, not propagated silently
+    bad = b.copy()
+    bad[5] = np.nan
+    with pytest.raises(_lib.IBMError) as e:
+        s.solve_schur(dev(bad))
+    assert e.value.status == _lib.IBM_ERR_NAN
+    # maxit reached
+    p, st = s.solve_schur(dev(b), maxit=1, rtol=1e-14, raise_on_error=False)
+    assert st["status"] == _lib.IBM_ERR_NOT_CONVERGED and st["iters"] == 1
+    # invalid options
+    with pytest.raises(_lib.IBMError):
+        s.solve_schur(dev(b), restart=0)
+    # markers whose delta support touches a wall face
+    X = np.array([[0.5], [0.5], [1.2 / 16]])
+    with pytest.raises(_lib.IBMError) as e:
+        s.set_markers(dev(X))
+    assert e.value.status == _lib.IBM_ERR_MARKER_DOMAIN
+    X = np.array([[0.5], [np.nan], [0.5]])
+    with pytest.raises(_lib.IBMError):
+        s.set_markers(dev(X))
+    s.close()
+    # a grid that does not coarsen to <= 512 cells is rejected at creation
+    with pytest.raises(_lib.IBMError):
+        IBMSolver(50, 50, 75)
