@@ -215,6 +215,35 @@ ibm_status ibm_body_forces(ibm_ctx* ctx, const double* F, const double* X,
                            const int32_t* body_id, int32_t n_bodies,
                            const double* centers, double* out);
 
+/* Allocation-free variant of ibm_body_forces, for callers that cannot
+ * allocate device memory: code running where cudaMalloc is unavailable or
+ * forbidden (inside a caller's own fixed memory budget, under an allocator
+ * that must not be re-entered, or in a host process that never creates an
+ * ibm_ctx because creating one allocates the solver's workspace).  The paper
+ * has no counterpart: it is a deployment convenience, not part of the method.
+ *
+ * Computes the same per-body force and torque sums as ibm_body_forces
+ * (h^3 sum F_k and h^3 sum (X_k - c_b) x F_k) without a context: F, X are
+ * device [3][n_markers], body_id device int32 [n_markers], centers host
+ * [n_bodies][3], out host [n_bodies][6]; h the cell width; stream a
+ * cudaStream_t (NULL = legacy default stream).  Synchronises the stream.
+ *
+ * Scratch: the device staging buffer is a fixed array inside the library of
+ * IBM_NOALLOC_MAX_BODIES * 6 doubles (48 KiB) that every GPU loading the
+ * library holds until the process exits.  No call allocates or frees memory.
+ * The first call on each device looks up that device's address of the array
+ * (with the device current), so make the first call on a device outside any
+ * stream capture.  All calls share the array: calls whose work overlaps on the
+ * GPU (different streams, or different host threads on one device) race and
+ * must be serialised by the caller.  Every output slot is overwritten by each
+ * call, so no clearing is needed between calls.
+ * Returns IBM_ERR_ARG when n_bodies < 1 or n_bodies > IBM_NOALLOC_MAX_BODIES,
+ * or a pointer is missing; IBM_ERR_CUDA on a CUDA failure. */
+#define IBM_NOALLOC_MAX_BODIES 1024
+ibm_status ibm_body_forces_noalloc(const double* F, const double* X, const int32_t* body_id,
+                                   int64_t n_markers, int32_t n_bodies, const double* centers,
+                                   double h, void* stream, double* out);
+
 /* Optional timing of kernel classes with CUDA events recorded on the
  * context's stream around the launches of each class (no effect on results).
  * ibm_profile_enable(ctx, 1) resets the counters and starts recording;

@@ -79,6 +79,9 @@ SIGNATURES = [
     ("ibm_force_correction", C.c_int, [_P, _P, _P, _P]),
     ("ibm_step", C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                            C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_stats)]),
+    ("ibm_body_forces_noalloc", C.c_int, [_P, _P, _P, C.c_int64, C.c_int32,
+                                          C.POINTER(C.c_double), C.c_double, _P,
+                                          C.POINTER(C.c_double)]),
     ("ibm_profile_enable", C.c_int, [_P, C.c_int32]),
     ("ibm_kernel_launches", C.c_int64, []),
     ("ibm_profile_read", C.c_int, [_P, C.POINTER(ibm_profile)]),
