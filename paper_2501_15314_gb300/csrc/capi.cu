@@ -82,20 +82,6 @@ __global__ void k_axpby_small(const double* __restrict__ x, double a, const doub
   if (i < n) out[i] = a * x[i] + b * y[i];
 }
 
-__global__ void k_d2f_scaled(const double* __restrict__ x, float* __restrict__ y, int64_t n,
-                             double s) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (float)(s * x[i]);
-}
-
-__global__ void k_f2d_add_scaled(const float* __restrict__ e, double* __restrict__ u, int64_t n,
-                                 double s) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    u[i] += s * (double)e[i];
-}
-
 bool bad_ptr(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 7) != 0; }
 
 ibm_status check_ctx(ibm_ctx* c) {
@@ -137,9 +123,9 @@ ibm_status ensure_krylov(ibm_ctx* c, int restart) {
 }
 
 ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out) {
-  launch_dot(x, x, n, c->red_part, c->red_out + 3 * (kMaxRestart + 2) + 8, c->stream);
+  launch_dot(x, x, n, c->red_part, c->red_out + 7 * (kMaxRestart + 2), c->stream);
   IBM_LAUNCH_CHECK(c);
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, c->red_out + 3 * (kMaxRestart + 2) + 8,
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, c->red_out + 7 * (kMaxRestart + 2),
                               sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   IBM_CUDA(c, cudaStreamSynchronize(c->stream));
   *out = std::sqrt(c->host_red[0]);
@@ -152,7 +138,7 @@ void free_all(ibm_ctx* c) {
   cudaFree(c->c1); cudaFree(c->c2); cudaFree(c->c3);
   cudaFree(c->f1); cudaFree(c->f2); cudaFree(c->f3); cudaFree(c->f4);
   cudaFree(c->g1); cudaFree(c->g2); cudaFree(c->g3); cudaFree(c->g4);
-  cudaFree(c->red_part); cudaFree(c->red_out); cudaFreeHost(c->host_red);
+  cudaFree(c->red_part); cudaFree(c->red_out); cudaFreeHost(c->host_red); cudaFree(c->helm_part);
   cudaFree(c->V); cudaFree(c->Z);
   for (int l = 0; l < c->n_levels; ++l) {
     MGLevel& L = c->lv[l];
@@ -161,9 +147,10 @@ void free_all(ibm_ctx* c) {
   }
   cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
   MarkerData& m = c->mk;
-  cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
+  cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
   cudaFree(m.t); cudaFree(m.t2);
-  cudaFree(m.entry_key); cudaFree(m.entry_coef); cudaFree(m.shell_cell); cudaFree(m.shell_off);
+  cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off);
+  cudaFree(m.ell_base); cudaFree(m.ell_len); cudaFree(m.ell_key); cudaFree(m.ell_coef);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -171,9 +158,12 @@ void free_all(ibm_ctx* c) {
   c->prof.clear();
 }
 
-// Predictor of Eq. (ustar): (a - nu Lap) u = rhs by FP64 defect correction;
-// each correction solves A e = r approximately with K Chebyshev steps in FP32
-// on the exact spectral bounds [a, a + 12 nu / h^2] of the operator.
+// Predictor of Eq. (ustar): (a - nu Lap) u = rhs by FP64 defect correction.
+// Each correction solves A e = r / ||r|| with K FP32 Chebyshev steps on the
+// exact spectral bounds [a, a + 12 nu / h^2] of A; K is chosen for the
+// reduction still needed (at most 1e-6 per correction, the FP32 limit), the
+// first step reads the FP64 residual and the last one accumulates into u.
+// Every FP64 residual is fused with its norm.
 ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
                            int* iters, double* relres) {
   cudaStream_t s = c->stream;
@@ -184,9 +174,6 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   const double lmin = a, lmax = a + 12.0 * nu_h2;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
   const double sigma = theta / delta;
-  // steps for a 1e-6 error reduction: T_K(sigma) >= 1e6
-  int K = (int)std::ceil(std::acosh(1e6) / std::acosh(sigma));
-  K = K < 4 ? 4 : (K > 60 ? 60 : K);
   double rnorm0;
   ibm_status st = norm2_host(c, rhs, nf, &rnorm0);
   if (st != IBM_OK) return st;
@@ -196,53 +183,52 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   *relres = 0.0;
   if (rnorm0 == 0.0) return IBM_OK;
   double* res = c->f3;
+  double* sdev = c->red_out + 7 * (kMaxRestart + 2) + 8;
   const double* rcur = rhs;   // residual of the zero iterate is rhs itself
-  for (int it = 0; it < o->helm_maxit; ++it) {
-    double rn = rnorm0;
+  double rn = rnorm0;
+  for (int it = 0;; ++it) {
     if (it > 0) {
-      launch_helm_apply(c->d, u, a, nu_h2, rhs, res, s);
+      const int64_t nb = launch_helm_residual(c->d, u, a, nu_h2, rhs, res, c->helm_part,
+                                              kMaxRestart + 2, s);
+      launch_final_reduce(c->helm_part, (int)nb, sdev, s);
       IBM_LAUNCH_CHECK(c);
-      if ((st = norm2_host(c, res, nf, &rn)) != IBM_OK) return st;
+      IBM_CUDA(c, cudaMemcpyAsync(c->host_red, sdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      IBM_CUDA(c, cudaStreamSynchronize(s));
+      rn = std::sqrt(c->host_red[0]);
       if (!std::isfinite(rn)) return set_err(c, IBM_ERR_NAN, "non-finite predictor residual");
       rcur = res;
     }
     *relres = rn / rnorm0;
     if (*relres <= o->helm_rtol) return IBM_OK;
-    // scale the residual to O(1) before rounding to FP32
-    const double sc = 1.0 / rn;
-    count_launch();
-    k_d2f_scaled<<<kRedBlocks, TPB, 0, s>>>(rcur, c->g1, nf, sc);
+    if (it >= o->helm_maxit) break;
+    // reduction wanted from this correction (with a 3x margin), FP32-limited
+    double want = o->helm_rtol / *relres / 3.0;
+    if (want < 1e-6) want = 1e-6;
+    int K = (int)std::ceil(std::acosh(1.0 / want) / std::acosh(sigma));
+    K = K < 2 ? 2 : (K > 60 ? 60 : K);
     float* eo = c->g2;
     float* e = c->g3;
     float* en = c->g4;
+    IBM_CUDA(c, cudaMemsetAsync(eo, 0, sizeof(float) * helm_fp32_size(c->d), s));
+    launch_helm_cheb(c->d, nullptr, nullptr, c->g1, rcur, 1.0 / rn, (float)a, (float)nu_h2,
+                     (float)(1.0 / theta), 0.f, e, nullptr, 0.0, 0, s);
     double rho_prev = 1.0 / sigma;
-    launch_helm_cheb(c->d, nullptr, nullptr, c->g1, (float)a, (float)nu_h2, (float)(1.0 / theta),
-                     0.f, e, 1, s);
-    IBM_CUDA(c, cudaMemsetAsync(eo, 0, sizeof(float) * nf, s));
     for (int q = 1; q < K; ++q) {
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
-      launch_helm_cheb(c->d, e, eo, c->g1, (float)a, (float)nu_h2, (float)(2.0 * rho / delta),
-                       (float)(rho * rho_prev), en, 0, s);
+      const int last = q == K - 1;
+      launch_helm_cheb(c->d, e, eo, c->g1, nullptr, 0.0, (float)a, (float)nu_h2,
+                       (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn,
+                       last ? 2 : 1, s);
       rho_prev = rho;
       float* t = eo; eo = e; e = en; en = t;
     }
-    count_launch();
-    k_f2d_add_scaled<<<kRedBlocks, TPB, 0, s>>>(e, u, nf, rn);
     IBM_LAUNCH_CHECK(c);
     *iters = it + 1;
   }
-  double rn;
-  launch_helm_apply(c->d, u, a, nu_h2, rhs, res, s);
-  IBM_LAUNCH_CHECK(c);
-  if ((st = norm2_host(c, res, nf, &rn)) != IBM_OK) return st;
-  *relres = rn / rnorm0;
-  if (*relres > o->helm_rtol) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "predictor did not reach helm_rtol %.3g (relres %.3g)", o->helm_rtol,
-             *relres);
-    return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
-  }
-  return IBM_OK;
+  char buf[160];
+  snprintf(buf, sizeof buf, "predictor did not reach helm_rtol %.3g (relres %.3g)", o->helm_rtol,
+           *relres);
+  return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
 }
 
 }  // namespace
@@ -298,15 +284,21 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
             cudaMalloc(&c->f2, sizeof(double) * nf) == cudaSuccess &&
             cudaMalloc(&c->f3, sizeof(double) * nf) == cudaSuccess &&
             cudaMalloc(&c->f4, sizeof(double) * nf) == cudaSuccess &&
-            cudaMalloc(&c->g1, sizeof(float) * nf) == cudaSuccess &&
-            cudaMalloc(&c->g2, sizeof(float) * nf) == cudaSuccess &&
-            cudaMalloc(&c->g3, sizeof(float) * nf) == cudaSuccess &&
-            cudaMalloc(&c->g4, sizeof(float) * nf) == cudaSuccess &&
+            cudaMalloc(&c->g1, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
+            cudaMalloc(&c->g2, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
+            cudaMalloc(&c->g3, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
+            cudaMalloc(&c->g4, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->red_part, sizeof(double) * kRedBlocks * (kMaxRestart + 2)) ==
                 cudaSuccess &&
-            cudaMalloc(&c->red_out, sizeof(double) * 4 * (kMaxRestart + 2) + 64 * sizeof(double)) ==
+            cudaMalloc(&c->red_out, sizeof(double) * 8 * (kMaxRestart + 2)) ==
                 cudaSuccess &&
-            cudaMallocHost(&c->host_red, sizeof(double) * 4 * (kMaxRestart + 2)) == cudaSuccess;
+            cudaMallocHost(&c->host_red, sizeof(double) * 8 * (kMaxRestart + 2)) == cudaSuccess;
+  {
+    // partial sums of the fused predictor residual norm (one per block)
+    const int64_t nb = (int64_t)div_up(g->nx + 1, 32) * div_up(g->ny + 1, 8) * 3 *
+                       div_up(g->nz + 1, 16);
+    ok = ok && cudaMalloc(&c->helm_part, sizeof(double) * nb * (kMaxRestart + 2)) == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     free_all(c);
@@ -458,13 +450,8 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   MarkerData& mk = c->mk;
 
   // 1. predictor (Eq. (ustar))
-  const double* adv = nullptr;
-  if (o->with_advection) {
-    launch_advection(c->d, u_n, inv_h, c->f4, str);
-    adv = c->f4;
-  }
-  launch_predictor_rhs(c->d, u_n, u_nm1, p_n, f_body, adv, 1.0 / (2.0 * c->dt), inv_h, c->f1,
-                       str);
+  launch_predictor_rhs_adv(c->d, u_n, u_nm1, p_n, f_body, o->with_advection, 1.0 / (2.0 * c->dt),
+                           inv_h, c->f1, str);
   if (n > 0) launch_shell_spread_faces(c, F_n, 1.0, c->f1);
   IBM_LAUNCH_CHECK(c);
   double* u_star = c->f2;
@@ -488,7 +475,7 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   double* pc = c->c3;
   IBM_CUDA(c, cudaMemsetAsync(pc, 0, sizeof(double) * c->m, str));
   ph = prof_begin(c, IBM_PROF_SOLVE);
-  s = fgmres_solve(c, c->c2, pc, o, st);
+  s = fgmres_solve(c, c->c2, pc, o, st, true);
   prof_end(c, ph);
   if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
   const ibm_status solve_status = s;

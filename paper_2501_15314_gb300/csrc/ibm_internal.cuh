@@ -63,10 +63,19 @@ struct MarkerData {
   int32_t* org = nullptr;   // [3][n]
   double* wf = nullptr;     // [3 axes][3 taps][n]
   double* wc = nullptr;     // [3 axes][3 taps][n]
+  double* cw = nullptr;     // [3 axes][4 cells][n] G^T-weighted face taps along
+                            // the component's own axis: (w_{a-1} - w_a) / h
   // cell-sorted (marker, slot) list for the atomic-free gathers
   int64_t n_entries = 0, entries_cap = 0;
   int32_t* entry_key = nullptr;   // marker * 64 + slot, sorted within a cell
-  double* entry_coef = nullptr;   // [3][n_entries] G^T R coefficients
+  // the same entries re-laid out for the B^T t gather: shell cells in groups
+  // of 32 (one warp), group w padded to its longest segment L_w and stored
+  // interleaved, entry p of lane l at ell_base[w] + 32 p + l
+  int64_t n_ell = 0, ell_cap = 0;
+  int32_t* ell_key = nullptr;
+  double* ell_coef = nullptr;     // [3][n_ell] G^T R coefficients (0 on padding)
+  int32_t* ell_base = nullptr;    // [n_groups + 1]
+  int32_t* ell_len = nullptr;     // [n_groups]
   int64_t n_shell = 0;
   int32_t* shell_cell = nullptr;  // [n_shell] cells touched by any marker
   int32_t* shell_off = nullptr;   // [n_shell + 1] segment offsets
@@ -103,8 +112,9 @@ struct ibm_ctx {
   float* g3 = nullptr;
   float* g4 = nullptr;
   double* red_part = nullptr;      // [kRedBlocks][kMaxRestart + 2] partials
-  double* red_out = nullptr;       // [kMaxRestart + 2] reduced values
+  double* red_out = nullptr;       // [8][kMaxRestart + 2] reduced values
   double* host_red = nullptr;      // pinned mirror of red_out
+  double* helm_part = nullptr;     // per-block partials of the predictor norm
 
   // Krylov bases
   double* V = nullptr;             // [(kMaxRestart + 1)][m]
@@ -162,12 +172,22 @@ void launch_grad_axpy(Dims d, const double* u_in, const double* p, double alpha,
 void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c,
                         double beta, double* out, cudaStream_t s);
 // predictor helpers
-void launch_helm_apply(Dims d, const double* u, double a, double nu_h2,
-                       const double* rhs, double* res, cudaStream_t s);
-void launch_helm_cheb(Dims d, const float* e, const float* e_old, const float* r,
-                      float a, float nu_h2, float alpha, float beta, float* e_new,
-                      int first, cudaStream_t s);
+// res = rhs - A u (FP64) with per-block sums of res^2 in part[b * stride];
+// returns the number of blocks (partials)
+int64_t launch_helm_residual(Dims d, const double* u, double a, double nu_h2,
+                             const double* rhs, double* res, double* part, int stride,
+                             cudaStream_t s);
+// number of floats of the predictor's padded FP32 face layout
+int64_t helm_fp32_size(Dims d);
+// one FP32 Chebyshev step of the predictor (see k_helm_cheb_v4)
+void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, const double* r64,
+                      double rs, float a, float nu_h2, float alpha, float beta, float* en,
+                      double* u, double us, int mode, cudaStream_t s);
 void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s);
+// predictor RHS with the convective term of u_n fused in (with_adv != 0)
+void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,
+                              const double* p_n, const double* f_body, int with_adv,
+                              double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
 void launch_predictor_rhs(Dims d, const double* u_n, const double* u_nm1,
                           const double* p_n, const double* f_body, const double* adv,
                           double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
@@ -185,8 +205,10 @@ void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double
 
 // ---- reductions and vector kernels (krylov.cu) ----
 // red_out[q] = <w, V_q>, q < nq (two-stage, fixed order)
+// (with div != null also quot[q] = out[q] / div[q])
 void launch_multidot(const double* w, const double* V, int64_t ld, int nq, int64_t n,
-                     double* part, double* out, cudaStream_t s);
+                     double* part, double* out, cudaStream_t s, const double* div = nullptr,
+                     double* quot = nullptr);
 // w -= sum_q coef[q] V_q  (coef on device), out = ||w||^2 (two-stage)
 void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const double* coef,
                       int64_t n, double* part, double* out, cudaStream_t s);
@@ -198,6 +220,8 @@ void launch_axpby(const double* x, double a, const double* y, double b, double* 
                   int64_t n, cudaStream_t s);
 void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const double* y,
                      int64_t n, cudaStream_t s);
+// out[0] = sum of part[b * (kMaxRestart + 2)], b < nb (fixed order)
+void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s);
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s);
 void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
                            cudaStream_t s);
@@ -213,8 +237,9 @@ ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, 
 
 // ---- solver (krylov.cu) ----
 ibm_status schur_apply(ibm_ctx* c, const double* v, double* out);
+// x_is_zero: the initial guess in x is known to be 0 (skips one S~ product)
 ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
-                        ibm_solve_stats* st);
+                        ibm_solve_stats* st, bool x_is_zero = false);
 
 // Counts one kernel launch (process-wide counter, ibm_kernel_launches).
 void count_launch();

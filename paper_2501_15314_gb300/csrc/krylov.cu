@@ -87,9 +87,12 @@ __global__ void __launch_bounds__(RT) k_axpy_norm(double* __restrict__ w,
   block_reduce_store<1>(acc, 1, part);
 }
 
-// out[q] = sum_b part[b][q], fixed-order tree (one block per q)
+// out[q] = sum_b part[b][q], fixed-order tree (one block per q); with div
+// != null also quot[q] = out[q] / div[q]
 __global__ void __launch_bounds__(RT) k_final_reduce(const double* __restrict__ part, int nb,
-                                                     double* __restrict__ out) {
+                                                     double* __restrict__ out,
+                                                     const double* __restrict__ div = nullptr,
+                                                     double* __restrict__ quot = nullptr) {
   const int q = blockIdx.x;
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * kOutStride + q];
@@ -101,6 +104,7 @@ __global__ void __launch_bounds__(RT) k_final_reduce(const double* __restrict__ 
     double t = 0.0;
     for (int w = 0; w < RT / 32; ++w) t += sh[w];
     out[q] = t;
+    if (div) quot[q] = t / div[q];
   }
 }
 
@@ -177,10 +181,11 @@ __global__ void k_add_scalar(double* __restrict__ x, int64_t n, const double* __
 }  // namespace
 
 void launch_multidot(const double* w, const double* V, int64_t ld, int nq, int64_t n,
-                     double* part, double* out, cudaStream_t s) {
+                     double* part, double* out, cudaStream_t s, const double* div,
+                     double* quot) {
   IBM_NQ_DISPATCH(nq, k_multidot, w, V, ld, nq, n, part);
   count_launch();
-  k_final_reduce<<<nq, RT, 0, s>>>(part, kRedBlocks, out);
+  k_final_reduce<<<nq, RT, 0, s>>>(part, kRedBlocks, out, div, quot);
 }
 
 void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const double* coef,
@@ -188,6 +193,11 @@ void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const doub
   IBM_NQ_DISPATCH(nq, k_axpy_norm, w, V, ld, nq, coef, n, part);
   count_launch();
   k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out);
+}
+
+void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s) {
+  count_launch();
+  k_final_reduce<<<1, RT, 0, s>>>(part, nb, out);
 }
 
 void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out,
@@ -256,22 +266,31 @@ ibm_status fetch(ibm_ctx* c, const double* dev, int n) {
 }  // namespace
 
 ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
-                        ibm_solve_stats* st) {
+                        ibm_solve_stats* st, bool x_is_zero) {
+  // The Arnoldi vectors are kept unnormalised: V_i with ||V_i||^2 = nrm2[i] on
+  // the device.  The preconditioner is applied to V_j as stored (flexible
+  // GMRES accepts any z_j; x = Z y uses the same z_j), the Gram-Schmidt
+  // coefficients are <w, V_i> / nrm2[i] (formed on the device), and the
+  // Hessenberg entries h_ij = <w, V_i> / ||V_i||, h_{j+1,j} = ||w|| on the host.
   cudaStream_t s = c->stream;
   const int64_t m = c->m;
   const int restart = o->restart;
   double* part = c->red_part;
-  double* hdev = c->red_out;                    // h column (and norm^2 at [j+1])
-  double* hdev2 = c->red_out + kOutStride;      // second Gram-Schmidt pass
-  double* ydev = c->red_out + 2 * kOutStride;   // solution coefficients
-  double* sdev = c->red_out + 3 * kOutStride;   // scalars
+  double* raw = c->red_out;                      // <w, V_i>
+  double* coef = c->red_out + kOutStride;        // <w, V_i> / nrm2[i]
+  double* raw2 = c->red_out + 2 * kOutStride;    // second Gram-Schmidt pass
+  double* coef2 = c->red_out + 3 * kOutStride;
+  double* nrm2 = c->red_out + 4 * kOutStride;    // ||V_i||^2
+  double* ydev = c->red_out + 5 * kOutStride;    // solution coefficients
+  double* sdev = c->red_out + 6 * kOutStride;    // scalars
+  double* hr = c->host_red;                      // host mirror (same offsets)
   ibm_status stt;
 
   // ||b||
   launch_dot(b, b, m, part, sdev, s);
   IBM_LAUNCH_CHECK(c);
   if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
-  const double bnorm = std::sqrt(c->host_red[0]);
+  const double bnorm = std::sqrt(hr[0]);
   if (!std::isfinite(bnorm)) return set_err(c, IBM_ERR_NAN, "non-finite right-hand side");
   int total = 0, cycles = 0;
   double relres = 0.0;
@@ -281,25 +300,34 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
     return IBM_OK;
   }
   std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart),
-      g(restart + 1), y(restart);
+      g(restart + 1), y(restart), rn(restart + 1);
   auto Hm = [&](int i, int j) -> double& { return H[(size_t)i * restart + j]; };
   double* V = c->V;
   double* Z = c->Z;
   bool converged = false;
   ibm_status final_status = IBM_OK;
+  bool first = true;
   while (true) {
-    // r0 = b - S x  into V_0
-    if ((stt = schur_apply(c, x, V)) != IBM_OK) return stt;
-    launch_axpby(b, 1.0, V, -1.0, V, m, s);
-    launch_dot(V, V, m, part, sdev, s);
-    IBM_LAUNCH_CHECK(c);
-    if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
-    const double beta = std::sqrt(c->host_red[0]);
+    // V_0 = r0 = b - S x, nrm2[0] = ||r0||^2 (r0 = b for a zero first guess)
+    double beta;
+    if (first && x_is_zero) {
+      IBM_CUDA(c, cudaMemcpyAsync(V, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+      IBM_CUDA(c, cudaMemcpyAsync(nrm2, sdev, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      beta = bnorm;
+    } else {
+      if ((stt = schur_apply(c, x, V)) != IBM_OK) return stt;
+      launch_axpby(b, 1.0, V, -1.0, V, m, s);
+      launch_dot(V, V, m, part, nrm2, s);
+      IBM_LAUNCH_CHECK(c);
+      if ((stt = fetch(c, nrm2, 1)) != IBM_OK) return stt;
+      beta = std::sqrt(hr[0]);
+    }
+    first = false;
     if (!std::isfinite(beta)) return set_err(c, IBM_ERR_NAN, "non-finite residual");
     relres = beta / bnorm;
     if (relres <= o->rtol) { converged = true; break; }
     if (total >= o->maxit) break;
-    launch_scale(V, m, nullptr, 1.0 / beta, s);
+    rn[0] = beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jused = 0;
@@ -314,28 +342,29 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
       prof_end(c, ph);
       if ((stt = schur_apply(c, zj, w)) != IBM_OK) return stt;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
-      launch_multidot(w, V, m, j + 1, m, part, hdev, s);
+      launch_multidot(w, V, m, j + 1, m, part, raw, s, nrm2, coef);
       prof_end(c, ph);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
-      launch_axpy_norm(w, V, m, j + 1, hdev, m, part, hdev + j + 1, s);
+      launch_axpy_norm(w, V, m, j + 1, coef, m, part, nrm2 + j + 1, s);
       prof_end(c, ph);
       if (o->reorth) {
-        launch_multidot(w, V, m, j + 1, m, part, hdev2, s);
-        launch_axpy_norm(w, V, m, j + 1, hdev2, m, part, hdev + j + 1, s);
+        launch_multidot(w, V, m, j + 1, m, part, raw2, s, nrm2, coef2);
+        launch_axpy_norm(w, V, m, j + 1, coef2, m, part, nrm2 + j + 1, s);
       }
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaMemcpyAsync(c->host_red, hdev, sizeof(double) * (j + 2),
+      IBM_CUDA(c, cudaMemcpyAsync(hr, raw, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+      IBM_CUDA(c, cudaMemcpyAsync(hr + 4 * kOutStride + j + 1, nrm2 + j + 1, sizeof(double),
                                   cudaMemcpyDeviceToHost, s));
       if (o->reorth)
-        IBM_CUDA(c, cudaMemcpyAsync(c->host_red + kOutStride, hdev2, sizeof(double) * (j + 1),
+        IBM_CUDA(c, cudaMemcpyAsync(hr + 2 * kOutStride, raw2, sizeof(double) * (j + 1),
                                     cudaMemcpyDeviceToHost, s));
       IBM_CUDA(c, cudaStreamSynchronize(s));
       for (int i = 0; i <= j; ++i)
-        Hm(i, j) = c->host_red[i] + (o->reorth ? c->host_red[kOutStride + i] : 0.0);
-      const double hn = std::sqrt(c->host_red[j + 1]);
+        Hm(i, j) = (hr[i] + (o->reorth ? hr[2 * kOutStride + i] : 0.0)) / rn[i];
+      const double hn = std::sqrt(hr[4 * kOutStride + j + 1]);
       if (!std::isfinite(hn)) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
       Hm(j + 1, j) = hn;
-      if (hn > 0.0) launch_scale(w, m, nullptr, 1.0 / hn, s);
+      rn[j + 1] = hn;
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
         Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
@@ -360,9 +389,9 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
         for (int q = i + 1; q < jused; ++q) acc -= Hm(i, q) * y[q];
         y[i] = acc / Hm(i, i);
       }
-      IBM_CUDA(c, cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jused, cudaMemcpyHostToDevice,
-                                  s));
-      IBM_CUDA(c, cudaStreamSynchronize(s));   // y is a stack buffer
+      double* hy = hr + 5 * kOutStride;
+      for (int i = 0; i < jused; ++i) hy[i] = y[i];
+      IBM_CUDA(c, cudaMemcpyAsync(ydev, hy, sizeof(double) * jused, cudaMemcpyHostToDevice, s));
       launch_gemv_acc(x, Z, m, jused, ydev, m, s);
       IBM_LAUNCH_CHECK(c);
     }

@@ -39,13 +39,14 @@ struct MkView {
   const int32_t* org;
   const double* wf;
   const double* wc;
+  const double* cw;
 };
 
-MkView view(const MarkerData& m) { return MkView{m.n, m.bf, m.bc, m.org, m.wf, m.wc}; }
+MkView view(const MarkerData& m) { return MkView{m.n, m.bf, m.bc, m.org, m.wf, m.wc, m.cw}; }
 
 __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __restrict__ X,
                                int32_t* bf, int32_t* bc, int32_t* org, double* wf, double* wc,
-                               int32_t* err) {
+                               double* cw, int32_t* err) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int ncell[3] = {d.nx, d.ny, d.nz};
@@ -60,6 +61,7 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
       bad = true;
       bf[e * n + k] = 1; bc[e * n + k] = 0; org[e * n + k] = 0;
       for (int q = 0; q < 3; ++q) { wf[(e * 3 + q) * n + k] = 0.0; wc[(e * 3 + q) * n + k] = 0.0; }
+      for (int q = 0; q < 4; ++q) cw[(e * 4 + q) * n + k] = 0.0;
       continue;
     }
     const int b_f = (int)fs - 1;   // face taps b_f .. b_f+2 at positions i h
@@ -69,11 +71,18 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
     bf[e * n + k] = b_f;
     bc[e * n + k] = b_c;
     org[e * n + k] = min(b_f - 1, b_c);
+    double W[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      wf[(e * 3 + q) * n + k] = roma_phi((double)(b_f + q) - s);
+      W[q] = roma_phi((double)(b_f + q) - s);
+      wf[(e * 3 + q) * n + k] = W[q];
       wc[(e * 3 + q) * n + k] = roma_phi((double)(b_c + q) + 0.5 - s);
     }
+    // cell b_f - 1 + q lies between faces b_f - 1 + q and b_f + q
+    cw[(e * 4 + 0) * n + k] = (0.0 - W[0]) * inv_h;
+    cw[(e * 4 + 1) * n + k] = (W[0] - W[1]) * inv_h;
+    cw[(e * 4 + 2) * n + k] = (W[1] - W[2]) * inv_h;
+    cw[(e * 4 + 3) * n + k] = (W[2] - 0.0) * inv_h;
   }
   if (bad) atomicOr(err, 1);
 }
@@ -136,19 +145,16 @@ __global__ void k_sort_segments(int64_t n_shell, const int32_t* __restrict__ off
   }
 }
 
-// Coefficient of G^T R e_{k,d} at global cell (g0, g1, g2).  Along d the cell
-// weight is (w_i - w_{i+1})/h with w the face-tap weights (cell i lies between
-// faces i and i+1); along the other axes it is the centre-tap weight.
-__device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcomp, const int g[3],
-                                           double inv_h) {
+// Coefficient of G^T R e_{k,d} at global cell g: along d the G^T-weighted
+// face taps cw (cell i lies between faces i and i+1), along the other two
+// axes the centre-tap weights; zero outside the 4 x 3 x 3 footprint.
+__device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcomp, const int g[3]) {
   double c = 1.0;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     if (e == dcomp) {
-      const int q = g[e] - mk.bf[e * mk.n + k];   // face index i - b_f, cell i
-      const double wi = (q >= 0 && q <= 2) ? mk.wf[(e * 3 + q) * mk.n + k] : 0.0;
-      const double wn = (q + 1 >= 0 && q + 1 <= 2) ? mk.wf[(e * 3 + q + 1) * mk.n + k] : 0.0;
-      c *= (wi - wn) * inv_h;
+      const int q = g[e] - (mk.bf[e * mk.n + k] - 1);
+      c *= (q >= 0 && q <= 3) ? mk.cw[(e * 4 + q) * mk.n + k] : 0.0;
     } else {
       const int q = g[e] - mk.bc[e * mk.n + k];
       c *= (q >= 0 && q <= 2) ? mk.wc[(e * 3 + q) * mk.n + k] : 0.0;
@@ -157,61 +163,112 @@ __device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcom
   return c;
 }
 
-__global__ void k_entry_coef(Dims d, MkView mk, int64_t n_entries, const int32_t* __restrict__ key,
-                             double inv_h, double* coef) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_entries) return;
-  const int32_t kk = key[t];
-  const int64_t k = kk >> 6;
-  const int s = kk & 63;
-  const int g[3] = {mk.org[k] + (s & 3), mk.org[mk.n + k] + ((s >> 2) & 3),
-                    mk.org[2 * mk.n + k] + (s >> 4)};
-#pragma unroll
-  for (int dc = 0; dc < 3; ++dc) coef[dc * n_entries + t] = gtr_coef(mk, k, dc, g, inv_h);
-}
-
-// t[d][k] = scale * sum_cells gtr_coef * v  (= scale * (R^T G v)_{k,d}).  One
-// thread per (marker, component); the coefficients are the same products as
-// the stored entry coefficients, so B and B^T are exact transposes.
+// t[d][k] = scale * (R^T G v)_{k,d} using the tensor-product form of the
+// footprint: sum_a cw_d[a] sum_b w_e1[b] sum_c w_e2[c] v.  Four consecutive
+// threads hold a = 0..3 of one (marker, component) and combine in a fixed
+// order with warp shuffles.
 __global__ void k_marker_grad_interp(Dims d, MkView mk, const double* __restrict__ v,
-                                     double inv_h, double scale, double* __restrict__ t) {
+                                     double scale, double* __restrict__ t) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= 3 * mk.n) return;
-  const int dc = (int)(tid / mk.n);
-  const int64_t k = tid - dc * mk.n;
-  // stencil extent: 4 cells along dc starting at b_f - 1, 3 cells elsewhere
-  int lo[3], len[3];
+  const int64_t nt = 12 * mk.n;
+  double part = 0.0;
+  int dc = 0;
+  int64_t k = 0;
+  if (tid < nt) {
+    const int64_t pk = tid >> 2;
+    const int a = (int)(tid & 3);
+    dc = (int)(pk / mk.n);
+    k = pk - dc * mk.n;
+    const int e1 = dc == 0 ? 1 : 0;
+    const int e2 = dc == 2 ? 1 : 2;
+    int g[3];
+    g[dc] = mk.bf[dc * mk.n + k] - 1 + a;
+    const int b1 = mk.bc[e1 * mk.n + k], b2 = mk.bc[e2 * mk.n + k];
+    const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+    double acc1 = 0.0;
 #pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    if (e == dc) { lo[e] = mk.bf[e * mk.n + k] - 1; len[e] = 4; }
-    else { lo[e] = mk.bc[e * mk.n + k]; len[e] = 3; }
-  }
-  double acc = 0.0;
-  for (int c2 = 0; c2 < len[2]; ++c2)
-    for (int c1 = 0; c1 < len[1]; ++c1)
-      for (int c0 = 0; c0 < len[0]; ++c0) {
-        const int g[3] = {lo[0] + c0, lo[1] + c1, lo[2] + c2};
-        const double cf = gtr_coef(mk, k, dc, g, inv_h);
-        acc = fma(cf, __ldg(v + cell_of(d, g[0], g[1], g[2])), acc);
+    for (int q1 = 0; q1 < 3; ++q1) {
+      g[e1] = b1 + q1;
+      double acc2 = 0.0;
+#pragma unroll
+      for (int q2 = 0; q2 < 3; ++q2) {
+        g[e2] = b2 + q2;
+        const int64_t cell = g[0] + g[1] * sy + (int64_t)g[2] * sz;
+        acc2 = fma(mk.wc[(e2 * 3 + q2) * mk.n + k], __ldg(v + cell), acc2);
       }
-  t[dc * mk.n + k] = scale * acc;
+      acc1 = fma(mk.wc[(e1 * 3 + q1) * mk.n + k], acc2, acc1);
+    }
+    part = mk.cw[(dc * 4 + a) * mk.n + k] * acc1;
+  }
+  const int lane = threadIdx.x & 31;
+  const int base = lane & ~3;
+  const double p0 = __shfl_sync(0xffffffffu, part, base);
+  const double p1 = __shfl_sync(0xffffffffu, part, base + 1);
+  const double p2 = __shfl_sync(0xffffffffu, part, base + 2);
+  const double p3 = __shfl_sync(0xffffffffu, part, base + 3);
+  if (tid < nt && (lane & 3) == 0) t[dc * mk.n + k] = scale * ((p0 + p1) + (p2 + p3));
 }
 
-// out[c] += scale * sum_{entries of c} sum_d coef_d t[d][k]   (shell cells)
-__global__ void k_shell_gradt(int64_t n_shell, const int32_t* __restrict__ shell_cell,
-                              const int32_t* __restrict__ off, const int32_t* __restrict__ key,
-                              const double* __restrict__ coef, int64_t n_entries, int64_t nmk,
-                              const double* __restrict__ t, double scale,
-                              double* __restrict__ out) {
+// Group lengths of the interleaved layout: len[w] = longest segment among the
+// 32 shell cells of group w, cnt[w] = 32 * len[w].
+__global__ void k_ell_len(int64_t n_shell, const int32_t* __restrict__ off, int32_t* len,
+                          int32_t* cnt) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ng = (n_shell + 31) / 32;
+  if (w >= ng) return;
+  int32_t L = 0;
+  for (int64_t q = 32 * w; q < min(32 * w + 32, n_shell); ++q) L = max(L, off[q + 1] - off[q]);
+  len[w] = L;
+  cnt[w] = 32 * L;
+}
+
+// Fills the interleaved layout with keys and G^T R coefficients (zero padding).
+__global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict__ off,
+                           const int32_t* __restrict__ key, const int32_t* __restrict__ base,
+                           const int32_t* __restrict__ len, const int32_t* __restrict__ shell_cell,
+                           Dims d, int64_t n_ell, int32_t* ekey, double* ecoef) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n_shell) return;
-  const int32_t a = off[q], b = off[q + 1];
+  const int64_t w = q >> 5;
+  const int lane = (int)(q & 31);
+  const int32_t a = off[q], nseg = off[q + 1] - a, L = len[w];
+  const int64_t c = shell_cell[q];
+  const int g[3] = {(int)(c % d.nx), (int)((c / d.nx) % d.ny), (int)(c / ((int64_t)d.nx * d.ny))};
+  for (int p = 0; p < L; ++p) {
+    const int64_t dst = base[w] + (int64_t)p * 32 + lane;
+    if (p < nseg) {
+      const int32_t kk = key[a + p];
+      ekey[dst] = kk;
+      const int64_t k = kk >> 6;
+#pragma unroll
+      for (int dc = 0; dc < 3; ++dc) ecoef[dc * n_ell + dst] = gtr_coef(mk, k, dc, g);
+    } else {
+      ekey[dst] = 0;
+#pragma unroll
+      for (int dc = 0; dc < 3; ++dc) ecoef[dc * n_ell + dst] = 0.0;
+    }
+  }
+}
+
+// out[c] += scale * sum over the entries of shell cell c (in marker order) of
+// sum_d coef_d t[d][k]; coalesced loads through the interleaved layout.
+__global__ void k_shell_gradt(int64_t n_shell, const int32_t* __restrict__ shell_cell,
+                              const int32_t* __restrict__ base, const int32_t* __restrict__ len,
+                              const int32_t* __restrict__ ekey, const double* __restrict__ ecoef,
+                              int64_t n_ell, int64_t nmk, const double* __restrict__ t,
+                              double scale, double* __restrict__ out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n_shell) return;
+  const int64_t w = q >> 5;
+  const int lane = (int)(q & 31);
+  const int32_t L = len[w];
+  int64_t idx = base[w] + lane;
   double acc = 0.0;
-  for (int32_t x = a; x < b; ++x) {
-    const int64_t k = key[x] >> 6;
-    acc = fma(coef[x], t[k], acc);
-    acc = fma(coef[n_entries + x], t[nmk + k], acc);
-    acc = fma(coef[2 * n_entries + x], t[2 * nmk + k], acc);
+  for (int p = 0; p < L; ++p, idx += 32) {
+    const int64_t k = ekey[idx] >> 6;
+    acc = fma(ecoef[idx], t[k], acc);
+    acc = fma(ecoef[n_ell + idx], t[nmk + k], acc);
+    acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
   }
   const int64_t c = shell_cell[q];
   out[c] = fma(scale, acc, out[c]);
@@ -399,12 +456,13 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
   MarkerData& m = c->mk;
   if (n <= m.cap) return IBM_OK;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
-  cudaFree(m.t); cudaFree(m.t2);
-  m.bf = m.bc = m.org = nullptr; m.wf = m.wc = m.t = m.t2 = nullptr; m.cap = 0;
+  cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2);
+  m.bf = m.bc = m.org = nullptr; m.wf = m.wc = m.cw = m.t = m.t2 = nullptr; m.cap = 0;
   const size_t ni = sizeof(int32_t) * 3 * n, nd = sizeof(double) * 9 * n;
   if (cudaMalloc(&m.bf, ni) != cudaSuccess || cudaMalloc(&m.bc, ni) != cudaSuccess ||
       cudaMalloc(&m.org, ni) != cudaSuccess || cudaMalloc(&m.wf, nd) != cudaSuccess ||
       cudaMalloc(&m.wc, nd) != cudaSuccess ||
+      cudaMalloc(&m.cw, sizeof(double) * 12 * n) != cudaSuccess ||
       cudaMalloc(&m.t, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess) {
     cudaGetLastError();
@@ -418,18 +476,39 @@ static ibm_status grow_entries(ibm_ctx* c, int64_t ne) {
   // shell cells never outnumber entries (each shell cell holds >= 1 entry)
   MarkerData& m = c->mk;
   if (ne <= m.entries_cap && m.entry_key) return IBM_OK;
-  cudaFree(m.entry_key); cudaFree(m.entry_coef); cudaFree(m.shell_cell); cudaFree(m.shell_off);
-  m.entry_key = nullptr; m.entry_coef = nullptr; m.shell_cell = nullptr; m.shell_off = nullptr;
+  cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_base);
+  cudaFree(m.ell_len);
+  m.entry_key = nullptr; m.shell_cell = nullptr; m.shell_off = nullptr; m.ell_base = nullptr;
+  m.ell_len = nullptr;
   m.entries_cap = 0;
   const int64_t cap = ne > 0 ? ne : 1;
   if (cudaMalloc(&m.entry_key, sizeof(int32_t) * cap) != cudaSuccess ||
-      cudaMalloc(&m.entry_coef, sizeof(double) * 3 * cap) != cudaSuccess ||
+      cudaMalloc(&m.ell_base, sizeof(int32_t) * (cap / 32 + 2)) != cudaSuccess ||
+      cudaMalloc(&m.ell_len, sizeof(int32_t) * (cap / 32 + 2)) != cudaSuccess ||
       cudaMalloc(&m.shell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.shell_off, sizeof(int32_t) * (cap + 1)) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, IBM_ERR_NOMEM, "marker entry list allocation failed");
   }
   m.entries_cap = cap;
+  return IBM_OK;
+}
+
+static ibm_status grow_ell(ibm_ctx* c, int64_t n_ell) {
+  MarkerData& m = c->mk;
+  if (n_ell <= m.ell_cap && m.ell_key) return IBM_OK;
+  cudaFree(m.ell_key);
+  cudaFree(m.ell_coef);
+  m.ell_key = nullptr;
+  m.ell_coef = nullptr;
+  m.ell_cap = 0;
+  const int64_t cap = n_ell > 0 ? n_ell : 1;
+  if (cudaMalloc(&m.ell_key, sizeof(int32_t) * cap) != cudaSuccess ||
+      cudaMalloc(&m.ell_coef, sizeof(double) * 3 * cap) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, IBM_ERR_NOMEM, "marker gather layout allocation failed");
+  }
+  m.ell_cap = cap;
   return IBM_OK;
 }
 
@@ -449,7 +528,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   IBM_CUDA(c, cudaMemsetAsync(c->dev_flag, 0, sizeof(int32_t), s));
   count_launch();
   k_marker_setup<<<div_up(n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org, m.wf,
-                                                 m.wc, c->dev_flag);
+                                                 m.wc, m.cw, c->dev_flag);
   IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->dev_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   IBM_CUDA(c, cudaStreamSynchronize(s));
@@ -496,10 +575,26 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   IBM_LAUNCH_CHECK(c);
   count_launch();
   k_sort_segments<<<div_up(ns, TPB), TPB, 0, s>>>(ns, m.shell_off, m.entry_key);
-  count_launch();
-  k_entry_coef<<<div_up(ne, TPB), TPB, 0, s>>>(c->d, mv, ne, m.entry_key, 1.0 / c->h,
-                                               m.entry_coef);
   IBM_LAUNCH_CHECK(c);
+  // interleaved layout for the B^T t gather
+  const int64_t ng = (ns + 31) / 32;
+  int32_t* cnt = c->cell_count;   // free again: reused for the group sizes
+  count_launch();
+  k_ell_len<<<div_up(ng, TPB), TPB, 0, s>>>(ns, m.shell_off, m.ell_len, cnt);
+  IBM_LAUNCH_CHECK(c);
+  st = exclusive_scan(c, cnt, m.ell_base, ng);
+  if (st != IBM_OK) return st;
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, m.ell_base + ng, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, s));
+  IBM_CUDA(c, cudaStreamSynchronize(s));
+  const int64_t n_ell = c->host_flag[0];
+  if ((st = grow_ell(c, n_ell)) != IBM_OK) return st;
+  count_launch();
+  k_ell_fill<<<div_up(ns, TPB), TPB, 0, s>>>(mv, ns, m.shell_off, m.entry_key, m.ell_base,
+                                             m.ell_len, m.shell_cell, c->d, n_ell, m.ell_key,
+                                             m.ell_coef);
+  IBM_LAUNCH_CHECK(c);
+  m.n_ell = n_ell;
   m.n_entries = ne;
   m.n_shell = ns;
   c->markers_set = true;
@@ -510,8 +605,7 @@ void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
-  k_marker_grad_interp<<<div_up(3 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v, 1.0 / c->h,
-                                                                     scale, t);
+  k_marker_grad_interp<<<div_up(12 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v, scale, t);
 }
 
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out) {
@@ -519,8 +613,8 @@ void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double
   if (m.n == 0 || m.n_shell == 0) return;
   count_launch();
   k_shell_gradt<<<div_up(m.n_shell, TPB), TPB, 0, c->stream>>>(
-      m.n_shell, m.shell_cell, m.shell_off, m.entry_key, m.entry_coef, m.n_entries, m.n, t, scale,
-      out);
+      m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
+      scale, out);
 }
 
 void launch_interp(ibm_ctx* c, const double* u, double* U) {

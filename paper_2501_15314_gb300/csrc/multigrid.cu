@@ -11,7 +11,9 @@
 // pseudo-inverse on the coarsest level (<= 512 cells).  Templates cover the
 // FP32 (mixed) and FP64 forms; only the inputs/outputs at the finest level are
 // FP64 in the mixed form.
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "ibm_internal.cuh"
@@ -23,7 +25,6 @@ namespace {
 constexpr int BX = 32, BY = 8;
 constexpr double kChebLo = 0.3, kChebHi = 2.0;
 
-dim3 grid3(Dims d) { return dim3(div_up(d.nx, BX), div_up(d.ny, BY), d.nz); }
 
 // Chebyshev-Richardson weights 1/lambda_i, lambda_i the roots of the degree-p
 // Chebyshev polynomial mapped to [lo, hi].
@@ -35,105 +36,568 @@ void cheb_weights(int p, double* w) {
   }
 }
 
-// Neighbour sum and count of the Neumann 7-point stencil at cell (i, j, k).
+// All level kernels march along z: a block of 32 x 8 threads owns a 32 x 8
+// column of cells over ZC consecutive planes, each thread keeps the planes
+// below, at and above its cell in registers, and the in-plane neighbours come
+// through L1.  One DRAM read per input array per cell, with several planes'
+// loads in flight per thread.
+constexpr int ZC = 16;
+
+dim3 zm_grid(Dims d) { return dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, ZC)); }
+
+// w / nn for nn = 0..6 (nn = number of existing neighbours of a cell).
 template <typename T>
-__device__ __forceinline__ T nb_sum(Dims d, const T* __restrict__ x, int64_t c, int i, int j, int k,
-                                    int& nn) {
-  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+struct WOverN {
+  T v[7];
+};
+
+template <typename T>
+WOverN<T> w_over_n(double w) {
+  WOverN<T> r;
+  r.v[0] = (T)0;
+  for (int q = 1; q < 7; ++q) r.v[q] = (T)(w / q);
+  return r;
+}
+
+// w / nn from the table with static indices only (a dynamically indexed
+// kernel-parameter array would be copied to local memory): interior cells
+// (nn = 6) use the stored quotient, boundary cells divide.
+template <typename T>
+__device__ __forceinline__ T wn_of(const WOverN<T>& wn, int nn) {
+  return nn == 6 ? wn.v[6] : wn.v[1] / (T)nn;
+}
+
+__device__ __forceinline__ int n_inplane(Dims d, int i, int j) {
+  return (i > 0) + (i < d.nx - 1) + (j > 0) + (j < d.ny - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T inplane_sum(const T* __restrict__ p, int64_t c, int i, int j, Dims d,
+                                         int64_t sy) {
   T s = 0;
-  nn = 0;
-  if (i > 0) { s += __ldg(x + c - 1); ++nn; }
-  if (i < d.nx - 1) { s += __ldg(x + c + 1); ++nn; }
-  if (j > 0) { s += __ldg(x + c - sy); ++nn; }
-  if (j < d.ny - 1) { s += __ldg(x + c + sy); ++nn; }
-  if (k > 0) { s += __ldg(x + c - sz); ++nn; }
-  if (k < d.nz - 1) { s += __ldg(x + c + sz); ++nn; }
+  if (i > 0) s += __ldg(p + c - 1);
+  if (i < d.nx - 1) s += __ldg(p + c + 1);
+  if (j > 0) s += __ldg(p + c - sy);
+  if (j < d.ny - 1) s += __ldg(p + c + sy);
   return s;
 }
 
-// x = w D^{-1} b   (first sweep from a zero iterate)
-template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_cheb_first(Dims d, const T* __restrict__ b,
-                                                        T* __restrict__ x, T w_h2) {
+// One Chebyshev-Richardson step: xo = x + w D^{-1} (b - L x), D = nn / h^2,
+// L x = (nn x_c - sum of neighbours) / h^2.  b may be FP64 while T is FP32,
+// and the output type TO may differ from T (FP64 result of the mixed cycle).
+template <typename T, typename TB, typename TO>
+__global__ void __launch_bounds__(BX * BY) k_sweep(Dims d, const T* __restrict__ x,
+                                                   const TB* __restrict__ b, TO* __restrict__ xo,
+                                                   WOverN<T> wn, T h2) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
-  const int nn = (i > 0) + (i < d.nx - 1) + (j > 0) + (j < d.ny - 1) + (k > 0) + (k < d.nz - 1);
-  const int64_t c = ((int64_t)k * d.ny + j) * d.nx + i;
-  x[c] = w_h2 * __ldg(b + c) / (T)nn;
+  const int z0 = blockIdx.z * ZC;
+  const int z1 = min(z0 + ZC, d.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  const int nip = n_inplane(d, i, j);
+  int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i;
+  T xp = z0 > 0 ? __ldg(x + c - sz) : (T)0;
+  T xc = __ldg(x + c);
+#pragma unroll 4
+  for (int z = z0; z < z1; ++z, c += sz) {
+    const T xn = (z + 1 < d.nz) ? __ldg(x + c + sz) : (T)0;
+    const int nn = nip + (z > 0) + (z < d.nz - 1);
+    const T s = inplane_sum(x, c, i, j, d, sy) + (xp + xn);
+    const T r = fma(h2, (T)__ldg(b + c), s - (T)nn * xc);
+    xo[c] = (TO)fma(wn_of(wn, nn), r, xc);
+    xp = xc;
+    xc = xn;
+  }
 }
 
-// xo = x + w D^{-1} (b - L x),  D = nn / h^2, L x = (nn x_c - sum) / h^2
-template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_cheb_sweep(Dims d, const T* __restrict__ x,
-                                                        const T* __restrict__ b,
-                                                        T* __restrict__ xo, T w, T h2) {
+// First smoothing step(s) from a zero iterate.  x1 = w0 D^{-1} b pointwise; with
+// two != 0 also the second step xo = x1 + w1 D^{-1} (b - L x1), evaluating x1 at
+// the neighbours from b on the fly (no x1 array).  bcopy (may be null) receives
+// b rounded to T, for the later kernels of the level.
+template <typename T, typename TB>
+__global__ void __launch_bounds__(BX * BY) k_first(Dims d, const TB* __restrict__ b,
+                                                   T* __restrict__ bcopy, T* __restrict__ xo,
+                                                   WOverN<T> w0h2n, WOverN<T> w1n, T h2, int two) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
-  const int64_t c = ((int64_t)k * d.ny + j) * d.nx + i;
-  int nn;
-  const T s = nb_sum(d, x, c, i, j, k, nn);
-  const T xc = __ldg(x + c);
-  // D^{-1}(b - Lx) = (h^2 b - nn xc + s) / nn
-  const T r = fma(h2, __ldg(b + c), s - (T)nn * xc);
-  xo[c] = fma(w, r / (T)nn, xc);
+  const int z0 = blockIdx.z * ZC;
+  const int z1 = min(z0 + ZC, d.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  const int nip = n_inplane(d, i, j);
+  int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i;
+  if (!two) {
+    for (int z = z0; z < z1; ++z, c += sz) {
+      const T bv = (T)__ldg(b + c);
+      if (bcopy) bcopy[c] = bv;
+      xo[c] = wn_of(w0h2n, nip + (z > 0) + (z < d.nz - 1)) * bv;
+    }
+    return;
+  }
+  // in-plane neighbour counts of the four in-plane neighbours
+  const int nxm = i > 0 ? n_inplane(d, i - 1, j) : 0;
+  const int nxp = i < d.nx - 1 ? n_inplane(d, i + 1, j) : 0;
+  const int nym = j > 0 ? n_inplane(d, i, j - 1) : 0;
+  const int nyp = j < d.ny - 1 ? n_inplane(d, i, j + 1) : 0;
+  auto nzc = [&](int z) { return (z > 0) + (z < d.nz - 1); };
+  // x1 below / at / above, carried along z
+  T x1p = z0 > 0 ? wn_of(w0h2n, nip + nzc(z0 - 1)) * (T)__ldg(b + c - sz) : (T)0;
+  T bcv = (T)__ldg(b + c);
+  T x1c = wn_of(w0h2n, nip + nzc(z0)) * bcv;
+#pragma unroll 2
+  for (int z = z0; z < z1; ++z, c += sz) {
+    T bnv = 0, x1n = 0;
+    if (z + 1 < d.nz) {
+      bnv = (T)__ldg(b + c + sz);
+      x1n = wn_of(w0h2n, nip + nzc(z + 1)) * bnv;
+    }
+    const int zc = nzc(z);
+    T s = x1p + x1n;
+    if (i > 0) s += wn_of(w0h2n, nxm + zc) * (T)__ldg(b + c - 1);
+    if (i < d.nx - 1) s += wn_of(w0h2n, nxp + zc) * (T)__ldg(b + c + 1);
+    if (j > 0) s += wn_of(w0h2n, nym + zc) * (T)__ldg(b + c - sy);
+    if (j < d.ny - 1) s += wn_of(w0h2n, nyp + zc) * (T)__ldg(b + c + sy);
+    const int nn = nip + zc;
+    if (bcopy) bcopy[c] = bcv;
+    const T r = fma(h2, bcv, s - (T)nn * x1c);
+    xo[c] = fma(wn_of(w1n, nn), r, x1c);
+    x1p = x1c;
+    x1c = x1n;
+    bcv = bnv;
+  }
 }
 
-// bc = average over the 8 children of (b - L x); x == nullptr means x = 0.
+// Residual restriction: bcoarse = average over the 8 children of (b - L x);
+// x == nullptr means x = 0.  One thread per coarse cell; the children are read
+// in x-pairs (2I, 2I+1).
 template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_resid_restrict(Dims d, Dims dc,
-                                                            const T* __restrict__ x,
-                                                            const T* __restrict__ b,
-                                                            T* __restrict__ bcoarse, T inv_h2) {
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
+  const typename Pair<T>::type v = __ldg(reinterpret_cast<const typename Pair<T>::type*>(p));
+  a = v.x;
+  b = v.y;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX * BY) k_restrict(Dims d, Dims dc, const T* __restrict__ x,
+                                                      const T* __restrict__ b,
+                                                      T* __restrict__ bcoarse, T inv_h2) {
   const int I = blockIdx.x * BX + threadIdx.x;
   const int J = blockIdx.y * BY + threadIdx.y;
-  const int K = blockIdx.z;
   if (I >= dc.nx || J >= dc.ny) return;
-  T acc = 0;
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  const int K0 = blockIdx.z * (ZC / 2);
+  const int K1 = min(K0 + ZC / 2, dc.nz);
+  for (int K = K0; K < K1; ++K) {
+    T acc = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
-    const int64_t c = ((int64_t)k * d.ny + j) * d.nx + i;
-    T r = __ldg(b + c);
-    if (x) {
-      int nn;
-      const T s = nb_sum(d, x, c, i, j, k, nn);
-      r -= ((T)nn * __ldg(x + c) - s) * inv_h2;
+    for (int dz = 0; dz < 2; ++dz) {
+      const int k = 2 * K + dz;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const int j = 2 * J + dy;
+        const int64_t c = (int64_t)k * sz + (int64_t)j * sy + 2 * I;
+        T b0, b1;
+        ld2(b + c, b0, b1);
+        T r0 = b0, r1 = b1;
+        if (x) {
+          T x0, x1;
+          ld2(x + c, x0, x1);
+          // neighbours of the pair
+          T s0 = x1, s1 = x0;
+          int n0 = 1, n1 = 1;
+          if (2 * I > 0) { s0 += __ldg(x + c - 1); ++n0; }
+          if (2 * I + 2 < d.nx) { s1 += __ldg(x + c + 2); ++n1; }
+          T a0, a1;
+          if (j > 0) { ld2(x + c - sy, a0, a1); s0 += a0; s1 += a1; ++n0; ++n1; }
+          if (j < d.ny - 1) { ld2(x + c + sy, a0, a1); s0 += a0; s1 += a1; ++n0; ++n1; }
+          if (k > 0) { ld2(x + c - sz, a0, a1); s0 += a0; s1 += a1; ++n0; ++n1; }
+          if (k < d.nz - 1) { ld2(x + c + sz, a0, a1); s0 += a0; s1 += a1; ++n0; ++n1; }
+          r0 -= ((T)n0 * x0 - s0) * inv_h2;
+          r1 -= ((T)n1 * x1 - s1) * inv_h2;
+        }
+        acc += r0 + r1;
+      }
     }
-    acc += r;
+    bcoarse[((int64_t)K * dc.ny + J) * dc.nx + I] = acc * (T)0.125;
   }
-  bcoarse[((int64_t)K * dc.ny + J) * dc.nx + I] = acc * (T)0.125;
 }
 
-// x += P xc  (trilinear, weights 3/4 parent and 1/4 neighbour per axis; at a
-// wall the neighbour is the parent itself).  x == nullptr-free form: if
-// overwrite != 0 then x = P xc.
+template <typename T, typename TO>
+__global__ void k_convert(const T* __restrict__ x, TO* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (TO)x[i];
+}
+
+// x (+)= P xc: trilinear, 3/4 parent and 1/4 neighbour per axis, the
+// neighbour replaced by the parent at a wall.  One thread per fine x-pair
+// (2I, 2I+1), which share the parent I; overwrite != 0 gives x = P xc.
 template <typename T>
 __global__ void __launch_bounds__(BX * BY) k_prolong(Dims d, Dims dc, const T* __restrict__ xc,
                                                      T* __restrict__ x, int overwrite) {
-  const int i = blockIdx.x * BX + threadIdx.x;
+  const int I = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= d.nx || j >= d.ny) return;
-  const int I = i >> 1, J = j >> 1, K = k >> 1;
-  const int In = (i & 1) ? min(I + 1, dc.nx - 1) : max(I - 1, 0);
+  if (I >= dc.nx || j >= d.ny) return;
+  const int z0 = blockIdx.z * ZC;
+  const int z1 = min(z0 + ZC, d.nz);
+  const int J = j >> 1;
   const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
-  const int Kn = (k & 1) ? min(K + 1, dc.nz - 1) : max(K - 1, 0);
+  const int Im = max(I - 1, 0), Ip = min(I + 1, dc.nx - 1);
   const int64_t sy = dc.nx, sz = (int64_t)dc.nx * dc.ny;
-  const T* p0 = xc + K * sz;
-  const T* p1 = xc + Kn * sz;
-  const T a00 = (T)0.75 * __ldg(p0 + J * sy + I) + (T)0.25 * __ldg(p0 + J * sy + In);
-  const T a01 = (T)0.75 * __ldg(p0 + Jn * sy + I) + (T)0.25 * __ldg(p0 + Jn * sy + In);
-  const T a10 = (T)0.75 * __ldg(p1 + J * sy + I) + (T)0.25 * __ldg(p1 + J * sy + In);
-  const T a11 = (T)0.75 * __ldg(p1 + Jn * sy + I) + (T)0.25 * __ldg(p1 + Jn * sy + In);
-  const T b0 = (T)0.75 * a00 + (T)0.25 * a01;
-  const T b1 = (T)0.75 * a10 + (T)0.25 * a11;
-  const T v = (T)0.75 * b0 + (T)0.25 * b1;
-  const int64_t c = ((int64_t)k * d.ny + j) * d.nx + i;
-  x[c] = overwrite ? v : x[c] + v;
+  for (int k = z0; k < z1; ++k) {
+    const int K = k >> 1;
+    const int Kn = (k & 1) ? min(K + 1, dc.nz - 1) : max(K - 1, 0);
+    // rows (J, K), (Jn, K), (J, Kn), (Jn, Kn); 3/4-1/4 in y and z first
+    const T* r00 = xc + K * sz + J * sy;
+    const T* r01 = xc + K * sz + Jn * sy;
+    const T* r10 = xc + Kn * sz + J * sy;
+    const T* r11 = xc + Kn * sz + Jn * sy;
+    auto yz = [&](int q) {
+      const T a = (T)0.75 * __ldg(r00 + q) + (T)0.25 * __ldg(r01 + q);
+      const T bb = (T)0.75 * __ldg(r10 + q) + (T)0.25 * __ldg(r11 + q);
+      return (T)0.75 * a + (T)0.25 * bb;
+    };
+    const T cm = yz(Im), c0 = yz(I), cp = yz(Ip);
+    const T v0 = (T)0.75 * c0 + (T)0.25 * cm;   // fine 2I   (neighbour I-1)
+    const T v1 = (T)0.75 * c0 + (T)0.25 * cp;   // fine 2I+1 (neighbour I+1)
+    const int64_t f = ((int64_t)k * d.ny + j) * d.nx + 2 * I;
+    typename Pair<T>::type* px = reinterpret_cast<typename Pair<T>::type*>(x + f);
+    typename Pair<T>::type o;
+    if (overwrite) {
+      o.x = v0;
+      o.y = v1;
+    } else {
+      o = *px;
+      o.x += v0;
+      o.y += v1;
+    }
+    *px = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 kernels for levels whose x-extent is a multiple of 4: each thread owns
+// four consecutive cells (one float4) of a row, a warp 128 cells, a block
+// 128 x VY cells over zc planes.  x-neighbours come from the adjacent lanes by
+// shuffles (scalar loads at the warp edges), z-neighbours from the registers
+// of the march, y-neighbours from L1.  16-byte loads keep enough bytes in
+// flight per SM to run near the DRAM bandwidth.
+constexpr int VY = 8;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st4(double* p, float4 v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ float4 ld4_any(const float* p) { return ld4(p); }
+__device__ __forceinline__ float4 ld4_any(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+__device__ __forceinline__ float ld1_any(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld1_any(const double* p) { return (float)__ldg(p); }
+
+// w / nn without dynamic indexing (nn in 1..6; 6 is the interior case)
+__device__ __forceinline__ float w_over(float w, int nn) {
+  return nn == 6 ? w * (1.f / 6.f) : __fdividef(w, (float)nn);
+}
+
+__device__ __forceinline__ float cheb_cell(float xc, float s, float bv, int nn, float w, float h2) {
+  return fmaf(w_over(w, nn), fmaf(h2, bv, s - (float)nn * xc), xc);
+}
+
+int vec_zc(Dims d) {
+  const int64_t bxy = (int64_t)div_up(d.nx / 4, 32) * div_up(d.ny, VY);
+  int64_t zc = (int64_t)d.nz * bxy / (152 * 4);
+  zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
+  return (int)zc;
+}
+
+dim3 vec_grid(Dims d, int zc) {
+  return dim3(div_up(d.nx / 4, 32), div_up(d.ny, VY), div_up(d.nz, zc));
+}
+
+bool vec_ok(Dims d) { return d.nx % 4 == 0; }
+
+// xo = x + w D^{-1} (b - L x) for four cells per thread.
+template <typename TO>
+__global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __restrict__ x,
+                                                      const float* __restrict__ b,
+                                                      TO* __restrict__ xo, float w, float h2,
+                                                      int zc) {
+  const int lane = threadIdx.x;
+  const int i0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * VY + threadIdx.y;
+  const bool act = i0 < d.nx && j < d.ny;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i0;
+  const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int ny_c = (j > 0) + (j < d.ny - 1);
+  const int n0 = ny_c + (i0 > 0) + 1, n3 = ny_c + 1 + (i0 + 3 < d.nx - 1);
+  const int n12 = ny_c + 2;
+  float4 xp = (act && z0 > 0) ? ld4(x + c - sz) : Z4;
+  float4 xc = act ? ld4(x + c) : Z4;
+  for (int z = z0; z < z1; ++z, c += sz) {
+    const float4 xn = (act && z + 1 < d.nz) ? ld4(x + c + sz) : Z4;
+    const float4 ym = (act && j > 0) ? ld4(x + c - sy) : Z4;
+    const float4 yp = (act && j < d.ny - 1) ? ld4(x + c + sy) : Z4;
+    const float4 bb = act ? ld4(b + c) : Z4;
+    float left = __shfl_up_sync(kFull, xc.w, 1);
+    float right = __shfl_down_sync(kFull, xc.x, 1);
+    if (lane == 0) left = (act && i0 > 0) ? __ldg(x + c - 1) : 0.f;
+    if (lane == 31) right = (act && i0 + 4 < d.nx) ? __ldg(x + c + 4) : 0.f;
+    const int zn = (z > 0) + (z < d.nz - 1);
+    float4 o;
+    o.x = cheb_cell(xc.x, (left + xc.y) + (ym.x + yp.x) + (xp.x + xn.x), bb.x, n0 + zn, w, h2);
+    o.y = cheb_cell(xc.y, (xc.x + xc.z) + (ym.y + yp.y) + (xp.y + xn.y), bb.y, n12 + zn, w, h2);
+    o.z = cheb_cell(xc.z, (xc.y + xc.w) + (ym.z + yp.z) + (xp.z + xn.z), bb.z, n12 + zn, w, h2);
+    o.w = cheb_cell(xc.w, (xc.z + right) + (ym.w + yp.w) + (xp.w + xn.w), bb.w, n3 + zn, w, h2);
+    if (act) st4(xo + c, o);
+    xp = xc;
+    xc = xn;
+  }
+}
+
+// First smoothing step(s) from a zero iterate (see k_first), four cells per
+// thread.  b may be FP64: each value is rounded once; x-neighbours move
+// between lanes by shuffles, the block's rows (and the two y-halo rows) are
+// staged as float4 in shared memory for the y-neighbours, z by the march.
+template <typename TB>
+__global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restrict__ b,
+                                                      float* __restrict__ bcopy,
+                                                      float* __restrict__ xo, float w0h2,
+                                                      float w1, float h2, int two, int zc) {
+  __shared__ float4 sb[VY + 2][32];
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int i0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * VY + ty;
+  const bool act = i0 < d.nx && j < d.ny;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i0;
+  const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int ny_c = (j > 0) + (j < d.ny - 1);
+  const int n0 = ny_c + (i0 > 0) + 1, n3 = ny_c + 1 + (i0 + 3 < d.nx - 1);
+  const int n12 = ny_c + 2;
+  if (!two) {
+    for (int z = z0; z < z1; ++z, c += sz) {
+      if (!act) continue;
+      const float4 bv = ld4_any(b + c);
+      const int zn = (z > 0) + (z < d.nz - 1);
+      float4 o;
+      o.x = w_over(w0h2, n0 + zn) * bv.x;
+      o.y = w_over(w0h2, n12 + zn) * bv.y;
+      o.z = w_over(w0h2, n12 + zn) * bv.z;
+      o.w = w_over(w0h2, n3 + zn) * bv.w;
+      if (bcopy) st4(bcopy + c, bv);
+      st4(xo + c, o);
+    }
+    return;
+  }
+  // in-plane neighbour counts: own cells, x-neighbours at i0-1 and i0+4, and
+  // the rows j-1, j+1 (same x)
+  const int cx_m = (i0 - 1 > 0) + 1 + (j > 0) + (j < d.ny - 1);            // cell i0-1
+  const int cx_p = 1 + (i0 + 4 < d.nx - 1) + (j > 0) + (j < d.ny - 1);      // cell i0+4
+  auto nrow = [&](int jj, int q) {
+    const int ii = i0 + q;
+    return (ii > 0) + (ii < d.nx - 1) + (jj > 0) + (jj < d.ny - 1);
+  };
+  int nown[4], nym[4], nyp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    nown[q] = nrow(j, q);
+    nym[q] = nrow(j - 1, q);
+    nyp[q] = nrow(j + 1, q);
+  }
+  float4 bp = (act && z0 > 0) ? ld4_any(b + c - sz) : Z4;
+  float4 bc = act ? ld4_any(b + c) : Z4;
+  for (int z = z0; z < z1; ++z, c += sz) {
+    const float4 bn = (act && z + 1 < d.nz) ? ld4_any(b + c + sz) : Z4;
+    sb[ty + 1][lane] = bc;
+    if (ty == 0) sb[0][lane] = (act && j > 0) ? ld4_any(b + c - sy) : Z4;
+    if (ty == VY - 1 || j == d.ny - 1)
+      sb[ty + 2][lane] = (act && j < d.ny - 1) ? ld4_any(b + c + sy) : Z4;
+    float left = __shfl_up_sync(kFull, bc.w, 1);
+    float right = __shfl_down_sync(kFull, bc.x, 1);
+    if (lane == 0) left = (act && i0 > 0) ? ld1_any(b + c - 1) : 0.f;
+    if (lane == 31) right = (act && i0 + 4 < d.nx) ? ld1_any(b + c + 4) : 0.f;
+    __syncthreads();
+    const float4 ym = sb[ty][lane];
+    const float4 yp = sb[ty + 2][lane];
+    const int zn = (z > 0) + (z < d.nz - 1);
+    const int znm = (z - 1 > 0) + (z - 1 < d.nz - 1);
+    const int znp = (z + 1 > 0) + (z + 1 < d.nz - 1);
+    const float bcv[4] = {bc.x, bc.y, bc.z, bc.w};
+    const float bpv[4] = {bp.x, bp.y, bp.z, bp.w};
+    const float bnv[4] = {bn.x, bn.y, bn.z, bn.w};
+    const float ymv[4] = {ym.x, ym.y, ym.z, ym.w};
+    const float ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+    // x1 = w0 h^2 b / nn at the own cells and the two x-halo cells
+    float x1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x1[q] = w_over(w0h2, nown[q] + zn) * bcv[q];
+    const float x1l = w_over(w0h2, cx_m + zn) * left;
+    const float x1r = w_over(w0h2, cx_p + zn) * right;
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ii = i0 + q;
+      float s = 0.f;
+      if (ii > 0) s += (q == 0) ? x1l : x1[q - 1];
+      if (ii < d.nx - 1) s += (q == 3) ? x1r : x1[q + 1];
+      if (j > 0) s += w_over(w0h2, nym[q] + zn) * ymv[q];
+      if (j < d.ny - 1) s += w_over(w0h2, nyp[q] + zn) * ypv[q];
+      if (z > 0) s += w_over(w0h2, nown[q] + znm) * bpv[q];
+      if (z < d.nz - 1) s += w_over(w0h2, nown[q] + znp) * bnv[q];
+      const int nn = nown[q] + zn;
+      o[q] = fmaf(w_over(w1, nn), fmaf(h2, bcv[q], s - (float)nn * x1[q]), x1[q]);
+    }
+    if (act) {
+      st4(xo + c, make_float4(o[0], o[1], o[2], o[3]));
+      if (bcopy) st4(bcopy + c, bc);
+    }
+    __syncthreads();
+    bp = bc;
+    bc = bn;
+  }
+}
+
+// Residual restriction, four fine cells (two coarse cells) per thread and
+// two fine rows (one coarse row); the march runs over fine planes.
+__global__ void __launch_bounds__(32 * VY) k_restrict_v4(Dims d, Dims dc,
+                                                         const float* __restrict__ x,
+                                                         const float* __restrict__ b,
+                                                         float* __restrict__ bcoarse, float inv_h2,
+                                                         int zcc) {
+  const int lane = threadIdx.x;
+  const int i0 = 4 * (blockIdx.x * 32 + lane);
+  const int J = blockIdx.y * VY + threadIdx.y;
+  const bool act = i0 < d.nx && J < dc.ny;
+  const int K0 = blockIdx.z * zcc;
+  const int K1 = min(K0 + zcc, dc.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int j0 = 2 * J;
+  // rows j0 (r = 0) and j0 + 1 (r = 1); in-plane counts per row and cell
+  int nin[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ii = i0 + q, jj = j0 + r;
+      nin[r][q] = (ii > 0) + (ii < d.nx - 1) + (jj > 0) + (jj < d.ny - 1);
+    }
+  const int zs = 2 * K0;
+  int64_t c = (int64_t)zs * sz + (int64_t)j0 * sy + i0;
+  float4 p0 = Z4, p1 = Z4, c0 = Z4, c1 = Z4;   // planes z-1 and z of rows r = 0, 1
+  if (x && act) {
+    if (zs > 0) { p0 = ld4(x + c - sz); p1 = ld4(x + c - sz + sy); }
+    c0 = ld4(x + c);
+    c1 = ld4(x + c + sy);
+  }
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int z = zs; z < 2 * K1; ++z, c += sz) {
+    float4 b0 = act ? ld4(b + c) : Z4;
+    float4 b1 = act ? ld4(b + c + sy) : Z4;
+    if (x) {
+      float4 n0 = Z4, n1 = Z4, ym = Z4, yp = Z4;
+      if (act && z + 1 < d.nz) { n0 = ld4(x + c + sz); n1 = ld4(x + c + sz + sy); }
+      if (act && j0 > 0) ym = ld4(x + c - sy);
+      if (act && j0 + 2 < d.ny) yp = ld4(x + c + 2 * sy);
+      float l0 = __shfl_up_sync(kFull, c0.w, 1), l1 = __shfl_up_sync(kFull, c1.w, 1);
+      float r0 = __shfl_down_sync(kFull, c0.x, 1), r1 = __shfl_down_sync(kFull, c1.x, 1);
+      if (lane == 0) {
+        l0 = (act && i0 > 0) ? __ldg(x + c - 1) : 0.f;
+        l1 = (act && i0 > 0) ? __ldg(x + c + sy - 1) : 0.f;
+      }
+      if (lane == 31) {
+        r0 = (act && i0 + 4 < d.nx) ? __ldg(x + c + 4) : 0.f;
+        r1 = (act && i0 + 4 < d.nx) ? __ldg(x + c + sy + 4) : 0.f;
+      }
+      const int zn = (z > 0) + (z < d.nz - 1);
+      // row 0: y-neighbours ym (row j0-1) and c1 (row j0+1)
+      b0.x -= ((float)(nin[0][0] + zn) * c0.x - ((l0 + c0.y) + (ym.x + c1.x) + (p0.x + n0.x))) * inv_h2;
+      b0.y -= ((float)(nin[0][1] + zn) * c0.y - ((c0.x + c0.z) + (ym.y + c1.y) + (p0.y + n0.y))) * inv_h2;
+      b0.z -= ((float)(nin[0][2] + zn) * c0.z - ((c0.y + c0.w) + (ym.z + c1.z) + (p0.z + n0.z))) * inv_h2;
+      b0.w -= ((float)(nin[0][3] + zn) * c0.w - ((c0.z + r0) + (ym.w + c1.w) + (p0.w + n0.w))) * inv_h2;
+      // row 1: y-neighbours c0 (row j0) and yp (row j0+2)
+      b1.x -= ((float)(nin[1][0] + zn) * c1.x - ((l1 + c1.y) + (c0.x + yp.x) + (p1.x + n1.x))) * inv_h2;
+      b1.y -= ((float)(nin[1][1] + zn) * c1.y - ((c1.x + c1.z) + (c0.y + yp.y) + (p1.y + n1.y))) * inv_h2;
+      b1.z -= ((float)(nin[1][2] + zn) * c1.z - ((c1.y + c1.w) + (c0.z + yp.z) + (p1.z + n1.z))) * inv_h2;
+      b1.w -= ((float)(nin[1][3] + zn) * c1.w - ((c1.z + r1) + (c0.w + yp.w) + (p1.w + n1.w))) * inv_h2;
+      p0 = c0; p1 = c1; c0 = n0; c1 = n1;
+    }
+    acc0 += (b0.x + b0.y) + (b1.x + b1.y);
+    acc1 += (b0.z + b0.w) + (b1.z + b1.w);
+    if (z & 1) {
+      if (act) {
+        const int64_t cc = ((int64_t)(z >> 1) * dc.ny + J) * dc.nx + (i0 >> 1);
+        *reinterpret_cast<float2*>(bcoarse + cc) = make_float2(acc0 * 0.125f, acc1 * 0.125f);
+      }
+      acc0 = acc1 = 0.f;
+    }
+  }
+}
+
+// x (+)= P xc for four fine cells per thread (parents I0 = 2q, I1 = 2q + 1).
+__global__ void __launch_bounds__(32 * VY) k_prolong_v4(Dims d, Dims dc,
+                                                        const float* __restrict__ xc,
+                                                        float* __restrict__ x, int overwrite,
+                                                        int zc) {
+  const int lane = threadIdx.x;
+  const int q = blockIdx.x * 32 + lane;
+  const int i0 = 4 * q;
+  const int j = blockIdx.y * VY + threadIdx.y;
+  if (i0 >= d.nx || j >= d.ny) return;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz);
+  const int I0 = 2 * q, I1 = 2 * q + 1;
+  const int Im = max(I0 - 1, 0), Ip = min(I1 + 1, dc.nx - 1);
+  const int J = j >> 1;
+  const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
+  const int64_t sy = dc.nx, sz = (int64_t)dc.nx * dc.ny;
+  for (int k = z0; k < z1; ++k) {
+    const int K = k >> 1;
+    const int Kn = (k & 1) ? min(K + 1, dc.nz - 1) : max(K - 1, 0);
+    const float* r00 = xc + K * sz + J * sy;
+    const float* r01 = xc + K * sz + Jn * sy;
+    const float* r10 = xc + Kn * sz + J * sy;
+    const float* r11 = xc + Kn * sz + Jn * sy;
+    auto yz = [&](int I) {
+      const float a = 0.75f * __ldg(r00 + I) + 0.25f * __ldg(r01 + I);
+      const float bb = 0.75f * __ldg(r10 + I) + 0.25f * __ldg(r11 + I);
+      return 0.75f * a + 0.25f * bb;
+    };
+    const float cm = yz(Im), ca = yz(I0), cb = yz(I1), cp = yz(Ip);
+    float4 v = make_float4(0.75f * ca + 0.25f * cm, 0.75f * ca + 0.25f * cb,
+                           0.75f * cb + 0.25f * ca, 0.75f * cb + 0.25f * cp);
+    const int64_t f = ((int64_t)k * d.ny + j) * d.nx + i0;
+    if (!overwrite) {
+      const float4 o = *reinterpret_cast<const float4*>(x + f);
+      v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+    }
+    st4(x + f, v);
+  }
 }
 
 // x = P b on the coarsest level: one block, dense pseudo-inverse.
@@ -148,17 +612,6 @@ __global__ void k_coarse_solve(const T* __restrict__ P, const T* __restrict__ b,
     for (int q = 0; q < mc; ++q) acc = fma(__ldg(P + (int64_t)r * mc + q), sb[q], acc);
     x[r] = acc;
   }
-}
-
-__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
-}
-__global__ void k_f2d(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (double)x[i];
 }
 
 // Gauss-Jordan inverse with partial pivoting (host, n <= kMaxCoarse).
@@ -215,52 +668,149 @@ const float* pinv_of<float>(ibm_ctx* c) { return c->coarse_pinv32; }
 template <>
 const double* pinv_of<double>(ibm_ctx* c) { return c->coarse_pinv64; }
 
-// p Chebyshev sweeps on level l starting from *x (zero if from_zero); the
-// result ends in *x (the sweep ping-pongs with *t and copies back if needed).
-template <typename T>
-void smooth(ibm_ctx* c, int l, const T* b, T* x, T* t, int p, bool from_zero, cudaStream_t s) {
-  if (p <= 0) return;
+// Pre-smoothing from a zero iterate: p Chebyshev steps on level l ending in x.
+// The first two steps run as one kernel (k_first); b may be the FP64 input of
+// the finest level, in which case bcopy receives its rounded copy.
+template <typename T, typename TB>
+void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cudaStream_t s) {
   MGLevel& L = c->lv[l];
   double w[8];
   cheb_weights(p, w);
   const double h2 = L.h * L.h;
+  const int two = p >= 2;
+  const bool vec = std::is_same<T, float>::value && vec_ok(L.d);
+  const int zc = vec_zc(L.d);
+  const int ph = l == 0 ? prof_begin(c, IBM_PROF_MG_SMOOTH_FINE) : -1;
+  count_launch();
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec)
+      k_first_v4<TB><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(
+          L.d, b, bcopy, x, (float)(w[0] * h2), (float)(two ? w[1] : 0.0), (float)h2, two, zc);
+  }
+  if (!vec)
+    k_first<T, TB><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(
+        L.d, b, bcopy, x, w_over_n<T>(w[0] * h2), w_over_n<T>(two ? w[1] : 0.0), (T)h2, two);
+  prof_end(c, ph);
+  const T* bb = bcopy ? bcopy : reinterpret_cast<const T*>(b);
   T* cur = x;
   T* nxt = t;
-  int q = 0;
-  if (from_zero) {
+  for (int q = two ? 2 : 1; q < p; ++q) {
     count_launch();
-    k_cheb_first<T><<<grid3(L.d), dim3(BX, BY), 0, s>>>(L.d, b, x, (T)(w[0] * h2));
-    q = 1;
-  }
-  for (; q < p; ++q) {
-    const int ph = l == 0 ? prof_begin(c, IBM_PROF_MG_SMOOTH_FINE) : -1;
-    count_launch();
-    k_cheb_sweep<T><<<grid3(L.d), dim3(BX, BY), 0, s>>>(L.d, cur, b, nxt, (T)w[q], (T)h2);
-    prof_end(c, ph);
+    if constexpr (std::is_same<T, float>::value) {
+      if (vec)
+        k_sweep_v4<float><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(L.d, cur, bb, nxt,
+                                                                      (float)w[q], (float)h2, zc);
+    }
+    if (!vec)
+      k_sweep<T, T, T><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(L.d, cur, bb, nxt,
+                                                            w_over_n<T>(w[q]), (T)h2);
     T* tmp = cur; cur = nxt; nxt = tmp;
   }
   if (cur != x) cudaMemcpyAsync(x, cur, sizeof(T) * L.m, cudaMemcpyDeviceToDevice, s);
 }
 
-// V-cycle on level l: x_l ~ L_l^{-1} b_l.
+// one smoothing step src -> dst on level l
+template <typename T, typename TO>
+void sweep_step(ibm_ctx* c, int l, const T* src, const T* b, TO* dst, double w, cudaStream_t s) {
+  MGLevel& L = c->lv[l];
+  const double h2 = L.h * L.h;
+  count_launch();
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec_ok(L.d)) {
+      const int zc = vec_zc(L.d);
+      k_sweep_v4<TO><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(L.d, src, b, dst, (float)w,
+                                                               (float)h2, zc);
+      return;
+    }
+  }
+  k_sweep<T, T, TO><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(L.d, src, b, dst, w_over_n<T>(w),
+                                                         (T)h2);
+}
+
+// Post-smoothing: p Chebyshev steps from x; the last step writes out (which
+// may be FP64 while T is FP32).  Intermediate iterates ping-pong between t and
+// x; out never aliases the step's input.
+template <typename T, typename TO>
+void post_smooth(ibm_ctx* c, int l, const T* b, T* x, T* t, int p, TO* out, cudaStream_t s) {
+  MGLevel& L = c->lv[l];
+  if (p <= 0) {
+    if ((const void*)out != (const void*)x) {
+      count_launch();
+      k_convert<T, TO><<<kRedBlocks, 256, 0, s>>>(x, out, L.m);
+    }
+    return;
+  }
+  double w[8];
+  cheb_weights(p, w);
+  const T* src = x;
+  for (int q = 0; q < p; ++q) {
+    const bool last = q == p - 1;
+    const int ph = l == 0 ? prof_begin(c, IBM_PROF_MG_SMOOTH_FINE) : -1;
+    if (last && (const void*)out != (const void*)src) {
+      sweep_step<T, TO>(c, l, src, b, out, w[q], s);
+      prof_end(c, ph);
+      return;
+    }
+    T* dst = (src == x) ? t : x;
+    sweep_step<T, T>(c, l, src, b, dst, w[q], s);
+    prof_end(c, ph);
+    src = dst;
+  }
+  // the last step landed in t or x while out aliases the other: copy
+  if ((const void*)src != (const void*)out)
+    cudaMemcpyAsync(out, src, sizeof(T) * L.m, cudaMemcpyDeviceToDevice, s);
+}
+
+// V-cycle on level l >= 1 (or level 0 in the FP64 form): x_l ~ L_l^{-1} b_l.
+template <typename T>
+void vcycle(ibm_ctx* c, int l, const T* b, T* x, T* t, int pre, int post, cudaStream_t s);
+
+template <typename T>
+void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cudaStream_t s) {
+  MGLevel& L = c->lv[l];
+  MGLevel& C = c->lv[l + 1];
+  LevelPtrs<T> cp = ptrs<T>(C);
+  const T* xin = pre > 0 ? x : nullptr;
+  bool done = false;
+  count_launch();
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec_ok(L.d)) {
+      const int zcc = std::max(1, vec_zc(L.d) / 2);
+      k_restrict_v4<<<dim3(div_up(L.d.nx / 4, 32), div_up(C.d.ny, VY), div_up(C.d.nz, zcc)),
+                      dim3(32, VY), 0, s>>>(L.d, C.d, xin, b, cp.b, (float)(1.0 / (L.h * L.h)),
+                                            zcc);
+      done = true;
+    }
+  }
+  if (!done)
+    k_restrict<T><<<dim3(div_up(C.d.nx, BX), div_up(C.d.ny, BY), div_up(C.d.nz, ZC / 2)),
+                    dim3(BX, BY), 0, s>>>(L.d, C.d, xin, b, cp.b, (T)(1.0 / (L.h * L.h)));
+  vcycle<T>(c, l + 1, cp.b, cp.x, cp.t, pre, post, s);
+  done = false;
+  count_launch();
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec_ok(L.d)) {
+      const int zc = vec_zc(L.d);
+      k_prolong_v4<<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(L.d, C.d, cp.x, x, pre > 0 ? 0 : 1,
+                                                              zc);
+      done = true;
+    }
+  }
+  if (!done)
+    k_prolong<T><<<dim3(div_up(C.d.nx, BX), div_up(L.d.ny, BY), div_up(L.d.nz, ZC)),
+                   dim3(BX, BY), 0, s>>>(L.d, C.d, cp.x, x, pre > 0 ? 0 : 1);
+}
+
 template <typename T>
 void vcycle(ibm_ctx* c, int l, const T* b, T* x, T* t, int pre, int post, cudaStream_t s) {
-  MGLevel& L = c->lv[l];
   if (l == c->n_levels - 1) {
     count_launch();
     k_coarse_solve<T><<<1, 256, 0, s>>>(pinv_of<T>(c), b, x, c->coarse_m);
     return;
   }
-  MGLevel& C = c->lv[l + 1];
-  LevelPtrs<T> cp = ptrs<T>(C);
-  smooth<T>(c, l, b, x, t, pre, true, s);
-  count_launch();
-  k_resid_restrict<T><<<grid3(C.d), dim3(BX, BY), 0, s>>>(L.d, C.d, pre > 0 ? x : nullptr, b, cp.b,
-                                                          (T)(1.0 / (L.h * L.h)));
-  vcycle<T>(c, l + 1, cp.b, cp.x, cp.t, pre, post, s);
-  count_launch();
-  k_prolong<T><<<grid3(L.d), dim3(BX, BY), 0, s>>>(L.d, C.d, cp.x, x, pre > 0 ? 0 : 1);
-  smooth<T>(c, l, b, x, t, post, false, s);
+  if (pre > 0) pre_smooth<T, T>(c, l, b, nullptr, x, t, pre, s);
+  coarse_correct<T>(c, l, b, x, pre, post, s);
+  post_smooth<T, T>(c, l, b, x, t, post, x, s);
 }
 
 }  // namespace
@@ -340,14 +890,29 @@ ibm_status mg_setup(ibm_ctx* c) {
 ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, int post) {
   cudaStream_t s = c->stream;
   MGLevel& L0 = c->lv[0];
+  if (c->n_levels == 1) {
+    // the whole grid is the coarsest level: the cycle is the exact pseudo-inverse
+    count_launch();
+    k_coarse_solve<double><<<1, 256, 0, s>>>(c->coarse_pinv64, r, z, c->coarse_m);
+    IBM_LAUNCH_CHECK(c);
+    return IBM_OK;
+  }
   if (prec == IBM_PREC_FP32) {
-    count_launch();
-    k_d2f<<<kRedBlocks, 256, 0, s>>>(r, L0.b32, L0.m);
-    vcycle<float>(c, 0, L0.b32, L0.x32, L0.t32, pre, post, s);
-    count_launch();
-    k_f2d<<<kRedBlocks, 256, 0, s>>>(L0.x32, z, L0.m);
+    // finest level: FP64 in, FP32 inside, FP64 out
+    if (pre > 0) {
+      pre_smooth<float, double>(c, 0, r, L0.b32, L0.x32, L0.t32, pre, s);
+    } else {
+      // only the rounded copy of r is needed (the zero iterate is never read)
+      count_launch();
+      k_first<float, double><<<zm_grid(L0.d), dim3(BX, BY), 0, s>>>(
+          L0.d, r, L0.b32, L0.t32, w_over_n<float>(0.0), w_over_n<float>(0.0), 0.f, 0);
+    }
+    coarse_correct<float>(c, 0, L0.b32, L0.x32, pre, post, s);
+    post_smooth<float, double>(c, 0, L0.b32, L0.x32, L0.t32, post, z, s);
   } else {
-    vcycle<double>(c, 0, r, z, L0.t64, pre, post, s);
+    if (pre > 0) pre_smooth<double, double>(c, 0, r, nullptr, z, L0.t64, pre, s);
+    coarse_correct<double>(c, 0, r, z, pre, post, s);
+    post_smooth<double, double>(c, 0, r, z, L0.t64, post, z, s);
   }
   IBM_LAUNCH_CHECK(c);
   return IBM_OK;

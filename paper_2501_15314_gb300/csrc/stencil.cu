@@ -126,78 +126,336 @@ __global__ void __launch_bounds__(BX * BY) k_gradt_axpby(Dims d, FaceGeom g,
   out[c] = cin ? fma(alpha, s, beta * __ldg(cin + c)) : alpha * s;
 }
 
-// Helmholtz residual of the predictor: res = rhs - (a u - nu Lap u) on
-// interior faces.  Along the face-normal axis the wall faces hold 0; along the
-// other axes the ghost beyond a wall is -u (no-slip at the wall midpoint).
-__global__ void __launch_bounds__(BX * BY) k_helm_residual(Dims d, FaceGeom g,
-                                                           const double* __restrict__ u,
-                                                           double a, double nu_h2,
-                                                           const double* __restrict__ rhs,
-                                                           double* __restrict__ res) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  const int p3[3] = {i, j, k};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (i >= g.n[c][0] || j >= g.n[c][1] || k >= g.n[c][2]) continue;
-    const int64_t f = fidx(g, c, i, j, k);
-    if (p3[c] == 0 || p3[c] == g.n[c][c] - 1) { res[f] = 0.0; continue; }
-    const double uc = __ldg(u + f);
-    double s = 0.0, diag = a + 6.0 * nu_h2;
-    const int64_t st[3] = {1, g.sy[c], g.sz[c]};
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const int n_e = g.n[c][e];
-      if (e == c) {   // neighbours are faces along their own normal
-        if (p3[e] - 1 > 0) s += __ldg(u + f - st[e]);
-        if (p3[e] + 1 < n_e - 1) s += __ldg(u + f + st[e]);
-      } else {
-        if (p3[e] > 0) s += __ldg(u + f - st[e]); else diag += nu_h2;
-        if (p3[e] < n_e - 1) s += __ldg(u + f + st[e]); else diag += nu_h2;
-      }
+// Predictor Helmholtz operator on the d-faces, A = a I - nu Lap_h with the
+// no-slip ghosts: A e = diag e_c - (nu / h^2) * (sum of neighbours), where the
+// face-normal axis reads the wall faces (which hold 0) and each cell-centred
+// axis adds nu / h^2 to diag for every missing neighbour (ghost = -e_c).
+// Kernels below march along z over ZH planes; blockIdx.z = comp * zchunks +
+// chunk, so one launch covers the three face grids.
+constexpr int ZH = 16;
+
+struct FaceThread {
+  int c, i, j, z0, z1, n0, n1, n2;
+  int64_t sy, sz, f0;
+  bool wall;       // the whole column is a wall-normal face (c = 0 or 1)
+  bool xm, xp, ym, yp;
+  int ghosts_xy;
+};
+
+__device__ __forceinline__ bool face_thread(const FaceGeom& g, int zchunks, FaceThread& t) {
+  t.c = blockIdx.z / zchunks;
+  const int zc = blockIdx.z - t.c * zchunks;
+  t.i = blockIdx.x * BX + threadIdx.x;
+  t.j = blockIdx.y * BY + threadIdx.y;
+  t.n0 = g.n[t.c][0];
+  t.n1 = g.n[t.c][1];
+  t.n2 = g.n[t.c][2];
+  t.z0 = zc * ZH;
+  if (t.i >= t.n0 || t.j >= t.n1 || t.z0 >= t.n2) return false;
+  t.z1 = min(t.z0 + ZH, t.n2);
+  t.sy = g.sy[t.c];
+  t.sz = g.sz[t.c];
+  t.f0 = g.off[t.c] + (int64_t)t.z0 * t.sz + (int64_t)t.j * t.sy + t.i;
+  t.wall = (t.c == 0 && (t.i == 0 || t.i == t.n0 - 1)) || (t.c == 1 && (t.j == 0 || t.j == t.n1 - 1));
+  t.xm = t.i > 0;
+  t.xp = t.i < t.n0 - 1;
+  t.ym = t.j > 0;
+  t.yp = t.j < t.n1 - 1;
+  t.ghosts_xy = 0;
+  if (t.c != 0) t.ghosts_xy += (!t.xm) + (!t.xp);
+  if (t.c != 1) t.ghosts_xy += (!t.ym) + (!t.yp);
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T face_inplane(const T* __restrict__ e, int64_t f, const FaceThread& t) {
+  T s = 0;
+  if (t.xm) s += __ldg(e + f - 1);
+  if (t.xp) s += __ldg(e + f + 1);
+  if (t.ym) s += __ldg(e + f - t.sy);
+  if (t.yp) s += __ldg(e + f + t.sy);
+  return s;
+}
+
+// Right-hand side of the predictor, Eq. (ustar), with the convective term
+// fused in: rhs = (4 u^n - u^{n-1}) / (2 dt) - G p^n + f - A(u^n) on interior
+// faces (0 on wall faces).  A is the central divergence form of k_advection
+// with the 1/2 averages folded into one factor 1/4:
+//   4 A = [ (u_+ + u_0)^2 - (u_0 + u_-)^2 ] along the component's own axis
+//       + sum over the two other axes of (flux at the upper edge - lower edge),
+//   flux = (u_e averaged pair sum) * (u_c averaged pair sum), 0 on walls.
+// The march runs along z; the flux through the lower z-edge (or, for u_z, the
+// lower cell-centred square) is the previous face's upper one and is reused.
+__global__ void __launch_bounds__(BX * BY) k_predictor_rhs_adv(
+    Dims d, FaceGeom g, int zchunks, const double* __restrict__ un,
+    const double* __restrict__ unm1, const double* __restrict__ pn,
+    const double* __restrict__ fb, int with_adv, double inv_2dt, double inv_h,
+    double* __restrict__ rhs) {
+  FaceThread t;
+  if (!face_thread(g, zchunks, t)) return;
+  const int c = t.c;
+  int64_t f = t.f0;
+  const int64_t csy = d.nx, csz = (int64_t)d.nx * d.ny;
+  const int64_t cstride[3] = {1, csy, csz};
+  // U(comp, x, y, z): face value, 0 on wall faces and outside the grid
+  auto U = [&](int comp, int x, int y, int z) -> double {
+    const int q[3] = {x, y, z};
+    if (x < 0 || y < 0 || z < 0 || x >= g.n[comp][0] || y >= g.n[comp][1] || z >= g.n[comp][2])
+      return 0.0;
+    if (q[comp] == 0 || q[comp] == g.n[comp][comp] - 1) return 0.0;
+    return __ldg(un + fidx(g, comp, x, y, z));
+  };
+  // flux on the edge between the c-face at p (p[c] = c-face index) and the
+  // e-face index qe along e (other coordinate from p): 4 * (avg u_e)(avg u_c)
+  auto eflux = [&](int e, int px, int py, int pz, int qe) -> double {
+    const int ne = g.n[e][e] - 1;   // cells along e
+    if (qe <= 0 || qe >= ne) return 0.0;
+    int a[3] = {px, py, pz};
+    a[e] = qe;
+    int b0[3] = {a[0], a[1], a[2]}, b1[3] = {a[0], a[1], a[2]};
+    b0[c] -= 1;   // u_e at the two cells adjacent along c
+    const double ue = U(e, b0[0], b0[1], b0[2]) + U(e, b1[0], b1[1], b1[2]);
+    int c0[3] = {a[0], a[1], a[2]}, c1[3] = {a[0], a[1], a[2]};
+    c0[e] = qe - 1;
+    const double uc = U(c, c0[0], c0[1], c0[2]) + U(c, c1[0], c1[1], c1[2]);
+    return ue * uc;
+  };
+  const int i = t.i, j = t.j;
+  double carry = 0.0;   // lower z-flux (c = 0, 1) or lower square (c = 2)
+  if (with_adv && !t.wall) {
+    if (c == 2) {
+      const double s0 = U(2, i, j, t.z0 - 1) + U(2, i, j, t.z0);
+      carry = s0 * s0;
+    } else {
+      carry = eflux(2, i, j, t.z0, t.z0);
     }
-    const double Au = fma(diag, uc, -nu_h2 * s);
-    res[f] = __ldg(rhs + f) - Au;
+  }
+  for (int z = t.z0; z < t.z1; ++z, f += t.sz) {
+    const bool wall = t.wall || (c == 2 && (z == 0 || z == t.n2 - 1));
+    if (wall) {
+      rhs[f] = 0.0;
+      if (with_adv) {
+        if (c == 2) {
+          const double s1 = U(2, i, j, z) + U(2, i, j, z + 1);
+          carry = s1 * s1;
+        } else {
+          carry = eflux(2, i, j, z, z + 1);
+        }
+      }
+      continue;
+    }
+    const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
+    double v = (4.0 * __ldg(un + f) - __ldg(unm1 + f)) * inv_2dt;
+    v -= (__ldg(pn + cp) - __ldg(pn + cp - cstride[c])) * inv_h;
+    if (fb) v += __ldg(fb + f);
+    if (with_adv) {
+      double acc;
+      if (c == 2) {
+        const double s1 = U(2, i, j, z) + U(2, i, j, z + 1);
+        const double up2 = s1 * s1;
+        acc = up2 - carry;
+        carry = up2;
+        acc += eflux(0, i, j, z, i + 1) - eflux(0, i, j, z, i);
+        acc += eflux(1, i, j, z, j + 1) - eflux(1, i, j, z, j);
+      } else {
+        // own axis (x for u_x, y for u_y)
+        int pp[3] = {i, j, z}, pm[3] = {i, j, z};
+        pp[c] += 1;
+        pm[c] -= 1;
+        const double u0 = __ldg(un + f);
+        const double up = U(c, pp[0], pp[1], pp[2]), um = U(c, pm[0], pm[1], pm[2]);
+        acc = (up - um) * (up + 2.0 * u0 + um);
+        const int o = 1 - c;   // the other in-plane axis
+        const int po = o == 0 ? i : j;
+        acc += eflux(o, i, j, z, po + 1) - eflux(o, i, j, z, po);
+        const double fz = eflux(2, i, j, z, z + 1);
+        acc += fz - carry;
+        carry = fz;
+      }
+      v -= 0.25 * inv_h * acc;
+    }
+    rhs[f] = v;
   }
 }
 
-// One Chebyshev step for A e = r in FP32 (A the predictor's Helmholtz
-// operator): e_new = e + beta (e - e_old) + alpha (r - A e); with first != 0
-// the iterate is 0 and e_new = alpha r.
-__global__ void __launch_bounds__(BX * BY) k_helm_cheb(Dims d, FaceGeom g,
-                                                       const float* __restrict__ e,
-                                                       const float* __restrict__ e_old,
-                                                       const float* __restrict__ r, float a,
-                                                       float nu_h2, float alpha, float beta,
-                                                       float* __restrict__ e_new, int first) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  const int p3[3] = {i, j, k};
-#pragma unroll
+// FP32 work arrays of the predictor use a padded copy of the face layout:
+// rows padded to a multiple of 4 values, so that every row starts on a
+// 16-byte boundary and a thread can own four consecutive faces (one float4).
+// Padding holds 0 and is never read as a neighbour.
+struct FaceGeom32 {
+  int n[3][3];
+  int64_t off[3], sy[3], sz[3];
+};
+
+FaceGeom32 make_face_geom32(Dims d) {
+  const FaceGeom g = make_face_geom(d);
+  FaceGeom32 p;
+  int64_t off = 0;
   for (int c = 0; c < 3; ++c) {
-    if (i >= g.n[c][0] || j >= g.n[c][1] || k >= g.n[c][2]) continue;
-    const int64_t f = fidx(g, c, i, j, k);
-    if (p3[c] == 0 || p3[c] == g.n[c][c] - 1) { e_new[f] = 0.f; continue; }
-    const float rc = __ldg(r + f);
-    if (first) { e_new[f] = alpha * rc; continue; }
-    const float ec = __ldg(e + f);
-    float s = 0.f, diag = a + 6.f * nu_h2;
-    const int64_t st[3] = {1, g.sy[c], g.sz[c]};
+    for (int a = 0; a < 3; ++a) p.n[c][a] = g.n[c][a];
+    p.sy[c] = (g.n[c][0] + 3) / 4 * 4;
+    p.sz[c] = p.sy[c] * g.n[c][1];
+    p.off[c] = off;
+    off += p.sz[c] * g.n[c][2];
+  }
+  return p;
+}
+
+constexpr int HVY = 8;
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// One FP32 Chebyshev step for A e = r on the padded layout, four faces per
+// thread; x-neighbours by shuffles, z by the march, y through L1.
+// mode 0: first step from e = 0, e_new = alpha r with r = rs * r64 rounded to
+// FP32 (stored in r32 for the later steps); mode 1: e_new = e + beta (e -
+// e_old) + alpha (r - A e); mode 2: the same step accumulated into the FP64
+// iterate, u += us * e_new.
+__global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
+    FaceGeom g, FaceGeom32 p, int zchunks, const float* __restrict__ e,
+    const float* __restrict__ eo, float* __restrict__ r32, const double* __restrict__ r64,
+    double rs, float a, float nu_h2, float alpha, float beta, float* __restrict__ en,
+    double* __restrict__ u, double us, int mode) {
+  const int c = blockIdx.z / zchunks;
+  const int zc = blockIdx.z - c * zchunks;
+  const int lane = threadIdx.x;
+  const int x0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * HVY + threadIdx.y;
+  const int n0 = p.n[c][0], n1 = p.n[c][1], n2 = p.n[c][2];
+  const int z0 = zc * ZH;
+  if (z0 >= n2 || blockIdx.x * 128 >= n0 || blockIdx.y * HVY >= n1) return;   // block-uniform
+  const int z1 = min(z0 + ZH, n2);
+  const bool act = x0 < n0 && j < n1;
+  const int64_t sy = p.sy[c], sz = p.sz[c];
+  int64_t f = p.off[c] + (int64_t)z0 * sz + (int64_t)j * sy + x0;
+  const int64_t sy64 = g.sy[c], sz64 = g.sz[c];
+  int64_t f64 = g.off[c] + (int64_t)z0 * sz64 + (int64_t)j * sy64 + x0;
+  const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // per-element validity and x-wall status
+  bool val[4], wallx[4];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int n_q = g.n[c][q];
-      if (q == c) {
-        if (p3[q] - 1 > 0) s += __ldg(e + f - st[q]);
-        if (p3[q] + 1 < n_q - 1) s += __ldg(e + f + st[q]);
-      } else {
-        if (p3[q] > 0) s += __ldg(e + f - st[q]); else diag += nu_h2;
-        if (p3[q] < n_q - 1) s += __ldg(e + f + st[q]); else diag += nu_h2;
+  for (int q = 0; q < 4; ++q) {
+    val[q] = act && (x0 + q < n0);
+    wallx[q] = c == 0 && (x0 + q == 0 || x0 + q == n0 - 1);
+  }
+  const bool wally = c == 1 && (j == 0 || j == n1 - 1);
+  if (mode == 0) {
+    for (int z = z0; z < z1; ++z, f += sz, f64 += sz64) {
+      const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
+      float r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        r[q] = (val[q] && !wallx[q] && !wally && !wallz) ? (float)(rs * __ldg(r64 + f64 + q)) : 0.f;
+      if (act) {
+        *reinterpret_cast<float4*>(r32 + f) = make_float4(r[0], r[1], r[2], r[3]);
+        *reinterpret_cast<float4*>(en + f) =
+            make_float4(alpha * r[0], alpha * r[1], alpha * r[2], alpha * r[3]);
       }
     }
-    const float res = rc - fmaf(diag, ec, -nu_h2 * s);
-    e_new[f] = ec + beta * (ec - __ldg(e_old + f)) + alpha * res;
+    return;
+  }
+  // ghost counts along y and z (cell-centred axes only), x per element
+  const int gy = (c != 1) ? ((j == 0) + (j == n1 - 1)) : 0;
+  int gx[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    gx[q] = (c != 0) ? ((x0 + q == 0) + (x0 + q == n0 - 1)) : 0;
+  const bool has_ym = j > 0, has_yp = j < n1 - 1;
+  float4 ep = (act && z0 > 0) ? *reinterpret_cast<const float4*>(e + f - sz) : Z4;
+  float4 ec = act ? *reinterpret_cast<const float4*>(e + f) : Z4;
+  for (int z = z0; z < z1; ++z, f += sz, f64 += sz64) {
+    const float4 ez = (act && z + 1 < n2) ? *reinterpret_cast<const float4*>(e + f + sz) : Z4;
+    const float4 ym = (act && has_ym) ? *reinterpret_cast<const float4*>(e + f - sy) : Z4;
+    const float4 yp = (act && has_yp) ? *reinterpret_cast<const float4*>(e + f + sy) : Z4;
+    const float4 rr = act ? *reinterpret_cast<const float4*>(r32 + f) : Z4;
+    const float4 eold = act ? *reinterpret_cast<const float4*>(eo + f) : Z4;
+    float left = __shfl_up_sync(kFullMask, ec.w, 1);
+    float right = __shfl_down_sync(kFullMask, ec.x, 1);
+    if (lane == 0) left = (act && x0 > 0) ? e[f - 1] : 0.f;
+    if (lane == 31) right = (act && x0 + 4 < n0) ? e[f + 4] : 0.f;
+    const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
+    const int gz = (c != 2) ? ((z == 0) + (z == n2 - 1)) : 0;
+    const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
+    const float evp[4] = {ep.x, ep.y, ep.z, ep.w};
+    const float evn[4] = {ez.x, ez.y, ez.z, ez.w};
+    const float vym[4] = {ym.x, ym.y, ym.z, ym.w};
+    const float vyp[4] = {yp.x, yp.y, yp.z, yp.w};
+    const float vr[4] = {rr.x, rr.y, rr.z, rr.w};
+    const float vo[4] = {eold.x, eold.y, eold.z, eold.w};
+    float out[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int x = x0 + q;
+      float sx = 0.f;
+      // x-neighbours exist inside the row; on a cell-centred x-axis the
+      // missing ones are ghosts (counted in gx), on the face axis the wall
+      // faces hold 0
+      if (x > 0) sx += (q == 0) ? left : ev[q - 1];
+      if (x < n0 - 1) sx += (q == 3) ? right : ev[q + 1];
+      const float s = sx + (vym[q] + vyp[q]) + (evp[q] + evn[q]);
+      const float diag = a + nu_h2 * (float)(6 + gx[q] + gy + gz);
+      const float res = vr[q] - fmaf(diag, ev[q], -nu_h2 * s);
+      const bool live = val[q] && !wallx[q] && !wally && !wallz;
+      out[q] = live ? ev[q] + beta * (ev[q] - vo[q]) + alpha * res : 0.f;
+    }
+    if (mode == 1) {
+      if (act) *reinterpret_cast<float4*>(en + f) = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (val[q] && !wallx[q] && !wally && !wallz) u[f64 + q] = fma(us, (double)out[q], u[f64 + q]);
+    }
+    ep = ec;
+    ec = ez;
+  }
+}
+
+// FP64 predictor residual res = rhs - A u on the interior faces (0 on wall
+// faces) with the block's sum of res^2 written to part[block * stride]
+// (fixed-order reduction; every block writes its partial).
+__global__ void __launch_bounds__(BX * BY) k_helm_residual(FaceGeom g, int zchunks,
+                                                           const double* __restrict__ u, double a,
+                                                           double nu_h2,
+                                                           const double* __restrict__ rhs,
+                                                           double* __restrict__ res,
+                                                           double* __restrict__ part,
+                                                           int stride) {
+  double acc = 0.0;
+  FaceThread t;
+  if (face_thread(g, zchunks, t)) {
+    int64_t f = t.f0;
+    if (t.wall) {
+      for (int z = t.z0; z < t.z1; ++z, f += t.sz) res[f] = 0.0;
+    } else {
+      const double diag_xy = a + 6.0 * nu_h2 + nu_h2 * (double)t.ghosts_xy;
+      double up = t.z0 > 0 ? __ldg(u + f - t.sz) : 0.0;
+      double uc = __ldg(u + f);
+      for (int z = t.z0; z < t.z1; ++z, f += t.sz) {
+        const double un = (z + 1 < t.n2) ? __ldg(u + f + t.sz) : 0.0;
+        double diag = diag_xy;
+        if (t.c != 2) diag += nu_h2 * (double)((z == 0) + (z == t.n2 - 1));
+        const bool wall = t.c == 2 && (z == 0 || z == t.n2 - 1);
+        const double sn = face_inplane(u, f, t) + (up + un);
+        const double r = wall ? 0.0 : __ldg(rhs + f) - fma(diag, uc, -nu_h2 * sn);
+        res[f] = r;
+        acc = fma(r, r, acc);
+        up = uc;
+        uc = un;
+      }
+    }
+  }
+  // block reduction in a fixed order
+  __shared__ double sh[BX * BY / 32];
+  const int tid = threadIdx.y * BX + threadIdx.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) sh[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double sblk = 0.0;
+    for (int w = 0; w < BX * BY / 32; ++w) sblk += sh[w];
+    const int64_t b =
+        ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[b * stride] = sblk;
   }
 }
 
@@ -321,24 +579,49 @@ void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c, 
                                                        out);
 }
 
-void launch_helm_apply(Dims d, const double* u, double a, double nu_h2, const double* rhs,
-                       double* res, cudaStream_t s) {
-  count_launch();
-  k_helm_residual<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u, a, nu_h2, rhs,
-                                                         res);
+int helm_zchunks(Dims d) { return div_up(d.nz + 1, ZH); }
+
+dim3 helm_grid(Dims d) {
+  return dim3(div_up(d.nx + 1, BX), div_up(d.ny + 1, BY), 3 * helm_zchunks(d));
 }
 
-void launch_helm_cheb(Dims d, const float* e, const float* e_old, const float* r, float a,
-                      float nu_h2, float alpha, float beta, float* e_new, int first,
-                      cudaStream_t s) {
+int64_t launch_helm_residual(Dims d, const double* u, double a, double nu_h2, const double* rhs,
+                             double* res, double* part, int stride, cudaStream_t s) {
+  const dim3 gr = helm_grid(d);
   count_launch();
-  k_helm_cheb<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), e, e_old, r, a, nu_h2,
-                                                     alpha, beta, e_new, first);
+  k_helm_residual<<<gr, dim3(BX, BY), 0, s>>>(make_face_geom(d), helm_zchunks(d), u, a, nu_h2, rhs,
+                                               res, part, stride);
+  return (int64_t)gr.x * gr.y * gr.z;
+}
+
+int64_t helm_fp32_size(Dims d) {
+  const FaceGeom32 p = make_face_geom32(d);
+  return p.off[2] + p.sz[2] * p.n[2][2];
+}
+
+void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, const double* r64,
+                      double rs, float a, float nu_h2, float alpha, float beta, float* en,
+                      double* u, double us, int mode, cudaStream_t s) {
+  const FaceGeom32 p = make_face_geom32(d);
+  const int zch = helm_zchunks(d);
+  const dim3 gr(div_up((int)p.sy[0] / 4, 32), div_up(d.ny + 1, HVY), 3 * zch);
+  count_launch();
+  k_helm_cheb_v4<<<gr, dim3(32, HVY), 0, s>>>(make_face_geom(d), p, zch, e, eo, r32, r64, rs, a,
+                                              nu_h2, alpha, beta, en, u, us, mode);
 }
 
 void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s) {
   count_launch();
   k_advection<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u, inv_h, out);
+}
+
+void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1, const double* p_n,
+                              const double* f_body, int with_adv, double inv_2dt, double inv_h,
+                              double* rhs, cudaStream_t s) {
+  count_launch();
+  k_predictor_rhs_adv<<<helm_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), helm_zchunks(d),
+                                                             u_n, u_nm1, p_n, f_body, with_adv,
+                                                             inv_2dt, inv_h, rhs);
 }
 
 void launch_predictor_rhs(Dims d, const double* u_n, const double* u_nm1, const double* p_n,
