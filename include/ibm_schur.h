@@ -70,6 +70,15 @@ typedef enum {
 
 typedef enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32 = 1 } ibm_precision;
 
+/* Arithmetic of the Arnoldi process (Schur products, Gram-Schmidt, solution
+ * update) inside FGMRES.  IBM_ARNOLDI_FP64: native FP64.  IBM_ARNOLDI_DS:
+ * vectors held as pairs hi + lo of FP32 numbers (about 48 significant bits),
+ * products and sums by error-free transformations on the FP32 pipes; only
+ * with the FP32 V-cycle on grids with nx a multiple of 4 (otherwise FP64 is
+ * used).  In both, the residual b - S~ x that decides convergence and starts
+ * every restart cycle is computed in native FP64. */
+typedef enum { IBM_ARNOLDI_FP64 = 0, IBM_ARNOLDI_DS = 1 } ibm_arnoldi;
+
 /* Grid description: cell counts, cell width, Reynolds number and time step
  * (a = 3/(2 dt) and nu = 1/Re enter the BDF2 predictor, Eq. (ustar), and the
  * correction right-hand sides below Eq. (Saddle)). */
@@ -94,6 +103,7 @@ typedef struct {
   int32_t helm_maxit;    /* predictor outer (FP64 defect) iterations         */
   int32_t with_advection;/* 1: include the explicit convective term of
                             Eq. (ustar) in the predictor                     */
+  int32_t arnoldi;       /* ibm_arnoldi                                      */
 } ibm_solve_opts;
 
 #define IBM_HIST_MAX 256
@@ -112,7 +122,7 @@ typedef struct {
 
 /* Fills *opts with defaults: FP32 V-cycle, rtol 1e-8, maxit 200, restart 40,
  * Chebyshev (2,2), single Gram-Schmidt pass, helm_rtol 1e-10, helm_maxit 8,
- * advection on. */
+ * advection on, double-single Arnoldi process. */
 void ibm_default_opts(ibm_solve_opts* opts);
 
 /* Creates a context for one grid and allocates the grid-sized workspace

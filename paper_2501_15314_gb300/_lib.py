@@ -23,6 +23,8 @@ IBM_ERR_MARKER_DOMAIN = 7
 IBM_ERR_STATE = 8
 IBM_PREC_FP64 = 0
 IBM_PREC_FP32 = 1
+IBM_ARNOLDI_FP64 = 0
+IBM_ARNOLDI_DS = 1
 HIST_MAX = 256
 
 STATUS_NAMES = {0: "IBM_OK", 1: "IBM_ERR_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_NOMEM",
@@ -39,7 +41,7 @@ class ibm_solve_opts(C.Structure):
     _fields_ = [("precond_prec", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32),
                 ("restart", C.c_int32), ("mg_pre", C.c_int32), ("mg_post", C.c_int32),
                 ("reorth", C.c_int32), ("helm_rtol", C.c_double), ("helm_maxit", C.c_int32),
-                ("with_advection", C.c_int32)]
+                ("with_advection", C.c_int32), ("arnoldi", C.c_int32)]
 
 
 class ibm_solve_stats(C.Structure):

@@ -101,6 +101,8 @@ ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o) {
     return set_err(c, IBM_ERR_ARG, "mg_pre, mg_post in 0..4, not both 0");
   if (!(o->helm_rtol > 0.0) || o->helm_maxit < 1)
     return set_err(c, IBM_ERR_ARG, "need helm_rtol > 0 and helm_maxit >= 1");
+  if (o->arnoldi != IBM_ARNOLDI_FP64 && o->arnoldi != IBM_ARNOLDI_DS)
+    return set_err(c, IBM_ERR_ARG, "arnoldi must be IBM_ARNOLDI_FP64 or IBM_ARNOLDI_DS");
   return IBM_OK;
 }
 
@@ -250,6 +252,7 @@ void ibm_default_opts(ibm_solve_opts* o) {
   o->helm_rtol = 1e-10;
   o->helm_maxit = 8;
   o->with_advection = 1;
+  o->arnoldi = IBM_ARNOLDI_DS;
 }
 
 ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {

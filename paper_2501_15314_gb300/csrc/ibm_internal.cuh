@@ -196,6 +196,7 @@ void launch_predictor_rhs(Dims d, const double* u_n, const double* u_nm1,
 ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);
 // t[d][k] = scale * (B v)_{k,d} = scale * (R^T G v)_{k,d}
 void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t);
+void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t);
 // out[cell] += scale * (G^T R t)[cell] on the shell cells
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);
 // U[d][k] = (R^T u)_{k,d}
@@ -234,6 +235,15 @@ ibm_status exclusive_scan(ibm_ctx* c, const int32_t* in, int32_t* out, int64_t n
 // ---- multigrid (multigrid.cu) ----
 ibm_status mg_setup(ibm_ctx* c);
 ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, int post);
+ibm_status mg_vcycle_f32(ibm_ctx* c, const float* r, float* z, int pre, int post);
+// V-cycle on the leading parts of an interleaved (hi, lo) pair vector
+ibm_status mg_vcycle_pair(ibm_ctx* c, const float2* r, float* z, int pre, int post);
+
+// ---- double-single Arnoldi process (krylov_df.cu) ----
+bool ds_supported(const ibm_ctx* c);
+ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w);
+ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
+                           ibm_solve_stats* st, bool x_is_zero);
 
 // ---- solver (krylov.cu) ----
 ibm_status schur_apply(ibm_ctx* c, const double* v, double* out);

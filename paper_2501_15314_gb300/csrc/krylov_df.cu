@@ -1,0 +1,556 @@
+// Arnoldi process of the mixed-precision FGMRES in double-single arithmetic.
+//
+// GB300 executes FP64 (and FP64<->FP32 conversions) at about 1/58 of its FP32
+// rate, which made the FP64 Schur product and Gram-Schmidt passes ALU-bound.
+// In the mixed form (FP32 V-cycle) the Krylov vectors are therefore held as
+// unevaluated sums hi + lo of two FP32 numbers ("double-single", about 48
+// significant bits), and the Schur product L z (z = V-cycle output, exactly
+// FP32), the multi-dot, the axpy + norm and the solution update run on the
+// FP32 pipes with error-free transformations:
+//   two_sum(a, b):  s = a + b, e = (a - (s - bb)) + (b - bb), bb = s - a
+//                   (Knuth), exact: a + b = s + e;
+//   two_prod(a, b): p = a b, e = fma(a, b, -p), exact: a b = p + e.
+// The marker term of S~ stays FP64 (it touches ~1% of the cells), the true
+// residual b - S~ x that decides convergence (and restarts) is evaluated in
+// native FP64, and dot products are reduced to FP64 per block.  Explicit
+// __f*_rn intrinsics keep the compiler from contracting or re-associating the
+// transformations.
+#include <cmath>
+#include <vector>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+namespace {
+
+constexpr int RT = kRedThreads;
+constexpr int kOutStride = kMaxRestart + 2;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct dsf {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dsf two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dsf fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dsf two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// (a.hi + a.lo) + (b.hi + b.lo)
+__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
+  dsf s = two_sum(a.hi, b.hi);
+  const dsf t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+// (a.hi + a.lo) * (b.hi + b.lo), dropping lo*lo  (used by the Laplacian's 1/h^2)
+__device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {
+  dsf p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dsf d_to_ds(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ dsf ds_shfl_down(dsf a, int o) {
+  return {__shfl_down_sync(kFull, a.hi, o), __shfl_down_sync(kFull, a.lo, o)};
+}
+
+// Reduces NQ double-single values across the block (warp shuffles, then the
+// warps in order) and stores the block sums as FP64 in part[block][q].
+template <int NQ>
+__device__ __forceinline__ void block_reduce_ds(dsf (&acc)[NQ], int nq, double* part) {
+  __shared__ float sh_hi[RT / 32][NQ];
+  __shared__ float sh_lo[RT / 32][NQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    dsf v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = ds_add(v, ds_shfl_down(v, o));
+    if (lane == 0) {
+      sh_hi[wid][q] = v.hi;
+      sh_lo[wid][q] = v.lo;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nq; q += RT) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) s += (double)sh_hi[w][q] + (double)sh_lo[w][q];
+    part[(int64_t)blockIdx.x * kOutStride + q] = s;
+  }
+}
+
+// hi/lo split of an FP64 vector into interleaved pairs
+__global__ void k_split(const double* __restrict__ x, float2* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const dsf d = d_to_ds(x[i]);
+    v[i] = make_float2(d.hi, d.lo);
+  }
+}
+
+// w = L z for FP32 z in double-single: the 7-point difference
+// nn z_c - sum of neighbours is summed exactly (two_sum chain), then scaled by
+// 1/h^2 (split into hi + lo).  Four cells per thread, x-neighbours by
+// shuffles, z by the march (as the FP32 smoothers).
+constexpr int LVY = 8;
+
+__device__ __forceinline__ dsf lap_cell(float zc, const float (&nb)[6], int nn, dsf ih2) {
+  // exact nn * zc as a pair, then subtract each neighbour exactly
+  dsf acc = two_prod((float)nn, zc);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const dsf t = two_sum(acc.hi, -nb[q]);
+    acc.hi = t.hi;
+    acc.lo = __fadd_rn(acc.lo, t.lo);
+  }
+  acc = fast_two_sum(acc.hi, acc.lo);
+  return ds_mul(acc, ih2);
+}
+
+__global__ void __launch_bounds__(32 * LVY) k_lap_ds(Dims d, const float* __restrict__ z,
+                                                     float2* __restrict__ w, float ih2_hi,
+                                                     float ih2_lo, int zc) {
+  const int lane = threadIdx.x;
+  const int i0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * LVY + threadIdx.y;
+  const bool act = i0 < d.nx && j < d.ny;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i0;
+  const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const dsf ih2 = {ih2_hi, ih2_lo};
+  const int ny_c = (j > 0) + (j < d.ny - 1);
+  const int nxq[4] = {(i0 > 0) + 1, 2, 2, 1 + (i0 + 3 < d.nx - 1)};
+  auto ld4 = [&](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
+  float4 zp = (act && z0 > 0) ? ld4(z + c - sz) : Z4;
+  float4 zcur = act ? ld4(z + c) : Z4;
+  for (int zz = z0; zz < z1; ++zz, c += sz) {
+    const float4 zn = (act && zz + 1 < d.nz) ? ld4(z + c + sz) : Z4;
+    const float4 ym = (act && j > 0) ? ld4(z + c - sy) : Z4;
+    const float4 yp = (act && j < d.ny - 1) ? ld4(z + c + sy) : Z4;
+    float left = __shfl_up_sync(kFull, zcur.w, 1);
+    float right = __shfl_down_sync(kFull, zcur.x, 1);
+    if (lane == 0) left = (act && i0 > 0) ? __ldg(z + c - 1) : 0.f;
+    if (lane == 31) right = (act && i0 + 4 < d.nx) ? __ldg(z + c + 4) : 0.f;
+    const int zn_c = (zz > 0) + (zz < d.nz - 1);
+    const float cv[4] = {zcur.x, zcur.y, zcur.z, zcur.w};
+    const float xl[4] = {left, zcur.x, zcur.y, zcur.z};
+    const float xr[4] = {zcur.y, zcur.z, zcur.w, right};
+    const float vym[4] = {ym.x, ym.y, ym.z, ym.w};
+    const float vyp[4] = {yp.x, yp.y, yp.z, yp.w};
+    const float vzp[4] = {zp.x, zp.y, zp.z, zp.w};
+    const float vzn[4] = {zn.x, zn.y, zn.z, zn.w};
+    float ohi[4], olo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // missing neighbours contribute 0 and are not counted
+      const float nb[6] = {xl[q], xr[q], vym[q], vyp[q], vzp[q], vzn[q]};
+      const dsf v = lap_cell(cv[q], nb, nxq[q] + ny_c + zn_c, ih2);
+      ohi[q] = v.hi;
+      olo[q] = v.lo;
+    }
+    if (act) {
+      float4* wp = reinterpret_cast<float4*>(w + c);
+      wp[0] = make_float4(ohi[0], olo[0], ohi[1], olo[1]);
+      wp[1] = make_float4(ohi[2], olo[2], ohi[3], olo[3]);
+    }
+    zp = zcur;
+    zcur = zn;
+  }
+}
+
+// Shell cells: w[c] += scale * (G^T R t)[c] with the FP64 sum of the cell's
+// entries (interleaved layout, as k_shell_gradt), added to the pair in FP64.
+__global__ void k_shell_gradt_ds(int64_t n_shell, const int32_t* __restrict__ shell_cell,
+                                 const int32_t* __restrict__ base, const int32_t* __restrict__ len,
+                                 const int32_t* __restrict__ ekey,
+                                 const double* __restrict__ ecoef, int64_t n_ell, int64_t nmk,
+                                 const double* __restrict__ t, double scale,
+                                 float2* __restrict__ wv) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n_shell) return;
+  const int64_t g = q >> 5;
+  const int lane = (int)(q & 31);
+  const int32_t L = len[g];
+  int64_t idx = base[g] + lane;
+  double acc = 0.0;
+  for (int p = 0; p < L; ++p, idx += 32) {
+    const int64_t k = ekey[idx] >> 6;
+    acc = fma(ecoef[idx], t[k], acc);
+    acc = fma(ecoef[n_ell + idx], t[nmk + k], acc);
+    acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
+  }
+  const int64_t c = shell_cell[q];
+  const float2 wc = wv[c];
+  const double v = (double)wc.x + (double)wc.y + scale * acc;
+  const dsf r = d_to_ds(v);
+  wv[c] = make_float2(r.hi, r.lo);
+}
+
+// Compensated accumulation of products: the running FP32 sum S and an FP32
+// accumulator E of everything S cannot hold (exact rounding errors of the
+// leading products and of the additions, plus the hi*lo cross terms).  The
+// value is S + E; E stays about 2^-24 |S|, so its own rounding is far below
+// the 2^-48 level of the pair representation.
+struct Comp {
+  float s, e;
+};
+
+__device__ __forceinline__ void comp_add_prod(Comp& acc, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);         // exact error of the leading product
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const dsf t = two_sum(acc.s, p);
+  acc.s = t.hi;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(e, t.lo));
+}
+
+__device__ __forceinline__ void comp_add_prod_f(Comp& acc, float ah, float al, float b) {
+  const float p = __fmul_rn(ah, b);
+  float e = __fmaf_rn(ah, b, -p);
+  e = __fmaf_rn(al, b, e);
+  const dsf t = two_sum(acc.s, p);
+  acc.s = t.hi;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(e, t.lo));
+}
+
+// part[b][q] = <w, V_q> over the block's elements (compensated FP32 sums,
+// block totals in FP64).
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_multidot_ds(const float2* __restrict__ w,
+                                                    const float2* __restrict__ V, int64_t ld,
+                                                    int nq, int64_t n, double* __restrict__ part) {
+  Comp acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    const float2 wi = __ldg(w + i);
+    float2 v[NQ];   // all loads first, then the arithmetic
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = q < nq ? __ldg(V + q * ld + i) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) comp_add_prod(acc[q], wi.x, wi.y, v[q].x, v[q].y);
+  }
+  dsf r[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) r[q] = fast_two_sum(acc[q].s, acc[q].e);
+  block_reduce_ds<NQ>(r, nq, part);
+}
+
+// w -= sum_q coef[q] V_q (coef as pairs), part[b][0] = sum of w^2 (FP64)
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_axpy_norm_ds(float2* __restrict__ w,
+                                                     const float2* __restrict__ V, int64_t ld,
+                                                     int nq, const float2* __restrict__ coef,
+                                                     int64_t n, double* __restrict__ part) {
+  float ch[NQ], cl[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float2 v = q < nq ? coef[q] : make_float2(0.f, 0.f);
+    ch[q] = v.x;
+    cl[q] = v.y;
+  }
+  Comp nrm = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    const float2 wi = w[i];
+    float2 v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = q < nq ? __ldg(V + q * ld + i) : make_float2(0.f, 0.f);
+    Comp t = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) comp_add_prod(t, ch[q], cl[q], v[q].x, v[q].y);
+    // w - (t.s + t.e) as a normalised pair
+    const dsf d = two_sum(wi.x, -t.s);
+    const dsf wn = fast_two_sum(d.hi, __fadd_rn(d.lo, __fsub_rn(wi.y, t.e)));
+    w[i] = make_float2(wn.hi, wn.lo);
+    comp_add_prod(nrm, wn.hi, wn.lo, wn.hi, wn.lo);
+  }
+  dsf r[1] = {fast_two_sum(nrm.s, nrm.e)};
+  block_reduce_ds<1>(r, 1, part);
+}
+
+// out[q] = sum_b part[b][q] (fixed order); quot[q] = out[q] / div[q] as an
+// FP64 value and as a hi/lo pair
+__global__ void __launch_bounds__(RT) k_final_reduce_ds(const double* __restrict__ part, int nb,
+                                                        double* __restrict__ out,
+                                                        const double* __restrict__ div,
+                                                        double* __restrict__ quot,
+                                                        float2* __restrict__ quot_ds) {
+  const int q = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * kOutStride + q];
+  __shared__ double sh[RT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < RT / 32; ++w) t += sh[w];
+    out[q] = t;
+    if (div) {
+      const double qv = t / div[q];
+      quot[q] = qv;
+      const dsf p = d_to_ds(qv);
+      quot_ds[q] = make_float2(p.hi, p.lo);
+    }
+  }
+}
+
+// x += sum_q y[q] Z_q for FP32 Z and double-single y, accumulated with the
+// compensated scheme and added to the FP64 x once.
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_gemv_ds(double* __restrict__ x,
+                                                const float* __restrict__ Z, int64_t ld, int nq,
+                                                const float2* __restrict__ y, int64_t n) {
+  float yh[NQ], yl[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float2 v = q < nq ? y[q] : make_float2(0.f, 0.f);
+    yh[q] = v.x;
+    yl[q] = v.y;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    float zq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) zq[q] = q < nq ? __ldg(Z + q * ld + i) : 0.f;
+    Comp acc = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) comp_add_prod_f(acc, yh[q], yl[q], zq[q]);
+    x[i] += (double)acc.s + (double)acc.e;
+  }
+}
+
+#define IBM_NQ_DISPATCH_DS(nq, KERNEL, ...)                                 \
+  do {                                                                      \
+    count_launch();                                                         \
+    if ((nq) <= 2) KERNEL<2><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);        \
+    else if ((nq) <= 4) KERNEL<4><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
+    else if ((nq) <= 8) KERNEL<8><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
+    else if ((nq) <= 12) KERNEL<12><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 16) KERNEL<16><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 24) KERNEL<24><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 32) KERNEL<32><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else if ((nq) <= 48) KERNEL<48><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else KERNEL<kMaxRestart + 1><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);    \
+  } while (0)
+
+int lap_zc(Dims d) {
+  const int64_t bxy = (int64_t)div_up(d.nx / 4, 32) * div_up(d.ny, LVY);
+  int64_t zc = (int64_t)d.nz * bxy / (152 * 4);
+  zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
+  return (int)zc;
+}
+
+ibm_status fetch(ibm_ctx* c, const double* dev, int n) {
+  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, dev, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                              c->stream));
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return IBM_OK;
+}
+
+}  // namespace
+
+bool ds_supported(const ibm_ctx* c) { return c->d.nx % 4 == 0 && c->n_levels > 1; }
+
+// w = S~ z for FP32 z, w as a hi/lo pair: double-single Laplacian, FP64 marker
+// term gathered from z and added on the shell cells.
+ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
+  cudaStream_t s = c->stream;
+  const double ih2 = 1.0 / (c->h * c->h);
+  const float ih2_hi = (float)ih2;
+  const float ih2_lo = (float)(ih2 - (double)ih2_hi);
+  const int zc = lap_zc(c->d);
+  int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
+  count_launch();
+  k_lap_ds<<<dim3(div_up(c->d.nx / 4, 32), div_up(c->d.ny, LVY), div_up(c->d.nz, zc)),
+             dim3(32, LVY), 0, s>>>(c->d, z, w, ih2_hi, ih2_lo, zc);
+  prof_end(c, ph);
+  const MarkerData& m = c->mk;
+  if (m.n > 0 && m.n_shell > 0) {
+    ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
+    launch_marker_grad_interp_f32(c, z, 2.0, m.t);
+    count_launch();
+    k_shell_gradt_ds<<<div_up(m.n_shell, 256), 256, 0, s>>>(
+        m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, m.t,
+        1.0, w);
+    prof_end(c, ph);
+  }
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
+                           ibm_solve_stats* st, bool x_is_zero) {
+  // Same flexible GMRES as fgmres_solve (unnormalised Arnoldi vectors with
+  // squared norms nrm2[i] on the device), with the vectors as FP32 pairs:
+  // Vhi/Vlo reuse the FP64 basis storage, Z holds the FP32 V-cycle outputs.
+  cudaStream_t s = c->stream;
+  const int64_t m = c->m;
+  const int restart = o->restart;
+  double* part = c->red_part;
+  double* raw = c->red_out;
+  double* coef = c->red_out + kOutStride;
+  float2* coef_ds = reinterpret_cast<float2*>(c->red_out + 2 * kOutStride);
+  double* nrm2 = c->red_out + 4 * kOutStride;
+  float2* y_ds = reinterpret_cast<float2*>(c->red_out + 5 * kOutStride);
+  double* sdev = c->red_out + 6 * kOutStride;
+  double* hr = c->host_red;
+  float2* V2 = reinterpret_cast<float2*>(c->V);
+  float* Zf = reinterpret_cast<float*>(c->Z);
+  double* r64 = c->c1;
+  ibm_status stt;
+
+  launch_dot(b, b, m, part, sdev, s);
+  IBM_LAUNCH_CHECK(c);
+  if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
+  const double bnorm = std::sqrt(hr[0]);
+  if (!std::isfinite(bnorm)) return set_err(c, IBM_ERR_NAN, "non-finite right-hand side");
+  int total = 0, cycles = 0;
+  double relres = 0.0;
+  if (bnorm == 0.0) {
+    IBM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * m, s));
+    if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; }
+    return IBM_OK;
+  }
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart),
+      g(restart + 1), y(restart), rn(restart + 1);
+  auto Hm = [&](int i, int j) -> double& { return H[(size_t)i * restart + j]; };
+  bool converged = false, first = true;
+  ibm_status final_status = IBM_OK;
+  while (true) {
+    // FP64 residual r0 = b - S~ x (r0 = b for a zero first guess)
+    double beta;
+    const double* r0 = b;
+    if (first && x_is_zero) {
+      IBM_CUDA(c, cudaMemcpyAsync(nrm2, sdev, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      beta = bnorm;
+    } else {
+      if ((stt = schur_apply(c, x, r64)) != IBM_OK) return stt;
+      launch_axpby(b, 1.0, r64, -1.0, r64, m, s);
+      launch_dot(r64, r64, m, part, nrm2, s);
+      IBM_LAUNCH_CHECK(c);
+      if ((stt = fetch(c, nrm2, 1)) != IBM_OK) return stt;
+      beta = std::sqrt(hr[0]);
+      r0 = r64;
+    }
+    first = false;
+    if (!std::isfinite(beta)) return set_err(c, IBM_ERR_NAN, "non-finite residual");
+    relres = beta / bnorm;
+    if (relres <= o->rtol) { converged = true; break; }
+    if (total >= o->maxit) break;
+    count_launch();
+    k_split<<<kRedBlocks, RT, 0, s>>>(r0, V2, m);
+    rn[0] = beta;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jused = 0;
+    bool breakdown = false;
+    for (int j = 0; j < restart && total < o->maxit; ++j) {
+      float* zj = Zf + (int64_t)j * m;
+      float2* w = V2 + (int64_t)(j + 1) * m;
+      int ph = prof_begin(c, IBM_PROF_VCYCLE);
+      if ((stt = mg_vcycle_pair(c, V2 + (int64_t)j * m, zj, o->mg_pre, o->mg_post)) != IBM_OK)
+        return stt;
+      prof_end(c, ph);
+      if ((stt = schur_apply_ds(c, zj, w)) != IBM_OK) return stt;
+      const int nq = j + 1;
+      ph = prof_begin(c, IBM_PROF_MULTIDOT);
+      IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
+      count_launch();
+      k_final_reduce_ds<<<nq, RT, 0, s>>>(part, kRedBlocks, raw, nrm2, coef, coef_ds);
+      prof_end(c, ph);
+      ph = prof_begin(c, IBM_PROF_AXPY_NORM);
+      IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part);
+      count_launch();
+      k_final_reduce_ds<<<1, RT, 0, s>>>(part, kRedBlocks, nrm2 + j + 1, nullptr, nullptr,
+                                          nullptr);
+      prof_end(c, ph);
+      IBM_LAUNCH_CHECK(c);
+      IBM_CUDA(c, cudaMemcpyAsync(hr, raw, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+      IBM_CUDA(c, cudaMemcpyAsync(hr + 4 * kOutStride + j + 1, nrm2 + j + 1, sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
+      IBM_CUDA(c, cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) Hm(i, j) = hr[i] / rn[i];
+      const double hn = std::sqrt(hr[4 * kOutStride + j + 1]);
+      if (!std::isfinite(hn)) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
+      Hm(j + 1, j) = hn;
+      rn[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
+        Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
+        Hm(i, j) = t;
+      }
+      const double den = std::hypot(Hm(j, j), Hm(j + 1, j));
+      if (den == 0.0) { breakdown = true; break; }
+      cs[j] = Hm(j, j) / den;
+      sn[j] = Hm(j + 1, j) / den;
+      Hm(j, j) = den;
+      Hm(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      jused = j + 1;
+      if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = std::fabs(g[j + 1]) / bnorm;
+      if (std::fabs(g[j + 1]) / bnorm <= o->rtol || hn == 0.0) break;
+    }
+    if (jused > 0) {
+      for (int i = jused - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int q = i + 1; q < jused; ++q) acc -= Hm(i, q) * y[q];
+        y[i] = acc / Hm(i, i);
+      }
+      float* hy = reinterpret_cast<float*>(hr + 5 * kOutStride);
+      for (int i = 0; i < jused; ++i) {
+        const float yh = (float)y[i];
+        hy[2 * i] = yh;
+        hy[2 * i + 1] = (float)(y[i] - (double)yh);
+      }
+      IBM_CUDA(c, cudaMemcpyAsync(y_ds, hy, sizeof(float2) * jused, cudaMemcpyHostToDevice, s));
+      IBM_NQ_DISPATCH_DS(jused, k_gemv_ds, x, Zf, m, jused, y_ds, m);
+      IBM_LAUNCH_CHECK(c);
+    }
+    ++cycles;
+    if (breakdown && jused == 0) { final_status = IBM_ERR_BREAKDOWN; break; }
+  }
+  launch_sum(x, m, part, sdev, s);
+  launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
+  IBM_LAUNCH_CHECK(c);
+  if (st) {
+    st->iters = total;
+    st->restarts = cycles;
+    st->relres_true = relres;
+  }
+  if (final_status != IBM_OK) return set_err(c, final_status, "FGMRES breakdown");
+  if (!converged) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "FGMRES did not reach rtol %.3g in %d iterations (relres %.3g)",
+             o->rtol, total, relres);
+    return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
+  }
+  return IBM_OK;
+}
+
+}  // namespace ibm

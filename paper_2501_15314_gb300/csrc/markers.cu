@@ -167,7 +167,8 @@ __device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcom
 // footprint: sum_a cw_d[a] sum_b w_e1[b] sum_c w_e2[c] v.  Four consecutive
 // threads hold a = 0..3 of one (marker, component) and combine in a fixed
 // order with warp shuffles.
-__global__ void k_marker_grad_interp(Dims d, MkView mk, const double* __restrict__ v,
+template <typename TV>
+__global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v,
                                      double scale, double* __restrict__ t) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = 12 * mk.n;
@@ -194,7 +195,7 @@ __global__ void k_marker_grad_interp(Dims d, MkView mk, const double* __restrict
       for (int q2 = 0; q2 < 3; ++q2) {
         g[e2] = b2 + q2;
         const int64_t cell = g[0] + g[1] * sy + (int64_t)g[2] * sz;
-        acc2 = fma(mk.wc[(e2 * 3 + q2) * mk.n + k], __ldg(v + cell), acc2);
+        acc2 = fma(mk.wc[(e2 * 3 + q2) * mk.n + k], (double)__ldg(v + cell), acc2);
       }
       acc1 = fma(mk.wc[(e1 * 3 + q1) * mk.n + k], acc2, acc1);
     }
@@ -605,7 +606,16 @@ void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
-  k_marker_grad_interp<<<div_up(12 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v, scale, t);
+  k_marker_grad_interp<double><<<div_up(12 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v,
+                                                                              scale, t);
+}
+
+void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0) return;
+  count_launch();
+  k_marker_grad_interp<float><<<div_up(12 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v,
+                                                                             scale, t);
 }
 
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out) {

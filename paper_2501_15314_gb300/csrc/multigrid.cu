@@ -311,6 +311,13 @@ __device__ __forceinline__ float4 ld4_any(const double* p) {
   const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
   return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
+// leading parts of four interleaved (hi, lo) pairs
+__device__ __forceinline__ float4 ld4_any(const float2* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  return make_float4(a.x, a.z, b.x, b.z);
+}
+__device__ __forceinline__ float ld1_any(const float2* p) { return __ldg(p).x; }
 __device__ __forceinline__ float ld1_any(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld1_any(const double* p) { return (float)__ldg(p); }
 
@@ -687,9 +694,11 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
       k_first_v4<TB><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(
           L.d, b, bcopy, x, (float)(w[0] * h2), (float)(two ? w[1] : 0.0), (float)h2, two, zc);
   }
-  if (!vec)
-    k_first<T, TB><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(
-        L.d, b, bcopy, x, w_over_n<T>(w[0] * h2), w_over_n<T>(two ? w[1] : 0.0), (T)h2, two);
+  if constexpr (!std::is_same<TB, float2>::value) {
+    if (!vec)
+      k_first<T, TB><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(
+          L.d, b, bcopy, x, w_over_n<T>(w[0] * h2), w_over_n<T>(two ? w[1] : 0.0), (T)h2, two);
+  }
   prof_end(c, ph);
   const T* bb = bcopy ? bcopy : reinterpret_cast<const T*>(b);
   T* cur = x;
@@ -914,6 +923,51 @@ ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, 
     coarse_correct<double>(c, 0, r, z, pre, post, s);
     post_smooth<double, double>(c, 0, r, z, L0.t64, post, z, s);
   }
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+// One V-cycle with FP32 input and output (the mixed Arnoldi process keeps
+// its vectors as FP32 pairs and feeds the leading FP32 part): r and z must not
+// alias the level-0 work arrays.
+ibm_status mg_vcycle_f32(ibm_ctx* c, const float* r, float* z, int pre, int post) {
+  cudaStream_t s = c->stream;
+  MGLevel& L0 = c->lv[0];
+  if (c->n_levels == 1 || !vec_ok(L0.d)) {
+    // small or odd grids: through the FP64 cycle
+    count_launch();
+    k_convert<float, double><<<kRedBlocks, 256, 0, s>>>(r, L0.b64, L0.m);
+    ibm_status st = mg_vcycle(c, L0.b64, L0.t64, IBM_PREC_FP32, pre, post);
+    if (st != IBM_OK) return st;
+    count_launch();
+    k_convert<double, float><<<kRedBlocks, 256, 0, s>>>(L0.t64, z, L0.m);
+    IBM_LAUNCH_CHECK(c);
+    return IBM_OK;
+  }
+  if (pre > 0) pre_smooth<float, float>(c, 0, r, nullptr, L0.x32, L0.t32, pre, s);
+  coarse_correct<float>(c, 0, r, L0.x32, pre, post, s);
+  post_smooth<float, float>(c, 0, r, L0.x32, L0.t32, post, z, s);
+  IBM_LAUNCH_CHECK(c);
+  return IBM_OK;
+}
+
+ibm_status mg_vcycle_pair(ibm_ctx* c, const float2* r, float* z, int pre, int post) {
+  cudaStream_t s = c->stream;
+  MGLevel& L0 = c->lv[0];
+  if (c->n_levels == 1 || !vec_ok(L0.d))
+    return set_err(c, IBM_ERR_ARG, "pair V-cycle needs a multilevel grid with nx % 4 == 0");
+  // the first kernel rounds nothing (the leading parts are FP32) and keeps a
+  // contiguous copy of them for the level's later kernels
+  const int zc = vec_zc(L0.d);
+  if (pre > 0) {
+    pre_smooth<float, float2>(c, 0, r, L0.b32, L0.x32, L0.t32, pre, s);
+  } else {
+    count_launch();
+    k_first_v4<float2><<<vec_grid(L0.d, zc), dim3(32, VY), 0, s>>>(L0.d, r, L0.b32, L0.t32, 0.f,
+                                                                   0.f, 0.f, 0, zc);
+  }
+  coarse_correct<float>(c, 0, L0.b32, L0.x32, pre, post, s);
+  post_smooth<float, float>(c, 0, L0.b32, L0.x32, L0.t32, post, z, s);
   IBM_LAUNCH_CHECK(c);
   return IBM_OK;
 }

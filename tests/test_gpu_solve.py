@@ -33,10 +33,14 @@ def setup(request, cuda_device):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-def test_solve_parity(setup, prec):
+MODES = [(0, 0), (1, 1), (1, 0)]
+MODE_IDS = ["fp64_vcycle", "fp32_vcycle_ds_arnoldi", "fp32_vcycle_fp64_arnoldi"]
+
+
+@pytest.mark.parametrize("prec,arnoldi", MODES, ids=MODE_IDS)
+def test_solve_parity(setup, prec, arnoldi):
     case, g, s, sysm, b, ref = setup
-    p, st = s.solve_schur(dev(b), rtol=1e-13, precond_prec=prec, maxit=300)
+    p, st = s.solve_schur(dev(b), rtol=1e-13, precond_prec=prec, arnoldi=arnoldi, maxit=300)
     assert st["relres_true"] <= 1e-13
     ph = host(p)
     assert abs(ph.mean()) < 1e-12 * np.abs(ph).max()
@@ -45,10 +49,10 @@ def test_solve_parity(setup, prec):
     assert rel(sysm.apply_S_tilde(ph), b) < 2e-13
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-def test_solve_throughput_setting(setup, prec):
+@pytest.mark.parametrize("prec,arnoldi", MODES, ids=MODE_IDS)
+def test_solve_throughput_setting(setup, prec, arnoldi):
     case, g, s, sysm, b, ref = setup
-    p, st = s.solve_schur(dev(b), rtol=1e-8, precond_prec=prec)
+    p, st = s.solve_schur(dev(b), rtol=1e-8, precond_prec=prec, arnoldi=arnoldi)
     ph = host(p)
     assert rel(sysm.apply_S_tilde(ph), b) <= 1e-8 * 1.001
     assert rel(ph, ref) < 1e-6
