@@ -11,8 +11,12 @@ FGMRES to a relative residual of 1e-8.
 A step = marker binning (ibm_set_markers) + ibm_step (predictor, correction
 right-hand sides, Schur solve, force recovery, update, diagnostics): every
 row of the hot path, one Schur solve per step, so steps/s = Schur solves/s.
-The headline `value` uses the mixed form (FP64 FGMRES, FP32 V-cycle); the FP64
-form and the solve alone are reported beside it.
+The headline `value` uses the mixed form (FP32 V-cycle, double-single Arnoldi
+process, FP64 true residual); the plain FP64 form (FP64 V-cycle and Arnoldi)
+and the solve alone are reported beside it.
+
+`--profile-step` runs one warm-up step and then one step bracketed by
+cudaProfilerStart/Stop (for `ncu --profile-from-start off`), and exits.
 
 Multi-GPU: replicas only (one independent workload per rank, no collective on
 the data path); `value` sums the ranks' step rates over the slowest rank's
@@ -220,9 +224,10 @@ def run_ours(args):
     out = dict(u=torch.empty_like(zf), p=torch.empty_like(zc), F=torch.empty_like(zk))
     stream = s.stream
 
-    def step(prec):
+    def step(prec, arnoldi=_lib.IBM_ARNOLDI_DS):
         s.set_markers(X)
-        _, st = s.step(zf, zf, zc, zk, U, f, out=out, precond_prec=prec, rtol=1e-8)
+        _, st = s.step(zf, zf, zc, zk, U, f, out=out, precond_prec=prec, arnoldi=arnoldi,
+                       rtol=1e-8)
         return st
 
     def barrier():
@@ -259,10 +264,10 @@ def run_ours(args):
     s.profile_enable(False)
     clk = clocks.stop()
 
-    # ---- FP64 form ----
+    # ---- FP64 form (FP64 V-cycle, FP64 Arnoldi) ----
     k64 = max(1, args.steps // 2)
-    step(_lib.IBM_PREC_FP64)
-    ms_fp64, st_fp64 = timed(lambda: step(_lib.IBM_PREC_FP64), k64)
+    step(_lib.IBM_PREC_FP64, _lib.IBM_ARNOLDI_FP64)
+    ms_fp64, st_fp64 = timed(lambda: step(_lib.IBM_PREC_FP64, _lib.IBM_ARNOLDI_FP64), k64)
 
     # ---- the solve alone, on a right-hand side of the step's form ----
     a = 1.5 / W.dt
@@ -270,9 +275,14 @@ def run_ours(args):
     rhs_F = a * (s.interp(f) - U)
     b = a * s.gradient_t(f) + 2.0 * s.gradient_t(s.spread(rhs_F))
     solve_only = {}
-    for name, prec in (("fp32_vcycle", _lib.IBM_PREC_FP32), ("fp64_vcycle", _lib.IBM_PREC_FP64)):
-        s.solve_schur(b, precond_prec=prec, rtol=1e-8)
-        msq, stq = timed(lambda: s.solve_schur(b, precond_prec=prec, rtol=1e-8)[1], k64)
+    for name, prec, arn in (("fp32_vcycle_ds_arnoldi", _lib.IBM_PREC_FP32, _lib.IBM_ARNOLDI_DS),
+                            ("fp32_vcycle_fp64_arnoldi", _lib.IBM_PREC_FP32,
+                             _lib.IBM_ARNOLDI_FP64),
+                            ("fp64_vcycle_fp64_arnoldi", _lib.IBM_PREC_FP64,
+                             _lib.IBM_ARNOLDI_FP64)):
+        kw = dict(precond_prec=prec, arnoldi=arn, rtol=1e-8)
+        s.solve_schur(b, **kw)
+        msq, stq = timed(lambda: s.solve_schur(b, **kw)[1], k64)
         solve_only[name] = {"solves_per_s": world * 1000.0 / msq, "ms": msq,
                             "iters": stq[-1]["iters"], "relres": stq[-1]["relres_true"]}
 
@@ -300,26 +310,40 @@ def run_ours(args):
     ms_e2e, _ = timed(e2e_step, args.steps)
 
     # ---- roofline of the dominant kernel class ----
+    # algorithmic bytes per launch (DRAM traffic the kernel must move at
+    # least once), summed over the timed region's launches of each class
     hbm, peak_kind = measured_peaks()
-    it_avg = statistics.mean(st["iters"] for st in st_mixed)
+    its = [st["iters"] for st in st_mixed]
+    nf_int = nf
+    gs_dot = sum(sum((j + 2) * 8.0 * m for j in range(it)) for it in its)
+    gs_axpy = sum(sum((j + 3) * 8.0 * m for j in range(it)) for it in its)
     kern = {
-        # name: (profile class, algorithmic bytes per launch)
-        "k_cheb_sweep<float> (finest V-cycle smoothing sweep, FP32)":
-            ("mg_smooth_fine", 12.0 * m),
-        "k_laplacian<double> (7-point FP64 Laplacian in S~ v)": ("laplacian_f64", 16.0 * m),
-        "k_multidot (Gram-Schmidt multi-dot, FP64)":
-            ("multidot", 8.0 * m * ((it_avg + 1) / 2.0 + 1.0)),
-        "k_axpy_norm (Gram-Schmidt axpy+norm, FP64)":
-            ("axpy_norm", 8.0 * m * ((it_avg + 1) / 2.0 + 2.0)),
+        # name: (profile class, total algorithmic bytes over the timed steps)
+        "k_helm_cheb_v4 (predictor FP32 Chebyshev step: read e, e_old, r; write e_new)":
+            ("helm_sweep", 16.0 * nf_int * prof["helm_sweep"]["launches"]),
+        "k_multidot_ds (Gram-Schmidt multi-dot on FP32 pairs: w and V_0..V_j)":
+            ("multidot", gs_dot),
+        "k_axpy_norm_ds (Gram-Schmidt axpy+norm on FP32 pairs: V_0..V_j, w in/out)":
+            ("axpy_norm", gs_axpy),
+        "k_lap_ds (Schur Laplacian, FP32 z in, FP32-pair w out)":
+            ("laplacian_f64", 12.0 * m * prof["laplacian_f64"]["launches"]),
+        "k_first_v4 + k_sweep_v4 (finest V-cycle smoothing)":
+            ("mg_smooth_fine", 40.0 / 3.0 * m * prof["mg_smooth_fine"]["launches"]),
     }
-    best = max(kern, key=lambda kk: prof[kern[kk][0]]["ms"])
-    cls, bytes_per = kern[best]
-    avg_ms = prof[cls]["ms"] / max(1, prof[cls]["launches"])
-    achieved = bytes_per / (avg_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-            "traffic": NCU_TRAFFIC.get(best), "avg_launch_ms": avg_ms,
-            "bytes_per_launch": bytes_per}
+    classes = {}
+    for name, (cls, tot_bytes) in kern.items():
+        t_ms = prof[cls]["ms"]
+        n_l = max(1, prof[cls]["launches"])
+        gbs = tot_bytes / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+        classes[name] = {"ms_per_step": t_ms / args.steps, "launches_per_step":
+                         n_l / args.steps, "achieved_gbs": gbs, "frac": gbs / hbm,
+                         "bytes_per_launch": tot_bytes / n_l, "avg_launch_ms": t_ms / n_l}
+    best = max(classes, key=lambda kk: classes[kk]["ms_per_step"])
+    cb = classes[best]
+    roof = {"bound": "hbm", "kernel": best, "achieved": cb["achieved_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": cb["frac"], "peak_kind": peak_kind,
+            "traffic": NCU_TRAFFIC.get(best), "avg_launch_ms": cb["avg_launch_ms"],
+            "bytes_per_launch": cb["bytes_per_launch"]}
     breakdown = {kk: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
                  for kk, v in prof.items() if v["launches"]}
 
@@ -327,15 +351,18 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 (FGMRES, Schur products) + f32 (V-cycle)", "data": "synthetic",
+            "dtype": "f32 V-cycle + f32-pair (double-single) Arnoldi; f64 residual, markers, "
+                     "predictor", "data": "synthetic",
             "config": workload_config(W),
             "fp64_form": {"value": world * 1000.0 / ms_fp64, "unit": UNIT, "ms_per_step": ms_fp64,
-                          "iters": st_fp64[-1]["iters"]},
+                          "iters": st_fp64[-1]["iters"],
+                          "what": "FP64 V-cycle + FP64 Arnoldi, same step"},
             "solve_only": solve_only,
             "iters": st_mixed[-1]["iters"], "relres_true": st_mixed[-1]["relres_true"],
             "helm_iters": st_mixed[-1]["helm_iters"],
             "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
-            "roofline": roof, "breakdown": breakdown, "gpu_launches": int(launches),
+            "roofline": roof, "kernel_classes": classes, "breakdown": breakdown,
+            "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}}
@@ -356,6 +383,47 @@ def run_ours(args):
     return 0
 
 
+def run_profile_step(args):
+    """One warm-up step, then one step inside cudaProfilerStart/Stop."""
+    import numpy as np
+    import torch
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+    W = wl.config(args.config, secondary=True)
+    if args.grid and args.grid != W.n:
+        # the same bodies and marker count on another grid (smaller captures)
+        W = wl.spheres_workload(f"{W.name}_at{args.grid}", args.grid, W.Re, W.dt, W.centers,
+                                W.radii, W.n_markers, args.config)
+    s = IBMSolver(W.n, Re=W.Re, dt=W.dt)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    X, U, f = dev(W.X), dev(W.U_gamma.ravel()), dev(W.f_body)
+    zf = torch.zeros(s.nf, dtype=torch.float64, device="cuda")
+    zc = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+    zk = torch.zeros(3 * W.n_markers, dtype=torch.float64, device="cuda")
+    prec = _lib.IBM_PREC_FP64 if args.fp64 else _lib.IBM_PREC_FP32
+    arn = _lib.IBM_ARNOLDI_FP64 if args.fp64 else _lib.IBM_ARNOLDI_DS
+
+    def step():
+        s.set_markers(X)
+        return s.step(zf, zf, zc, zk, U, f, precond_prec=prec, arnoldi=arn, rtol=1e-8,
+                      restart=args.restart)[1]
+
+    step()
+    torch.cuda.synchronize()
+    l0 = s.lib.ibm_kernel_launches()
+    torch.cuda.cudart().cudaProfilerStart()
+    t = time.perf_counter()
+    st = step()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile_step": W.name, "ms": 1e3 * t, "iters": st["iters"],
+                      "launches": int(s.lib.ibm_kernel_launches() - l0)}), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,7 +432,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true")
+    ap.add_argument("--fp64", action="store_true", help="profile the plain FP64 form")
+    ap.add_argument("--grid", type=int, default=0, help="profile step: grid size override")
+    ap.add_argument("--restart", type=int, default=40, help="profile step: FGMRES restart")
     args = ap.parse_args()
+    if args.profile_step:
+        return run_profile_step(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -126,7 +126,8 @@ typedef struct {
 void ibm_default_opts(ibm_solve_opts* opts);
 
 /* Creates a context for one grid and allocates the grid-sized workspace
- * (multigrid hierarchy, Krylov bases for restart <= 64, temporaries).
+ * (multigrid hierarchy, temporaries); the Krylov bases are allocated by the
+ * first solve for its restart length (grown when a later solve asks more).
  * stream: a cudaStream_t (may be NULL for the legacy default stream).
  * Requires nx, ny, nz >= 4 and h > 0, Re > 0, dt > 0.  Synchronises. */
 ibm_status ibm_create(const ibm_grid_desc* grid, void* stream, ibm_ctx** out);
@@ -260,7 +261,8 @@ ibm_status ibm_body_forces_noalloc(const double* F, const double* X, const int32
  * ibm_profile_read synchronises the stream and returns, per class, the summed
  * event-measured milliseconds and the number of timed launches. */
 enum {
-  IBM_PROF_LAPLACIAN_F64 = 0,  /* 7-point FP64 Laplacian inside S~ v        */
+  IBM_PROF_LAPLACIAN_F64 = 0,  /* 7-point Laplacian inside S~ v (FP64, or
+                                  double-single in the mixed Arnoldi)       */
   IBM_PROF_SCHUR_MARKERS = 1,  /* B v gather + B^T t shell gather in S~ v   */
   IBM_PROF_VCYCLE = 2,         /* one whole V-cycle (all levels)            */
   IBM_PROF_MULTIDOT = 3,       /* Gram-Schmidt multi-dot (+ final reduce)   */
@@ -270,6 +272,8 @@ enum {
   IBM_PROF_STEP = 7,           /* whole ibm_step                            */
   IBM_PROF_MARKER_BUILD = 8,   /* ibm_set_markers                           */
   IBM_PROF_MG_SMOOTH_FINE = 9, /* one finest-level smoothing sweep kernel   */
+  IBM_PROF_HELM_SWEEP = 10,    /* one inner FP32 Chebyshev step of the
+                                  predictor (middle steps only)             */
   IBM_PROF_NCLASS = 16
 };
 typedef struct {

@@ -52,7 +52,7 @@ class ibm_solve_stats(C.Structure):
 
 PROF_NCLASS = 16
 PROF_NAMES = ["laplacian_f64", "schur_markers", "vcycle", "multidot", "axpy_norm", "predictor",
-              "solve", "step", "marker_build", "mg_smooth_fine"]
+              "solve", "step", "marker_build", "mg_smooth_fine", "helm_sweep"]
 
 
 class ibm_profile(C.Structure):

@@ -218,9 +218,11 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
     for (int q = 1; q < K; ++q) {
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
       const int last = q == K - 1;
+      const int ph = last ? -1 : prof_begin(c, IBM_PROF_HELM_SWEEP);
       launch_helm_cheb(c->d, e, eo, c->g1, nullptr, 0.0, (float)a, (float)nu_h2,
                        (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn,
                        last ? 2 : 1, s);
+      prof_end(c, ph);
       rho_prev = rho;
       float* t = eo; eo = e; e = en; en = t;
     }
@@ -308,8 +310,11 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
     delete c;
     return IBM_ERR_NOMEM;
   }
-  ibm_status st = mg_setup(c);
-  if (st == IBM_OK) st = ensure_krylov(c, 40);
+  // the predictor's FP32 arrays: wall faces beyond the launched x-range are
+  // never written and must read as 0
+  for (float* buf : {c->g1, c->g2, c->g3, c->g4})
+    if (cudaMemset(buf, 0, sizeof(float) * helm_fp32_size(c->d)) != cudaSuccess) ok = false;
+  ibm_status st = ok ? mg_setup(c) : IBM_ERR_CUDA;
   if (st == IBM_OK && cudaDeviceSynchronize() != cudaSuccess) st = IBM_ERR_CUDA;
   if (st != IBM_OK) {
     cudaGetLastError();

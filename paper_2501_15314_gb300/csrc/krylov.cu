@@ -272,7 +272,8 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   // GMRES accepts any z_j; x = Z y uses the same z_j), the Gram-Schmidt
   // coefficients are <w, V_i> / nrm2[i] (formed on the device), and the
   // Hessenberg entries h_ij = <w, V_i> / ||V_i||, h_{j+1,j} = ||w|| on the host.
-  if (o->precond_prec == IBM_PREC_FP32 && o->arnoldi == IBM_ARNOLDI_DS && ds_supported(c))
+  if (o->precond_prec == IBM_PREC_FP32 && o->arnoldi == IBM_ARNOLDI_DS && !o->reorth &&
+      ds_supported(c))
     return fgmres_solve_ds(c, b, x, o, st, x_is_zero);
   cudaStream_t s = c->stream;
   const int64_t m = c->m;

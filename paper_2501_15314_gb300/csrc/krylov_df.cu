@@ -96,12 +96,15 @@ __device__ __forceinline__ void block_reduce_ds(dsf (&acc)[NQ], int nq, double* 
   }
 }
 
-// hi/lo split of an FP64 vector into interleaved pairs
-__global__ void k_split(const double* __restrict__ x, float2* __restrict__ v, int64_t n) {
+// hi/lo split of an FP64 vector into interleaved pairs; the leading parts
+// are also written contiguously to hi (the next V-cycle's input)
+__global__ void k_split(const double* __restrict__ x, float2* __restrict__ v,
+                        float* __restrict__ hi, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const dsf d = d_to_ds(x[i]);
     v[i] = make_float2(d.hi, d.lo);
+    hi[i] = d.hi;
   }
 }
 
@@ -262,7 +265,8 @@ template <int NQ>
 __global__ void __launch_bounds__(RT) k_axpy_norm_ds(float2* __restrict__ w,
                                                      const float2* __restrict__ V, int64_t ld,
                                                      int nq, const float2* __restrict__ coef,
-                                                     int64_t n, double* __restrict__ part) {
+                                                     int64_t n, double* __restrict__ part,
+                                                     float* __restrict__ hi) {
   float ch[NQ], cl[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -284,6 +288,7 @@ __global__ void __launch_bounds__(RT) k_axpy_norm_ds(float2* __restrict__ w,
     const dsf d = two_sum(wi.x, -t.s);
     const dsf wn = fast_two_sum(d.hi, __fadd_rn(d.lo, __fsub_rn(wi.y, t.e)));
     w[i] = make_float2(wn.hi, wn.lo);
+    hi[i] = wn.hi;
     comp_add_prod(nrm, wn.hi, wn.lo, wn.hi, wn.lo);
   }
   dsf r[1] = {fast_two_sum(nrm.s, nrm.e)};
@@ -420,6 +425,8 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   double* hr = c->host_red;
   float2* V2 = reinterpret_cast<float2*>(c->V);
   float* Zf = reinterpret_cast<float*>(c->Z);
+  // leading parts of the newest basis vector, contiguous: the V-cycle input
+  float* vin = c->lv[0].b32;
   double* r64 = c->c1;
   ibm_status stt;
 
@@ -462,7 +469,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     if (relres <= o->rtol) { converged = true; break; }
     if (total >= o->maxit) break;
     count_launch();
-    k_split<<<kRedBlocks, RT, 0, s>>>(r0, V2, m);
+    k_split<<<kRedBlocks, RT, 0, s>>>(r0, V2, vin, m);
     rn[0] = beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -472,8 +479,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       float* zj = Zf + (int64_t)j * m;
       float2* w = V2 + (int64_t)(j + 1) * m;
       int ph = prof_begin(c, IBM_PROF_VCYCLE);
-      if ((stt = mg_vcycle_pair(c, V2 + (int64_t)j * m, zj, o->mg_pre, o->mg_post)) != IBM_OK)
-        return stt;
+      if ((stt = mg_vcycle_f32(c, vin, zj, o->mg_pre, o->mg_post)) != IBM_OK) return stt;
       prof_end(c, ph);
       if ((stt = schur_apply_ds(c, zj, w)) != IBM_OK) return stt;
       const int nq = j + 1;
@@ -483,7 +489,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       k_final_reduce_ds<<<nq, RT, 0, s>>>(part, kRedBlocks, raw, nrm2, coef, coef_ds);
       prof_end(c, ph);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
-      IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part);
+      IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);
       count_launch();
       k_final_reduce_ds<<<1, RT, 0, s>>>(part, kRedBlocks, nrm2 + j + 1, nullptr, nullptr,
                                           nullptr);

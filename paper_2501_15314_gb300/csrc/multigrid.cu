@@ -440,17 +440,25 @@ __global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restri
   float4 bc = act ? ld4_any(b + c) : Z4;
   for (int z = z0; z < z1; ++z, c += sz) {
     const float4 bn = (act && z + 1 < d.nz) ? ld4_any(b + c + sz) : Z4;
-    sb[ty + 1][lane] = bc;
-    if (ty == 0) sb[0][lane] = (act && j > 0) ? ld4_any(b + c - sy) : Z4;
-    if (ty == VY - 1 || j == d.ny - 1)
-      sb[ty + 2][lane] = (act && j < d.ny - 1) ? ld4_any(b + c + sy) : Z4;
+    float4 ym, yp;
+    if constexpr (std::is_same<TB, float>::value) {
+      // FP32 input: the y-neighbour rows come straight through L1
+      ym = (act && j > 0) ? ld4_any(b + c - sy) : Z4;
+      yp = (act && j < d.ny - 1) ? ld4_any(b + c + sy) : Z4;
+    } else {
+      // rounded once, shared through shared memory
+      sb[ty + 1][lane] = bc;
+      if (ty == 0) sb[0][lane] = (act && j > 0) ? ld4_any(b + c - sy) : Z4;
+      if (ty == VY - 1 || j == d.ny - 1)
+        sb[ty + 2][lane] = (act && j < d.ny - 1) ? ld4_any(b + c + sy) : Z4;
+      __syncthreads();
+      ym = sb[ty][lane];
+      yp = sb[ty + 2][lane];
+    }
     float left = __shfl_up_sync(kFull, bc.w, 1);
     float right = __shfl_down_sync(kFull, bc.x, 1);
     if (lane == 0) left = (act && i0 > 0) ? ld1_any(b + c - 1) : 0.f;
     if (lane == 31) right = (act && i0 + 4 < d.nx) ? ld1_any(b + c + 4) : 0.f;
-    __syncthreads();
-    const float4 ym = sb[ty][lane];
-    const float4 yp = sb[ty + 2][lane];
     const int zn = (z > 0) + (z < d.nz - 1);
     const int znm = (z - 1 > 0) + (z - 1 < d.nz - 1);
     const int znp = (z + 1 > 0) + (z + 1 < d.nz - 1);
@@ -483,7 +491,7 @@ __global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restri
       st4(xo + c, make_float4(o[0], o[1], o[2], o[3]));
       if (bcopy) st4(bcopy + c, bc);
     }
-    __syncthreads();
+    if constexpr (!std::is_same<TB, float>::value) __syncthreads();
     bp = bc;
     bc = bn;
   }
@@ -928,8 +936,9 @@ ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, 
 }
 
 // One V-cycle with FP32 input and output (the mixed Arnoldi process keeps
-// its vectors as FP32 pairs and feeds the leading FP32 part): r and z must not
-// alias the level-0 work arrays.
+// its vectors as FP32 pairs and feeds the leading FP32 part).  r may be the
+// level-0 right-hand-side array itself (it is only read); z must not alias
+// the level-0 work arrays.
 ibm_status mg_vcycle_f32(ibm_ctx* c, const float* r, float* z, int pre, int post) {
   cudaStream_t s = c->stream;
   MGLevel& L0 = c->lv[0];

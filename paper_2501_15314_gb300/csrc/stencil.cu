@@ -604,7 +604,10 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, const
                       double* u, double us, int mode, cudaStream_t s) {
   const FaceGeom32 p = make_face_geom32(d);
   const int zch = helm_zchunks(d);
-  const dim3 gr(div_up((int)p.sy[0] / 4, 32), div_up(d.ny + 1, HVY), 3 * zch);
+  // x-blocks cover the nx first points of every row (a multiple of 4 when
+  // rounded up); for u_x the remaining point x = nx is a wall face, never
+  // written and kept 0 since the arrays were cleared at creation
+  const dim3 gr(div_up(div_up(d.nx, 4), 32), div_up(d.ny + 1, HVY), 3 * zch);
   count_launch();
   k_helm_cheb_v4<<<gr, dim3(32, HVY), 0, s>>>(make_face_geom(d), p, zch, e, eo, r32, r64, rs, a,
                                               nu_h2, alpha, beta, en, u, us, mode);
