@@ -321,10 +321,13 @@ __device__ __forceinline__ float ld1_any(const float2* p) { return __ldg(p).x; }
 __device__ __forceinline__ float ld1_any(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld1_any(const double* p) { return (float)__ldg(p); }
 
-// w / nn without dynamic indexing (nn in 1..6; 6 is the interior case)
-__device__ __forceinline__ float w_over(float w, int nn) {
-  return nn == 6 ? w * (1.f / 6.f) : __fdividef(w, (float)nn);
+// w / nn without division or dynamic indexing (nn in 1..6; 6 is the
+// interior case): 1/nn by a chain of selects
+__device__ __forceinline__ float inv_nn(int nn) {
+  return nn >= 6 ? (1.f / 6.f)
+                 : (nn == 5 ? 0.2f : (nn == 4 ? 0.25f : (nn == 3 ? (1.f / 3.f) : (nn == 2 ? 0.5f : 1.f))));
 }
+__device__ __forceinline__ float w_over(float w, int nn) { return w * inv_nn(nn); }
 
 __device__ __forceinline__ float cheb_cell(float xc, float s, float bv, int nn, float w, float h2) {
   return fmaf(w_over(w, nn), fmaf(h2, bv, s - (float)nn * xc), xc);
@@ -358,9 +361,15 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
   const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
   int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i0;
   const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // x-counts of the four cells; on rows/planes away from the y and z walls
+  // the neighbour count is 4 + x-count and the weight w/nn is fixed per thread
+  int ax[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ax[q] = (i0 + q > 0) + (i0 + q < d.nx - 1);
+  float wi[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) wi[q] = w_over(w, ax[q] + 4);
   const int ny_c = (j > 0) + (j < d.ny - 1);
-  const int n0 = ny_c + (i0 > 0) + 1, n3 = ny_c + 1 + (i0 + 3 < d.nx - 1);
-  const int n12 = ny_c + 2;
   float4 xp = (act && z0 > 0) ? ld4(x + c - sz) : Z4;
   float4 xc = act ? ld4(x + c) : Z4;
   for (int z = z0; z < z1; ++z, c += sz) {
@@ -373,12 +382,24 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
     if (lane == 0) left = (act && i0 > 0) ? __ldg(x + c - 1) : 0.f;
     if (lane == 31) right = (act && i0 + 4 < d.nx) ? __ldg(x + c + 4) : 0.f;
     const int zn = (z > 0) + (z < d.nz - 1);
-    float4 o;
-    o.x = cheb_cell(xc.x, (left + xc.y) + (ym.x + yp.x) + (xp.x + xn.x), bb.x, n0 + zn, w, h2);
-    o.y = cheb_cell(xc.y, (xc.x + xc.z) + (ym.y + yp.y) + (xp.y + xn.y), bb.y, n12 + zn, w, h2);
-    o.z = cheb_cell(xc.z, (xc.y + xc.w) + (ym.z + yp.z) + (xp.z + xn.z), bb.z, n12 + zn, w, h2);
-    o.w = cheb_cell(xc.w, (xc.z + right) + (ym.w + yp.w) + (xp.w + xn.w), bb.w, n3 + zn, w, h2);
-    if (act) st4(xo + c, o);
+    const bool inner = ny_c == 2 && zn == 2;
+    const float xv[4] = {xc.x, xc.y, xc.z, xc.w};
+    const float xl[4] = {left, xc.x, xc.y, xc.z};
+    const float xr[4] = {xc.y, xc.z, xc.w, right};
+    const float vym[4] = {ym.x, ym.y, ym.z, ym.w};
+    const float vyp[4] = {yp.x, yp.y, yp.z, yp.w};
+    const float vzp[4] = {xp.x, xp.y, xp.z, xp.w};
+    const float vzn[4] = {xn.x, xn.y, xn.z, xn.w};
+    const float vb[4] = {bb.x, bb.y, bb.z, bb.w};
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int nn = ax[q] + ny_c + zn;
+      const float s = (xl[q] + xr[q]) + (vym[q] + vyp[q]) + (vzp[q] + vzn[q]);
+      const float wq = inner ? wi[q] : w_over(w, nn);
+      o[q] = fmaf(wq, fmaf(h2, vb[q], s - (float)nn * xv[q]), xv[q]);
+    }
+    if (act) st4(xo + c, make_float4(o[0], o[1], o[2], o[3]));
     xp = xc;
     xc = xn;
   }
@@ -436,6 +457,17 @@ __global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restri
     nym[q] = nrow(j - 1, q);
     nyp[q] = nrow(j + 1, q);
   }
+  // per-thread weights away from the y and z walls (neighbour count 4 + x-count)
+  int ax[4];
+  float r_own[4], w1_own[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ax[q] = (i0 + q > 0) + (i0 + q < d.nx - 1);
+    r_own[q] = w_over(w0h2, ax[q] + 4);
+    w1_own[q] = w_over(w1, ax[q] + 4);
+  }
+  const float r_l = w_over(w0h2, ((i0 - 1 > 0) + 1) + 4);
+  const float r_r = w_over(w0h2, (1 + (i0 + 4 < d.nx - 1)) + 4);
   float4 bp = (act && z0 > 0) ? ld4_any(b + c - sz) : Z4;
   float4 bc = act ? ld4_any(b + c) : Z4;
   for (int z = z0; z < z1; ++z, c += sz) {
@@ -467,25 +499,43 @@ __global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restri
     const float bnv[4] = {bn.x, bn.y, bn.z, bn.w};
     const float ymv[4] = {ym.x, ym.y, ym.z, ym.w};
     const float ypv[4] = {yp.x, yp.y, yp.z, yp.w};
-    // x1 = w0 h^2 b / nn at the own cells and the two x-halo cells
-    float x1[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x1[q] = w_over(w0h2, nown[q] + zn) * bcv[q];
-    const float x1l = w_over(w0h2, cx_m + zn) * left;
-    const float x1r = w_over(w0h2, cx_p + zn) * right;
     float o[4];
+    if (j >= 2 && j <= d.ny - 3 && z >= 2 && z <= d.nz - 3) {
+      // rows and planes two cells away from the y and z walls: every
+      // neighbour count is 4 + its x-count, so the weights are per-thread
+      // constants
+      const float xl[4] = {left, bcv[0], bcv[1], bcv[2]};
+      const float xr[4] = {bcv[1], bcv[2], bcv[3], right};
+      const float rl[4] = {r_l, r_own[0], r_own[1], r_own[2]};
+      const float rr[4] = {r_own[1], r_own[2], r_own[3], r_r};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int ii = i0 + q;
-      float s = 0.f;
-      if (ii > 0) s += (q == 0) ? x1l : x1[q - 1];
-      if (ii < d.nx - 1) s += (q == 3) ? x1r : x1[q + 1];
-      if (j > 0) s += w_over(w0h2, nym[q] + zn) * ymv[q];
-      if (j < d.ny - 1) s += w_over(w0h2, nyp[q] + zn) * ypv[q];
-      if (z > 0) s += w_over(w0h2, nown[q] + znm) * bpv[q];
-      if (z < d.nz - 1) s += w_over(w0h2, nown[q] + znp) * bnv[q];
-      const int nn = nown[q] + zn;
-      o[q] = fmaf(w_over(w1, nn), fmaf(h2, bcv[q], s - (float)nn * x1[q]), x1[q]);
+      for (int q = 0; q < 4; ++q) {
+        const int nn = ax[q] + 4;
+        const float x1q = r_own[q] * bcv[q];
+        const float s = fmaf(rl[q], xl[q], rr[q] * xr[q]) +
+                        r_own[q] * ((ymv[q] + ypv[q]) + (bpv[q] + bnv[q]));
+        o[q] = fmaf(w1_own[q], fmaf(h2, bcv[q], s - (float)nn * x1q), x1q);
+      }
+    } else {
+      // x1 = w0 h^2 b / nn at the own cells and the two x-halo cells
+      float x1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x1[q] = w_over(w0h2, nown[q] + zn) * bcv[q];
+      const float x1l = w_over(w0h2, cx_m + zn) * left;
+      const float x1r = w_over(w0h2, cx_p + zn) * right;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int ii = i0 + q;
+        float s = 0.f;
+        if (ii > 0) s += (q == 0) ? x1l : x1[q - 1];
+        if (ii < d.nx - 1) s += (q == 3) ? x1r : x1[q + 1];
+        if (j > 0) s += w_over(w0h2, nym[q] + zn) * ymv[q];
+        if (j < d.ny - 1) s += w_over(w0h2, nyp[q] + zn) * ypv[q];
+        if (z > 0) s += w_over(w0h2, nown[q] + znm) * bpv[q];
+        if (z < d.nz - 1) s += w_over(w0h2, nown[q] + znp) * bnv[q];
+        const int nn = nown[q] + zn;
+        o[q] = fmaf(w_over(w1, nn), fmaf(h2, bcv[q], s - (float)nn * x1[q]), x1[q]);
+      }
     }
     if (act) {
       st4(xo + c, make_float4(o[0], o[1], o[2], o[3]));
@@ -613,6 +663,161 @@ __global__ void __launch_bounds__(32 * VY) k_prolong_v4(Dims d, Dims dc,
     }
     st4(x + f, v);
   }
+}
+
+// ---------------------------------------------------------------------------
+// The V-cycle below a level of at most kChainCells cells, in one CTA: every
+// level's x, b and a ping-pong buffer live in shared memory, phases are
+// separated by __syncthreads, so the five to eight launches per coarse level
+// (each a few microseconds of latency for a few thousand cells) become one.
+constexpr int kChainCells = 4096;
+constexpr int kChainMax = 6;
+constexpr int kChainThreads = 1024;
+
+struct CoarseChain {
+  int nlev;                    // levels in the chain (the last is the coarsest)
+  Dims d[kChainMax];
+  float h2[kChainMax];
+  int off[kChainMax + 1];      // cell offsets of the levels in the smem arrays
+  float wpre[8], wpost[8];     // Chebyshev-Richardson weights
+  int pre, post;
+  const float* pinv;           // dense pseudo-inverse of the coarsest level
+  int mc;
+};
+
+__device__ __forceinline__ void cell_ijk(Dims d, int c, int& i, int& j, int& k) {
+  i = c % d.nx;
+  j = (c / d.nx) % d.ny;
+  k = c / (d.nx * d.ny);
+}
+
+__device__ __forceinline__ float lap_nb(Dims d, const float* x, int c, int& nn) {
+  int i, j, k;
+  cell_ijk(d, c, i, j, k);
+  float s = 0.f;
+  nn = 0;
+  if (i > 0) { s += x[c - 1]; ++nn; }
+  if (i < d.nx - 1) { s += x[c + 1]; ++nn; }
+  if (j > 0) { s += x[c - d.nx]; ++nn; }
+  if (j < d.ny - 1) { s += x[c + d.nx]; ++nn; }
+  if (k > 0) { s += x[c - d.nx * d.ny]; ++nn; }
+  if (k < d.nz - 1) { s += x[c + d.nx * d.ny]; ++nn; }
+  return s;
+}
+
+// p Chebyshev steps on one level in shared memory; from_zero starts at x = 0.
+// Ends with the result in x (t is the ping-pong buffer).
+__device__ void chain_smooth(const CoarseChain& ch, int l, float* x, float* t, const float* b,
+                             const float* w, int p, bool from_zero) {
+  const Dims d = ch.d[l];
+  const int m = d.nx * d.ny * d.nz;
+  const float h2 = ch.h2[l];
+  float* cur = x;
+  float* nxt = t;
+  int q = 0;
+  if (from_zero && p > 0) {
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      int i, j, k;
+      cell_ijk(d, c, i, j, k);
+      const int nn = (i > 0) + (i < d.nx - 1) + (j > 0) + (j < d.ny - 1) + (k > 0) + (k < d.nz - 1);
+      x[c] = w[0] * h2 * b[c] * inv_nn(nn);
+    }
+    __syncthreads();
+    q = 1;
+  }
+  for (; q < p; ++q) {
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      int nn;
+      const float s = lap_nb(d, cur, c, nn);
+      nxt[c] = fmaf(w[q] * inv_nn(nn), fmaf(h2, b[c], s - (float)nn * cur[c]), cur[c]);
+    }
+    __syncthreads();
+    float* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  if (cur != x) {
+    for (int c = threadIdx.x; c < m; c += blockDim.x) x[c] = cur[c];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
+                                                                const float* __restrict__ b_in,
+                                                                float* __restrict__ x_out) {
+  extern __shared__ float sm[];
+  const int tot = ch.off[ch.nlev];
+  float* xs = sm;
+  float* bs = sm + tot;
+  float* ts = sm + 2 * tot;
+  const int m0 = ch.off[1];
+  for (int c = threadIdx.x; c < m0; c += blockDim.x) bs[c] = b_in[c];
+  __syncthreads();
+  // descend
+  for (int l = 0; l < ch.nlev - 1; ++l) {
+    float* x = xs + ch.off[l];
+    float* b = bs + ch.off[l];
+    float* t = ts + ch.off[l];
+    chain_smooth(ch, l, x, t, b, ch.wpre, ch.pre, true);
+    const Dims d = ch.d[l], dc = ch.d[l + 1];
+    const int mcl = dc.nx * dc.ny * dc.nz;
+    const float ih2 = 1.f / ch.h2[l];
+    float* bc = bs + ch.off[l + 1];
+    for (int C = threadIdx.x; C < mcl; C += blockDim.x) {
+      int I, J, K;
+      cell_ijk(dc, C, I, J, K);
+      float acc = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        const int c = ((2 * K + (q >> 2)) * d.ny + 2 * J + ((q >> 1) & 1)) * d.nx + 2 * I + (q & 1);
+        float r = b[c];
+        if (ch.pre > 0) {
+          int nn;
+          const float s = lap_nb(d, x, c, nn);
+          r -= ((float)nn * x[c] - s) * ih2;
+        }
+        acc += r;
+      }
+      bc[C] = acc * 0.125f;
+    }
+    __syncthreads();
+  }
+  // coarsest: dense pseudo-inverse
+  {
+    const int l = ch.nlev - 1;
+    float* x = xs + ch.off[l];
+    const float* b = bs + ch.off[l];
+    for (int r = threadIdx.x; r < ch.mc; r += blockDim.x) {
+      float acc = 0.f;
+      for (int q = 0; q < ch.mc; ++q) acc = fmaf(__ldg(ch.pinv + r * ch.mc + q), b[q], acc);
+      x[r] = acc;
+    }
+    __syncthreads();
+  }
+  // ascend
+  for (int l = ch.nlev - 2; l >= 0; --l) {
+    float* x = xs + ch.off[l];
+    float* b = bs + ch.off[l];
+    float* t = ts + ch.off[l];
+    const float* xc = xs + ch.off[l + 1];
+    const Dims d = ch.d[l], dc = ch.d[l + 1];
+    const int m = d.nx * d.ny * d.nz;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      int i, j, k;
+      cell_ijk(d, c, i, j, k);
+      const int I = i >> 1, J = j >> 1, K = k >> 1;
+      const int In = (i & 1) ? min(I + 1, dc.nx - 1) : max(I - 1, 0);
+      const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
+      const int Kn = (k & 1) ? min(K + 1, dc.nz - 1) : max(K - 1, 0);
+      auto X = [&](int a, int bb, int cc) { return xc[(cc * dc.ny + bb) * dc.nx + a]; };
+      const float a00 = 0.75f * X(I, J, K) + 0.25f * X(In, J, K);
+      const float a01 = 0.75f * X(I, Jn, K) + 0.25f * X(In, Jn, K);
+      const float a10 = 0.75f * X(I, J, Kn) + 0.25f * X(In, J, Kn);
+      const float a11 = 0.75f * X(I, Jn, Kn) + 0.25f * X(In, Jn, Kn);
+      const float v = 0.75f * (0.75f * a00 + 0.25f * a01) + 0.25f * (0.75f * a10 + 0.25f * a11);
+      x[c] = ch.pre > 0 ? x[c] + v : v;
+    }
+    __syncthreads();
+    chain_smooth(ch, l, x, t, b, ch.wpost, ch.post, false);
+  }
+  for (int c = threadIdx.x; c < m0; c += blockDim.x) x_out[c] = xs[c];
 }
 
 // x = P b on the coarsest level: one block, dense pseudo-inverse.
@@ -818,8 +1023,50 @@ void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cuda
                    dim3(BX, BY), 0, s>>>(L.d, C.d, cp.x, x, pre > 0 ? 0 : 1);
 }
 
+// Launches the one-CTA cycle from level l down; false if it does not apply.
+bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post,
+                  cudaStream_t s) {
+  const int nlev = c->n_levels - l;
+  if (nlev < 2 || nlev > kChainMax || c->lv[l].m > kChainCells) return false;
+  CoarseChain ch;
+  ch.nlev = nlev;
+  ch.off[0] = 0;
+  for (int q = 0; q < nlev; ++q) {
+    ch.d[q] = c->lv[l + q].d;
+    ch.h2[q] = (float)(c->lv[l + q].h * c->lv[l + q].h);
+    ch.off[q + 1] = ch.off[q] + (int)c->lv[l + q].m;
+  }
+  double w[8];
+  cheb_weights(pre > 0 ? pre : 1, w);
+  for (int q = 0; q < 8; ++q) ch.wpre[q] = q < pre ? (float)w[q] : 0.f;
+  cheb_weights(post > 0 ? post : 1, w);
+  for (int q = 0; q < 8; ++q) ch.wpost[q] = q < post ? (float)w[q] : 0.f;
+  ch.pre = pre;
+  ch.post = post;
+  ch.pinv = c->coarse_pinv32;
+  ch.mc = c->coarse_m;
+  const size_t smem = sizeof(float) * 3 * ch.off[nlev];
+  if (smem > 200 * 1024) return false;
+  // the shared-memory limit is raised once per device
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  if (!attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_coarse_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
+      return false;
+    attr_set[dev] = true;
+  }
+  count_launch();
+  k_coarse_chain<<<1, kChainThreads, smem, s>>>(ch, b, x);
+  return true;
+}
+
 template <typename T>
 void vcycle(ibm_ctx* c, int l, const T* b, T* x, T* t, int pre, int post, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (l > 0 && chain_vcycle(c, l, b, x, pre, post, s)) return;
+  }
   if (l == c->n_levels - 1) {
     count_launch();
     k_coarse_solve<T><<<1, 256, 0, s>>>(pinv_of<T>(c), b, x, c->coarse_m);
