@@ -32,6 +32,10 @@ Modules:
                  force recovery, update (Eqs. (ustar)-(Saddle),
                  (ApproxSchurPrimalP), (ApproxSchurPrimalF), (u_n_plus_1)) and
                  the force/torque diagnostics (Eq. (IBM_force)).
+* ``adjoint``    reverse-mode derivative of that step and of the body force /
+                 torque sums with respect to U^Gamma and the marker positions
+                 (through phi', the derivative of Eq. (delta)); the paper has
+                 no adjoint, so this differentiates the step as written.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` except the full-step convergence order, which the

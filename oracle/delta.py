@@ -4,6 +4,9 @@ FP64, CPU.  TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * ``phi(r)``: Delta r * delta(r) of Eq. (delta), with r in units of the cell
   width: (1 + sqrt(1 - 3 r^2))/3 for |r| <= 1/2,
   (5 - 3|r| - sqrt(1 - 3 (1 - |r|)^2))/6 for 1/2 < |r| <= 3/2, else 0.
+* ``phi_prime(r)``: d phi / dr, from differentiating the two branches of
+  Eq. (delta): -r / sqrt(1 - 3 r^2) for |r| <= 1/2 and
+  -sign(r) (1 + (1 - |r|)/sqrt(1 - 3 (1 - |r|)^2)) / 2 for 1/2 < |r| < 3/2.
 * ``regularization_matrix``: R with (R F)_i = dx^3 sum_k F_k delta^3(x_i - X_k)
   (Eq. (regularization)).  dx^3 delta^3 = phi phi phi, so the entry for face i
   of component d and the d-component of marker k is
@@ -20,7 +23,10 @@ with ``ValueError``.
 Pins (tests/test_oracle_delta.py): closed-form values and the zeroth, first
 and squared-sum moments of phi; R^T computed by an independent brute-force
 double loop over all faces and markers; partition of unity; force
-conservation; the average row sum of R^T R against Table A1.
+conservation; the average row sum of R^T R against Table A1.  phi_prime
+and ``regularization_derivative`` are pinned to central differences of phi
+and R, the values -1 and 0 at the breakpoints and the differentiated moment
+identities (tests/test_oracle_adjoint.py).
 """
 from __future__ import annotations
 
@@ -44,6 +50,20 @@ def phi(r):
     return out
 
 
+def phi_prime(r):
+    """Derivative of ``phi`` with respect to r (r in cell widths)."""
+    r = np.asarray(r, dtype=np.float64)
+    a = np.abs(r)
+    out = np.zeros_like(r)
+    inner = a <= 0.5
+    outer = (a > 0.5) & (a < 1.5)
+    ri = r[inner]
+    out[inner] = -ri / np.sqrt(1.0 - 3.0 * ri * ri)
+    q = 1.0 - a[outer]
+    out[outer] = -np.sign(r[outer]) * 0.5 * (1.0 + q / np.sqrt(1.0 - 3.0 * q * q))
+    return out
+
+
 def _axis_candidates(s, offset, n_points):
     """Grid indices j with positions (j + offset) within two cells of s
     (s in cell widths); returns indices (N, 5) and distances (N, 5)."""
@@ -57,6 +77,17 @@ def regularization_matrix(g: Grid, X) -> sp.csr_matrix:
     """R (n_faces x 3N) of Eq. (regularization); X has shape (3, N) (rows
     x, y, z of the markers).  Raises ValueError if any nonzero weight falls on
     a non-interior face."""
+    return _regularization(g, X, None)
+
+
+def regularization_derivative(g: Grid, X, axis: int) -> sp.csr_matrix:
+    """dR/dX_axis: the entry of face i and marker column d*N + k is the
+    derivative of R's entry with respect to coordinate ``axis`` of marker k,
+    -(1/h) phi'((x_axis,i - X_axis,k)/h) times the other two phi factors."""
+    return _regularization(g, X, axis)
+
+
+def _regularization(g: Grid, X, deriv_axis):
     X = np.asarray(X, dtype=np.float64).reshape(3, -1)
     N = X.shape[1]
     h = g.h
@@ -70,7 +101,10 @@ def regularization_matrix(g: Grid, X) -> sp.csr_matrix:
             offset = 0.0 if e == d else 0.5       # face axis vs centre axis
             j, dist = _axis_candidates(X[e] / h, offset, n_pts[e])
             idx.append(j)
-            w.append(phi(dist))
+            if e == deriv_axis:
+                w.append(-phi_prime(dist) / h)
+            else:
+                w.append(phi(dist))
         # outer product of the three 1-D candidate sets: (N, 5, 5, 5)
         W = (w[2][:, :, None, None] * w[1][:, None, :, None]
              * w[0][:, None, None, :])
