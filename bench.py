@@ -309,6 +309,9 @@ def run_ours(args):
     e2e_step()
     ms_e2e, _ = timed(e2e_step, args.steps)
 
+    # ---- adjoint of the step (transposed Schur solve) ----
+    adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
+
     # ---- roofline of the dominant kernel class ----
     # algorithmic bytes per launch (DRAM traffic the kernel must move at
     # least once), summed over the timed region's launches of each class
@@ -362,6 +365,7 @@ def run_ours(args):
             "helm_iters": st_mixed[-1]["helm_iters"],
             "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
             "roofline": roof, "kernel_classes": classes, "breakdown": breakdown,
+            "adjoint": adjoint,
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -381,6 +385,56 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, K):
+    """Adjoint of one step: on the headline workload (mixed form, rtol 1e-8,
+    cotangent of drag_z + torque_z of body 0) and on the 128^3 oscillating
+    sphere with 16000 markers (FP64 form, rtol 1e-13, the gradient-check
+    setting).  Times ibm_adjoint_step after its forward step."""
+    import numpy as np
+    import torch
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+
+    def one(solver, Xd, Ud, fd, o_u, o_F, z_k, bid, centers, kw):
+        solver.set_markers(Xd)
+        solver.step(torch.zeros_like(o_u), torch.zeros_like(o_u),
+                    torch.zeros(solver.m, dtype=torch.float64, device="cuda"), z_k, Ud, fd,
+                    out=dict(u=o_u, p=torch.empty(solver.m, dtype=torch.float64, device="cuda"),
+                             F=o_F), **kw)
+        loads = solver.body_forces(o_F, Xd, bid, centers)
+        w = np.zeros_like(loads)
+        w[0, 2] = w[0, 5] = -1.0
+        F_bar, _, _ = solver.body_forces_adjoint(o_F, Xd, bid, centers, w, loads)
+        solver.adjoint_step(o_u, z_k, o_F, F_bar, **kw)
+        ms, st = timed(lambda: solver.adjoint_step(o_u, z_k, o_F, F_bar, **kw)[2], K)
+        return ms, st[-1]
+
+    res = {}
+    kw = dict(precond_prec=_lib.IBM_PREC_FP32, rtol=1e-8)
+    bid = torch.from_numpy(W.body_id.astype(np.int32)).cuda()
+    ms, st = one(s, X, U, f, out["u"], out["F"], zk, bid, W.centers, kw)
+    res["headline_workload_mixed"] = {"adjoint_solves_per_s": 1000.0 / ms, "ms": ms,
+                                      "iters": st["iters"], "relres": st["relres_true"]}
+    W4 = wl.config(4, secondary=True)
+    s4 = IBMSolver(W4.n, Re=W4.Re, dt=W4.dt)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    X4, U4, f4 = dv(W4.X), dv(W4.U_gamma.ravel()), dv(W4.f_body)
+    u4 = torch.empty(s4.nf, dtype=torch.float64, device="cuda")
+    F4 = torch.empty(3 * W4.n_markers, dtype=torch.float64, device="cuda")
+    z4 = torch.zeros_like(F4)
+    bid4 = torch.from_numpy(W4.body_id.astype(np.int32)).cuda()
+    kw64 = dict(precond_prec=_lib.IBM_PREC_FP64, arnoldi=_lib.IBM_ARNOLDI_FP64, rtol=1e-13,
+                helm_rtol=1e-14, helm_maxit=12)
+    ms4, st4 = one(s4, X4, U4, f4, u4, F4, z4, bid4, W4.centers, kw64)
+    res["oscillating_sphere128_fp64"] = {
+        "workload": (f"{W4.name}: 128^3, sphere r 0.15 at t = 1 of the oscillation, "
+                     f"{W4.n_markers} markers, Re {W4.Re}, dt {W4.dt}, from rest"),
+        "adjoint_ms": ms4, "iters": st4["iters"], "relres": st4["relres_true"]}
+    s4.close()
+    return res
 
 
 def run_profile_step(args):

@@ -255,6 +255,51 @@ ibm_status ibm_body_forces_noalloc(const double* F, const double* X, const int32
                                    int64_t n_markers, int32_t n_bodies, const double* centers,
                                    double h, void* stream, double* out);
 
+/* ---- Adjoint of one step ------------------------------------------------
+ * The paper differentiates nothing; these calls give the exact derivative of
+ * the one-way step above (scalar C mode, Eqs. (ustar)-(ApproxSchurPrimalF),
+ * (u_n_plus_1)) so that gradients of the hydrodynamic force and torque on a
+ * body can be taken with respect to the prescribed marker velocities U^Gamma
+ * and the marker positions X.  With a = 3/(2 dt) and F_bar = dJ/dF^{n+1}:
+ *   lambda = S~^+ (2 B^T F_bar)      (S~ symmetric: the transposed solve)
+ *   U_bar  = 2a (F_bar - B lambda)
+ *   X_bar  = (R F' - a u^{n+1})^T dR (U_bar / a) - (G lambda)^T dR F'
+ *            + mu^T dR F^n,   H mu = a G lambda - R U_bar
+ * where dR is the derivative of R's entries (products of Eq. (delta)'s phi)
+ * with respect to each marker's own coordinates, H the predictor operator of
+ * Eq. (ustar) and F' = F^{n+1} - F^n.  The mu term needs one predictor solve
+ * and is skipped when F^n is zero.  */
+
+/* Adjoint of ibm_step.  Inputs are the markers last set (the same as for the
+ * forward step), the forward step's u^{n+1} (device packed faces), F^n and
+ * F^{n+1} (device [3][n_markers]; F_n may be NULL for F^n = 0) and
+ * F_bar = dJ/dF^{n+1} (device [3][n_markers]).  Outputs: U_bar = dJ/dU^Gamma
+ * and X_bar = the part of dJ/dX that flows through R (both device
+ * [3][n_markers], overwritten; a loss that also depends on X directly, like a
+ * torque's lever arm, adds its own part, see ibm_body_forces_adjoint).  The
+ * forward step must have run in scalar C mode with the same opts; the
+ * adjoint solve uses opts (precond_prec, rtol, ...), and stats receives its
+ * iteration count and true residual (helm_* for the mu solve).  Uses the
+ * context's workspace: not concurrent with other calls on the same context.
+ * Returns IBM_ERR_NOT_CONVERGED if the adjoint solve missed rtol (outputs
+ * still written).  Synchronises. */
+ibm_status ibm_adjoint_step(ibm_ctx* ctx, const double* u_np1, const double* F_n,
+                            const double* F_np1, const double* F_bar, double* U_bar,
+                            double* X_bar, const ibm_solve_opts* opts,
+                            ibm_solve_stats* stats);
+
+/* Adjoint of ibm_body_forces for J = sum_b w_b . out_b (w host
+ * [n_bodies][6], weights on [force | torque]; out host [n_bodies][6] = the
+ * forward result).  Writes F_bar = dJ/dF (device [3][n_markers]:
+ * h^3 (w_F + w_T x (X_k - c_b))), X_bar_lever = dJ/dX through the lever arms
+ * (device [3][n_markers]: h^3 F_k x w_T; may be NULL) and centers_bar
+ * (host [n_bodies][3]: -force_b x w_T, from out).  Markers whose body_id is
+ * outside [0, n_bodies) get zeros.  Synchronises. */
+ibm_status ibm_body_forces_adjoint(ibm_ctx* ctx, const double* F, const double* X,
+                                   const int32_t* body_id, int32_t n_bodies,
+                                   const double* centers, const double* w, const double* out,
+                                   double* F_bar, double* X_bar_lever, double* centers_bar);
+
 /* Optional timing of kernel classes with CUDA events recorded on the
  * context's stream around the launches of each class (no effect on results).
  * ibm_profile_enable(ctx, 1) resets the counters and starts recording;
@@ -274,6 +319,7 @@ enum {
   IBM_PROF_MG_SMOOTH_FINE = 9, /* one finest-level smoothing sweep kernel   */
   IBM_PROF_HELM_SWEEP = 10,    /* one inner FP32 Chebyshev step of the
                                   predictor (middle steps only)             */
+  IBM_PROF_ADJOINT = 11,       /* whole ibm_adjoint_step                    */
   IBM_PROF_NCLASS = 16
 };
 typedef struct {

@@ -52,7 +52,7 @@ class ibm_solve_stats(C.Structure):
 
 PROF_NCLASS = 16
 PROF_NAMES = ["laplacian_f64", "schur_markers", "vcycle", "multidot", "axpy_norm", "predictor",
-              "solve", "step", "marker_build", "mg_smooth_fine", "helm_sweep"]
+              "solve", "step", "marker_build", "mg_smooth_fine", "helm_sweep", "adjoint"]
 
 
 class ibm_profile(C.Structure):
@@ -89,6 +89,11 @@ SIGNATURES = [
     ("ibm_profile_read", C.c_int, [_P, C.POINTER(ibm_profile)]),
     ("ibm_body_forces", C.c_int, [_P, _P, _P, _P, C.c_int32, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
+    ("ibm_adjoint_step", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.POINTER(ibm_solve_opts),
+                                   C.POINTER(ibm_solve_stats)]),
+    ("ibm_body_forces_adjoint", C.c_int, [_P, _P, _P, _P, C.c_int32, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double), _P, _P,
+                                          C.POINTER(C.c_double)]),
 ]
 
 _lib = None

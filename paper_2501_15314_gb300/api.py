@@ -192,6 +192,49 @@ class IBMSolver:
         return {name: dict(ms=p.ms[i], launches=p.launches[i])
                 for i, name in enumerate(_lib.PROF_NAMES)}
 
+    def adjoint_step(self, u_np1, F_n, F_np1, F_bar, raise_on_error=True, **kw):
+        """Adjoint of ``step`` (markers as last set, same options): returns
+        (U_bar, X_bar, stats) for the cotangent F_bar = dJ/dF^{n+1}; X_bar is
+        the part of dJ/dX that flows through R.  F_n may be None (zero)."""
+        nmk = 3 * self.n_markers
+        U_bar = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda")
+        X_bar = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda")
+        o = self.opts(**kw)
+        st = _lib.ibm_solve_stats()
+        status = self.lib.ibm_adjoint_step(
+            self.ctx, _ptr(u_np1, numel=self.nf, name="u_np1"),
+            _ptr(F_n, numel=nmk, name="F_n") if (nmk and F_n is not None) else None,
+            _ptr(F_np1, numel=nmk, name="F_np1") if nmk else None,
+            _ptr(F_bar, numel=nmk, name="F_bar") if nmk else None,
+            _ptr(U_bar, name="U_bar") if nmk else None,
+            _ptr(X_bar, name="X_bar") if nmk else None, C.byref(o), C.byref(st))
+        if raise_on_error:
+            check(status, self.ctx)
+        d = _stats_dict(st)
+        d["status"] = status
+        return U_bar[:nmk], X_bar[:nmk], d
+
+    def body_forces_adjoint(self, F, X, body_id, centers, w, out):
+        """Adjoint of ``body_forces`` for J = sum(w * out): returns
+        (F_bar (device), X_bar through the lever arms (device),
+        centers_bar (host numpy))."""
+        import numpy as np
+        centers = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, 3))
+        nb = centers.shape[0]
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(nb, 6))
+        out = np.ascontiguousarray(np.asarray(out, dtype=np.float64).reshape(nb, 6))
+        nmk = 3 * self.n_markers
+        F_bar = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda")
+        X_bar = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda")
+        c_bar = np.zeros((nb, 3))
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+        check(self.lib.ibm_body_forces_adjoint(
+            self.ctx, _ptr(F, name="F") if nmk else None, _ptr(X, name="X") if nmk else None,
+            _ptr(body_id, dtype=torch.int32, name="body_id") if nmk else None, nb,
+            dp(centers), dp(w), dp(out), _ptr(F_bar, name="F_bar") if nmk else None,
+            _ptr(X_bar, name="X_bar") if nmk else None, dp(c_bar)), self.ctx)
+        return F_bar[:nmk], X_bar[:nmk], c_bar
+
     def body_forces(self, F, X, body_id, centers):
         import numpy as np
         centers = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, 3))

@@ -82,6 +82,8 @@ __global__ void k_axpby_small(const double* __restrict__ x, double a, const doub
   if (i < n) out[i] = a * x[i] + b * y[i];
 }
 
+}  // namespace
+
 bool bad_ptr(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 7) != 0; }
 
 ibm_status check_ctx(ibm_ctx* c) {
@@ -134,7 +136,7 @@ ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out) {
   return IBM_OK;
 }
 
-void free_all(ibm_ctx* c) {
+static void free_all(ibm_ctx* c) {
   cudaFree(c->cell_count); cudaFree(c->cell_start); cudaFree(c->cell_flag); cudaFree(c->scan_tmp);
   cudaFree(c->dev_flag); cudaFreeHost(c->host_flag);
   cudaFree(c->c1); cudaFree(c->c2); cudaFree(c->c3);
@@ -150,7 +152,7 @@ void free_all(ibm_ctx* c) {
   cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
-  cudaFree(m.t); cudaFree(m.t2);
+  cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc);
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off);
   cudaFree(m.ell_base); cudaFree(m.ell_len); cudaFree(m.ell_key); cudaFree(m.ell_coef);
   for (auto& r : c->prof) {
@@ -235,7 +237,6 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
 }
 
-}  // namespace
 }  // namespace ibm
 
 using namespace ibm;

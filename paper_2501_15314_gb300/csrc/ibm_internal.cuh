@@ -65,6 +65,8 @@ struct MarkerData {
   double* wc = nullptr;     // [3 axes][3 taps][n]
   double* cw = nullptr;     // [3 axes][4 cells][n] G^T-weighted face taps along
                             // the component's own axis: (w_{a-1} - w_a) / h
+  double* dwf = nullptr;    // [3 axes][3 taps][n] phi' at the face taps
+  double* dwc = nullptr;    // [3 axes][3 taps][n] phi' at the centre taps
   // cell-sorted (marker, slot) list for the atomic-free gathers
   int64_t n_entries = 0, entries_cap = 0;
   int32_t* entry_key = nullptr;   // marker * 64 + slot, sorted within a cell
@@ -200,7 +202,19 @@ void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, dou
 // out[cell] += scale * (G^T R t)[cell] on the shell cells
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);
 // U[d][k] = (R^T u)_{k,d}
+// argument and workspace helpers shared by the C entry points (capi.cu)
+bool bad_ptr(const void* p);
+ibm_status check_ctx(ibm_ctx* c);
+ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o);
+ibm_status ensure_krylov(ibm_ctx* c, int restart);
+ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out);
+// (a - nu Lap) u = rhs of Eq. (ustar) to o->helm_rtol; uses f3 and g1..g4
+ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
+                           int* iters, double* relres);
 void launch_interp(ibm_ctx* c, const double* u, double* U);
+// Xbar[e][k] (+)= scale * sum_d m[d][k] * sum_i f_d,i dR_{i,(d,k)}/dX_{e,k}
+void launch_interp_dpos(ibm_ctx* c, const double* f, const double* m, double scale,
+                        bool accumulate, double* Xbar);
 // u[face] = beta * u[face] + scale * (R F)[face] on shell faces only
 void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double* u);
 

@@ -32,6 +32,19 @@ __device__ __forceinline__ double roma_phi(double r) {
   return 0.0;
 }
 
+// d phi / dr of Eq. (delta), r in cell widths (differentiated branch by
+// branch; continuous, with value -sign(r) at |r| = 1/2 and 0 at |r| = 3/2).
+__device__ __forceinline__ double roma_dphi(double r) {
+  const double a = fabs(r);
+  if (a <= 0.5) return -r / sqrt(1.0 - 3.0 * r * r);
+  if (a < 1.5) {
+    const double q = 1.0 - a;
+    const double v = -0.5 * (1.0 + q / sqrt(1.0 - 3.0 * q * q));
+    return r > 0.0 ? v : -v;
+  }
+  return 0.0;
+}
+
 struct MkView {
   int64_t n;
   const int32_t* bf;
@@ -46,7 +59,7 @@ MkView view(const MarkerData& m) { return MkView{m.n, m.bf, m.bc, m.org, m.wf, m
 
 __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __restrict__ X,
                                int32_t* bf, int32_t* bc, int32_t* org, double* wf, double* wc,
-                               double* cw, int32_t* err) {
+                               double* cw, double* dwf, double* dwc, int32_t* err) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int ncell[3] = {d.nx, d.ny, d.nz};
@@ -60,7 +73,10 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
     if (!(fs > -1e9 && fs < 1e9 && fc > -1e9 && fc < 1e9)) {
       bad = true;
       bf[e * n + k] = 1; bc[e * n + k] = 0; org[e * n + k] = 0;
-      for (int q = 0; q < 3; ++q) { wf[(e * 3 + q) * n + k] = 0.0; wc[(e * 3 + q) * n + k] = 0.0; }
+      for (int q = 0; q < 3; ++q) {
+        wf[(e * 3 + q) * n + k] = 0.0; wc[(e * 3 + q) * n + k] = 0.0;
+        dwf[(e * 3 + q) * n + k] = 0.0; dwc[(e * 3 + q) * n + k] = 0.0;
+      }
       for (int q = 0; q < 4; ++q) cw[(e * 4 + q) * n + k] = 0.0;
       continue;
     }
@@ -77,6 +93,8 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
       W[q] = roma_phi((double)(b_f + q) - s);
       wf[(e * 3 + q) * n + k] = W[q];
       wc[(e * 3 + q) * n + k] = roma_phi((double)(b_c + q) + 0.5 - s);
+      dwf[(e * 3 + q) * n + k] = roma_dphi((double)(b_f + q) - s);
+      dwc[(e * 3 + q) * n + k] = roma_dphi((double)(b_c + q) + 0.5 - s);
     }
     // cell b_f - 1 + q lies between faces b_f - 1 + q and b_f + q
     cw[(e * 4 + 0) * n + k] = (0.0 - W[0]) * inv_h;
@@ -457,12 +475,15 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
   MarkerData& m = c->mk;
   if (n <= m.cap) return IBM_OK;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
-  cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2);
-  m.bf = m.bc = m.org = nullptr; m.wf = m.wc = m.cw = m.t = m.t2 = nullptr; m.cap = 0;
+  cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc);
+  m.bf = m.bc = m.org = nullptr;
+  m.wf = m.wc = m.cw = m.t = m.t2 = m.dwf = m.dwc = nullptr;
+  m.cap = 0;
   const size_t ni = sizeof(int32_t) * 3 * n, nd = sizeof(double) * 9 * n;
   if (cudaMalloc(&m.bf, ni) != cudaSuccess || cudaMalloc(&m.bc, ni) != cudaSuccess ||
       cudaMalloc(&m.org, ni) != cudaSuccess || cudaMalloc(&m.wf, nd) != cudaSuccess ||
-      cudaMalloc(&m.wc, nd) != cudaSuccess ||
+      cudaMalloc(&m.wc, nd) != cudaSuccess || cudaMalloc(&m.dwf, nd) != cudaSuccess ||
+      cudaMalloc(&m.dwc, nd) != cudaSuccess ||
       cudaMalloc(&m.cw, sizeof(double) * 12 * n) != cudaSuccess ||
       cudaMalloc(&m.t, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess) {
@@ -529,7 +550,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   IBM_CUDA(c, cudaMemsetAsync(c->dev_flag, 0, sizeof(int32_t), s));
   count_launch();
   k_marker_setup<<<div_up(n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org, m.wf,
-                                                 m.wc, m.cw, c->dev_flag);
+                                                 m.wc, m.cw, m.dwf, m.dwc, c->dev_flag);
   IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->dev_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   IBM_CUDA(c, cudaStreamSynchronize(s));
@@ -627,11 +648,85 @@ void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double
       scale, out);
 }
 
+// Position derivative of the interpolation, contracted with a marker field:
+// for marker k and axis e,
+//   Xbar[e][k] (+)= scale sum_d m[d][k] sum_{taps i of component d}
+//                   f_d,i d(phi phi phi)_i / dX_{e,k},
+// d/dX_e of phi((x_e - X_e)/h) being -phi'/h.  Four lanes per marker (lanes
+// d = 0, 1, 2 take the velocity components, lane 3 idles); the three
+// components are combined by shuffles in a fixed order.
+__global__ void k_interp_dpos(Dims d, MkView mk, const double* __restrict__ dwf,
+                              const double* __restrict__ dwc, const double* __restrict__ f,
+                              const double* __restrict__ mv, double scale, double inv_h,
+                              int accumulate, double* __restrict__ Xbar) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t k = tid >> 2;
+  const int dc = (int)(tid & 3);
+  const bool act = k < mk.n && dc < 3;
+  double g[3] = {0.0, 0.0, 0.0};
+  if (act) {
+    const FaceDims fd = face_dims(d);
+    const int64_t off = dc == 0 ? 0 : (dc == 1 ? fd.nfx : fd.nfx + fd.nfy);
+    const int64_t sy = d.nx + (dc == 0 ? 1 : 0);
+    const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
+    int b[3];
+    double w[3][3], dw[3][3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      b[e] = (e == dc) ? mk.bf[e * mk.n + k] : mk.bc[e * mk.n + k];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        w[e][q] = (e == dc) ? mk.wf[(e * 3 + q) * mk.n + k] : mk.wc[(e * 3 + q) * mk.n + k];
+        dw[e][q] = (e == dc) ? dwf[(e * 3 + q) * mk.n + k] : dwc[(e * 3 + q) * mk.n + k];
+      }
+    }
+    for (int c2 = 0; c2 < 3; ++c2) {
+      for (int c1 = 0; c1 < 3; ++c1) {
+        const int64_t base = off + (int64_t)(b[2] + c2) * sz + (int64_t)(b[1] + c1) * sy + b[0];
+#pragma unroll
+        for (int c0 = 0; c0 < 3; ++c0) {
+          const double v = __ldg(f + base + c0);
+          g[0] = fma(v, dw[0][c0] * w[1][c1] * w[2][c2], g[0]);
+          g[1] = fma(v, w[0][c0] * dw[1][c1] * w[2][c2], g[1]);
+          g[2] = fma(v, w[0][c0] * w[1][c1] * dw[2][c2], g[2]);
+        }
+      }
+    }
+    const double mm = mv[dc * mk.n + k];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) g[e] *= mm;
+  }
+  // lanes (d = 0, 1, 2, 3) of one marker are adjacent: sum in the order
+  // (0 + 1) + (2 + 3)
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    g[e] += __shfl_xor_sync(0xffffffffu, g[e], 1);
+    g[e] += __shfl_xor_sync(0xffffffffu, g[e], 2);
+  }
+  if (k < mk.n && dc == 0) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const double v = -scale * inv_h * g[e];
+      Xbar[e * mk.n + k] = accumulate ? Xbar[e * mk.n + k] + v : v;
+    }
+  }
+}
+
 void launch_interp(ibm_ctx* c, const double* u, double* U) {
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
   k_interp<<<div_up(3 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), u, U);
+}
+
+void launch_interp_dpos(ibm_ctx* c, const double* f, const double* mvec, double scale,
+                        bool accumulate, double* Xbar) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0) return;
+  count_launch();
+  k_interp_dpos<<<div_up(4 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), m.dwf, m.dwc, f, mvec,
+                                                              scale, 1.0 / c->h,
+                                                              accumulate ? 1 : 0, Xbar);
 }
 
 void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double* u) {

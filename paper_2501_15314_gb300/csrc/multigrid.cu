@@ -329,10 +329,6 @@ __device__ __forceinline__ float inv_nn(int nn) {
 }
 __device__ __forceinline__ float w_over(float w, int nn) { return w * inv_nn(nn); }
 
-__device__ __forceinline__ float cheb_cell(float xc, float s, float bv, int nn, float w, float h2) {
-  return fmaf(w_over(w, nn), fmaf(h2, bv, s - (float)nn * xc), xc);
-}
-
 int vec_zc(Dims d) {
   const int64_t bxy = (int64_t)div_up(d.nx / 4, 32) * div_up(d.ny, VY);
   int64_t zc = (int64_t)d.nz * bxy / (152 * 4);

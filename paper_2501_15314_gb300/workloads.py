@@ -163,7 +163,10 @@ def config(index: int, secondary: bool = False) -> Workload:
     1: 32^3, one sphere r = 0.2 at the centre, Re 100, dt 0.01
     2: 128^3, one sphere r = 0.15 at the centre, Re 100, dt 2e-3
     3: 256^3, eight spheres, radii uniform in [0.05, 0.1], Re 200, dt 1e-3
-    4: 128^3, one sphere r = 0.15 (adjoint workload), Re 100, dt 2e-3
+    4: 128^3, the transversely oscillating sphere of Sec. 6.1.1 (adjoint
+       workload): r = 0.15 (D = 0.3), A/D = 1, at nondimensional time t = 1
+       of Eq. (u_z_and_z): centre z = 0.5 - A cos(t), every marker moving
+       with U = sin(t) e_z; Re 100, dt 2e-3, from rest, no body force
     5: 384^3, one sphere r = 0.08, Re 50, dt 5e-4
     Primary marker counts put markers at spacing h; ``secondary`` uses the
     stated totals (1000, 16000, 60000, 16000, 25000)."""
@@ -171,10 +174,11 @@ def config(index: int, secondary: bool = False) -> Workload:
     if index == 1:
         return spheres_workload("sphere32", 32, 100.0, 0.01, [[0.5] * 3], [0.2],
                                 1000 if secondary else None, index, rng=rng)
-    if index in (2, 4):
-        return spheres_workload(f"sphere128_{index}", 128, 100.0, 2e-3,
-                                [[0.5] * 3], [0.15],
+    if index == 2:
+        return spheres_workload("sphere128", 128, 100.0, 2e-3, [[0.5] * 3], [0.15],
                                 16000 if secondary else None, index, rng=rng)
+    if index == 4:
+        return oscillating_sphere(128, 16000 if secondary else None, t=1.0)
     if index == 3:
         n = 256
         centers, radii = place_spheres(8, 0.05, 0.1, 1.0 / n, rng)
@@ -185,6 +189,28 @@ def config(index: int, secondary: bool = False) -> Workload:
                                 [[0.5, 0.5, 0.7]], [0.08],
                                 25000 if secondary else None, index, rng=rng)
     raise ValueError(index)
+
+
+def oscillating_sphere(n: int, n_markers: int | None, t: float = 1.0, radius: float = 0.15,
+                       amp_ratio: float = 1.0, Re: float = 100.0, dt: float = 2e-3) -> Workload:
+    """One sphere of diameter D = 2 radius oscillating along z (Eq. (U_z) in
+    the nondimensional form (u_z_and_z), lengths in units of D): at time t
+    the centre sits at 0.5 - A cos(t D/A) and every marker moves with
+    sin(t D/A) e_z, A = amp_ratio D.  Zero body force."""
+    D = 2.0 * radius
+    A = amp_ratio * D
+    centre = np.array([[0.5, 0.5, 0.5 - A * np.cos(t * D / A)]])
+    h = 1.0 / n
+    nm = markers_for_spacing(radius, h) if n_markers is None else n_markers
+    X = fibonacci_sphere(nm, radius, centre[0])
+    body_id = np.zeros(nm, dtype=np.int32)
+    U = np.zeros((3, nm))
+    U[2] = np.sin(t * D / A)
+    nf = 3 * n * n * (n + 1)
+    lag_spacing = np.sqrt(4.0 * np.pi * radius ** 2 / nm)
+    info = dict(spacing_ratio=h / lag_spacing, counts=[nm], t=t, amp_ratio=amp_ratio)
+    return Workload(f"oscillating_sphere{n}", n, Re, dt, X, body_id, centre,
+                    np.array([radius]), U, np.zeros(nf), info)
 
 
 def small_spheres(n: int, n_bodies: int, seed: int, r_lo: float, r_hi: float,
