@@ -10,7 +10,17 @@ With B = R^T G and C = R^T R (Eq. (Saddle)):
   force  F' = C^{-1}(B p' - RHS_F)  (Eq. (SchurPrimalF));
 * scalar approximation C^{-1} ~ 2 I: S~_p = L + 2 B^T B (Eq. (tildeSp)),
   RHS  RHS_p + 2 B^T RHS_F  (Eq. (ApproxSchurPrimalP)),
-  force  F' = 2 (B p' - RHS_F)  (Eq. (ApproxSchurPrimalF)).
+  force  F' = 2 (B p' - RHS_F)  (Eq. (ApproxSchurPrimalF));
+* the sign-consistent form ("consistent"): asking the update of
+  Eq. (u_n_plus_1), u^{n+1} = u* + (1/a)(-G p' + R F'), to satisfy
+  G^T u^{n+1} = 0 and R^T u^{n+1} = U^Gamma exactly gives
+  [[L, -B^T], [B, -C]] [p'; F'] = [RHS_p; RHS_F] (the sign Eq.
+  (modified_poisson) implies), Schur complement
+  S_c = L - B^T C^{-1} B = G^T (I - R C^{-1} R^T) G, RHS
+  RHS_p - B^T C^{-1} RHS_F and the same force formula as the exact form.
+  R C^{-1} R^T is an orthogonal projection, so S_c is positive
+  semi-definite with spec(L^+ S_c) in [0, 1]: it is not bounded below the
+  way S_p is, which is why the paper's form is the one preconditioned by L.
 
 L is singular (Neumann walls, constants in its null space); B 1 = R^T G 1 = 0,
 so S~_p and S_p share that null space and every right-hand side built from
@@ -91,6 +101,25 @@ class SchurSystem:
         """S_p v = L v + B^T C^{-1} B v, Eq. (SchurPrimal)."""
         v = np.asarray(v, dtype=np.float64)
         return mac.apply_L(self.g, v) + self.apply_BT(self.C_solve(self.apply_B(v)))
+
+    def apply_S_consistent(self, v):
+        """S_c v = L v - B^T C^{-1} B v (sign-consistent form)."""
+        v = np.asarray(v, dtype=np.float64)
+        return mac.apply_L(self.g, v) - self.apply_BT(self.C_solve(self.apply_B(v)))
+
+    def dense_S_consistent(self):
+        Bd = self.B.toarray()
+        Cd = self.C.toarray()
+        return self.L.toarray() - Bd.T @ np.linalg.solve(Cd, Bd)
+
+    def saddle_matrix_consistent(self):
+        """[[L, -B^T], [B, -C]], dense."""
+        return np.block([[self.L.toarray(), -self.B.T.toarray()],
+                         [self.B.toarray(), -self.C.toarray()]])
+
+    def rhs_consistent(self, rhs_p, rhs_F):
+        """RHS_p - B^T C^{-1} RHS_F."""
+        return np.asarray(rhs_p) - self.apply_BT(self.C_solve(rhs_F))
 
     def dense_S_tilde(self):
         B = self.B
@@ -193,9 +222,11 @@ def fgmres(apply_A, b, apply_M, rtol=1e-13, restart=60, maxit=600, x0=None):
 
 def solve_schur(sys: SchurSystem, b, mode="scalar", rtol=1e-13, restart=60,
                 maxit=600, workers=None):
-    """Mean-zero p' solving S~_p p' = b (mode "scalar") or S_p p' = b (mode
-    "exact") by FGMRES preconditioned with the exact L^+ (Sec. 4.1-4.2)."""
-    A = sys.apply_S_tilde if mode == "scalar" else sys.apply_S_exact
+    """Mean-zero p' solving S~_p p' = b (mode "scalar"), S_p p' = b (mode
+    "exact") or S_c p' = b (mode "consistent") by FGMRES preconditioned with
+    the exact L^+ (Sec. 4.1-4.2)."""
+    A = {"scalar": sys.apply_S_tilde, "exact": sys.apply_S_exact,
+         "consistent": sys.apply_S_consistent}[mode]
     M = lambda r: mac.laplacian_pinv(sys.g, r, workers=workers)
     x, it, rel, hist = fgmres(A, b, M, rtol=rtol, restart=restart, maxit=maxit)
     return mac.remove_mean(x), it, rel, hist

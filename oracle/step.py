@@ -10,7 +10,8 @@ Sec. 3.1, in the paper's order:
 2. correction right-hand sides below Eq. (Saddle):
    RHS_p = -(3/(2 dt)) div u* = a G^T u*,  RHS_F = a (R^T u* - U^Gamma);
 3. Schur solve S~_p p' = RHS_p + 2 B^T RHS_F  (Eq. (ApproxSchurPrimalP)),
-   or the exact S_p form (Eq. (SchurPrimalP));
+   or the exact S_p form (Eq. (SchurPrimalP)), or the sign-consistent form
+   (``oracle.schur``; then div and slip of u^{n+1} vanish exactly);
 4. force recovery F' = 2 (B p' - RHS_F)  (Eq. (ApproxSchurPrimalF)) or
    C^{-1}(B p' - RHS_F)  (Eq. (SchurPrimalF));
 5. update, Eq. (u_n_plus_1) and the correction step that follows Eq. (divfree):
@@ -123,8 +124,10 @@ def step(g: mac.Grid, Re: float, dt: float, X, U_gamma, f_body,
     rhs_F = a * (sys.R.T @ u_star - U_gamma)
     if mode == "scalar":
         b = sys.rhs_scalar(rhs_p, rhs_F)
-    else:
+    elif mode == "exact":
         b = sys.rhs_exact(rhs_p, rhs_F)
+    else:
+        b = sys.rhs_consistent(rhs_p, rhs_F)
     p_corr, iters, relres, hist = solve_schur(sys, b, mode=mode, rtol=rtol,
                                               workers=workers)
     if mode == "scalar":
