@@ -311,6 +311,7 @@ def run_ours(args):
 
     # ---- adjoint of the step (transposed Schur solve) ----
     adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
+    c_modes = cmode_bench(timed, max(1, k64 // 2))
 
     # ---- roofline of the dominant kernel class ----
     # algorithmic bytes per launch (DRAM traffic the kernel must move at
@@ -365,7 +366,7 @@ def run_ours(args):
             "helm_iters": st_mixed[-1]["helm_iters"],
             "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
             "roofline": roof, "kernel_classes": classes, "breakdown": breakdown,
-            "adjoint": adjoint,
+            "adjoint": adjoint, "c_modes": c_modes,
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -434,6 +435,42 @@ def adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, K):
                      f"{W4.n_markers} markers, Re {W4.Re}, dt {W4.dt}, from rest"),
         "adjoint_ms": ms4, "iters": st4["iters"], "relres": st4["relres_true"]}
     s4.close()
+    return res
+
+
+def cmode_bench(timed, K):
+    """The three treatments of C = R^T R on one Schur solve of the step's form
+    at 128^3 (one sphere r = 0.15, markers at spacing h: C is well enough
+    conditioned for the inner conjugate gradients), rtol 1e-8, FP32 V-cycle
+    with the double-single Arnoldi process."""
+    import numpy as np
+    import torch
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+    W2 = wl.config(2)
+    s2 = IBMSolver(W2.n, Re=W2.Re, dt=W2.dt)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    s2.set_markers(dv(W2.X))
+    f2 = dv(W2.f_body)
+    a = 1.5 / W2.dt
+    rhs_F = a * (s2.interp(f2) - dv(W2.U_gamma.ravel()))
+    b = a * s2.gradient_t(f2) + 2.0 * s2.gradient_t(s2.spread(rhs_F))
+    res = {"workload": (f"{W2.name}: 128^3, one sphere r 0.15, {W2.n_markers} markers "
+                        f"(spacing h), solve of the step's form, rtol 1e-8")}
+    for name, mode in (("scalar", _lib.IBM_CMODE_SCALAR), ("exact", _lib.IBM_CMODE_EXACT),
+                       ("consistent", _lib.IBM_CMODE_CONSISTENT)):
+        kw = dict(precond_prec=_lib.IBM_PREC_FP32, rtol=1e-8, maxit=400, restart=60,
+                  c_mode=mode, c_rtol=1e-12)
+        if mode == _lib.IBM_CMODE_SCALAR:
+            s2.solve_schur(b, raise_on_error=False, **kw)
+        # the C modes run for seconds: one timed solve, after the scalar one
+        # has set up the workspace
+        k = K if mode == _lib.IBM_CMODE_SCALAR else 1
+        ms, st = timed(lambda: s2.solve_schur(b, raise_on_error=False, **kw)[1], k)
+        res[name] = {"solves_per_s": 1000.0 / ms, "ms": ms, "iters": st[-1]["iters"],
+                     "relres": st[-1]["relres_true"], "inner_cg_iters": st[-1]["c_iters"]}
+    s2.close()
     return res
 
 

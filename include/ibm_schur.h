@@ -79,6 +79,22 @@ typedef enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32 = 1 } ibm_precision;
  * every restart cycle is computed in native FP64. */
 typedef enum { IBM_ARNOLDI_FP64 = 0, IBM_ARNOLDI_DS = 1 } ibm_arnoldi;
 
+/* Treatment of C = R^T R (the (2,2) block of Eq. (Saddle)).
+ * IBM_CMODE_SCALAR: C^{-1} ~ 2 I, the paper's production operator
+ *   S~ = L + 2 B^T B (Eqs. (tildeSp)-(ApproxSchurPrimalF)).
+ * IBM_CMODE_EXACT: S = L + B^T C^{-1} B, b = RHS_p + B^T C^{-1} RHS_F,
+ *   F' = C^{-1}(B p' - RHS_F) (Eqs. (SchurPrimal)-(SchurPrimalF)), the
+ *   operator of the spectral theorem of Sec. 5; C^{-1} by conjugate
+ *   gradients on C (matrix-free R^T R) to c_rtol inside every product.
+ * IBM_CMODE_CONSISTENT: the sign-consistent system [[L, -B^T], [B, -C]]
+ *   that the update of Eq. (u_n_plus_1) implies when G^T u^{n+1} = 0 and
+ *   R^T u^{n+1} = U^Gamma are imposed exactly: S = L - B^T C^{-1} B,
+ *   b = RHS_p - B^T C^{-1} RHS_F, F' as in EXACT.  S is only positive
+ *   semi-definite with spec(L^+ S) in [0, 1], so the Laplacian
+ *   preconditioner does not bound its iteration count (offered to compare
+ *   the two readings of the sign of Eq. (Saddle)). */
+typedef enum { IBM_CMODE_SCALAR = 0, IBM_CMODE_EXACT = 1, IBM_CMODE_CONSISTENT = 2 } ibm_cmode;
+
 /* Grid description: cell counts, cell width, Reynolds number and time step
  * (a = 3/(2 dt) and nu = 1/Re enter the BDF2 predictor, Eq. (ustar), and the
  * correction right-hand sides below Eq. (Saddle)). */
@@ -104,6 +120,9 @@ typedef struct {
   int32_t with_advection;/* 1: include the explicit convective term of
                             Eq. (ustar) in the predictor                     */
   int32_t arnoldi;       /* ibm_arnoldi                                      */
+  int32_t c_mode;        /* ibm_cmode                                        */
+  double c_rtol;         /* inner CG on C: relative residual target          */
+  int32_t c_maxit;       /* inner CG on C: iteration limit per solve         */
 } ibm_solve_opts;
 
 #define IBM_HIST_MAX 256
@@ -118,11 +137,14 @@ typedef struct {
   double helm_relres;     /* predictor relative residual (ibm_step only)     */
   double div_l2;          /* ||G^T u^{n+1}||_2            (ibm_step only)    */
   double slip_l2;         /* ||R^T u^{n+1} - U^Gamma||_2  (ibm_step only)    */
+  int64_t c_iters;        /* inner CG iterations on C, summed (EXACT and
+                             CONSISTENT modes)                               */
 } ibm_solve_stats;
 
 /* Fills *opts with defaults: FP32 V-cycle, rtol 1e-8, maxit 200, restart 40,
  * Chebyshev (2,2), single Gram-Schmidt pass, helm_rtol 1e-10, helm_maxit 8,
- * advection on, double-single Arnoldi process. */
+ * advection on, double-single Arnoldi process, scalar C mode (c_rtol 1e-14,
+ * c_maxit 500 for the other modes). */
 void ibm_default_opts(ibm_solve_opts* opts);
 
 /* Creates a context for one grid and allocates the grid-sized workspace
@@ -156,8 +178,9 @@ ibm_status ibm_set_markers(ibm_ctx* ctx, int64_t n_markers, const double* X);
  * Eq. (Saddle).  v and out must not alias.  Asynchronous. */
 ibm_status ibm_apply_laplacian(ibm_ctx* ctx, const double* v, double* out);
 
-/* out = S~ v = L v + 2 B^T B v, Eq. (tildeSp) (cells -> cells).  v and out
- * must not alias.  Asynchronous. */
+/* out = S~ v = L v + 2 B^T B v, Eq. (tildeSp) (cells -> cells), the scalar
+ * C mode (ibm_apply_schur_opts for the others).  v and out must not alias.
+ * Asynchronous. */
 ibm_status ibm_apply_schur(ibm_ctx* ctx, const double* v, double* out);
 
 /* z = M^{-1} r: one multigrid V-cycle for the Neumann Laplacian (Chebyshev
@@ -193,18 +216,35 @@ ibm_status ibm_gradient_t(ibm_ctx* ctx, const double* u, double* out);
 ibm_status ibm_solve_schur(ibm_ctx* ctx, const double* b, double* p,
                            const ibm_solve_opts* opts, ibm_solve_stats* stats);
 
-/* F' = 2 (B p - RHS_F), Eq. (ApproxSchurPrimalF) ([3][n_markers]).
- * Asynchronous. */
+/* F' = 2 (B p - RHS_F), Eq. (ApproxSchurPrimalF) ([3][n_markers]), the
+ * scalar C mode.  Asynchronous. */
 ibm_status ibm_force_correction(ibm_ctx* ctx, const double* p,
                                 const double* rhs_F, double* F_corr);
+
+/* out = S v for the C mode of opts (c_mode, c_rtol, c_maxit; the other
+ * fields are ignored): S~ v, (L + B^T C^{-1} B) v or (L - B^T C^{-1} B) v.
+ * c_iters (may be NULL) receives the inner CG iterations.  Returns
+ * IBM_ERR_NOT_CONVERGED if an inner CG missed c_rtol.  Synchronises in the
+ * non-scalar modes (the CG checks its residual on the host). */
+ibm_status ibm_apply_schur_opts(ibm_ctx* ctx, const double* v, double* out,
+                                const ibm_solve_opts* opts, int64_t* c_iters);
+
+/* s = C^{-1} t with C = R^T R ([3][n_markers] device vectors, t and s must
+ * not alias): conjugate gradients on C, products matrix-free (spread to the
+ * shell faces, interpolate back), to ||t - C s|| <= c_rtol ||t|| within
+ * c_maxit iterations (IBM_ERR_NOT_CONVERGED otherwise, s holds the last
+ * iterate).  iters may be NULL.  Synchronises. */
+ibm_status ibm_apply_c_inverse(ibm_ctx* ctx, const double* t, double* s, double c_rtol,
+                               int32_t c_maxit, int32_t* iters);
 
 /* One one-way SIMPLE-IBM time step (Sec. 3.1) with the markers last set:
  *   1. predictor (Eq. (ustar)): (3/(2dt) - Lap/Re) u* = (4u^n - u^{n-1})/(2dt)
  *      - G p^n + R F^n - (u.grad u)^n + f_body, solved by FP64 defect
  *      correction around FP32 Chebyshev sweeps to helm_rtol;
  *   2. RHS_p = (3/(2dt)) G^T u*, RHS_F = (3/(2dt)) (R^T u* - U_gamma);
- *   3. ibm_solve_schur on b = RHS_p + 2 B^T RHS_F;
- *   4. F' = 2 (B p' - RHS_F);
+ *   3. ibm_solve_schur on b = RHS_p + 2 B^T RHS_F (scalar C mode;
+ *      RHS_p +- B^T C^{-1} RHS_F in the EXACT / CONSISTENT modes);
+ *   4. F' = 2 (B p' - RHS_F) (scalar; C^{-1}(B p' - RHS_F) otherwise);
  *   5. u^{n+1} = u* + (2dt/3)(-G p' + R F'), p^{n+1} = p^n + p',
  *      F^{n+1} = F^n + F'  (Eq. (u_n_plus_1) and the correction step);
  *   6. diagnostics ||G^T u^{n+1}||, ||R^T u^{n+1} - U_gamma|| into stats.
@@ -277,7 +317,8 @@ ibm_status ibm_body_forces_noalloc(const double* F, const double* X, const int32
  * and X_bar = the part of dJ/dX that flows through R (both device
  * [3][n_markers], overwritten; a loss that also depends on X directly, like a
  * torque's lever arm, adds its own part, see ibm_body_forces_adjoint).  The
- * forward step must have run in scalar C mode with the same opts; the
+ * forward step must have run in scalar C mode (other modes: IBM_ERR_ARG)
+ * with the same opts; the
  * adjoint solve uses opts (precond_prec, rtol, ...), and stats receives its
  * iteration count and true residual (helm_* for the mu solve).  Uses the
  * context's workspace: not concurrent with other calls on the same context.

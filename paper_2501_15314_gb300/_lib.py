@@ -25,6 +25,9 @@ IBM_PREC_FP64 = 0
 IBM_PREC_FP32 = 1
 IBM_ARNOLDI_FP64 = 0
 IBM_ARNOLDI_DS = 1
+IBM_CMODE_SCALAR = 0
+IBM_CMODE_EXACT = 1
+IBM_CMODE_CONSISTENT = 2
 HIST_MAX = 256
 
 STATUS_NAMES = {0: "IBM_OK", 1: "IBM_ERR_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_NOMEM",
@@ -41,13 +44,15 @@ class ibm_solve_opts(C.Structure):
     _fields_ = [("precond_prec", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32),
                 ("restart", C.c_int32), ("mg_pre", C.c_int32), ("mg_post", C.c_int32),
                 ("reorth", C.c_int32), ("helm_rtol", C.c_double), ("helm_maxit", C.c_int32),
-                ("with_advection", C.c_int32), ("arnoldi", C.c_int32)]
+                ("with_advection", C.c_int32), ("arnoldi", C.c_int32), ("c_mode", C.c_int32),
+                ("c_rtol", C.c_double), ("c_maxit", C.c_int32)]
 
 
 class ibm_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("relres_true", C.c_double),
                 ("relres_hist", C.c_double * HIST_MAX), ("helm_iters", C.c_int32),
-                ("helm_relres", C.c_double), ("div_l2", C.c_double), ("slip_l2", C.c_double)]
+                ("helm_relres", C.c_double), ("div_l2", C.c_double), ("slip_l2", C.c_double),
+                ("c_iters", C.c_int64)]
 
 
 PROF_NCLASS = 16
@@ -89,6 +94,10 @@ SIGNATURES = [
     ("ibm_profile_read", C.c_int, [_P, C.POINTER(ibm_profile)]),
     ("ibm_body_forces", C.c_int, [_P, _P, _P, _P, C.c_int32, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
+    ("ibm_apply_schur_opts", C.c_int, [_P, _P, _P, C.POINTER(ibm_solve_opts),
+                                       C.POINTER(C.c_int64)]),
+    ("ibm_apply_c_inverse", C.c_int, [_P, _P, _P, C.c_double, C.c_int32,
+                                      C.POINTER(C.c_int32)]),
     ("ibm_adjoint_step", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.POINTER(ibm_solve_opts),
                                    C.POINTER(ibm_solve_stats)]),
     ("ibm_body_forces_adjoint", C.c_int, [_P, _P, _P, _P, C.c_int32, C.POINTER(C.c_double),

@@ -31,7 +31,8 @@ def _stats_dict(st: _lib.ibm_solve_stats) -> dict:
     n = min(st.iters, _lib.HIST_MAX)
     return dict(iters=st.iters, restarts=st.restarts, relres_true=st.relres_true,
                 relres_hist=list(st.relres_hist[:n]), helm_iters=st.helm_iters,
-                helm_relres=st.helm_relres, div_l2=st.div_l2, slip_l2=st.slip_l2)
+                helm_relres=st.helm_relres, div_l2=st.div_l2, slip_l2=st.slip_l2,
+                c_iters=st.c_iters)
 
 
 class IBMSolver:
@@ -90,11 +91,32 @@ class IBMSolver:
                                            _ptr(out, numel=self.m, name="out")), self.ctx)
         return out
 
-    def apply_schur(self, v, out=None):
+    def apply_schur(self, v, out=None, **kw):
+        """S v: the scalar form S~ by default; with keyword options (c_mode,
+        c_rtol, c_maxit) the form they select."""
         out = self._cells() if out is None else out
-        check(self.lib.ibm_apply_schur(self.ctx, _ptr(v, numel=self.m, name="v"),
-                                       _ptr(out, numel=self.m, name="out")), self.ctx)
+        if not kw:
+            check(self.lib.ibm_apply_schur(self.ctx, _ptr(v, numel=self.m, name="v"),
+                                           _ptr(out, numel=self.m, name="out")), self.ctx)
+            return out
+        o = self.opts(**kw)
+        it = C.c_int64(0)
+        check(self.lib.ibm_apply_schur_opts(self.ctx, _ptr(v, numel=self.m, name="v"),
+                                            _ptr(out, numel=self.m, name="out"), C.byref(o),
+                                            C.byref(it)), self.ctx)
+        self.last_c_iters = it.value
         return out
+
+    def apply_c_inverse(self, t, c_rtol=1e-14, c_maxit=500, out=None):
+        """s = C^{-1} t, C = R^T R, by conjugate gradients; returns (s, iterations)."""
+        nmk = 3 * self.n_markers
+        out = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda") if out is None else out
+        it = C.c_int32(0)
+        if nmk:
+            check(self.lib.ibm_apply_c_inverse(self.ctx, _ptr(t, numel=nmk, name="t"),
+                                               _ptr(out, name="s"), c_rtol, c_maxit,
+                                               C.byref(it)), self.ctx)
+        return out[:nmk], it.value
 
     def precond(self, r, prec=IBM_PREC_FP32, pre=2, post=2, out=None):
         out = self._cells() if out is None else out

@@ -74,7 +74,10 @@ ibm_status ibm_adjoint_step(ibm_ctx* c, const double* u_np1, const double* F_n,
     return set_err(c, IBM_ERR_ARG, "outputs must not alias inputs");
   ibm_status s = check_opts(c, o);
   if (s != IBM_OK) return s;
+  if (o->c_mode != IBM_CMODE_SCALAR)
+    return set_err(c, IBM_ERR_ARG, "the adjoint covers the scalar C mode only");
   if ((s = ensure_krylov(c, o->restart)) != IBM_OK) return s;
+  set_cmode(c, o);
   ibm_solve_stats local;
   if (!st) st = &local;
   memset(st, 0, sizeof(*st));

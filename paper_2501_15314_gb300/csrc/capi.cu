@@ -105,7 +105,19 @@ ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o) {
     return set_err(c, IBM_ERR_ARG, "need helm_rtol > 0 and helm_maxit >= 1");
   if (o->arnoldi != IBM_ARNOLDI_FP64 && o->arnoldi != IBM_ARNOLDI_DS)
     return set_err(c, IBM_ERR_ARG, "arnoldi must be IBM_ARNOLDI_FP64 or IBM_ARNOLDI_DS");
+  if (o->c_mode != IBM_CMODE_SCALAR && o->c_mode != IBM_CMODE_EXACT &&
+      o->c_mode != IBM_CMODE_CONSISTENT)
+    return set_err(c, IBM_ERR_ARG, "c_mode must be IBM_CMODE_SCALAR, _EXACT or _CONSISTENT");
+  if (o->c_mode != IBM_CMODE_SCALAR && (!(o->c_rtol > 0.0) || o->c_maxit < 1))
+    return set_err(c, IBM_ERR_ARG, "need c_rtol > 0 and c_maxit >= 1");
   return IBM_OK;
+}
+
+void set_cmode(ibm_ctx* c, const ibm_solve_opts* o) {
+  c->cmode = o ? o->c_mode : IBM_CMODE_SCALAR;
+  c->c_rtol = o ? o->c_rtol : 1e-14;
+  c->c_maxit = o ? o->c_maxit : 500;
+  c->c_iters = 0;
 }
 
 ibm_status ensure_krylov(ibm_ctx* c, int restart) {
@@ -152,7 +164,8 @@ static void free_all(ibm_ctx* c) {
   cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
-  cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc);
+  cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc); cudaFree(m.cg);
+  cudaFree(m.t3); cudaFree(c->cg_scal);
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off);
   cudaFree(m.ell_base); cudaFree(m.ell_len); cudaFree(m.ell_key); cudaFree(m.ell_coef);
   for (auto& r : c->prof) {
@@ -256,6 +269,9 @@ void ibm_default_opts(ibm_solve_opts* o) {
   o->helm_maxit = 8;
   o->with_advection = 1;
   o->arnoldi = IBM_ARNOLDI_DS;
+  o->c_mode = IBM_CMODE_SCALAR;
+  o->c_rtol = 1e-14;
+  o->c_maxit = 500;
 }
 
 ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
@@ -361,7 +377,21 @@ ibm_status ibm_apply_laplacian(ibm_ctx* c, const double* v, double* out) {
 ibm_status ibm_apply_schur(ibm_ctx* c, const double* v, double* out) {
   if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
   if (bad_ptr(v) || bad_ptr(out) || v == out) return set_err(c, IBM_ERR_ARG, "bad v/out");
+  set_cmode(c, nullptr);
   return schur_apply(c, v, out);
+}
+
+ibm_status ibm_apply_schur_opts(ibm_ctx* c, const double* v, double* out,
+                                const ibm_solve_opts* o, int64_t* c_iters) {
+  if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
+  if (bad_ptr(v) || bad_ptr(out) || v == out) return set_err(c, IBM_ERR_ARG, "bad v/out");
+  const ibm_status s = check_opts(c, o);
+  if (s != IBM_OK) return s;
+  set_cmode(c, o);
+  const ibm_status r = schur_apply(c, v, out);
+  if (c_iters) *c_iters = c->c_iters;
+  set_cmode(c, nullptr);
+  return r;
 }
 
 ibm_status ibm_apply_laplacian_precond(ibm_ctx* c, const double* r, double* z, int32_t prec,
@@ -416,9 +446,12 @@ ibm_status ibm_solve_schur(ibm_ctx* c, const double* b, double* p, const ibm_sol
   if (s != IBM_OK) return s;
   if ((s = ensure_krylov(c, o->restart)) != IBM_OK) return s;
   if (st) memset(st, 0, sizeof(*st));
+  set_cmode(c, o);
   const int ph = prof_begin(c, IBM_PROF_SOLVE);
   s = fgmres_solve(c, b, p, o, st);
   prof_end(c, ph);
+  if (st) st->c_iters = c->c_iters;
+  set_cmode(c, nullptr);
   return s;
 }
 
@@ -453,10 +486,13 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   ibm_solve_stats local;
   if (!st) st = &local;
   memset(st, 0, sizeof(*st));
+  set_cmode(c, o);
   cudaStream_t str = c->stream;
   const double a = 1.5 / c->dt;
   const double inv_h = 1.0 / c->h;
   MarkerData& mk = c->mk;
+  const bool scalar = o->c_mode == IBM_CMODE_SCALAR;
+  const double csign = o->c_mode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0;
 
   // 1. predictor (Eq. (ustar))
   launch_predictor_rhs_adv(c->d, u_n, u_nm1, p_n, f_body, o->with_advection, 1.0 / (2.0 * c->dt),
@@ -476,7 +512,15 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
     launch_interp(c, u_star, mk.t2);
     count_launch();
     k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t2, a, U_gamma, -a, mk.t2, 3 * n);
-    launch_shell_gradt_spread(c, mk.t2, 2.0, c->c2);
+    if (scalar) {
+      launch_shell_gradt_spread(c, mk.t2, 2.0, c->c2);
+    } else {
+      // RHS_F kept in t3 (the Schur products use t and t2); b = RHS_p +- B^T C^{-1} RHS_F
+      IBM_CUDA(c, cudaMemcpyAsync(mk.t3, mk.t2, sizeof(double) * 3 * n,
+                                  cudaMemcpyDeviceToDevice, str));
+      if ((s = c_solve(c, mk.t3, mk.t2, c->c_rtol, c->c_maxit, nullptr)) != IBM_OK) return s;
+      launch_shell_gradt_spread(c, mk.t2, csign, c->c2);
+    }
   }
   IBM_LAUNCH_CHECK(c);
 
@@ -494,8 +538,15 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   launch_grad_axpy(c->d, u_star, pc, -(2.0 * c->dt / 3.0) * inv_h, u_np1, str);
   if (n > 0) {
     launch_marker_grad_interp(c, pc, 1.0, mk.t);
-    count_launch();
-    k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t, 2.0, mk.t2, -2.0, mk.t, 3 * n);
+    if (scalar) {
+      count_launch();
+      k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t, 2.0, mk.t2, -2.0, mk.t, 3 * n);
+    } else {
+      // F' = C^{-1} (B p' - RHS_F)
+      count_launch();
+      k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t, 1.0, mk.t3, -1.0, mk.t3, 3 * n);
+      if ((s = c_solve(c, mk.t3, mk.t, c->c_rtol, c->c_maxit, nullptr)) != IBM_OK) return s;
+    }
     count_launch();
     k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(F_n, 1.0, mk.t, 1.0, F_np1, 3 * n);
     launch_shell_spread_faces(c, mk.t, 2.0 * c->dt / 3.0, u_np1);
@@ -513,6 +564,8 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
     IBM_LAUNCH_CHECK(c);
     if ((s = norm2_host(c, mk.t2, 3 * n, &st->slip_l2)) != IBM_OK) return s;
   }
+  st->c_iters = c->c_iters;
+  set_cmode(c, nullptr);
   return solve_status;
 }
 

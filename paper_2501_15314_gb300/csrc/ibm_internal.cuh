@@ -67,6 +67,8 @@ struct MarkerData {
                             // the component's own axis: (w_{a-1} - w_a) / h
   double* dwf = nullptr;    // [3 axes][3 taps][n] phi' at the face taps
   double* dwc = nullptr;    // [3 axes][3 taps][n] phi' at the centre taps
+  double* cg = nullptr;     // [3][3n] conjugate-gradient work vectors for C^{-1}
+  double* t3 = nullptr;     // [3][n] per-marker scratch (RHS_F in the C modes)
   // cell-sorted (marker, slot) list for the atomic-free gathers
   int64_t n_entries = 0, entries_cap = 0;
   int32_t* entry_key = nullptr;   // marker * 64 + slot, sorted within a cell
@@ -132,6 +134,13 @@ struct ibm_ctx {
 
   ibm::MarkerData mk;
   bool markers_set = false;
+
+  // C mode of the running call (set from the options at every entry point)
+  int cmode = 0;
+  double c_rtol = 1e-14;
+  int c_maxit = 500;
+  int64_t c_iters = 0;             // inner CG iterations since the call began
+  double* cg_scal = nullptr;       // [8] device scalars of the CG on C
 
   // event timing of kernel classes (ibm_profile_enable)
   bool prof_on = false;
@@ -217,6 +226,13 @@ void launch_interp_dpos(ibm_ctx* c, const double* f, const double* m, double sca
                         bool accumulate, double* Xbar);
 // u[face] = beta * u[face] + scale * (R F)[face] on shell faces only
 void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double* u);
+// u = R F on the shell faces only (written, not accumulated)
+void launch_shell_spread_faces_set(ibm_ctx* c, const double* F, double* u);
+// ---- C = R^T R (cmode.cu) ----
+void apply_C(ibm_ctx* c, const double* v, double* out);
+ibm_status c_solve(ibm_ctx* c, const double* t, double* s, double rtol, int maxit, int* iters);
+// the ctx's C mode from the options (and the CG counter reset)
+void set_cmode(ibm_ctx* c, const ibm_solve_opts* o);
 
 // ---- reductions and vector kernels (krylov.cu) ----
 // red_out[q] = <w, V_q>, q < nq (two-stage, fixed order)

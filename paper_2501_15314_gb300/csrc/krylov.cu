@@ -247,8 +247,16 @@ ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
   launch_laplacian<double>(c->d, v, out, 1.0 / (c->h * c->h), c->stream);
   prof_end(c, ph);
   ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
-  launch_marker_grad_interp(c, v, 2.0, c->mk.t);
-  launch_shell_gradt_spread(c, c->mk.t, 1.0, out);
+  if (c->cmode == IBM_CMODE_SCALAR) {
+    launch_marker_grad_interp(c, v, 2.0, c->mk.t);
+    launch_shell_gradt_spread(c, c->mk.t, 1.0, out);
+  } else if (c->mk.n > 0) {
+    // out +- B^T C^{-1} B v (exact / sign-consistent forms)
+    launch_marker_grad_interp(c, v, 1.0, c->mk.t);
+    const ibm_status s = c_solve(c, c->mk.t, c->mk.t2, c->c_rtol, c->c_maxit, nullptr);
+    if (s != IBM_OK) { prof_end(c, ph); return s; }
+    launch_shell_gradt_spread(c, c->mk.t2, c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0, out);
+  }
   prof_end(c, ph);
   IBM_LAUNCH_CHECK(c);
   return IBM_OK;

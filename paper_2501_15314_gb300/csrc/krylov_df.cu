@@ -396,11 +396,22 @@ ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
   const MarkerData& m = c->mk;
   if (m.n > 0 && m.n_shell > 0) {
     ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
-    launch_marker_grad_interp_f32(c, z, 2.0, m.t);
+    const double* t = m.t;
+    double sign = 1.0;
+    if (c->cmode == IBM_CMODE_SCALAR) {
+      launch_marker_grad_interp_f32(c, z, 2.0, m.t);
+    } else {
+      // +- B^T C^{-1} B z (exact / sign-consistent forms), C^{-1} in FP64
+      launch_marker_grad_interp_f32(c, z, 1.0, m.t);
+      const ibm_status st = c_solve(c, m.t, m.t2, c->c_rtol, c->c_maxit, nullptr);
+      if (st != IBM_OK) { prof_end(c, ph); return st; }
+      t = m.t2;
+      sign = c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0;
+    }
     count_launch();
     k_shell_gradt_ds<<<div_up(m.n_shell, 256), 256, 0, s>>>(
-        m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, m.t,
-        1.0, w);
+        m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
+        sign, w);
     prof_end(c, ph);
   }
   IBM_LAUNCH_CHECK(c);

@@ -332,7 +332,7 @@ __global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
                                      const int32_t* __restrict__ shell_cell,
                                      const int32_t* __restrict__ off,
                                      const int32_t* __restrict__ key,
-                                     const double* __restrict__ F, double scale,
+                                     const double* __restrict__ F, double scale, int set,
                                      double* __restrict__ u) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= 3 * n_shell) return;
@@ -365,7 +365,7 @@ __global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
   const int64_t sy = d.nx + (dc == 0 ? 1 : 0);
   const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
   const int64_t f = foff + ck * sz + cj * sy + ci;
-  u[f] = fma(scale, acc, u[f]);
+  u[f] = set ? scale * acc : fma(scale, acc, u[f]);
 }
 
 // ---- exclusive scan of int32 (three phases, 4096 elements per block) ----
@@ -476,8 +476,9 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
   if (n <= m.cap) return IBM_OK;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
   cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc);
+  cudaFree(m.cg); cudaFree(m.t3);
   m.bf = m.bc = m.org = nullptr;
-  m.wf = m.wc = m.cw = m.t = m.t2 = m.dwf = m.dwc = nullptr;
+  m.wf = m.wc = m.cw = m.t = m.t2 = m.dwf = m.dwc = m.cg = m.t3 = nullptr;
   m.cap = 0;
   const size_t ni = sizeof(int32_t) * 3 * n, nd = sizeof(double) * 9 * n;
   if (cudaMalloc(&m.bf, ni) != cudaSuccess || cudaMalloc(&m.bc, ni) != cudaSuccess ||
@@ -486,7 +487,9 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
       cudaMalloc(&m.dwc, nd) != cudaSuccess ||
       cudaMalloc(&m.cw, sizeof(double) * 12 * n) != cudaSuccess ||
       cudaMalloc(&m.t, sizeof(double) * 3 * n) != cudaSuccess ||
-      cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess) {
+      cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&m.t3, sizeof(double) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&m.cg, sizeof(double) * 9 * n) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, IBM_ERR_NOMEM, "marker workspace allocation failed");
   }
@@ -734,7 +737,15 @@ void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double
   if (m.n == 0 || m.n_shell == 0) return;
   count_launch();
   k_shell_spread_faces<<<div_up(3 * m.n_shell, TPB), TPB, 0, c->stream>>>(
-      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, scale, u);
+      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, scale, 0, u);
+}
+
+void launch_shell_spread_faces_set(ibm_ctx* c, const double* F, double* u) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0 || m.n_shell == 0) return;
+  count_launch();
+  k_shell_spread_faces<<<div_up(3 * m.n_shell, TPB), TPB, 0, c->stream>>>(
+      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, 1.0, 1, u);
 }
 
 }  // namespace ibm
