@@ -312,6 +312,7 @@ def run_ours(args):
     # ---- adjoint of the step (transposed Schur solve) ----
     adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
     c_modes = cmode_bench(timed, max(1, k64 // 2))
+    porous = porous_bench(timed, k64)
 
     # ---- roofline of the dominant kernel class ----
     # algorithmic bytes per launch (DRAM traffic the kernel must move at
@@ -366,7 +367,7 @@ def run_ours(args):
             "helm_iters": st_mixed[-1]["helm_iters"],
             "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
             "roofline": roof, "kernel_classes": classes, "breakdown": breakdown,
-            "adjoint": adjoint, "c_modes": c_modes,
+            "adjoint": adjoint, "c_modes": c_modes, "porous": porous,
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -435,6 +436,41 @@ def adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, K):
                      f"{W4.n_markers} markers, Re {W4.Re}, dt {W4.dt}, from rest"),
         "adjoint_ms": ms4, "iters": st4["iters"], "relres": st4["relres_true"]}
     s4.close()
+    return res
+
+
+def porous_bench(timed, K):
+    """The headline step (mixed form, rtol 1e-8) on a second geometry: the
+    porous spheres of Sec. 6.1.2 (7 and 14 sub-spheres of Table 1, markers at
+    spacing h) at 256^3."""
+    import numpy as np
+    import torch
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    res = {}
+    for k in (7, 14):
+        Wp = wl.porous_sphere(256, k)
+        sp = IBMSolver(Wp.n, Re=Wp.Re, dt=Wp.dt)
+        X, U, f = dv(Wp.X), dv(Wp.U_gamma.ravel()), dv(Wp.f_body)
+        zf = torch.zeros(sp.nf, dtype=torch.float64, device="cuda")
+        zc = torch.zeros(sp.m, dtype=torch.float64, device="cuda")
+        zk = torch.zeros(3 * Wp.n_markers, dtype=torch.float64, device="cuda")
+        o = dict(u=torch.empty_like(zf), p=torch.empty_like(zc), F=torch.empty_like(zk))
+
+        def one():
+            sp.set_markers(X)
+            return sp.step(zf, zf, zc, zk, U, f, out=o, precond_prec=_lib.IBM_PREC_FP32,
+                           rtol=1e-8)[1]
+        one()
+        ms, st = timed(one, K)
+        res[f"{k}_subspheres"] = {
+            "workload": (f"{Wp.name}: 256^3, {k} sub-spheres r {Wp.radii[0]:.4f} in a bounding "
+                         f"sphere D 0.3 at t = 1 of the oscillation, {Wp.n_markers} markers"),
+            "steps_per_s": 1000.0 / ms, "ms": ms, "iters": st[-1]["iters"],
+            "relres": st[-1]["relres_true"]}
+        sp.close()
     return res
 
 

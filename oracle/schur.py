@@ -4,7 +4,7 @@ complement, FP64, CPU.  TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 With B = R^T G and C = R^T R (Eq. (Saddle)):
 
 * saddle matrix  [[L, B^T], [B, -C]] (Eq. (Saddle), read literally: the
-  paper's Theorem 1, Table 1 and every iteration count refer to this form);
+  paper's Theorem 1, Table 2 (PrecResults) and every iteration count refer to this form);
 * exact primal Schur complement S_p = L + B^T C^{-1} B (Eq. (SchurPrimal)),
   RHS  RHS_p + B^T C^{-1} RHS_F  (Eq. (SchurPrimalP)),
   force  F' = C^{-1}(B p' - RHS_F)  (Eq. (SchurPrimalF));
@@ -36,7 +36,7 @@ Krylov iteration (Sec. 4.2).
 
 Pins (tests/test_oracle_schur.py): dense brute-force solve on small grids;
 Theorem 1 (spec(L^+ S_p) in [1, 2]) by a dense generalised eigenproblem;
-spec(L^+ S~_p) near [1, 2] as in Table 1; the Schur elimination against a
+spec(L^+ S~_p) near [1, 2] as in Table 2 (PrecResults); the Schur elimination against a
 direct block solve of Eq. (Saddle); no markers gives p' = L^+ b;
 grid-independent FGMRES iteration counts and the large unpreconditioned count
 (Sec. 6.2).

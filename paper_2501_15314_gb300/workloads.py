@@ -213,6 +213,55 @@ def oscillating_sphere(n: int, n_markers: int | None, t: float = 1.0, radius: fl
                     np.array([radius]), U, np.zeros(nf), info)
 
 
+# Table 1 (label spheresCenters) of the paper: centres of the sub-spheres of
+# the porous-sphere models of Sec. 6.1.2, in units of the bounding diameter D
+# (the table prints 10x these values) relative to the bounding centre, and the
+# sub-sphere radius in units of D.  The 14-sphere entry 1 prints y = -2.287;
+# the symmetry of entries 1-4 gives -2.2875, used here.
+POROUS_CENTRES = {
+    7: (0.193, [(1.1140, -1.9296, -2.1126), (-2.2281, 0.0, -2.1126), (1.1140, 1.9296, -2.1126),
+                (-1.5009, -2.5997, 0.64522), (3.0019, 0.0, 0.64522), (-1.5009, 2.5997, 0.64522),
+                (0.0, 0.0, 3.0704)]),
+    14: (0.161, [(0.0, -2.2875, -2.4917), (-2.2875, 0.0, -2.4917), (2.2875, 0.0, -2.4917),
+                 (0.0, 2.2875, -2.4917), (-2.3820, -2.3820, -0.30478), (2.3820, -2.3820, -0.30478),
+                 (-2.3820, 2.3820, -0.30478), (2.3820, 2.3820, -0.30478), (0.0, 0.0, 0.0),
+                 (0.0, -2.8412, 1.8355), (-2.8412, 0.0, 1.8355), (2.8412, 0.0, 1.8355),
+                 (0.0, 2.8412, 1.8355), (0.0, 0.0, 3.3825)]),
+}
+
+
+def porous_sphere(n: int, n_sub: int, t: float = 1.0, D: float = 0.3, amp_ratio: float = 1.0,
+                  Re: float = 100.0, dt: float = 2e-3, spacing_ratio: float = 1.0) -> Workload:
+    """The porous sphere of Sec. 6.1.2: n_sub (7 or 14) rigid sub-spheres
+    packed in a bounding sphere of diameter D (Table 1), each radius reduced
+    by half a cell width, the whole array oscillating along z like the sphere
+    of Sec. 6.1.1 (Eq. (u_z_and_z), A = amp_ratio D, at time t): bounding
+    centre (0.5, 0.5, 0.5 - A cos(t D/A)), every marker moving with
+    sin(t D/A) e_z.  Markers at Lagrangian spacing h / spacing_ratio on every
+    sub-sphere; zero body force."""
+    r_unit, cents = POROUS_CENTRES[n_sub]
+    h = 1.0 / n
+    A = amp_ratio * D
+    c0 = np.array([0.5, 0.5, 0.5 - A * np.cos(t * D / A)])
+    centers = c0[None, :] + 0.1 * D * np.asarray(cents, dtype=np.float64)
+    r_sub = r_unit * D - 0.5 * h
+    Xs, ids = [], []
+    for b, c in enumerate(centers):
+        nm = markers_for_spacing(r_sub, h / spacing_ratio)
+        Xs.append(fibonacci_sphere(nm, r_sub, c))
+        ids.append(np.full(nm, b, dtype=np.int32))
+    X = np.concatenate(Xs, axis=1)
+    body_id = np.concatenate(ids)
+    U = np.zeros_like(X)
+    U[2] = np.sin(t * D / A)
+    nf = 3 * n * n * (n + 1)
+    area = 4.0 * np.pi * r_sub ** 2 * n_sub
+    info = dict(spacing_ratio=h / np.sqrt(area / X.shape[1]), counts=[len(i) for i in ids],
+                t=t, bounding_centre=c0.tolist(), D=D, r_sub=r_sub)
+    return Workload(f"porous{n_sub}_{n}", n, Re, dt, X, body_id, centers,
+                    np.full(n_sub, r_sub), U, np.zeros(nf), info)
+
+
 def small_spheres(n: int, n_bodies: int, seed: int, r_lo: float, r_hi: float,
                   Re: float = 100.0, dt: float = 0.01,
                   spacing_ratio: float = 1.0) -> Workload:

@@ -1,5 +1,5 @@
 """Pins of oracle.delta (Roma delta, R, R^T) to closed forms, brute force and
-the paper's Table A1."""
+the paper's Table A1 (RtR_spacing)."""
 import numpy as np
 import pytest
 
@@ -98,7 +98,7 @@ def test_C_diagonal_is_one_eighth():
 
 
 def test_table_a1_rtr_row_sums():
-    # Appendix A, Table A1: average row sum of R^T R against spacing ratio
+    # Appendix A, Table A1 (RtR_spacing): average row sum of R^T R against spacing ratio
     table = load_golden("table_a1_rtr_rowsums.txt")
     g = mac.Grid(32)
     for ratio, lo, hi, avg in table:

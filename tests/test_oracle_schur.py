@@ -1,5 +1,5 @@
 """Pins of oracle.schur: brute-force block solves, the spectral theorem of
-Sec. 5, Table 1's behaviour of the scalar approximation, and the
+Sec. 5, Table 2 (PrecResults)'s behaviour of the scalar approximation, and the
 grid-independent iteration counts of Sec. 6.2."""
 import numpy as np
 import pytest
@@ -57,12 +57,12 @@ def test_theorem_spectrum_in_1_2(n):
     Sq = Q.T @ sys.dense_S_exact() @ Q
     ev = np.linalg.eigvals(np.linalg.solve(Lq, Sq)).real
     assert ev.min() >= 1.0 - 1e-9 and ev.max() <= 2.0 + 1e-9
-    assert ev.max() > 1.9     # the upper bound is nearly attained (Table 1)
+    assert ev.max() > 1.9     # the upper bound is nearly attained (Table 2, PrecResults)
 
 
-def test_scalar_approximation_spectrum_like_table1():
-    # Table 1: spec(L^{-1} S~_p) starts at 1 and reaches close to 2
-    tab = load_golden("table1_spectrum.txt")
+def test_scalar_approximation_spectrum_like_table2():
+    # Table 2 (PrecResults): spec(L^{-1} S~_p) starts at 1 and reaches close to 2
+    tab = load_golden("table2_spectrum.txt")
     sys, _ = _system(8, r=0.25)
     Q = _mean_zero_basis(sys.g.m)
     Lq = Q.T @ sys.L.toarray() @ Q
