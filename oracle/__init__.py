@@ -32,6 +32,12 @@ Modules:
                  force recovery, update (Eqs. (ustar)-(Saddle),
                  (ApproxSchurPrimalP), (ApproxSchurPrimalF), (u_n_plus_1)) and
                  the force/torque diagnostics (Eq. (IBM_force)).
+* ``fsi``        two-way coupled rigid spheres (Sec. 3.2): position and
+                 Rodrigues orientation prediction, Newton's laws in BDF2 form
+                 (Eqs. (bdy_linear_vel_iter), (bdy_angular_vel_iter)) with the
+                 enclosed-fluid momentum from volume fractions
+                 (Eq. (volume_integrals)), the relaxed correction loop with
+                 its L1 stopping rule (Eq. (convergence_criterion)).
 * ``adjoint``    reverse-mode derivative of that step and of the body force /
                  torque sums with respect to U^Gamma and the marker positions
                  (through phi', the derivative of Eq. (delta)); the paper has

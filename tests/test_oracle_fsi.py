@@ -1,0 +1,182 @@
+"""Pins of oracle.fsi (two-way coupled rigid spheres, Sec. 3.2): volume
+fractions and fluid momentum against exact volumes and rigid-body integrals,
+the Rodrigues increment against a rotation, the BDF2 rigid update against
+free fall, the step against oracle.step for fixed bodies, the fixed point of
+the correction loop, and a heavy sphere falling slower than in vacuum."""
+import numpy as np
+import pytest
+
+from oracle import fsi, mac, step
+from paper_2501_15314_gb300 import workloads as wl
+
+
+def _cell_alpha_volume(n, c, r):
+    g = mac.Grid(n)
+    return fsi.volume_fraction(g, 0, c, r).sum() * g.h ** 3
+
+
+def test_volume_fraction_second_order():
+    c, r = np.array([0.503, 0.49, 0.511]), 0.23
+    V = 4.0 * np.pi * r ** 3 / 3.0
+    errs = [abs(_cell_alpha_volume(n, c, r) - V) / V for n in (16, 32, 64)]
+    assert errs[2] < 2e-3
+    assert errs[1] / errs[2] > 2.5 and errs[0] / errs[1] > 2.5    # about 4x per halving
+
+
+def test_volume_fraction_range():
+    g = mac.Grid(24)
+    a = fsi.volume_fraction(g, 1, [0.5, 0.5, 0.5], 0.3)
+    assert a.min() >= 0.0 and a.max() <= 1.0
+    x, y, z = g.face_coords(1)
+    d = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+    assert np.all(a[d < 0.3 - g.h] == 1.0) and np.all(a[d > 0.3 + g.h] == 0.0)
+
+
+def test_fluid_momentum_uniform_and_rotating_fields():
+    g = mac.Grid(48)
+    c, r = np.array([0.5, 0.52, 0.47]), 0.25
+    b = fsi.RigidSphere(r, 2.0, c, c)
+    U = np.array([0.3, -0.7, 1.1])
+    comps = []
+    for d in range(3):
+        x, _, _ = g.face_coords(d)
+        comps.append(np.full(x.shape, U[d]))
+    lin, ang = fsi.fluid_momentum(g, g.pack_faces(*comps), c, r)
+    np.testing.assert_allclose(lin, b.volume * U, rtol=5e-3)
+    assert np.abs(ang).max() < 5e-3 * b.volume * r * np.abs(U).max()
+    w = np.array([0.4, -1.3, 0.9])
+    comps = []
+    for d in range(3):
+        x, y, z = g.face_coords(d)
+        rr = (x - c[0], y - c[1], z - c[2])
+        comps.append(w[(d + 1) % 3] * rr[(d + 2) % 3] - w[(d + 2) % 3] * rr[(d + 1) % 3])
+    lin, ang = fsi.fluid_momentum(g, g.pack_faces(*comps), c, r)
+    np.testing.assert_allclose(ang, b.inertia * w, rtol=1e-2)
+    assert np.abs(lin).max() < 1e-2 * b.volume * r * np.abs(w).max()
+
+
+def test_rodrigues_increment_rotates_by_the_ab2_angle():
+    om, om_prev, dt = np.array([0.3, -1.2, 0.8]), np.array([0.1, 0.2, -0.4]), 0.05
+    Rd = fsi.rodrigues_increment(om, om_prev, dt)
+    np.testing.assert_allclose(Rd @ Rd.T, np.eye(3), atol=1e-14)
+    assert abs(np.linalg.det(Rd) - 1.0) < 1e-14
+    axis = om / np.linalg.norm(om)
+    np.testing.assert_allclose(Rd @ axis, axis, atol=1e-14)
+    gam = dt * (1.5 * np.linalg.norm(om) - 0.5 * np.linalg.norm(om_prev))
+    v = np.cross(axis, [1.0, 0.0, 0.0])
+    v /= np.linalg.norm(v)
+    assert abs(np.dot(Rd @ v, v) - np.cos(gam)) < 1e-14
+    assert abs(np.dot(np.cross(v, Rd @ v), axis) - np.sin(gam)) < 1e-14
+    np.testing.assert_allclose(fsi.rodrigues_increment(np.zeros(3), om, dt), np.eye(3))
+
+
+def test_rigid_update_free_fall_is_exact():
+    # no fluid: u_s(t) = ((theta - 1)/theta) g t is linear in t, which BDF2
+    # reproduces exactly from exact starting values
+    dt, th, g = 0.01, 3.0, np.array([0.0, 0.0, -9.81])
+    acc = (th - 1.0) / th * g
+    b = fsi.RigidSphere(0.1, th, np.zeros(3), np.zeros(3))
+    b.us_prev, b.us = 0.0 * acc, dt * acc
+    z = np.zeros(3)
+    for n in range(1, 6):
+        us, _ = fsi.rigid_velocities(b, dt, z, z, z, z, g)
+        np.testing.assert_allclose(us, (n + 1) * dt * acc, rtol=1e-13)
+        b.us_prev, b.us = b.us, us
+
+
+def test_rigidly_moving_enclosed_fluid_leaves_the_reduced_mass():
+    """theta V du_s/dt = -F + d/dt int_{V_p} u dV: when the enclosed fluid
+    moves with the body (int u dV = V u_s at every level), the body responds
+    like a mass (theta - 1) V (and inertia (theta - 1) J) to the IB force and
+    torque."""
+    dt, th = 0.02, 2.5
+    b = fsi.RigidSphere(0.15, th, np.zeros(3), np.zeros(3))
+    V, J = b.volume, b.inertia
+    b.us, b.us_prev = np.array([0.2, -0.1, 0.4]), np.array([0.1, 0.0, 0.35])
+    b.om, b.om_prev = np.array([1.0, 0.5, -0.2]), np.array([0.8, 0.6, -0.1])
+    b.mom, b.mom_prev = V * b.us, V * b.us_prev
+    b.amom, b.amom_prev = J * b.om, J * b.om_prev
+    F, T = np.array([0.03, -0.02, 0.05]), np.array([-0.004, 0.002, 0.001])
+    us_exp = (4 * b.us - b.us_prev) / 3 - (2 * dt / 3) * F / ((th - 1) * V)
+    om_exp = (4 * b.om - b.om_prev) / 3 - (2 * dt / 3) * T / ((th - 1) * J)
+    us, om = fsi.rigid_velocities(b, dt, F, T, V * us_exp, J * om_exp, np.zeros(3))
+    np.testing.assert_allclose(us, us_exp, rtol=1e-12)
+    np.testing.assert_allclose(om, om_exp, rtol=1e-12)
+
+
+def _body_setup(n, theta=2.0, free=True, r=0.2, c=(0.5, 0.52, 0.49), seed=3):
+    W = wl.spheres_workload("t", n, 100.0, 0.01, [c], [r], None, seed)
+    X = W.X.reshape(3, -1)
+    cc = np.asarray(c, dtype=np.float64)
+    b = fsi.RigidSphere(r, theta, cc.copy(), cc.copy(), free=free)
+    return W, X, X - cc[:, None], np.zeros(X.shape[1], dtype=np.int32), b
+
+
+def test_fixed_body_one_correction_equals_one_way_step():
+    n = 12
+    W, X, L0, bid, b = _body_setup(n, free=False)
+    g = mac.Grid(n)
+    rng = np.random.default_rng(1)
+    mask = g.interior_face_mask_packed()
+    u_n = 0.2 * rng.standard_normal(g.n_faces) * mask
+    u_nm1 = 0.2 * rng.standard_normal(g.n_faces) * mask
+    p_n = rng.standard_normal(g.m)
+    F_n = rng.standard_normal(3 * X.shape[1])
+    out = fsi.fsi_step(g, W.Re, W.dt, [b], L0, bid, u_n, u_nm1, p_n, F_n, W.f_body,
+                       xi=1.0, max_inner=1)
+    ref = step.step(g, W.Re, W.dt, X, np.zeros_like(X), W.f_body, u_n=u_n, u_nm1=u_nm1,
+                    p_n=p_n, F_n=F_n)
+    for k in ("u", "p", "F"):
+        np.testing.assert_allclose(out[k], ref[k], atol=1e-12 * np.abs(ref[k]).max())
+    np.testing.assert_allclose(out["X"], X, atol=0)
+
+
+def test_corrections_approach_the_constrained_fixed_point():
+    """Eq. (pressure_force_iterative_system): at the loop's fixed point the
+    right-hand side (div u, R^T u - U) vanishes.  With C^{-1} ~ 2 I the slip
+    error contracts by (I - 2C) per correction, slowly for C's small
+    eigenvalues, so the pin is the monotone decrease of both residuals and of
+    ||F'||_1 / ||F||_1, and the exact BDF2 position for constant velocity."""
+    n = 12
+    g = mac.Grid(n)
+    res = []
+    for k in (1, 4, 16, 64):
+        W, X, L0, bid, b = _body_setup(n, free=False)
+        b.us = b.us_prev = np.array([0.3, -0.2, 0.5])
+        b.xc_prev = b.xc - W.dt * b.us
+        out = fsi.fsi_step(g, W.Re, W.dt, [b], L0, bid, np.zeros(g.n_faces),
+                           np.zeros(g.n_faces), np.zeros(g.m), np.zeros(3 * X.shape[1]),
+                           W.f_body, xi=1.0, tol=0.0, max_inner=k)
+        sysm = out["sys"]
+        div = np.linalg.norm(sysm.G.T @ out["u"])
+        slip = np.linalg.norm((sysm.R.T @ out["u"]).reshape(3, -1) - b.us[:, None])
+        res.append((div, slip, out["ratio"]))
+        # constant velocity: (4 x^n - x^{n-1})/3 + (2/3) dt u = x^n + dt u
+        np.testing.assert_allclose(out["X"], X + W.dt * b.us[:, None], atol=1e-15)
+    div, slip, ratio = map(np.array, zip(*res))
+    assert np.all(np.diff(div) < 0) and np.all(np.diff(ratio) < 0)
+    assert div[-1] < 1e-2 * div[0] and slip[-1] < 0.3 * slip[0]
+
+
+def test_heavy_sphere_falls_slower_than_in_vacuum():
+    """A sphere of density ratio 1.5 released from rest: it accelerates
+    downwards, less than in vacuum ((theta - 1)/theta g), without sideways
+    drift.  On this coarse grid the correction loop levels off near
+    ||F'||_1/||F||_1 = 2e-3 (the forces are small just after release)."""
+    n = 16
+    W, X, L0, bid, b = _body_setup(n, theta=1.5, r=0.18, c=(0.5, 0.5, 0.55))
+    g = mac.Grid(n)
+    grav = np.array([0.0, 0.0, -1.0])
+    dt = 0.01
+    u, um1, p = np.zeros(g.n_faces), np.zeros(g.n_faces), np.zeros(g.m)
+    F = np.zeros(3 * X.shape[1])
+    for _ in range(3):
+        out = fsi.fsi_step(g, 20.0, dt, [b], L0, bid, u, um1, p, F, None, gravity=grav,
+                           xi=0.8, tol=1e-3, max_inner=40)
+        assert out["ratio"] < 1e-2
+        um1, u, p, F = u, out["u"], out["p"], out["F"]
+    t = 3 * dt
+    vacuum = (b.theta - 1.0) / b.theta * grav[2] * t
+    assert vacuum < b.us[2] < 0.0                  # falls, but slower than in vacuum
+    assert abs(b.us[0]) + abs(b.us[1]) < 1e-3 * abs(b.us[2])
+    assert b.xc[2] < 0.55
