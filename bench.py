@@ -313,6 +313,8 @@ def run_ours(args):
     adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
     c_modes = cmode_bench(timed, max(1, k64 // 2))
     porous = porous_bench(timed, k64)
+    fsi = fsi_bench(timed, 3, 2)
+    multistep = multistep_bench()
 
     # ---- roofline of the dominant kernel class ----
     # algorithmic bytes per launch (DRAM traffic the kernel must move at
@@ -367,7 +369,8 @@ def run_ours(args):
             "helm_iters": st_mixed[-1]["helm_iters"],
             "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
             "roofline": roof, "kernel_classes": classes, "breakdown": breakdown,
-            "adjoint": adjoint, "c_modes": c_modes, "porous": porous,
+            "adjoint": adjoint, "c_modes": c_modes, "porous": porous, "two_way_fsi": fsi,
+            "multistep": multistep,
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -436,6 +439,98 @@ def adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, K):
                      f"{W4.n_markers} markers, Re {W4.Re}, dt {W4.dt}, from rest"),
         "adjoint_ms": ms4, "iters": st4["iters"], "relres": st4["relres_true"]}
     s4.close()
+    return res
+
+
+def multistep_bench(steps=10):
+    """Ten consecutive one-way steps at 128^3 (one sphere r 0.15, markers at
+    spacing h, Re 100, dt 2e-3, sine-mode body force; the markers stay put;
+    the stated 16000 markers, spacing h/1.86, make the scalar-C time
+    integration diverge, as Table A1 of the paper reports above 1.58):
+    mixed form (FP32 V-cycle, double-single Arnoldi, rtol 1e-8) against the
+    FP64 form (rtol 1e-12), time per step of each and their per-step
+    difference ||x_mixed - x_fp64|| / ||x_fp64|| for u, p, F (the error
+    against the oracle is in the parity tests)."""
+    import numpy as np
+    import torch
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+    W = wl.config(2)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    X, U, f = dv(W.X), dv(W.U_gamma.ravel()), dv(W.f_body)
+    forms = {"mixed": dict(precond_prec=1, rtol=1e-8),
+             "fp64": dict(precond_prec=0, arnoldi=0, rtol=1e-12, helm_rtol=1e-13,
+                          helm_maxit=12)}
+    runs = {}
+    for name, kw in forms.items():
+        s = IBMSolver(W.n, Re=W.Re, dt=W.dt)
+        s.set_markers(X)
+        z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")  # noqa: E731
+        st = dict(u=z(s.nf), um1=z(s.nf), p=z(s.m), F=z(3 * W.n_markers))
+        hist, its = [], []
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(steps):
+            out, stat = s.step(st["u"], st["um1"], st["p"], st["F"], U, f, **kw)
+            st["um1"], st["u"], st["p"], st["F"] = st["u"], out["u"], out["p"], out["F"]
+            hist.append({k: v.clone() for k, v in out.items()})
+            its.append(stat["iters"])
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        runs[name] = (e0.elapsed_time(e1) / steps, hist, its)
+        s.close()
+    diff = []
+    for a, b in zip(runs["mixed"][1], runs["fp64"][1]):
+        diff.append({k: float(torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k]))
+                     for k in ("u", "p", "F")})
+    return {"workload": (f"{W.name}: 128^3, sphere r 0.15, {W.n_markers} markers, Re {W.Re}, "
+                         f"dt {W.dt}, {steps} consecutive steps from rest"),
+            "ms_per_step_mixed": runs["mixed"][0], "ms_per_step_fp64": runs["fp64"][0],
+            "iters_mixed": runs["mixed"][2], "iters_fp64": runs["fp64"][2],
+            "mixed_vs_fp64_per_step": diff}
+
+
+def fsi_bench(timed, K, W, n=384):
+    """Two-way coupled step (Sec. 3.2) of the sedimenting sphere: r = 0.08,
+    density ratio 1.05, Re 50, dt 5e-4, gravity 10 along -z, released from
+    rest at (0.5, 0.5, 0.7), markers at spacing h; FP32 V-cycle, inner Schur
+    solves to 1e-2, corrections until ||F'||_1/||F||_1 < 1e-3 (xi = 1).  W
+    untimed steps from rest, then K timed steps."""
+    import numpy as np
+    import torch
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver, RigidSpheres
+    r, th, dt = 0.08, 1.05, 5e-4
+    nm = wl.markers_for_spacing(r, 1.0 / n)
+    L0 = torch.from_numpy(wl.fibonacci_sphere(nm, r, [0.0, 0.0, 0.0])).cuda()
+    bid = torch.zeros(nm, dtype=torch.int32, device="cuda")
+    sp = RigidSpheres([r], [th], [(0.5, 0.5, 0.7)])
+    s = IBMSolver(n, Re=50.0, dt=dt)
+    z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")  # noqa: E731
+    st_ = dict(u=z(s.nf), um1=z(s.nf), p=z(s.m), F=z(3 * nm))
+    outs = [dict(X=z(3 * nm), u=z(s.nf), p=z(s.m), F=z(3 * nm)) for _ in range(3)]
+    cnt = [0]
+
+    def one():
+        o = outs[cnt[0] % 3]
+        cnt[0] += 1
+        out, st = s.fsi_step(sp, L0, bid, st_["u"], st_["um1"], st_["p"], st_["F"], None,
+                             out=o, gravity=(0.0, 0.0, -10.0), xi=1.0, tol=1e-3, max_inner=200,
+                             rtol=1e-2, raise_on_error=False)
+        st_["um1"], st_["u"], st_["p"], st_["F"] = st_["u"], out["u"], out["p"], out["F"]
+        return st
+    for _ in range(W):
+        one()
+    ms, sts = timed(one, K)
+    res = {"workload": (f"sediment{n}: {n}^3, sphere r {r} density ratio {th}, Re 50, dt {dt}, "
+                        f"g 10, {nm} markers, steps {W + 1}..{W + K} after release"),
+           "ms_per_step": ms, "steps_per_s": 1000.0 / ms,
+           "corrections_per_step": [st["inner"] for st in sts],
+           "fgmres_iters_per_step": [st["fgmres_iters"] for st in sts],
+           "ratio": [st["ratio"] for st in sts],
+           "u_s_z": float(sp.get("us")[0, 2])}
+    s.close()
     return res
 
 

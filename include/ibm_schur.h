@@ -295,6 +295,76 @@ ibm_status ibm_body_forces_noalloc(const double* F, const double* X, const int32
                                    int64_t n_markers, int32_t n_bodies, const double* centers,
                                    double h, void* stream, double* out);
 
+/* ---- Two-way coupled rigid spheres (Sec. 3.2) ---------------------------
+ * Per sphere, the state at t^n and t^{n-1} that the BDF2 forms of Newton's
+ * laws (Eqs. (bdy_linear_vel_iter), (bdy_angular_vel_iter)) and the
+ * Rodrigues orientation update (Eqs. (rotat_axis)-(next_time_step_matr))
+ * need.  Lengths are those of the grid (fluid density 1): a sphere of radius
+ * r has volume V = 4 pi r^3/3 and moment of inertia theta J, J = 2 V r^2/5.
+ * Host memory; ibm_fsi_step advances it to t^{n+1}. */
+typedef struct {
+  double radius;                  /* sphere radius                          */
+  double theta;                   /* density ratio rho_p / rho_f            */
+  double xc[3], xc_prev[3];       /* centre at t^n, t^{n-1}                 */
+  double us[3], us_prev[3];       /* translational velocity                 */
+  double om[3], om_prev[3];       /* angular velocity (inertial frame)      */
+  double om_cs[3], om_cs_prev[3]; /* angular velocity (body frame)          */
+  double rot[9];                  /* orientation R^n, row-major, maps body-
+                                     frame vectors to the inertial frame    */
+  double mom[3], mom_prev[3];     /* enclosed fluid momentum int_{V_p} u dV */
+  double amom[3], amom_prev[3];   /* int_{V_p} (x - x_c) x u dV             */
+  int32_t free_motion;            /* 1: Newton's laws; 0: velocities held
+                                     (prescribed translation / rotation)   */
+} ibm_rigid_sphere;
+
+typedef struct {
+  double gravity[3];   /* acceleration of gravity g (the paper's -Fr^-2 e_z);
+                          the body feels (theta - 1)/theta g               */
+  double xi;           /* relaxation of the corrections (0.6 .. 1.1)        */
+  double tol;          /* stop when ||F'||_1 / ||F^{(n,k+1)}||_1 < tol
+                          (Eq. (convergence_criterion); 1e-3)              */
+  int32_t max_inner;   /* correction limit per step                        */
+} ibm_fsi_opts;
+
+typedef struct {
+  int32_t inner;          /* corrections taken                             */
+  int32_t fgmres_iters;   /* FGMRES iterations, summed over the corrections */
+  double ratio;           /* last ||F'||_1 / ||F^{(n,k+1)}||_1               */
+  int32_t helm_iters;     /* predictor outer iterations                     */
+  double helm_relres;
+} ibm_fsi_stats;
+
+/* Defaults: no gravity, xi 1, tol 1e-3, max_inner 50. */
+void ibm_default_fsi_opts(ibm_fsi_opts* fopts);
+
+/* One two-way coupled step (Sec. 3.2.1), scalar C mode:
+ *   Step 1: each sphere's centre by (4 x^n - x^{n-1})/3 + (2/3) dt u_s^n and
+ *     orientation R^{n+1} = R^n R_Delta (Rodrigues, Adams-Bashforth angle);
+ *     markers X_k = x_c^{n+1} + R^{n+1} L0_k, written to X_np1 and set on
+ *     the context (as ibm_set_markers);
+ *   Step 2: the predictor of Eq. (ustar_two_way) (as ibm_step);
+ *   Step 3: corrections k = 0, 1, ... : u_s, omega_s from Newton's laws with
+ *     the IB force/torque of F^{(n,k)} and the enclosed-fluid momentum of
+ *     Eq. (volume_integrals) (volume fractions from the signed distance at
+ *     the corners of each face's control volume); U = u_s + omega x (X - x_c);
+ *     the Schur solve of Eq. (pressure_force_iterative_system); relaxed
+ *     updates p += xi p', F += xi F', u += xi (2dt/3)(-G p' + R F'); until
+ *     ||F'||_1/||F||_1 < tol or max_inner corrections.
+ * bodies: host [n_bodies], advanced to t^{n+1} on success (left unchanged on
+ * error).  L0: device [3][n_markers] body-frame offsets (X - x_c at R = I);
+ * body_id: device int32 [n_markers] in [0, n_bodies).  u_n, u_nm1 (faces),
+ * p_n (cells), F_n ([3][n_markers]), f_body (faces, may be NULL): device
+ * inputs; X_np1, u_np1, p_np1, F_np1: device outputs, not aliasing inputs.
+ * IBM_ERR_NOT_CONVERGED when max_inner is reached above tol (outputs and
+ * bodies still advanced).  Synchronises. */
+ibm_status ibm_fsi_step(ibm_ctx* ctx, int32_t n_bodies, ibm_rigid_sphere* bodies,
+                        int64_t n_markers, const double* L0, const int32_t* body_id,
+                        const double* u_n, const double* u_nm1, const double* p_n,
+                        const double* F_n, const double* f_body, double* X_np1,
+                        double* u_np1, double* p_np1, double* F_np1,
+                        const ibm_solve_opts* opts, const ibm_fsi_opts* fopts,
+                        ibm_fsi_stats* stats);
+
 /* ---- Adjoint of one step ------------------------------------------------
  * The paper differentiates nothing; these calls give the exact derivative of
  * the one-way step above (scalar C mode, Eqs. (ustar)-(ApproxSchurPrimalF),
@@ -361,6 +431,7 @@ enum {
   IBM_PROF_HELM_SWEEP = 10,    /* one inner FP32 Chebyshev step of the
                                   predictor (middle steps only)             */
   IBM_PROF_ADJOINT = 11,       /* whole ibm_adjoint_step                    */
+  IBM_PROF_FSI = 12,           /* whole ibm_fsi_step                        */
   IBM_PROF_NCLASS = 16
 };
 typedef struct {

@@ -55,9 +55,31 @@ class ibm_solve_stats(C.Structure):
                 ("c_iters", C.c_int64)]
 
 
+class ibm_rigid_sphere(C.Structure):
+    _fields_ = [("radius", C.c_double), ("theta", C.c_double),
+                ("xc", C.c_double * 3), ("xc_prev", C.c_double * 3),
+                ("us", C.c_double * 3), ("us_prev", C.c_double * 3),
+                ("om", C.c_double * 3), ("om_prev", C.c_double * 3),
+                ("om_cs", C.c_double * 3), ("om_cs_prev", C.c_double * 3),
+                ("rot", C.c_double * 9),
+                ("mom", C.c_double * 3), ("mom_prev", C.c_double * 3),
+                ("amom", C.c_double * 3), ("amom_prev", C.c_double * 3),
+                ("free_motion", C.c_int32)]
+
+
+class ibm_fsi_opts(C.Structure):
+    _fields_ = [("gravity", C.c_double * 3), ("xi", C.c_double), ("tol", C.c_double),
+                ("max_inner", C.c_int32)]
+
+
+class ibm_fsi_stats(C.Structure):
+    _fields_ = [("inner", C.c_int32), ("fgmres_iters", C.c_int32), ("ratio", C.c_double),
+                ("helm_iters", C.c_int32), ("helm_relres", C.c_double)]
+
+
 PROF_NCLASS = 16
 PROF_NAMES = ["laplacian_f64", "schur_markers", "vcycle", "multidot", "axpy_norm", "predictor",
-              "solve", "step", "marker_build", "mg_smooth_fine", "helm_sweep", "adjoint"]
+              "solve", "step", "marker_build", "mg_smooth_fine", "helm_sweep", "adjoint", "fsi"]
 
 
 class ibm_profile(C.Structure):
@@ -98,6 +120,10 @@ SIGNATURES = [
                                        C.POINTER(C.c_int64)]),
     ("ibm_apply_c_inverse", C.c_int, [_P, _P, _P, C.c_double, C.c_int32,
                                       C.POINTER(C.c_int32)]),
+    ("ibm_default_fsi_opts", None, [C.POINTER(ibm_fsi_opts)]),
+    ("ibm_fsi_step", C.c_int, [_P, C.c_int32, C.POINTER(ibm_rigid_sphere), C.c_int64, _P, _P,
+                               _P, _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ibm_solve_opts),
+                               C.POINTER(ibm_fsi_opts), C.POINTER(ibm_fsi_stats)]),
     ("ibm_adjoint_step", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.POINTER(ibm_solve_opts),
                                    C.POINTER(ibm_solve_stats)]),
     ("ibm_body_forces_adjoint", C.c_int, [_P, _P, _P, _P, C.c_int32, C.POINTER(C.c_double),

@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import IBM_PREC_FP32, IBM_PREC_FP64, check
 
-__all__ = ["IBMSolver", "IBM_PREC_FP32", "IBM_PREC_FP64"]
+__all__ = ["IBMSolver", "RigidSpheres", "IBM_PREC_FP32", "IBM_PREC_FP64"]
 
 
 def _ptr(t: torch.Tensor, dtype=torch.float64, numel=None, name="tensor") -> int:
@@ -33,6 +33,40 @@ def _stats_dict(st: _lib.ibm_solve_stats) -> dict:
                 relres_hist=list(st.relres_hist[:n]), helm_iters=st.helm_iters,
                 helm_relres=st.helm_relres, div_l2=st.div_l2, slip_l2=st.slip_l2,
                 c_iters=st.c_iters)
+
+
+class RigidSpheres:
+    """Host state of rigid spheres for ``IBMSolver.fsi_step`` (a ctypes array
+    of ibm_rigid_sphere, advanced in place by every step)."""
+
+    def __init__(self, radii, thetas, centers, velocities=None, omegas=None, free=True):
+        import numpy as np
+        centers = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
+        nb = centers.shape[0]
+        radii = np.broadcast_to(np.asarray(radii, dtype=np.float64), (nb,))
+        thetas = np.broadcast_to(np.asarray(thetas, dtype=np.float64), (nb,))
+        vel = np.zeros((nb, 3)) if velocities is None else \
+            np.asarray(velocities, dtype=np.float64).reshape(nb, 3)
+        omg = np.zeros((nb, 3)) if omegas is None else \
+            np.asarray(omegas, dtype=np.float64).reshape(nb, 3)
+        free = np.broadcast_to(np.asarray(free), (nb,))
+        self.arr = (_lib.ibm_rigid_sphere * nb)()
+        for b in range(nb):
+            s = self.arr[b]
+            s.radius, s.theta = float(radii[b]), float(thetas[b])
+            for e in range(3):
+                s.xc[e] = s.xc_prev[e] = centers[b, e]
+                s.us[e] = s.us_prev[e] = vel[b, e]
+                s.om[e] = s.om_prev[e] = omg[b, e]
+                s.om_cs[e] = s.om_cs_prev[e] = omg[b, e]
+            for q in range(9):
+                s.rot[q] = 1.0 if q % 4 == 0 else 0.0
+            s.free_motion = 1 if free[b] else 0
+        self.n = nb
+
+    def get(self, name):
+        import numpy as np
+        return np.array([list(getattr(self.arr[b], name)) for b in range(self.n)])
 
 
 class IBMSolver:
@@ -204,6 +238,39 @@ class IBMSolver:
         d = _stats_dict(st)
         d["status"] = status
         return out, d
+
+    def fsi_step(self, spheres: "RigidSpheres", L0, body_id, u_n, u_nm1, p_n, F_n, f_body=None,
+                 out=None, gravity=(0.0, 0.0, 0.0), xi=1.0, tol=1e-3, max_inner=50,
+                 raise_on_error=True, **kw):
+        """One two-way coupled step (Sec. 3.2); spheres advance in place.
+        Returns (dict(X, u, p, F), stats)."""
+        L0 = L0.reshape(3, -1)
+        n = L0.shape[1]
+        nmk = 3 * n
+        if out is None:
+            out = dict(X=torch.empty(nmk, dtype=torch.float64, device="cuda"), u=self._faces(),
+                       p=self._cells(), F=torch.empty(nmk, dtype=torch.float64, device="cuda"))
+        o = self.opts(**kw)
+        fo = _lib.ibm_fsi_opts()
+        self.lib.ibm_default_fsi_opts(C.byref(fo))
+        for e in range(3):
+            fo.gravity[e] = float(gravity[e])
+        fo.xi, fo.tol, fo.max_inner = float(xi), float(tol), int(max_inner)
+        st = _lib.ibm_fsi_stats()
+        status = self.lib.ibm_fsi_step(
+            self.ctx, spheres.n, spheres.arr, n, _ptr(L0, numel=nmk, name="L0"),
+            _ptr(body_id, dtype=torch.int32, numel=n, name="body_id"),
+            _ptr(u_n, numel=self.nf, name="u_n"), _ptr(u_nm1, numel=self.nf, name="u_nm1"),
+            _ptr(p_n, numel=self.m, name="p_n"), _ptr(F_n, numel=nmk, name="F_n"),
+            _ptr(f_body, numel=self.nf, name="f_body") if f_body is not None else None,
+            _ptr(out["X"], numel=nmk, name="X"), _ptr(out["u"], numel=self.nf, name="u"),
+            _ptr(out["p"], numel=self.m, name="p"), _ptr(out["F"], numel=nmk, name="F"),
+            C.byref(o), C.byref(fo), C.byref(st))
+        if raise_on_error:
+            check(status, self.ctx)
+        self.n_markers = n
+        return out, dict(inner=st.inner, fgmres_iters=st.fgmres_iters, ratio=st.ratio,
+                         helm_iters=st.helm_iters, helm_relres=st.helm_relres, status=status)
 
     def profile_enable(self, on=True):
         check(self.lib.ibm_profile_enable(self.ctx, 1 if on else 0), self.ctx)

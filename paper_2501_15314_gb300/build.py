@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB_NAME = "libibmschur.so"
 SOURCES = ["capi.cu", "krylov.cu", "krylov_df.cu", "multigrid.cu", "markers.cu", "stencil.cu",
-           "noalloc.cu", "adjoint.cu", "cmode.cu"]
+           "noalloc.cu", "adjoint.cu", "cmode.cu", "fsi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{INCLUDE}", f"-I{CSRC}"]

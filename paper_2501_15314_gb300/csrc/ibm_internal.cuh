@@ -170,6 +170,16 @@ ibm_status cuda_err(ibm_ctx* c, cudaError_t e, const char* where);
     if (e_ != cudaSuccess) return ::ibm::cuda_err((ctx), e_, "kernel launch"); \
   } while (0)
 
+// argument and workspace helpers shared by the C entry points (capi.cu)
+bool bad_ptr(const void* p);
+ibm_status check_ctx(ibm_ctx* c);
+ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o);
+ibm_status ensure_krylov(ibm_ctx* c, int restart);
+ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out);
+// (a - nu Lap) u = rhs of Eq. (ustar) to o->helm_rtol; uses f3 and g1..g4
+ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
+                           int* iters, double* relres);
+
 // ---- stencils (stencil.cu) ----
 // out = scale * L v  (Neumann 7-point, L = G^T G with h folded into scale)
 template <typename T>
@@ -211,15 +221,6 @@ void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, dou
 // out[cell] += scale * (G^T R t)[cell] on the shell cells
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);
 // U[d][k] = (R^T u)_{k,d}
-// argument and workspace helpers shared by the C entry points (capi.cu)
-bool bad_ptr(const void* p);
-ibm_status check_ctx(ibm_ctx* c);
-ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o);
-ibm_status ensure_krylov(ibm_ctx* c, int restart);
-ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out);
-// (a - nu Lap) u = rhs of Eq. (ustar) to o->helm_rtol; uses f3 and g1..g4
-ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
-                           int* iters, double* relres);
 void launch_interp(ibm_ctx* c, const double* u, double* U);
 // Xbar[e][k] (+)= scale * sum_d m[d][k] * sum_i f_d,i dR_{i,(d,k)}/dX_{e,k}
 void launch_interp_dpos(ibm_ctx* c, const double* f, const double* m, double scale,
