@@ -41,7 +41,7 @@ def lib_path() -> Path:
 
 def build(verbose: bool = False, force: bool = False) -> Path:
     out = lib_path()
-    deps = [CSRC / s for s in SOURCES] + [CSRC / "ibm_internal.cuh", INCLUDE / "ibm_schur.h"]
+    deps = [CSRC / s for s in SOURCES] + [CSRC / "ibm_internal.cuh", CSRC / "ds.cuh", INCLUDE / "ibm_schur.h"]
     if (not force and out.exists()
             and out.stat().st_mtime > max(p.stat().st_mtime for p in deps)):
         return out

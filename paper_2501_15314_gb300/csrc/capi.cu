@@ -153,7 +153,7 @@ static void free_all(ibm_ctx* c) {
   cudaFree(c->dev_flag); cudaFreeHost(c->host_flag);
   cudaFree(c->c1); cudaFree(c->c2); cudaFree(c->c3);
   cudaFree(c->f1); cudaFree(c->f2); cudaFree(c->f3); cudaFree(c->f4);
-  cudaFree(c->g1); cudaFree(c->g2); cudaFree(c->g3); cudaFree(c->g4);
+  cudaFree(c->g1); cudaFree(c->g2); cudaFree(c->g3); cudaFree(c->g4); cudaFree(c->g5);
   cudaFree(c->red_part); cudaFree(c->red_out); cudaFreeHost(c->host_red); cudaFree(c->helm_part);
   cudaFree(c->V); cudaFree(c->Z);
   for (int l = 0; l < c->n_levels; ++l) {
@@ -175,12 +175,16 @@ static void free_all(ibm_ctx* c) {
   c->prof.clear();
 }
 
-// Predictor of Eq. (ustar): (a - nu Lap) u = rhs by FP64 defect correction.
-// Each correction solves A e = r / ||r|| with K FP32 Chebyshev steps on the
-// exact spectral bounds [a, a + 12 nu / h^2] of A; K is chosen for the
-// reduction still needed (at most 1e-6 per correction, the FP32 limit), the
-// first step reads the FP64 residual and the last one accumulates into u.
-// Every FP64 residual is fused with its norm.
+// Predictor of Eq. (ustar): (a - nu Lap) u = rhs by defect correction.  Each
+// correction solves A e = r^ with K FP32 Chebyshev steps on the exact
+// spectral bounds [a, a + 12 nu / h^2] of A, where r^ = r / ||r|| is held in
+// double-single (FP32 pair) arithmetic, and adds ||r|| e to the FP64 iterate;
+// K is chosen for the reduction still needed (at most 1e-6 per correction,
+// the FP32 limit).  The next residual is ||r|| (r^ - A e), formed in
+// double-single on the FP32 pipes (k_helm_resid_ds) together with its norm:
+// no FP64 residual pass, and the residual is as accurate as an FP64 one
+// (about 2^-46 relative to the previous residual, plus the rounding of the
+// FP64 iterate).
 ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
                            int* iters, double* relres) {
   cudaStream_t s = c->stream;
@@ -199,24 +203,25 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   *iters = 0;
   *relres = 0.0;
   if (rnorm0 == 0.0) return IBM_OK;
-  double* res = c->f3;
   double* sdev = c->red_out + 7 * (kMaxRestart + 2) + 8;
-  const double* rcur = rhs;   // residual of the zero iterate is rhs itself
-  double rn = rnorm0;
+  float* eK = nullptr;        // the last correction e (input of the next residual)
+  double rn = rnorm0;         // ||r|| of the current residual
+  double qn = rnorm0;         // norm of the stored (unnormalised) residual pair
   for (int it = 0;; ++it) {
     if (it > 0) {
-      const int64_t nb = launch_helm_residual(c->d, u, a, nu_h2, rhs, res, c->helm_part,
+      // (g1, g5) = r^ - A e_K; ||r_new|| = ||r|| * ||r^ - A e_K||
+      const int64_t nb = launch_helm_resid_ds(c->d, eK, c->g1, c->g5, a, nu_h2, c->helm_part,
                                               kMaxRestart + 2, s);
       launch_final_reduce(c->helm_part, (int)nb, sdev, s);
       IBM_LAUNCH_CHECK(c);
       IBM_CUDA(c, cudaMemcpyAsync(c->host_red, sdev, sizeof(double), cudaMemcpyDeviceToHost, s));
       IBM_CUDA(c, cudaStreamSynchronize(s));
-      rn = std::sqrt(c->host_red[0]);
+      qn = std::sqrt(c->host_red[0]);
+      rn *= qn;
       if (!std::isfinite(rn)) return set_err(c, IBM_ERR_NAN, "non-finite predictor residual");
-      rcur = res;
     }
     *relres = rn / rnorm0;
-    if (*relres <= o->helm_rtol) return IBM_OK;
+    if (*relres <= o->helm_rtol || rn == 0.0) return IBM_OK;
     if (it >= o->helm_maxit) break;
     // reduction wanted from this correction (with a 3x margin), FP32-limited
     double want = o->helm_rtol / *relres / 3.0;
@@ -227,20 +232,22 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
     float* e = c->g3;
     float* en = c->g4;
     IBM_CUDA(c, cudaMemsetAsync(eo, 0, sizeof(float) * helm_fp32_size(c->d), s));
-    launch_helm_cheb(c->d, nullptr, nullptr, c->g1, rcur, 1.0 / rn, (float)a, (float)nu_h2,
-                     (float)(1.0 / theta), 0.f, e, nullptr, 0.0, 0, s);
+    // r^ = r / ||r||: from the FP64 right-hand side first, then from the pair
+    launch_helm_cheb(c->d, nullptr, nullptr, c->g1, c->g5, it == 0 ? rhs : nullptr, 1.0 / qn,
+                     (float)a, (float)nu_h2, (float)(1.0 / theta), 0.f, e, nullptr, 0.0, 0, s);
     double rho_prev = 1.0 / sigma;
     for (int q = 1; q < K; ++q) {
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
       const int last = q == K - 1;
       const int ph = last ? -1 : prof_begin(c, IBM_PROF_HELM_SWEEP);
-      launch_helm_cheb(c->d, e, eo, c->g1, nullptr, 0.0, (float)a, (float)nu_h2,
+      launch_helm_cheb(c->d, e, eo, c->g1, nullptr, nullptr, 0.0, (float)a, (float)nu_h2,
                        (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn,
                        last ? 2 : 1, s);
       prof_end(c, ph);
       rho_prev = rho;
       float* t = eo; eo = e; e = en; en = t;
     }
+    eK = e;   // after the rotation the last output is in e
     IBM_LAUNCH_CHECK(c);
     *iters = it + 1;
   }
@@ -310,6 +317,7 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
             cudaMalloc(&c->g2, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->g3, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->g4, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
+            cudaMalloc(&c->g5, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->red_part, sizeof(double) * kRedBlocks * (kMaxRestart + 2)) ==
                 cudaSuccess &&
             cudaMalloc(&c->red_out, sizeof(double) * 8 * (kMaxRestart + 2)) ==
@@ -329,7 +337,7 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
   }
   // the predictor's FP32 arrays: wall faces beyond the launched x-range are
   // never written and must read as 0
-  for (float* buf : {c->g1, c->g2, c->g3, c->g4})
+  for (float* buf : {c->g1, c->g2, c->g3, c->g4, c->g5})
     if (cudaMemset(buf, 0, sizeof(float) * helm_fp32_size(c->d)) != cudaSuccess) ok = false;
   ibm_status st = ok ? mg_setup(c) : IBM_ERR_CUDA;
   if (st == IBM_OK && cudaDeviceSynchronize() != cudaSuccess) st = IBM_ERR_CUDA;

@@ -1,0 +1,90 @@
+// Double-single arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significant bits).  GB300 runs FP64 arithmetic, and
+// conversions between FP64 and FP32, at about 1/58 of its FP32 rate, so the
+// FP64-accurate parts of the hot path that would otherwise be bound by the
+// FP64 pipe are written with these error-free transformations on the FP32
+// pipes:
+//   two_sum(a, b):  s = a + b, e = (a - (s - bb)) + (b - bb), bb = s - a
+//                   (Knuth), exact: a + b = s + e;
+//   two_prod(a, b): p = a b, e = fma(a, b, -p), exact: a b = p + e.
+// Explicit __f*_rn intrinsics keep the compiler from contracting or
+// re-associating them.
+#pragma once
+
+#include <cstdint>
+
+namespace ibm {
+
+struct dsf {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dsf two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dsf fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dsf two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// (a.hi + a.lo) + (b.hi + b.lo)
+__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
+  dsf s = two_sum(a.hi, b.hi);
+  const dsf t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.hi, -a.lo}; }
+// (a.hi + a.lo) + b for an FP32 b
+__device__ __forceinline__ dsf ds_add_f(dsf a, float b) {
+  dsf s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+// (a.hi + a.lo) * (b.hi + b.lo), dropping lo*lo
+__device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {
+  dsf p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+// (a.hi + a.lo) * b for an FP32 b
+__device__ __forceinline__ dsf ds_mul_f(dsf a, float b) {
+  dsf p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+
+// x = hi + lo to within 2^-46 |x| without FP64 arithmetic: hi takes the sign,
+// the exponent and the top 23 fraction bits of x, lo the next 23 fraction
+// bits, read as an integer (exactly, through the FP32 significand of
+// 2^23 + m) and scaled by a power of two; the lowest 6 fraction bits are
+// dropped.  Zero and subnormal x give (0, 0); |x| outside [2^-80, 2^101)
+// (far from the values of the flow) falls back to FP64 conversions.
+__device__ __forceinline__ dsf split_exact(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  if (ex == 0) return {0.f, 0.f};
+  const int E = ex - 1023;
+  if (E < -80 || E > 100) {
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) |
+                                   (unsigned)((b >> 29) & 0x7fffffu));
+  const unsigned m23 = (unsigned)((b >> 6) & 0x7fffffu);
+  const float mf = __fsub_rn(__uint_as_float(0x4b000000u | m23), 8388608.0f);
+  const float lo = __fmul_rn(mf, __uint_as_float((unsigned)(E - 46 + 127) << 23));
+  return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
+}  // namespace ibm

@@ -115,6 +115,7 @@ struct ibm_ctx {
   float* g2 = nullptr;
   float* g3 = nullptr;
   float* g4 = nullptr;
+  float* g5 = nullptr;             // low parts of the predictor's residual
   double* red_part = nullptr;      // [kRedBlocks][kMaxRestart + 2] partials
   double* red_out = nullptr;       // [8][kMaxRestart + 2] reduced values
   double* host_red = nullptr;      // pinned mirror of red_out
@@ -193,17 +194,16 @@ void launch_grad_axpy(Dims d, const double* u_in, const double* p, double alpha,
 void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c,
                         double beta, double* out, cudaStream_t s);
 // predictor helpers
-// res = rhs - A u (FP64) with per-block sums of res^2 in part[b * stride];
-// returns the number of blocks (partials)
-int64_t launch_helm_residual(Dims d, const double* u, double a, double nu_h2,
-                             const double* rhs, double* res, double* part, int stride,
-                             cudaStream_t s);
+// (rhi, rlo) = (rhi, rlo) - A e in double-single (see k_helm_resid_ds) with
+// per-block sums of the new hi^2 in part[b * stride]; returns the block count
+int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, double a,
+                             double nu_h2, double* part, int stride, cudaStream_t s);
 // number of floats of the predictor's padded FP32 face layout
 int64_t helm_fp32_size(Dims d);
 // one FP32 Chebyshev step of the predictor (see k_helm_cheb_v4)
-void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, const double* r64,
-                      double rs, float a, float nu_h2, float alpha, float beta, float* en,
-                      double* u, double us, int mode, cudaStream_t s);
+void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
+                      const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
+                      float* en, double* u, double us, int mode, cudaStream_t s);
 void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s);
 // predictor RHS with the convective term of u_n fused in (with_adv != 0)
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,

@@ -7,17 +7,14 @@
 // significant bits), and the Schur product L z (z = V-cycle output, exactly
 // FP32), the multi-dot, the axpy + norm and the solution update run on the
 // FP32 pipes with error-free transformations:
-//   two_sum(a, b):  s = a + b, e = (a - (s - bb)) + (b - bb), bb = s - a
-//                   (Knuth), exact: a + b = s + e;
-//   two_prod(a, b): p = a b, e = fma(a, b, -p), exact: a b = p + e.
+//   two_sum, two_prod and the double-single sums and products of ds.cuh.
 // The marker term of S~ stays FP64 (it touches ~1% of the cells), the true
 // residual b - S~ x that decides convergence (and restarts) is evaluated in
-// native FP64, and dot products are reduced to FP64 per block.  Explicit
-// __f*_rn intrinsics keep the compiler from contracting or re-associating the
-// transformations.
+// native FP64, and dot products are reduced to FP64 per block.
 #include <cmath>
 #include <vector>
 
+#include "ds.cuh"
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -28,40 +25,6 @@ constexpr int RT = kRedThreads;
 constexpr int kOutStride = kMaxRestart + 2;
 constexpr unsigned kFull = 0xffffffffu;
 
-struct dsf {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dsf two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ dsf fast_two_sum(float a, float b) {   // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dsf two_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-// (a.hi + a.lo) + (b.hi + b.lo)
-__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
-  dsf s = two_sum(a.hi, b.hi);
-  const dsf t = two_sum(a.lo, b.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
-  return fast_two_sum(s.hi, s.lo);
-}
-// (a.hi + a.lo) * (b.hi + b.lo), dropping lo*lo  (used by the Laplacian's 1/h^2)
-__device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {
-  dsf p = two_prod(a.hi, b.hi);
-  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
-  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
-  return fast_two_sum(p.hi, p.lo);
-}
 __device__ __forceinline__ dsf d_to_ds(double x) {
   const float hi = (float)x;
   return {hi, (float)(x - (double)hi)};

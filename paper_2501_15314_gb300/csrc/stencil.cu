@@ -6,6 +6,7 @@
 // Thread layout: one thread per grid point, blocks of 32 x 8 in (x, y) and one
 // z-plane per blockIdx.z, so that a warp reads 32 consecutive x values of each
 // neighbour row (coalesced; the y/z neighbours hit L1/L2).
+#include "ds.cuh"
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -245,8 +246,10 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_adv(
       continue;
     }
     const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
-    double v = (4.0 * __ldg(un + f) - __ldg(unm1 + f)) * inv_2dt;
-    v -= (__ldg(pn + cp) - __ldg(pn + cp - cstride[c])) * inv_h;
+    // (4 u^n - u^{n-1}) / (2 dt) - (p_+ - p_-) / h (+ f): two FMAs, one
+    // multiply and one subtraction
+    double v = fma(__ldg(un + f), 4.0 * inv_2dt, -inv_2dt * __ldg(unm1 + f));
+    v = fma(-inv_h, __ldg(pn + cp) - __ldg(pn + cp - cstride[c]), v);
     if (fb) v += __ldg(fb + f);
     if (with_adv) {
       double acc;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_adv(
         acc += fz - carry;
         carry = fz;
       }
-      v -= 0.25 * inv_h * acc;
+      v = fma(-0.25 * inv_h, acc, v);
     }
     rhs[f] = v;
   }
@@ -306,15 +309,18 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 // One FP32 Chebyshev step for A e = r on the padded layout, four faces per
 // thread; x-neighbours by shuffles, z by the march, y through L1.
-// mode 0: first step from e = 0, e_new = alpha r with r = rs * r64 rounded to
-// FP32 (stored in r32 for the later steps); mode 1: e_new = e + beta (e -
-// e_old) + alpha (r - A e); mode 2: the same step accumulated into the FP64
-// iterate, u += us * e_new.
+// mode 0: first step from e = 0: the normalised residual r^ = rs r is formed
+// in double-single from r64 (FP64, split without FP64 arithmetic) or, when
+// r64 is null, from the pair (r32, rlo) in place; r^ is kept in (r32, rlo)
+// and e_new = alpha r^.hi.  mode 1: e_new = e + beta (e - e_old) +
+// alpha (r - A e) with r = r32; mode 2: the same step, accumulated into the
+// FP64 iterate, u += us * e_new, and stored in e_new (the next residual
+// reads it).
 __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     FaceGeom g, FaceGeom32 p, int zchunks, const float* __restrict__ e,
-    const float* __restrict__ eo, float* __restrict__ r32, const double* __restrict__ r64,
-    double rs, float a, float nu_h2, float alpha, float beta, float* __restrict__ en,
-    double* __restrict__ u, double us, int mode) {
+    const float* __restrict__ eo, float* __restrict__ r32, float* __restrict__ rlo,
+    const double* __restrict__ r64, float rs_hi, float rs_lo, float a, float nu_h2, float alpha,
+    float beta, float* __restrict__ en, double* __restrict__ u, double us, int mode) {
   const int c = blockIdx.z / zchunks;
   const int zc = blockIdx.z - c * zchunks;
   const int lane = threadIdx.x;
@@ -339,16 +345,30 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
   }
   const bool wally = c == 1 && (j == 0 || j == n1 - 1);
   if (mode == 0) {
+    const dsf rs = {rs_hi, rs_lo};
     for (int z = z0; z < z1; ++z, f += sz, f64 += sz64) {
       const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
-      float r[4];
+      float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
+      if (act && !r64) {
+        const float4 a4 = *reinterpret_cast<const float4*>(r32 + f);
+        const float4 b4 = *reinterpret_cast<const float4*>(rlo + f);
+        h4[0] = a4.x; h4[1] = a4.y; h4[2] = a4.z; h4[3] = a4.w;
+        l4[0] = b4.x; l4[1] = b4.y; l4[2] = b4.z; l4[3] = b4.w;
+      }
+      float rh[4], rl[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        r[q] = (val[q] && !wallx[q] && !wally && !wallz) ? (float)(rs * __ldg(r64 + f64 + q)) : 0.f;
+      for (int q = 0; q < 4; ++q) {
+        const bool live = val[q] && !wallx[q] && !wally && !wallz;
+        dsf v = {0.f, 0.f};
+        if (live) v = ds_mul(r64 ? split_exact(__ldg(r64 + f64 + q)) : dsf{h4[q], l4[q]}, rs);
+        rh[q] = v.hi;
+        rl[q] = v.lo;
+      }
       if (act) {
-        *reinterpret_cast<float4*>(r32 + f) = make_float4(r[0], r[1], r[2], r[3]);
+        *reinterpret_cast<float4*>(r32 + f) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<float4*>(rlo + f) = make_float4(rl[0], rl[1], rl[2], rl[3]);
         *reinterpret_cast<float4*>(en + f) =
-            make_float4(alpha * r[0], alpha * r[1], alpha * r[2], alpha * r[3]);
+            make_float4(alpha * rh[0], alpha * rh[1], alpha * rh[2], alpha * rh[3]);
       }
     }
     return;
@@ -397,9 +417,8 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
       const bool live = val[q] && !wallx[q] && !wally && !wallz;
       out[q] = live ? ev[q] + beta * (ev[q] - vo[q]) + alpha * res : 0.f;
     }
-    if (mode == 1) {
-      if (act) *reinterpret_cast<float4*>(en + f) = make_float4(out[0], out[1], out[2], out[3]);
-    } else {
+    if (act) *reinterpret_cast<float4*>(en + f) = make_float4(out[0], out[1], out[2], out[3]);
+    if (mode == 2) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (val[q] && !wallx[q] && !wally && !wallz) u[f64 + q] = fma(us, (double)out[q], u[f64 + q]);
@@ -409,53 +428,109 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
   }
 }
 
-// FP64 predictor residual res = rhs - A u on the interior faces (0 on wall
-// faces) with the block's sum of res^2 written to part[block * stride]
-// (fixed-order reduction; every block writes its partial).
-__global__ void __launch_bounds__(BX * BY) k_helm_residual(FaceGeom g, int zchunks,
-                                                           const double* __restrict__ u, double a,
-                                                           double nu_h2,
-                                                           const double* __restrict__ rhs,
-                                                           double* __restrict__ res,
-                                                           double* __restrict__ part,
-                                                           int stride) {
-  double acc = 0.0;
-  FaceThread t;
-  if (face_thread(g, zchunks, t)) {
-    int64_t f = t.f0;
-    if (t.wall) {
-      for (int z = t.z0; z < t.z1; ++z, f += t.sz) res[f] = 0.0;
-    } else {
-      const double diag_xy = a + 6.0 * nu_h2 + nu_h2 * (double)t.ghosts_xy;
-      double up = t.z0 > 0 ? __ldg(u + f - t.sz) : 0.0;
-      double uc = __ldg(u + f);
-      for (int z = t.z0; z < t.z1; ++z, f += t.sz) {
-        const double un = (z + 1 < t.n2) ? __ldg(u + f + t.sz) : 0.0;
-        double diag = diag_xy;
-        if (t.c != 2) diag += nu_h2 * (double)((z == 0) + (z == t.n2 - 1));
-        const bool wall = t.c == 2 && (z == 0 || z == t.n2 - 1);
-        const double sn = face_inplane(u, f, t) + (up + un);
-        const double r = wall ? 0.0 : __ldg(rhs + f) - fma(diag, uc, -nu_h2 * sn);
-        res[f] = r;
-        acc = fma(r, r, acc);
-        up = uc;
-        uc = un;
-      }
-    }
+// Next normalised residual of the predictor's defect correction, in
+// double-single arithmetic on the FP32 pipes: after a correction that solved
+// A e = r^ (r^ = r / ||r|| held as the pair (rhi, rlo)) and added ||r|| e to
+// the FP64 iterate, the new residual is ||r|| (r^ - A e).  This kernel forms
+// q = r^ - A e exactly enough (A e of the FP32 e with error-free sums and
+// products, about 2^-46 relative to r^) and writes it back to (rhi, rlo); the
+// block's sum of q.hi^2 goes to part[block * stride] (every block writes
+// one).  The FP64 pipe is not used.
+__global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
+    FaceGeom32 p, int zchunks, const float* __restrict__ e, float* __restrict__ rhi,
+    float* __restrict__ rlo, float a_hi, float a_lo, float nu_hi, float nu_lo,
+    double* __restrict__ part, int stride) {
+  const int c = blockIdx.z / zchunks;
+  const int zc = blockIdx.z - c * zchunks;
+  const int lane = threadIdx.x;
+  const int x0 = 4 * (blockIdx.x * 32 + lane);
+  const int j = blockIdx.y * HVY + threadIdx.y;
+  const int n0 = p.n[c][0], n1 = p.n[c][1], n2 = p.n[c][2];
+  const int z0 = zc * ZH;
+  const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  if (z0 >= n2 || blockIdx.x * 128 >= n0 || blockIdx.y * HVY >= n1) {   // block-uniform
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[blk * stride] = 0.0;
+    return;
   }
-  // block reduction in a fixed order
-  __shared__ double sh[BX * BY / 32];
-  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int z1 = min(z0 + ZH, n2);
+  const bool act = x0 < n0 && j < n1;
+  const int64_t sy = p.sy[c], sz = p.sz[c];
+  int64_t f = p.off[c] + (int64_t)z0 * sz + (int64_t)j * sy + x0;
+  const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool val[4], wallx[4];
+  int gx[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((tid & 31) == 0) sh[tid >> 5] = acc;
+  for (int q = 0; q < 4; ++q) {
+    val[q] = act && (x0 + q < n0);
+    wallx[q] = c == 0 && (x0 + q == 0 || x0 + q == n0 - 1);
+    gx[q] = (c != 0) ? ((x0 + q == 0) + (x0 + q == n0 - 1)) : 0;
+  }
+  const bool wally = c == 1 && (j == 0 || j == n1 - 1);
+  const int gy = (c != 1) ? ((j == 0) + (j == n1 - 1)) : 0;
+  const bool has_ym = j > 0, has_yp = j < n1 - 1;
+  const dsf A = {a_hi, a_lo}, NU = {nu_hi, nu_lo};
+  const dsf D6 = ds_add(A, ds_mul_f(NU, 6.f));
+  float acc = 0.f;
+  float4 ep = (act && z0 > 0) ? *reinterpret_cast<const float4*>(e + f - sz) : Z4;
+  float4 ec = act ? *reinterpret_cast<const float4*>(e + f) : Z4;
+  for (int z = z0; z < z1; ++z, f += sz) {
+    const float4 ez = (act && z + 1 < n2) ? *reinterpret_cast<const float4*>(e + f + sz) : Z4;
+    const float4 ym = (act && has_ym) ? *reinterpret_cast<const float4*>(e + f - sy) : Z4;
+    const float4 yp = (act && has_yp) ? *reinterpret_cast<const float4*>(e + f + sy) : Z4;
+    const float4 rh = act ? *reinterpret_cast<const float4*>(rhi + f) : Z4;
+    const float4 rl = act ? *reinterpret_cast<const float4*>(rlo + f) : Z4;
+    float left = __shfl_up_sync(kFullMask, ec.w, 1);
+    float right = __shfl_down_sync(kFullMask, ec.x, 1);
+    if (lane == 0) left = (act && x0 > 0) ? e[f - 1] : 0.f;
+    if (lane == 31) right = (act && x0 + 4 < n0) ? e[f + 4] : 0.f;
+    const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
+    const int gz = (c != 2) ? ((z == 0) + (z == n2 - 1)) : 0;
+    const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
+    const float evp[4] = {ep.x, ep.y, ep.z, ep.w};
+    const float evn[4] = {ez.x, ez.y, ez.z, ez.w};
+    const float vym[4] = {ym.x, ym.y, ym.z, ym.w};
+    const float vyp[4] = {yp.x, yp.y, yp.z, yp.w};
+    const float vrh[4] = {rh.x, rh.y, rh.z, rh.w};
+    const float vrl[4] = {rl.x, rl.y, rl.z, rl.w};
+    float oh[4], ol[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int x = x0 + q;
+      const float xl = (x > 0) ? ((q == 0) ? left : ev[q - 1]) : 0.f;
+      const float xr = (x < n0 - 1) ? ((q == 3) ? right : ev[q + 1]) : 0.f;
+      dsf s = two_sum(xl, xr);
+      s = ds_add_f(s, vym[q]);
+      s = ds_add_f(s, vyp[q]);
+      s = ds_add_f(s, evp[q]);
+      s = ds_add_f(s, evn[q]);
+      const int gh = gx[q] + gy + gz;
+      const dsf diag = gh == 0 ? D6 : ds_add(A, ds_mul_f(NU, (float)(6 + gh)));
+      const dsf Ae = ds_add(ds_mul_f(diag, ev[q]), ds_neg(ds_mul(NU, s)));
+      dsf qv = ds_add(dsf{vrh[q], vrl[q]}, ds_neg(Ae));
+      const bool live = val[q] && !wallx[q] && !wally && !wallz;
+      if (!live) qv = dsf{0.f, 0.f};
+      oh[q] = qv.hi;
+      ol[q] = qv.lo;
+      acc = fmaf(qv.hi, qv.hi, acc);
+    }
+    if (act) {
+      *reinterpret_cast<float4*>(rhi + f) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+      *reinterpret_cast<float4*>(rlo + f) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+    }
+    ep = ec;
+    ec = ez;
+  }
+  // block reduction (FP64, fixed order)
+  double v = (double)acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
+  __shared__ double sh[HVY];
+  if (lane == 0) sh[threadIdx.y] = v;
   __syncthreads();
-  if (tid == 0) {
-    double sblk = 0.0;
-    for (int w = 0; w < BX * BY / 32; ++w) sblk += sh[w];
-    const int64_t b =
-        ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    part[b * stride] = sblk;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double t = 0.0;
+    for (int w = 0; w < HVY; ++w) t += sh[w];
+    part[blk * stride] = t;
   }
 }
 
@@ -585,32 +660,38 @@ dim3 helm_grid(Dims d) {
   return dim3(div_up(d.nx + 1, BX), div_up(d.ny + 1, BY), 3 * helm_zchunks(d));
 }
 
-int64_t launch_helm_residual(Dims d, const double* u, double a, double nu_h2, const double* rhs,
-                             double* res, double* part, int stride, cudaStream_t s) {
-  const dim3 gr = helm_grid(d);
-  count_launch();
-  k_helm_residual<<<gr, dim3(BX, BY), 0, s>>>(make_face_geom(d), helm_zchunks(d), u, a, nu_h2, rhs,
-                                               res, part, stride);
-  return (int64_t)gr.x * gr.y * gr.z;
-}
-
 int64_t helm_fp32_size(Dims d) {
   const FaceGeom32 p = make_face_geom32(d);
   return p.off[2] + p.sz[2] * p.n[2][2];
 }
 
-void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, const double* r64,
-                      double rs, float a, float nu_h2, float alpha, float beta, float* en,
-                      double* u, double us, int mode, cudaStream_t s) {
+// x-blocks cover the nx first points of every row (a multiple of 4 when
+// rounded up); for u_x the remaining point x = nx is a wall face, never
+// written and kept 0 since the arrays were cleared at creation
+dim3 helm_v4_grid(Dims d) {
+  return dim3(div_up(div_up(d.nx, 4), 32), div_up(d.ny + 1, HVY), 3 * helm_zchunks(d));
+}
+
+void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
+                      const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
+                      float* en, double* u, double us, int mode, cudaStream_t s) {
   const FaceGeom32 p = make_face_geom32(d);
-  const int zch = helm_zchunks(d);
-  // x-blocks cover the nx first points of every row (a multiple of 4 when
-  // rounded up); for u_x the remaining point x = nx is a wall face, never
-  // written and kept 0 since the arrays were cleared at creation
-  const dim3 gr(div_up(div_up(d.nx, 4), 32), div_up(d.ny + 1, HVY), 3 * zch);
+  const float rs_hi = (float)rs, rs_lo = (float)(rs - (double)rs_hi);
   count_launch();
-  k_helm_cheb_v4<<<gr, dim3(32, HVY), 0, s>>>(make_face_geom(d), p, zch, e, eo, r32, r64, rs, a,
-                                              nu_h2, alpha, beta, en, u, us, mode);
+  k_helm_cheb_v4<<<helm_v4_grid(d), dim3(32, HVY), 0, s>>>(
+      make_face_geom(d), p, helm_zchunks(d), e, eo, r32, rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha,
+      beta, en, u, us, mode);
+}
+
+int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, double a,
+                             double nu_h2, double* part, int stride, cudaStream_t s) {
+  const dim3 gr = helm_v4_grid(d);
+  const float a_hi = (float)a, a_lo = (float)(a - (double)a_hi);
+  const float n_hi = (float)nu_h2, n_lo = (float)(nu_h2 - (double)n_hi);
+  count_launch();
+  k_helm_resid_ds<<<gr, dim3(32, HVY), 0, s>>>(make_face_geom32(d), helm_zchunks(d), e, rhi, rlo,
+                                               a_hi, a_lo, n_hi, n_lo, part, stride);
+  return (int64_t)gr.x * gr.y * gr.z;
 }
 
 void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s) {
