@@ -42,9 +42,15 @@ METRIC = "Schur solves/s at 256^3 to 1e-8 residual, FP32-precond vs FP64; HBM fr
 UNIT = "solves/s"
 SAMPLE_ITERS = 3           # FGMRES iterations in the CPU oracle's bounded sample
 
-# DRAM bytes (read + write) per launch of the dominant kernels from one ncu
-# capture (profiles/*.md), null once the kernel has changed since.
-NCU_TRAFFIC = {}
+# DRAM traffic / algorithmic bytes of each timed kernel class, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of every launch of one
+# step) of the same kernels on the eight-sphere workload at 192^3, where the
+# capture fits the profiling size rule; the traffic of a 256^3 launch is this
+# ratio times its algorithmic bytes (traffic grows with the units processed:
+# cells x vectors).  profiles/ncu_traffic_step_spheres8_192.md has the
+# command and the per-kernel numbers.  A class whose kernel changes after the
+# capture must be removed here (its traffic then reads null).
+NCU_TRAFFIC_RATIO = {"axpy_norm": 0.925, "multidot": 0.906, "helm_sweep": 1.314}
 
 
 def env_rank():
@@ -161,7 +167,9 @@ def workload_config(W):
                         f"step from rest, FGMRES rtol 1e-8",
             "grid": [W.n, W.n, W.n], "markers": W.n_markers, "bodies": len(W.radii),
             "Re": W.Re, "dt": W.dt, "rtol": 1e-8,
-            "l2": "no flush: every field (>= 134 MB) exceeds the 129 MB L2",
+            "l2": ("no flush: one step streams tens of GB (FP64 fields 134-403 MB, Krylov "
+                   "basis GBs) through the 129 MB L2, so no step starts with the previous "
+                   "step's data resident"),
             "parallelism": "replicas"}
 
 
@@ -287,27 +295,75 @@ def run_ours(args):
                             "iters": stq[-1]["iters"], "relres": stq[-1]["relres_true"]}
 
     # ---- end to end through the public API with host buffers ----
-    pin = lambda t: t.cpu().pin_memory()
+    # Every step copies its inputs from pinned host memory and its results
+    # back.  The copies run on a second stream, pipelined with the steps:
+    # step k+1's inputs go in and step k-1's results come out while step k
+    # computes (two device buffer sets, ordered by events).
+    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
     h_in = dict(X=pin(X), U=pin(U), f=pin(f), u_n=pin(zf), u_nm1=pin(zf), p_n=pin(zc),
                 F_n=pin(zk))
-    d_in = {kk: torch.empty_like(v, device="cuda") for kk, v in h_in.items()}
-    h_out = {kk: torch.empty(v.shape, dtype=v.dtype).pin_memory() for kk, v in out.items()}
+    d_in = [{kk: torch.empty_like(v, device="cuda") for kk, v in h_in.items()} for _ in range(2)]
+    d_out = [{kk: torch.empty_like(v) for kk, v in out.items()} for _ in range(2)]
+    h_out = [{kk: torch.empty(v.shape, dtype=v.dtype).pin_memory() for kk, v in out.items()}
+             for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
-    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out[0].values())
+    cstream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    ev_in, ev_done, ev_outc = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    for q in range(2):
+        ev_done[q].record(stream)
+        ev_outc[q].record(stream)
 
-    def e2e_step():
-        for kk in h_in:
-            d_in[kk].copy_(h_in[kk], non_blocking=True)
-        s.set_markers(d_in["X"])
-        _, st = s.step(d_in["u_n"], d_in["u_nm1"], d_in["p_n"], d_in["F_n"], d_in["U"],
-                       d_in["f"], out=out, precond_prec=_lib.IBM_PREC_FP32, rtol=1e-8)
-        for kk in h_out:
-            h_out[kk].copy_(out[kk], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return st
+    def copy_in(b):
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(ev_done[b])          # the step that last read buffer b
+            for kk in h_in:
+                d_in[b][kk].copy_(h_in[kk], non_blocking=True)
+            ev_in[b].record(cstream)
 
-    e2e_step()
-    ms_e2e, _ = timed(e2e_step, args.steps)
+    def copy_out(b):
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(ev_done[b])
+            for kk in h_out[b]:
+                h_out[b][kk].copy_(d_out[b][kk], non_blocking=True)
+            ev_outc[b].record(cstream)
+
+    def e2e_run(K):
+        copy_in(0)
+        stats = []
+        for k in range(K):
+            b = k & 1
+            if k + 1 < K:
+                copy_in(1 - b)                      # inputs of step k+1
+            stream.wait_event(ev_in[b])
+            stream.wait_event(ev_outc[b])           # results of step k-2 are out
+            s.set_markers(d_in[b]["X"])
+            _, st = s.step(d_in[b]["u_n"], d_in[b]["u_nm1"], d_in[b]["p_n"], d_in[b]["F_n"],
+                           d_in[b]["U"], d_in[b]["f"], out=d_out[b],
+                           precond_prec=_lib.IBM_PREC_FP32, rtol=1e-8)
+            ev_done[b].record(stream)
+            copy_out(b)
+            stats.append(st)
+        for q in range(2):
+            stream.wait_event(ev_outc[q])           # every result is on the host
+        return stats
+
+    e2e_run(2)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_run(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
 
     # ---- adjoint of the step (transposed Schur solve) ----
     adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
@@ -349,7 +405,10 @@ def run_ours(args):
     cb = classes[best]
     roof = {"bound": "hbm", "kernel": best, "achieved": cb["achieved_gbs"], "peak": hbm,
             "unit": "GB/s", "frac": cb["frac"], "peak_kind": peak_kind,
-            "traffic": NCU_TRAFFIC.get(best), "avg_launch_ms": cb["avg_launch_ms"],
+            "traffic": (NCU_TRAFFIC_RATIO[kern[best][0]] * cb["bytes_per_launch"]
+                        if kern[best][0] in NCU_TRAFFIC_RATIO else None),
+            "traffic_source": "ncu DRAM bytes per algorithmic byte at 192^3, scaled to this "
+                              "launch's units", "avg_launch_ms": cb["avg_launch_ms"],
             "bytes_per_launch": cb["bytes_per_launch"]}
     breakdown = {kk: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
                  for kk, v in prof.items() if v["launches"]}
@@ -374,7 +433,9 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}}
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+                    "copies": "pinned host buffers, H2D/D2H on a second stream pipelined "
+                              "with the steps (double-buffered)"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, det = oracle_sample(W, oracle_iterations(args.config))
         line["cpu_baseline"] = {
