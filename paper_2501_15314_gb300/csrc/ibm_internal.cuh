@@ -204,14 +204,11 @@ int64_t helm_fp32_size(Dims d);
 void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
                       const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
                       float* en, double* u, double us, int mode, cudaStream_t s);
-void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s);
-// predictor RHS with the convective term of u_n fused in (with_adv != 0)
+// predictor RHS with the convective term of u_n fused in (with_adv != 0),
+// evaluated in double-single arithmetic (see k_predictor_rhs_ds)
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,
                               const double* p_n, const double* f_body, int with_adv,
                               double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
-void launch_predictor_rhs(Dims d, const double* u_n, const double* u_nm1,
-                          const double* p_n, const double* f_body, const double* adv,
-                          double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
 
 // ---- markers (markers.cu) ----
 ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);

@@ -133,6 +133,13 @@ __global__ void __launch_bounds__(BX * BY) k_gradt_axpby(Dims d, FaceGeom g,
 // axis adds nu / h^2 to diag for every missing neighbour (ghost = -e_c).
 // Kernels below march along z over ZH planes; blockIdx.z = comp * zchunks +
 // chunk, so one launch covers the three face grids.
+// x[c] for a runtime c in 0..2 without dynamic indexing (which would copy a
+// kernel-parameter struct to local memory)
+template <typename T>
+__device__ __forceinline__ T sel3(int c, T a, T b, T d) {
+  return c == 0 ? a : (c == 1 ? b : d);
+}
+
 constexpr int ZH = 16;
 
 struct FaceThread {
@@ -148,15 +155,15 @@ __device__ __forceinline__ bool face_thread(const FaceGeom& g, int zchunks, Face
   const int zc = blockIdx.z - t.c * zchunks;
   t.i = blockIdx.x * BX + threadIdx.x;
   t.j = blockIdx.y * BY + threadIdx.y;
-  t.n0 = g.n[t.c][0];
-  t.n1 = g.n[t.c][1];
-  t.n2 = g.n[t.c][2];
+  t.n0 = sel3(t.c, g.n[0][0], g.n[1][0], g.n[2][0]);
+  t.n1 = sel3(t.c, g.n[0][1], g.n[1][1], g.n[2][1]);
+  t.n2 = sel3(t.c, g.n[0][2], g.n[1][2], g.n[2][2]);
   t.z0 = zc * ZH;
   if (t.i >= t.n0 || t.j >= t.n1 || t.z0 >= t.n2) return false;
   t.z1 = min(t.z0 + ZH, t.n2);
-  t.sy = g.sy[t.c];
-  t.sz = g.sz[t.c];
-  t.f0 = g.off[t.c] + (int64_t)t.z0 * t.sz + (int64_t)t.j * t.sy + t.i;
+  t.sy = sel3(t.c, g.sy[0], g.sy[1], g.sy[2]);
+  t.sz = sel3(t.c, g.sz[0], g.sz[1], g.sz[2]);
+  t.f0 = sel3(t.c, g.off[0], g.off[1], g.off[2]) + (int64_t)t.z0 * t.sz + (int64_t)t.j * t.sy + t.i;
   t.wall = (t.c == 0 && (t.i == 0 || t.i == t.n0 - 1)) || (t.c == 1 && (t.j == 0 || t.j == t.n1 - 1));
   t.xm = t.i > 0;
   t.xp = t.i < t.n0 - 1;
@@ -178,106 +185,138 @@ __device__ __forceinline__ T face_inplane(const T* __restrict__ e, int64_t f, co
   return s;
 }
 
+// Exact FP64 value of an FP32 number without the FP64 pipe (sign, re-biased
+// exponent and the 23 fraction bits moved into place; subnormal x, far below
+// the values of the flow, give 0).
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u) return 0.0;
+  if (ex == 0xffu) return (double)x;
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(ex + (1023u - 127u)) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// u_E at (x, y, z) of its own face grid, split into an FP32 pair
+template <int E>
+__device__ __forceinline__ dsf ldu(const FaceGeom& g, const double* __restrict__ u, int x, int y,
+                                   int z) {
+  return split_exact(__ldg(u + g.off[E] + (int64_t)z * g.sz[E] + (int64_t)y * g.sy[E] + x));
+}
+
+// Convective flux on the edge between the C-face at (x, y, z) and the E-face
+// index q along E (E != C): (sum of the two u_E adjacent along C) times
+// (sum of the two u_C adjacent along E); 0 on the walls (q = 0 or the last
+// E-face).  For an interior C-face every value read is an interior face.
+template <int C, int E>
+__device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const double* __restrict__ u,
+                                            int x, int y, int z, int q) {
+  if (q <= 0 || q >= g.n[E][E] - 1) return dsf{0.f, 0.f};
+  const int ax = E == 0 ? q : x, ay = E == 1 ? q : y, az = E == 2 ? q : z;
+  const dsf ue = ds_add(ldu<E>(g, u, ax - (C == 0), ay - (C == 1), az - (C == 2)),
+                        ldu<E>(g, u, ax, ay, az));
+  const dsf uc = ds_add(ldu<C>(g, u, ax - (E == 0), ay - (E == 1), az - (E == 2)),
+                        ldu<C>(g, u, ax, ay, az));
+  return ds_mul(ue, uc);
+}
+
 // Right-hand side of the predictor, Eq. (ustar), with the convective term
-// fused in: rhs = (4 u^n - u^{n-1}) / (2 dt) - G p^n + f - A(u^n) on interior
-// faces (0 on wall faces).  A is the central divergence form of k_advection
-// with the 1/2 averages folded into one factor 1/4:
-//   4 A = [ (u_+ + u_0)^2 - (u_0 + u_-)^2 ] along the component's own axis
-//       + sum over the two other axes of (flux at the upper edge - lower edge),
-//   flux = (u_e averaged pair sum) * (u_c averaged pair sum), 0 on walls.
+// fused in, for the C-faces (one launch per velocity component):
+//   rhs = (4 u^n - u^{n-1}) / (2 dt) - G p^n + f - A(u^n) on interior faces
+// (0 on wall faces).  A is the central divergence form on the MAC grid (the
+// cell-centred square of u_C averaged along C, and on the edges the product
+// of u_E averaged along C with u_C averaged along E, 0 on walls) with the 1/2
+// averages folded into one factor 1/4:
+//   4 A = [ (u_+ + u_0)^2 - (u_0 + u_-)^2 ] along C
+//       + sum over the two other axes of (flux at the upper edge - lower edge).
 // The march runs along z; the flux through the lower z-edge (or, for u_z, the
 // lower cell-centred square) is the previous face's upper one and is reused.
-__global__ void __launch_bounds__(BX * BY) k_predictor_rhs_adv(
-    Dims d, FaceGeom g, int zchunks, const double* __restrict__ un,
-    const double* __restrict__ unm1, const double* __restrict__ pn,
-    const double* __restrict__ fb, int with_adv, double inv_2dt, double inv_h,
-    double* __restrict__ rhs) {
-  FaceThread t;
-  if (!face_thread(g, zchunks, t)) return;
-  const int c = t.c;
-  int64_t f = t.f0;
+// The FP64 pipe of GB300 is ~58x slower than its FP32 pipes, so every FP64
+// input is split exactly into an FP32 pair (split_exact, integer operations)
+// and the formula is evaluated in double-single arithmetic (about 2^-46
+// relative); the FP64 result is the exact sum of the pair (one FP64 add).
+// Templating on C makes every stride and boundary test a compile-time case.
+template <int C>
+__global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
+    Dims d, FaceGeom g, const double* __restrict__ un, const double* __restrict__ unm1,
+    const double* __restrict__ pn, const double* __restrict__ fb, int with_adv, dsf c4, dsf c1,
+    dsf cp_h, dsf ca, double* __restrict__ rhs) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int n0 = g.n[C][0], n1 = g.n[C][1], n2 = g.n[C][2];
+  const int z0 = blockIdx.z * ZH;
+  if (i >= n0 || j >= n1) return;
+  const int z1 = min(z0 + ZH, n2);
+  const int64_t sy = g.sy[C], sz = g.sz[C];
+  int64_t f = g.off[C] + (int64_t)z0 * sz + (int64_t)j * sy + i;
+  const bool col_wall = (C == 0 && (i == 0 || i == n0 - 1)) || (C == 1 && (j == 0 || j == n1 - 1));
+  if (col_wall) {
+    for (int z = z0; z < z1; ++z, f += sz) rhs[f] = 0.0;
+    return;
+  }
   const int64_t csy = d.nx, csz = (int64_t)d.nx * d.ny;
-  const int64_t cstride[3] = {1, csy, csz};
-  // U(comp, x, y, z): face value, 0 on wall faces and outside the grid
-  auto U = [&](int comp, int x, int y, int z) -> double {
-    const int q[3] = {x, y, z};
-    if (x < 0 || y < 0 || z < 0 || x >= g.n[comp][0] || y >= g.n[comp][1] || z >= g.n[comp][2])
-      return 0.0;
-    if (q[comp] == 0 || q[comp] == g.n[comp][comp] - 1) return 0.0;
-    return __ldg(un + fidx(g, comp, x, y, z));
-  };
-  // flux on the edge between the c-face at p (p[c] = c-face index) and the
-  // e-face index qe along e (other coordinate from p): 4 * (avg u_e)(avg u_c)
-  auto eflux = [&](int e, int px, int py, int pz, int qe) -> double {
-    const int ne = g.n[e][e] - 1;   // cells along e
-    if (qe <= 0 || qe >= ne) return 0.0;
-    int a[3] = {px, py, pz};
-    a[e] = qe;
-    int b0[3] = {a[0], a[1], a[2]}, b1[3] = {a[0], a[1], a[2]};
-    b0[c] -= 1;   // u_e at the two cells adjacent along c
-    const double ue = U(e, b0[0], b0[1], b0[2]) + U(e, b1[0], b1[1], b1[2]);
-    int c0[3] = {a[0], a[1], a[2]}, c1[3] = {a[0], a[1], a[2]};
-    c0[e] = qe - 1;
-    const double uc = U(c, c0[0], c0[1], c0[2]) + U(c, c1[0], c1[1], c1[2]);
-    return ue * uc;
-  };
-  const int i = t.i, j = t.j;
-  double carry = 0.0;   // lower z-flux (c = 0, 1) or lower square (c = 2)
-  if (with_adv && !t.wall) {
-    if (c == 2) {
-      const double s0 = U(2, i, j, t.z0 - 1) + U(2, i, j, t.z0);
-      carry = s0 * s0;
+  const int64_t cstr = C == 0 ? 1 : (C == 1 ? csy : csz);
+  const dsf Z = {0.f, 0.f};
+  auto sq = [](dsf x) { return ds_mul(x, x); };
+  // lower z-flux (C = 0, 1) or lower cell-centred square (C = 2)
+  dsf carry = Z;
+  if (with_adv) {
+    if (C == 2) {
+      const dsf lo = (z0 - 1 >= 1) ? ldu<2>(g, un, i, j, z0 - 1) : Z;
+      const dsf mid = (z0 >= 1 && z0 <= n2 - 2) ? ldu<2>(g, un, i, j, z0) : Z;
+      carry = sq(ds_add(lo, mid));
     } else {
-      carry = eflux(2, i, j, t.z0, t.z0);
+      carry = edge_flux_ds<C, 2>(g, un, i, j, z0, z0);
     }
   }
-  for (int z = t.z0; z < t.z1; ++z, f += t.sz) {
-    const bool wall = t.wall || (c == 2 && (z == 0 || z == t.n2 - 1));
-    if (wall) {
+  for (int z = z0; z < z1; ++z, f += sz) {
+    if (C == 2 && (z == 0 || z == n2 - 1)) {
       rhs[f] = 0.0;
       if (with_adv) {
-        if (c == 2) {
-          const double s1 = U(2, i, j, z) + U(2, i, j, z + 1);
-          carry = s1 * s1;
-        } else {
-          carry = eflux(2, i, j, z, z + 1);
-        }
+        const dsf mid = (z >= 1 && z <= n2 - 2) ? ldu<2>(g, un, i, j, z) : Z;
+        const dsf hi = (z + 1 <= n2 - 2) ? ldu<2>(g, un, i, j, z + 1) : Z;
+        carry = sq(ds_add(mid, hi));
       }
       continue;
     }
     const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
-    // (4 u^n - u^{n-1}) / (2 dt) - (p_+ - p_-) / h (+ f): two FMAs, one
-    // multiply and one subtraction
-    double v = fma(__ldg(un + f), 4.0 * inv_2dt, -inv_2dt * __ldg(unm1 + f));
-    v = fma(-inv_h, __ldg(pn + cp) - __ldg(pn + cp - cstride[c]), v);
-    if (fb) v += __ldg(fb + f);
+    const dsf u0 = split_exact(__ldg(un + f));
+    // 4/(2dt) u^n - 1/(2dt) u^{n-1} - (p_+ - p_-)/h (+ f)
+    dsf v = ds_add(ds_mul(c4, u0), ds_neg(ds_mul(c1, split_exact(__ldg(unm1 + f)))));
+    const dsf dp = ds_add(split_exact(__ldg(pn + cp)), ds_neg(split_exact(__ldg(pn + cp - cstr))));
+    v = ds_add(v, ds_neg(ds_mul(cp_h, dp)));
+    if (fb) v = ds_add(v, split_exact(__ldg(fb + f)));
     if (with_adv) {
-      double acc;
-      if (c == 2) {
-        const double s1 = U(2, i, j, z) + U(2, i, j, z + 1);
-        const double up2 = s1 * s1;
-        acc = up2 - carry;
+      dsf acc;
+      if (C == 2) {
+        const dsf up = (z + 1 <= n2 - 2) ? ldu<2>(g, un, i, j, z + 1) : Z;
+        const dsf up2 = sq(ds_add(u0, up));
+        acc = ds_add(up2, ds_neg(carry));
         carry = up2;
-        acc += eflux(0, i, j, z, i + 1) - eflux(0, i, j, z, i);
-        acc += eflux(1, i, j, z, j + 1) - eflux(1, i, j, z, j);
+        acc = ds_add(acc, ds_add(edge_flux_ds<2, 0>(g, un, i, j, z, i + 1),
+                                 ds_neg(edge_flux_ds<2, 0>(g, un, i, j, z, i))));
+        acc = ds_add(acc, ds_add(edge_flux_ds<2, 1>(g, un, i, j, z, j + 1),
+                                 ds_neg(edge_flux_ds<2, 1>(g, un, i, j, z, j))));
       } else {
-        // own axis (x for u_x, y for u_y)
-        int pp[3] = {i, j, z}, pm[3] = {i, j, z};
-        pp[c] += 1;
-        pm[c] -= 1;
-        const double u0 = __ldg(un + f);
-        const double up = U(c, pp[0], pp[1], pp[2]), um = U(c, pm[0], pm[1], pm[2]);
-        acc = (up - um) * (up + 2.0 * u0 + um);
-        const int o = 1 - c;   // the other in-plane axis
-        const int po = o == 0 ? i : j;
-        acc += eflux(o, i, j, z, po + 1) - eflux(o, i, j, z, po);
-        const double fz = eflux(2, i, j, z, z + 1);
-        acc += fz - carry;
+        // own axis: (u_+ - u_-)(u_+ + 2 u_0 + u_-), wall faces read as 0
+        constexpr int O = 1 - C;   // the other in-plane axis
+        const int pc = C == 0 ? i : j, nc = C == 0 ? n0 : n1;
+        const dsf up = (pc + 1 <= nc - 2) ? ldu<C>(g, un, i + (C == 0), j + (C == 1), z) : Z;
+        const dsf um = (pc - 1 >= 1) ? ldu<C>(g, un, i - (C == 0), j - (C == 1), z) : Z;
+        const dsf two_u0 = {2.f * u0.hi, 2.f * u0.lo};
+        acc = ds_mul(ds_add(up, ds_neg(um)), ds_add(ds_add(up, um), two_u0));
+        const int po = O == 0 ? i : j;
+        acc = ds_add(acc, ds_add(edge_flux_ds<C, O>(g, un, i, j, z, po + 1),
+                                 ds_neg(edge_flux_ds<C, O>(g, un, i, j, z, po))));
+        const dsf fz = edge_flux_ds<C, 2>(g, un, i, j, z, z + 1);
+        acc = ds_add(acc, ds_add(fz, ds_neg(carry)));
         carry = fz;
       }
-      v = fma(-0.25 * inv_h, acc, v);
+      v = ds_add(v, ds_neg(ds_mul(ca, acc)));
     }
-    rhs[f] = v;
+    rhs[f] = f2d_exact(v.hi) + f2d_exact(v.lo);
   }
 }
 
@@ -326,15 +365,18 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
   const int lane = threadIdx.x;
   const int x0 = 4 * (blockIdx.x * 32 + lane);
   const int j = blockIdx.y * HVY + threadIdx.y;
-  const int n0 = p.n[c][0], n1 = p.n[c][1], n2 = p.n[c][2];
+  const int n0 = sel3(c, p.n[0][0], p.n[1][0], p.n[2][0]);
+  const int n1 = sel3(c, p.n[0][1], p.n[1][1], p.n[2][1]);
+  const int n2 = sel3(c, p.n[0][2], p.n[1][2], p.n[2][2]);
   const int z0 = zc * ZH;
   if (z0 >= n2 || blockIdx.x * 128 >= n0 || blockIdx.y * HVY >= n1) return;   // block-uniform
   const int z1 = min(z0 + ZH, n2);
   const bool act = x0 < n0 && j < n1;
-  const int64_t sy = p.sy[c], sz = p.sz[c];
-  int64_t f = p.off[c] + (int64_t)z0 * sz + (int64_t)j * sy + x0;
-  const int64_t sy64 = g.sy[c], sz64 = g.sz[c];
-  int64_t f64 = g.off[c] + (int64_t)z0 * sz64 + (int64_t)j * sy64 + x0;
+  const int64_t sy = sel3(c, p.sy[0], p.sy[1], p.sy[2]), sz = sel3(c, p.sz[0], p.sz[1], p.sz[2]);
+  int64_t f = sel3(c, p.off[0], p.off[1], p.off[2]) + (int64_t)z0 * sz + (int64_t)j * sy + x0;
+  const int64_t sy64 = sel3(c, g.sy[0], g.sy[1], g.sy[2]);
+  const int64_t sz64 = sel3(c, g.sz[0], g.sz[1], g.sz[2]);
+  int64_t f64 = sel3(c, g.off[0], g.off[1], g.off[2]) + (int64_t)z0 * sz64 + (int64_t)j * sy64 + x0;
   const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // per-element validity and x-wall status
   bool val[4], wallx[4];
@@ -445,7 +487,9 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
   const int lane = threadIdx.x;
   const int x0 = 4 * (blockIdx.x * 32 + lane);
   const int j = blockIdx.y * HVY + threadIdx.y;
-  const int n0 = p.n[c][0], n1 = p.n[c][1], n2 = p.n[c][2];
+  const int n0 = sel3(c, p.n[0][0], p.n[1][0], p.n[2][0]);
+  const int n1 = sel3(c, p.n[0][1], p.n[1][1], p.n[2][1]);
+  const int n2 = sel3(c, p.n[0][2], p.n[1][2], p.n[2][2]);
   const int z0 = zc * ZH;
   const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (z0 >= n2 || blockIdx.x * 128 >= n0 || blockIdx.y * HVY >= n1) {   // block-uniform
@@ -454,8 +498,8 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
   }
   const int z1 = min(z0 + ZH, n2);
   const bool act = x0 < n0 && j < n1;
-  const int64_t sy = p.sy[c], sz = p.sz[c];
-  int64_t f = p.off[c] + (int64_t)z0 * sz + (int64_t)j * sy + x0;
+  const int64_t sy = sel3(c, p.sy[0], p.sy[1], p.sy[2]), sz = sel3(c, p.sz[0], p.sz[1], p.sz[2]);
+  int64_t f = sel3(c, p.off[0], p.off[1], p.off[2]) + (int64_t)z0 * sz + (int64_t)j * sy + x0;
   const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   bool val[4], wallx[4];
   int gx[4];
@@ -534,92 +578,6 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
   }
 }
 
-// Explicit convective term of Eq. (ustar): central finite-volume divergence
-// form div(u u_c) on the MAC grid.  Along e == c the flux lives at cell
-// centres (square of u_c averaged along c); along e != c on the edge shared by
-// the c-face and the e-face: (u_e averaged along c) * (u_c averaged along e),
-// zero on walls (wall-normal velocity 0).
-__device__ __forceinline__ double edge_flux(const FaceGeom& g, const double* __restrict__ u,
-                                            int c, int e, int pc[3]) {
-  // pc: point with pc[c] = c-face index, pc[e] = e-face index (0..n_e).
-  const int ne = g.n[e][e] - 1;   // cells along e
-  if (pc[e] <= 0 || pc[e] >= ne) return 0.0;
-  int q[3] = {pc[0], pc[1], pc[2]};
-  // u_e at e-face pc[e], averaged over the two cells adjacent along c
-  q[c] = pc[c] - 1;
-  const double ue0 = face_val(g, u, e, q[0], q[1], q[2]);
-  q[c] = pc[c];
-  const double ue1 = face_val(g, u, e, q[0], q[1], q[2]);
-  // u_c at c-face pc[c], averaged over the two cells adjacent along e
-  int r[3] = {pc[0], pc[1], pc[2]};
-  r[e] = pc[e] - 1;
-  const double uc0 = face_val(g, u, c, r[0], r[1], r[2]);
-  r[e] = pc[e];
-  const double uc1 = face_val(g, u, c, r[0], r[1], r[2]);
-  return 0.25 * (ue0 + ue1) * (uc0 + uc1);
-}
-
-__global__ void __launch_bounds__(BX * BY) k_advection(Dims d, FaceGeom g,
-                                                       const double* __restrict__ u,
-                                                       double inv_h, double* __restrict__ out) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-#pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
-    if (i >= g.n[c][0] || j >= g.n[c][1] || k >= g.n[c][2]) continue;
-    const int64_t f = fidx(g, c, i, j, k);
-    int p[3] = {i, j, k};
-    if (p[c] == 0 || p[c] == g.n[c][c] - 1) { out[f] = 0.0; continue; }
-    double acc = 0.0;
-    for (int e = 0; e < 3; ++e) {
-      if (e == c) {
-        int q[3] = {i, j, k};
-        const double um = face_val(g, u, c, q[0], q[1], q[2]);
-        q[c] = p[c] + 1;
-        const double up = face_val(g, u, c, q[0], q[1], q[2]);
-        q[c] = p[c] - 1;
-        const double umm = face_val(g, u, c, q[0], q[1], q[2]);
-        const double cp = 0.5 * (um + up), cm = 0.5 * (umm + um);
-        acc += cp * cp - cm * cm;
-      } else {
-        int q[3] = {i, j, k};
-        q[e] = p[e] + 1;
-        const double fp = edge_flux(g, u, c, e, q);
-        q[e] = p[e];
-        const double fm = edge_flux(g, u, c, e, q);
-        acc += fp - fm;
-      }
-    }
-    out[f] = acc * inv_h;
-  }
-}
-
-// rhs = (4 u^n - u^{n-1}) / (2 dt) - G p^n + f - adv on interior faces.
-__global__ void __launch_bounds__(BX * BY) k_predictor_rhs(
-    Dims d, FaceGeom g, const double* __restrict__ un, const double* __restrict__ unm1,
-    const double* __restrict__ pn, const double* __restrict__ fb,
-    const double* __restrict__ adv, double inv_2dt, double inv_h, double* __restrict__ rhs) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
-  const int p3[3] = {i, j, k};
-  const int64_t cs[3] = {1, sy, sz};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (i >= g.n[c][0] || j >= g.n[c][1] || k >= g.n[c][2]) continue;
-    const int64_t f = fidx(g, c, i, j, k);
-    if (p3[c] == 0 || p3[c] == g.n[c][c] - 1) { rhs[f] = 0.0; continue; }
-    const int64_t cp = k * sz + j * sy + i;
-    double v = (4.0 * __ldg(un + f) - __ldg(unm1 + f)) * inv_2dt;
-    v -= (__ldg(pn + cp) - __ldg(pn + cp - cs[c])) * inv_h;
-    if (fb) v += __ldg(fb + f);
-    if (adv) v -= __ldg(adv + f);
-    rhs[f] = v;
-  }
-}
-
 }  // namespace
 
 template <typename T>
@@ -694,26 +652,28 @@ int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, dou
   return (int64_t)gr.x * gr.y * gr.z;
 }
 
-void launch_advection(Dims d, const double* u, double inv_h, double* out, cudaStream_t s) {
-  count_launch();
-  k_advection<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u, inv_h, out);
+// dsf of an FP64 constant (host)
+dsf host_ds(double x) {
+  const float hi = (float)x;
+  return dsf{hi, (float)(x - (double)hi)};
 }
 
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1, const double* p_n,
                               const double* f_body, int with_adv, double inv_2dt, double inv_h,
                               double* rhs, cudaStream_t s) {
+  const FaceGeom g = make_face_geom(d);
+  const dsf c4 = host_ds(4.0 * inv_2dt), c1 = host_ds(inv_2dt), cph = host_ds(inv_h),
+            ca = host_ds(0.25 * inv_h);
+  const dim3 b(BX, BY);
   count_launch();
-  k_predictor_rhs_adv<<<helm_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), helm_zchunks(d),
-                                                             u_n, u_nm1, p_n, f_body, with_adv,
-                                                             inv_2dt, inv_h, rhs);
-}
-
-void launch_predictor_rhs(Dims d, const double* u_n, const double* u_nm1, const double* p_n,
-                          const double* f_body, const double* adv, double inv_2dt, double inv_h,
-                          double* rhs, cudaStream_t s) {
+  k_predictor_rhs_ds<0><<<dim3(div_up(d.nx + 1, BX), div_up(d.ny, BY), div_up(d.nz, ZH)), b, 0,
+                          s>>>(d, g, u_n, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
   count_launch();
-  k_predictor_rhs<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u_n, u_nm1, p_n,
-                                                         f_body, adv, inv_2dt, inv_h, rhs);
+  k_predictor_rhs_ds<1><<<dim3(div_up(d.nx, BX), div_up(d.ny + 1, BY), div_up(d.nz, ZH)), b, 0,
+                          s>>>(d, g, u_n, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
+  count_launch();
+  k_predictor_rhs_ds<2><<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz + 1, ZH)), b, 0,
+                          s>>>(d, g, u_n, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
 }
 
 }  // namespace ibm
