@@ -162,6 +162,9 @@ static void free_all(ibm_ctx* c) {
     cudaFree(L.x64); cudaFree(L.b64); cudaFree(L.t64);
   }
   cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
   cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc); cudaFree(m.cg);
@@ -322,7 +325,10 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
                 cudaSuccess &&
             cudaMalloc(&c->red_out, sizeof(double) * 8 * (kMaxRestart + 2)) ==
                 cudaSuccess &&
-            cudaMallocHost(&c->host_red, sizeof(double) * 8 * (kMaxRestart + 2)) == cudaSuccess;
+            cudaMallocHost(&c->host_red, sizeof(double) * 8 * (kMaxRestart + 2)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
   {
     // partial sums of the fused predictor residual norm (one per block)
     const int64_t nb = (int64_t)div_up(g->nx + 1, 32) * div_up(g->ny + 1, 8) * 3 *

@@ -95,6 +95,10 @@ struct ibm_ctx {
   int64_t m, nf;
   ibm::FaceDims fd;
   cudaStream_t stream;
+  // internal side stream and events: the marker gather of a Schur product
+  // runs on it concurrently with the Laplacian
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 
   // grid-sized scratch (FP64)
@@ -213,8 +217,11 @@ void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,
 // ---- markers (markers.cu) ----
 ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);
 // t[d][k] = scale * (B v)_{k,d} = scale * (R^T G v)_{k,d}
-void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t);
-void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t);
+// (on stream st when given, else the context's stream)
+void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t,
+                               cudaStream_t st = nullptr);
+void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t,
+                                   cudaStream_t st = nullptr);
 // out[cell] += scale * (G^T R t)[cell] on the shell cells
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);
 // U[d][k] = (R^T u)_{k,d}

@@ -241,14 +241,21 @@ void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale
 
 // ---------------------------------------------------------------------------
 ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
-  // out = L v + 2 B^T (B v): t = 2 R^T G v per marker, out = L v, then the
-  // shell cells gather G^T R t.
+  // out = L v + 2 B^T (B v): t = 2 R^T G v per marker (on the side stream,
+  // concurrently with out = L v), then the shell cells gather G^T R t.
+  const bool fork = c->cmode == IBM_CMODE_SCALAR && c->mk.n > 0;
+  if (fork) {
+    IBM_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    IBM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    launch_marker_grad_interp(c, v, 2.0, c->mk.t, c->side);
+    IBM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+  }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
   launch_laplacian<double>(c->d, v, out, 1.0 / (c->h * c->h), c->stream);
   prof_end(c, ph);
   ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
-  if (c->cmode == IBM_CMODE_SCALAR) {
-    launch_marker_grad_interp(c, v, 2.0, c->mk.t);
+  if (fork) {
+    IBM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     launch_shell_gradt_spread(c, c->mk.t, 1.0, out);
   } else if (c->mk.n > 0) {
     // out +- B^T C^{-1} B v (exact / sign-consistent forms)

@@ -351,18 +351,27 @@ ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
   const float ih2_hi = (float)ih2;
   const float ih2_lo = (float)(ih2 - (double)ih2_hi);
   const int zc = lap_zc(c->d);
+  const MarkerData& m = c->mk;
+  // the marker gather t = 2 R^T G z runs on the side stream, concurrently
+  // with the Laplacian; the shell scatter into w waits for both
+  const bool fork = c->cmode == IBM_CMODE_SCALAR && m.n > 0 && m.n_shell > 0;
+  if (fork) {
+    IBM_CUDA(c, cudaEventRecord(c->ev_fork, s));
+    IBM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    launch_marker_grad_interp_f32(c, z, 2.0, m.t, c->side);
+    IBM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+  }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
   count_launch();
   k_lap_ds<<<dim3(div_up(c->d.nx / 4, 32), div_up(c->d.ny, LVY), div_up(c->d.nz, zc)),
              dim3(32, LVY), 0, s>>>(c->d, z, w, ih2_hi, ih2_lo, zc);
   prof_end(c, ph);
-  const MarkerData& m = c->mk;
   if (m.n > 0 && m.n_shell > 0) {
     ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
     const double* t = m.t;
     double sign = 1.0;
-    if (c->cmode == IBM_CMODE_SCALAR) {
-      launch_marker_grad_interp_f32(c, z, 2.0, m.t);
+    if (fork) {
+      IBM_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     } else {
       // +- B^T C^{-1} B z (exact / sign-consistent forms), C^{-1} in FP64
       launch_marker_grad_interp_f32(c, z, 1.0, m.t);

@@ -626,20 +626,22 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   return IBM_OK;
 }
 
-void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t) {
+void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t,
+                               cudaStream_t st) {
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
-  k_marker_grad_interp<double><<<div_up(12 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v,
-                                                                              scale, t);
+  k_marker_grad_interp<double><<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
+      c->d, view(m), v, scale, t);
 }
 
-void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t) {
+void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t,
+                                   cudaStream_t st) {
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
-  k_marker_grad_interp<float><<<div_up(12 * m.n, TPB), TPB, 0, c->stream>>>(c->d, view(m), v,
-                                                                             scale, t);
+  k_marker_grad_interp<float><<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
+      c->d, view(m), v, scale, t);
 }
 
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out) {
