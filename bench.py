@@ -350,6 +350,20 @@ def run_ours(args):
         return stats
 
     e2e_run(2)
+    # the host link's rate on this machine (one input set in, one result set out)
+    torch.cuda.synchronize()
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with torch.cuda.stream(cstream):
+        c0.record(cstream)
+        for kk in h_in:
+            d_in[0][kk].copy_(h_in[kk], non_blocking=True)
+        c1.record(cstream)
+        for kk in h_out[0]:
+            h_out[0][kk].copy_(d_out[0][kk], non_blocking=True)
+        c2.record(cstream)
+    torch.cuda.synchronize()
+    h2d_gbs = h2d / (c0.elapsed_time(c1) * 1e6)
+    d2h_gbs = d2h / (c1.elapsed_time(c2) * 1e6)
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -435,7 +449,8 @@ def run_ours(args):
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                     "copies": "pinned host buffers, H2D/D2H on a second stream pipelined "
-                              "with the steps (double-buffered)"}}
+                              "with the steps (double-buffered)",
+                    "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, det = oracle_sample(W, oracle_iterations(args.config))
         line["cpu_baseline"] = {

@@ -63,28 +63,41 @@ __device__ __forceinline__ dsf ds_mul_f(dsf a, float b) {
   return fast_two_sum(p.hi, p.lo);
 }
 
-// x = hi + lo to within 2^-46 |x| without FP64 arithmetic: hi takes the sign,
-// the exponent and the top 23 fraction bits of x, lo the next 23 fraction
-// bits, read as an integer (exactly, through the FP32 significand of
-// 2^23 + m) and scaled by a power of two; the lowest 6 fraction bits are
-// dropped.  Zero and subnormal x give (0, 0); |x| outside [2^-80, 2^101)
-// (far from the values of the flow) falls back to FP64 conversions.
+// x = hi + lo to within 2^-46 |x| without FP64 arithmetic or conversions
+// (which run on the slow FP64 pipe): hi takes the sign, the exponent and the
+// top 23 fraction bits of x, lo the next 23 fraction bits, read as an integer
+// (exactly, through the FP32 significand of 2^23 + m) and scaled by a power
+// of two; the lowest 6 fraction bits are dropped.  Integer operations only,
+// also on the edge cases: |x| < 2^-80 (zero, subnormal or far below the
+// values of the flow) gives (0, 0), |x| >= 2^101 (and inf, NaN) gives
+// (+-inf, 0), which the callers' finiteness checks report.
 __device__ __forceinline__ dsf split_exact(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7ffu);
-  if (ex == 0) return {0.f, 0.f};
-  const int E = ex - 1023;
-  if (E < -80 || E > 100) {
-    const float hi = (float)x;
-    return {hi, (float)(x - (double)hi)};
-  }
+  const int E = (int)((b >> 52) & 0x7ffu) - 1023;
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (E < -80) return {0.f, 0.f};
+  if (E > 100) return {__uint_as_float(sign | 0x7f800000u), 0.f};
   const float hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) |
                                    (unsigned)((b >> 29) & 0x7fffffu));
   const unsigned m23 = (unsigned)((b >> 6) & 0x7fffffu);
   const float mf = __fsub_rn(__uint_as_float(0x4b000000u | m23), 8388608.0f);
   const float lo = __fmul_rn(mf, __uint_as_float((unsigned)(E - 46 + 127) << 23));
   return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
+// Exact FP64 value of an FP32 number without the FP64 pipe: sign, re-biased
+// exponent and the 23 fraction bits moved into place (integer operations
+// only); subnormal x, far below the values of the flow, give +-0, inf and
+// NaN keep their class.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long frac = (unsigned long long)(u & 0x7fffffu) << 29;
+  const unsigned long long e64 = ex == 0u ? 0ull
+                                          : (ex == 0xffu ? 0x7ffull
+                                                         : (unsigned long long)(ex + (1023u - 127u)));
+  return __longlong_as_double((long long)(sign | (e64 << 52) | (ex == 0u ? 0ull : frac)));
 }
 
 }  // namespace ibm

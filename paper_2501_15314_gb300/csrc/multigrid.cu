@@ -332,7 +332,7 @@ __device__ __forceinline__ float w_over(float w, int nn) { return w * inv_nn(nn)
 int vec_zc(Dims d) {
   const int64_t bxy = (int64_t)div_up(d.nx / 4, 32) * div_up(d.ny, VY);
   int64_t zc = (int64_t)d.nz * bxy / (152 * 4);
-  zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
+  zc = zc < 1 ? 1 : (zc > 4 ? 4 : zc);
   return (int)zc;
 }
 

@@ -142,63 +142,6 @@ __device__ __forceinline__ T sel3(int c, T a, T b, T d) {
 
 constexpr int ZH = 16;
 
-struct FaceThread {
-  int c, i, j, z0, z1, n0, n1, n2;
-  int64_t sy, sz, f0;
-  bool wall;       // the whole column is a wall-normal face (c = 0 or 1)
-  bool xm, xp, ym, yp;
-  int ghosts_xy;
-};
-
-__device__ __forceinline__ bool face_thread(const FaceGeom& g, int zchunks, FaceThread& t) {
-  t.c = blockIdx.z / zchunks;
-  const int zc = blockIdx.z - t.c * zchunks;
-  t.i = blockIdx.x * BX + threadIdx.x;
-  t.j = blockIdx.y * BY + threadIdx.y;
-  t.n0 = sel3(t.c, g.n[0][0], g.n[1][0], g.n[2][0]);
-  t.n1 = sel3(t.c, g.n[0][1], g.n[1][1], g.n[2][1]);
-  t.n2 = sel3(t.c, g.n[0][2], g.n[1][2], g.n[2][2]);
-  t.z0 = zc * ZH;
-  if (t.i >= t.n0 || t.j >= t.n1 || t.z0 >= t.n2) return false;
-  t.z1 = min(t.z0 + ZH, t.n2);
-  t.sy = sel3(t.c, g.sy[0], g.sy[1], g.sy[2]);
-  t.sz = sel3(t.c, g.sz[0], g.sz[1], g.sz[2]);
-  t.f0 = sel3(t.c, g.off[0], g.off[1], g.off[2]) + (int64_t)t.z0 * t.sz + (int64_t)t.j * t.sy + t.i;
-  t.wall = (t.c == 0 && (t.i == 0 || t.i == t.n0 - 1)) || (t.c == 1 && (t.j == 0 || t.j == t.n1 - 1));
-  t.xm = t.i > 0;
-  t.xp = t.i < t.n0 - 1;
-  t.ym = t.j > 0;
-  t.yp = t.j < t.n1 - 1;
-  t.ghosts_xy = 0;
-  if (t.c != 0) t.ghosts_xy += (!t.xm) + (!t.xp);
-  if (t.c != 1) t.ghosts_xy += (!t.ym) + (!t.yp);
-  return true;
-}
-
-template <typename T>
-__device__ __forceinline__ T face_inplane(const T* __restrict__ e, int64_t f, const FaceThread& t) {
-  T s = 0;
-  if (t.xm) s += __ldg(e + f - 1);
-  if (t.xp) s += __ldg(e + f + 1);
-  if (t.ym) s += __ldg(e + f - t.sy);
-  if (t.yp) s += __ldg(e + f + t.sy);
-  return s;
-}
-
-// Exact FP64 value of an FP32 number without the FP64 pipe (sign, re-biased
-// exponent and the 23 fraction bits moved into place; subnormal x, far below
-// the values of the flow, give 0).
-__device__ __forceinline__ double f2d_exact(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0u) return 0.0;
-  if (ex == 0xffu) return (double)x;
-  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                               ((unsigned long long)(ex + (1023u - 127u)) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)b);
-}
-
 // u_E at (x, y, z) of its own face grid, split into an FP32 pair
 template <int E>
 __device__ __forceinline__ dsf ldu(const FaceGeom& g, const double* __restrict__ u, int x, int y,
