@@ -50,7 +50,7 @@ SAMPLE_ITERS = 3           # FGMRES iterations in the CPU oracle's bounded sampl
 # cells x vectors).  profiles/ncu_traffic_step_spheres8_192.md has the
 # command and the per-kernel numbers.  A class whose kernel changes after the
 # capture must be removed here (its traffic then reads null).
-NCU_TRAFFIC_RATIO = {"axpy_norm": 0.925, "multidot": 0.906, "helm_sweep": 1.314}
+NCU_TRAFFIC_RATIO = {}
 
 
 def env_rank():
@@ -232,7 +232,7 @@ def run_ours(args):
     out = dict(u=torch.empty_like(zf), p=torch.empty_like(zc), F=torch.empty_like(zk))
     stream = s.stream
 
-    def step(prec, arnoldi=_lib.IBM_ARNOLDI_DS):
+    def step(prec, arnoldi=_lib.IBM_ARNOLDI_FP32):
         s.set_markers(X)
         _, st = s.step(zf, zf, zc, zk, U, f, out=out, precond_prec=prec, arnoldi=arnoldi,
                        rtol=1e-8)
@@ -284,6 +284,8 @@ def run_ours(args):
     b = a * s.gradient_t(f) + 2.0 * s.gradient_t(s.spread(rhs_F))
     solve_only = {}
     for name, prec, arn in (("fp32_vcycle_ds_arnoldi", _lib.IBM_PREC_FP32, _lib.IBM_ARNOLDI_DS),
+                            ("fp32_vcycle_fp32_arnoldi", _lib.IBM_PREC_FP32,
+                             _lib.IBM_ARNOLDI_FP32),
                             ("fp32_vcycle_fp64_arnoldi", _lib.IBM_PREC_FP32,
                              _lib.IBM_ARNOLDI_FP64),
                             ("fp64_vcycle_fp64_arnoldi", _lib.IBM_PREC_FP64,
@@ -390,22 +392,20 @@ def run_ours(args):
     # algorithmic bytes per launch (DRAM traffic the kernel must move at
     # least once), summed over the timed region's launches of each class
     hbm, peak_kind = measured_peaks()
-    its = [st["iters"] for st in st_mixed]
-    nf_int = nf
-    gs_dot = sum(sum((j + 2) * 8.0 * m for j in range(it)) for it in its)
-    gs_axpy = sum(sum((j + 3) * 8.0 * m for j in range(it)) for it in its)
+    # algorithmic bytes of each timed class as the library counts them per
+    # launch (every array read or written once; Gram-Schmidt from the actual
+    # basis length of each launch and the element size of the Arnoldi form)
     kern = {
-        # name: (profile class, total algorithmic bytes over the timed steps)
         "k_helm_cheb_v4 (predictor FP32 Chebyshev step: read e, e_old, r; write e_new)":
-            ("helm_sweep", 16.0 * nf_int * prof["helm_sweep"]["launches"]),
-        "k_multidot_ds (Gram-Schmidt multi-dot on FP32 pairs: w and V_0..V_j)":
-            ("multidot", gs_dot),
-        "k_axpy_norm_ds (Gram-Schmidt axpy+norm on FP32 pairs: V_0..V_j, w in/out)":
-            ("axpy_norm", gs_axpy),
-        "k_lap_ds (Schur Laplacian, FP32 z in, FP32-pair w out)":
-            ("laplacian_f64", 12.0 * m * prof["laplacian_f64"]["launches"]),
+            ("helm_sweep", prof["helm_sweep"]["bytes"]),
+        "k_multidot_sp (Gram-Schmidt multi-dot on FP32 vectors: w and V_0..V_j)":
+            ("multidot", prof["multidot"]["bytes"]),
+        "k_axpy_norm_sp (Gram-Schmidt axpy+norm on FP32 vectors: V_0..V_j, w in/out)":
+            ("axpy_norm", prof["axpy_norm"]["bytes"]),
+        "k_lap_ds<float> (Schur Laplacian, FP32 z in, exact product rounded to FP32 out)":
+            ("laplacian_f64", prof["laplacian_f64"]["bytes"]),
         "k_first_v4 + k_sweep_v4 (finest V-cycle smoothing)":
-            ("mg_smooth_fine", 40.0 / 3.0 * m * prof["mg_smooth_fine"]["launches"]),
+            ("mg_smooth_fine", prof["mg_smooth_fine"]["bytes"]),
     }
     classes = {}
     for name, (cls, tot_bytes) in kern.items():
@@ -431,8 +431,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 V-cycle + f32-pair (double-single) Arnoldi; f64 residual, markers, "
-                     "predictor", "data": "synthetic",
+            "dtype": "f32 V-cycle + f32 Arnoldi cycles refined by the f64 residual; "
+                     "double-single predictor, f64 markers and true residual",
+            "data": "synthetic",
             "config": workload_config(W),
             "fp64_form": {"value": world * 1000.0 / ms_fp64, "unit": UNIT, "ms_per_step": ms_fp64,
                           "iters": st_fp64[-1]["iters"],
@@ -700,7 +701,7 @@ def run_profile_step(args):
     zc = torch.zeros(s.m, dtype=torch.float64, device="cuda")
     zk = torch.zeros(3 * W.n_markers, dtype=torch.float64, device="cuda")
     prec = _lib.IBM_PREC_FP64 if args.fp64 else _lib.IBM_PREC_FP32
-    arn = _lib.IBM_ARNOLDI_FP64 if args.fp64 else _lib.IBM_ARNOLDI_DS
+    arn = _lib.IBM_ARNOLDI_FP64 if args.fp64 else _lib.IBM_ARNOLDI_FP32
 
     def step():
         s.set_markers(X)

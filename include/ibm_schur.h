@@ -73,11 +73,16 @@ typedef enum { IBM_PREC_FP64 = 0, IBM_PREC_FP32 = 1 } ibm_precision;
 /* Arithmetic of the Arnoldi process (Schur products, Gram-Schmidt, solution
  * update) inside FGMRES.  IBM_ARNOLDI_FP64: native FP64.  IBM_ARNOLDI_DS:
  * vectors held as pairs hi + lo of FP32 numbers (about 48 significant bits),
- * products and sums by error-free transformations on the FP32 pipes; only
- * with the FP32 V-cycle on grids with nx a multiple of 4 (otherwise FP64 is
- * used).  In both, the residual b - S~ x that decides convergence and starts
- * every restart cycle is computed in native FP64. */
-typedef enum { IBM_ARNOLDI_FP64 = 0, IBM_ARNOLDI_DS = 1 } ibm_arnoldi;
+ * products and sums by error-free transformations on the FP32 pipes.
+ * IBM_ARNOLDI_FP32: vectors held as single FP32 numbers (half the bytes of
+ * the pairs; the Schur product still formed exactly and rounded once, the
+ * sums compensated); a restart cycle ends once its residual estimate has
+ * fallen by the FP32 limit (about 4e-6) and the next one starts from the FP64
+ * residual, as mixed-precision iterative refinement.  DS and FP32 apply with
+ * the FP32 V-cycle on grids with nx a multiple of 4 (otherwise FP64 is
+ * used).  In all forms the residual b - S~ x that decides convergence and
+ * starts every restart cycle is computed in native FP64. */
+typedef enum { IBM_ARNOLDI_FP64 = 0, IBM_ARNOLDI_DS = 1, IBM_ARNOLDI_FP32 = 2 } ibm_arnoldi;
 
 /* Treatment of C = R^T R (the (2,2) block of Eq. (Saddle)).
  * IBM_CMODE_SCALAR: C^{-1} ~ 2 I, the paper's production operator
@@ -143,8 +148,8 @@ typedef struct {
 
 /* Fills *opts with defaults: FP32 V-cycle, rtol 1e-8, maxit 200, restart 40,
  * Chebyshev (2,2), single Gram-Schmidt pass, helm_rtol 1e-10, helm_maxit 8,
- * advection on, double-single Arnoldi process, scalar C mode (c_rtol 1e-14,
- * c_maxit 500 for the other modes). */
+ * advection on, FP32 Arnoldi process with FP64 restarts, scalar C mode
+ * (c_rtol 1e-14, c_maxit 500 for the other modes). */
 void ibm_default_opts(ibm_solve_opts* opts);
 
 /* Creates a context for one grid and allocates the grid-sized workspace
@@ -437,6 +442,9 @@ enum {
 typedef struct {
   double ms[IBM_PROF_NCLASS];
   int64_t launches[IBM_PROF_NCLASS];
+  double bytes[IBM_PROF_NCLASS];   /* algorithmic DRAM bytes of the timed
+                                      kernels (every array read or written
+                                      once; 0 where not counted)            */
 } ibm_profile;
 
 ibm_status ibm_profile_enable(ibm_ctx* ctx, int32_t on);

@@ -25,6 +25,7 @@ IBM_PREC_FP64 = 0
 IBM_PREC_FP32 = 1
 IBM_ARNOLDI_FP64 = 0
 IBM_ARNOLDI_DS = 1
+IBM_ARNOLDI_FP32 = 2
 IBM_CMODE_SCALAR = 0
 IBM_CMODE_EXACT = 1
 IBM_CMODE_CONSISTENT = 2
@@ -83,7 +84,8 @@ PROF_NAMES = ["laplacian_f64", "schur_markers", "vcycle", "multidot", "axpy_norm
 
 
 class ibm_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * PROF_NCLASS), ("launches", C.c_int64 * PROF_NCLASS)]
+    _fields_ = [("ms", C.c_double * PROF_NCLASS), ("launches", C.c_int64 * PROF_NCLASS),
+                ("bytes", C.c_double * PROF_NCLASS)]
 
 
 _P = C.c_void_p

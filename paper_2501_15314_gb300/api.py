@@ -278,7 +278,7 @@ class IBMSolver:
     def profile_read(self) -> dict:
         p = _lib.ibm_profile()
         check(self.lib.ibm_profile_read(self.ctx, C.byref(p)), self.ctx)
-        return {name: dict(ms=p.ms[i], launches=p.launches[i])
+        return {name: dict(ms=p.ms[i], launches=p.launches[i], bytes=p.bytes[i])
                 for i, name in enumerate(_lib.PROF_NAMES)}
 
     def adjoint_step(self, u_np1, F_n, F_np1, F_bar, raise_on_error=True, **kw):

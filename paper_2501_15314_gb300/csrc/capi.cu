@@ -43,8 +43,9 @@ int prof_begin(ibm_ctx* c, int cls) {
   return h;
 }
 
-void prof_end(ibm_ctx* c, int h) {
+void prof_end(ibm_ctx* c, int h, double bytes) {
   if (h < 0) return;
+  c->prof[h].bytes = bytes;
   cudaEventRecord(c->prof[h].b, c->stream);
 }
 
@@ -103,8 +104,9 @@ ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o) {
     return set_err(c, IBM_ERR_ARG, "mg_pre, mg_post in 0..4, not both 0");
   if (!(o->helm_rtol > 0.0) || o->helm_maxit < 1)
     return set_err(c, IBM_ERR_ARG, "need helm_rtol > 0 and helm_maxit >= 1");
-  if (o->arnoldi != IBM_ARNOLDI_FP64 && o->arnoldi != IBM_ARNOLDI_DS)
-    return set_err(c, IBM_ERR_ARG, "arnoldi must be IBM_ARNOLDI_FP64 or IBM_ARNOLDI_DS");
+  if (o->arnoldi != IBM_ARNOLDI_FP64 && o->arnoldi != IBM_ARNOLDI_DS &&
+      o->arnoldi != IBM_ARNOLDI_FP32)
+    return set_err(c, IBM_ERR_ARG, "arnoldi must be IBM_ARNOLDI_FP64, _DS or _FP32");
   if (o->c_mode != IBM_CMODE_SCALAR && o->c_mode != IBM_CMODE_EXACT &&
       o->c_mode != IBM_CMODE_CONSISTENT)
     return set_err(c, IBM_ERR_ARG, "c_mode must be IBM_CMODE_SCALAR, _EXACT or _CONSISTENT");
@@ -246,7 +248,7 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
       launch_helm_cheb(c->d, e, eo, c->g1, nullptr, nullptr, 0.0, (float)a, (float)nu_h2,
                        (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn,
                        last ? 2 : 1, s);
-      prof_end(c, ph);
+      prof_end(c, ph, 16.0 * (double)c->nf);   // e, e_old, r read; e_new written
       rho_prev = rho;
       float* t = eo; eo = e; e = en; en = t;
     }
@@ -278,7 +280,7 @@ void ibm_default_opts(ibm_solve_opts* o) {
   o->helm_rtol = 1e-10;
   o->helm_maxit = 8;
   o->with_advection = 1;
-  o->arnoldi = IBM_ARNOLDI_DS;
+  o->arnoldi = IBM_ARNOLDI_FP32;
   o->c_mode = IBM_CMODE_SCALAR;
   o->c_rtol = 1e-14;
   o->c_maxit = 500;
@@ -615,6 +617,7 @@ ibm_status ibm_profile_read(ibm_ctx* c, ibm_profile* out) {
     if (k >= 0 && k < IBM_PROF_NCLASS) {
       out->ms[k] += ms;
       out->launches[k] += 1;
+      out->bytes[k] += c->prof[i].bytes;
     }
   }
   return IBM_OK;

@@ -152,6 +152,7 @@ struct ibm_ctx {
   struct ProfRec {
     int cls;
     cudaEvent_t a, b;
+    double bytes;   // algorithmic bytes of the timed kernels
   };
   std::vector<ProfRec> prof;
   size_t prof_used = 0;
@@ -292,7 +293,9 @@ void count_launch();
 // Records a start event for class cls (returns a handle, -1 when off) and the
 // matching end event.
 int prof_begin(ibm_ctx* c, int cls);
-void prof_end(ibm_ctx* c, int handle);
+// bytes: the algorithmic DRAM bytes of the timed kernels (each array read or
+// written once), summed per class by ibm_profile_read
+void prof_end(ibm_ctx* c, int handle, double bytes = 0.0);
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -252,7 +252,7 @@ ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
   }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
   launch_laplacian<double>(c->d, v, out, 1.0 / (c->h * c->h), c->stream);
-  prof_end(c, ph);
+  prof_end(c, ph, 16.0 * (double)c->m);
   ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
   if (fork) {
     IBM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
@@ -287,7 +287,8 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   // GMRES accepts any z_j; x = Z y uses the same z_j), the Gram-Schmidt
   // coefficients are <w, V_i> / nrm2[i] (formed on the device), and the
   // Hessenberg entries h_ij = <w, V_i> / ||V_i||, h_{j+1,j} = ||w|| on the host.
-  if (o->precond_prec == IBM_PREC_FP32 && o->arnoldi == IBM_ARNOLDI_DS && !o->reorth &&
+  if (o->precond_prec == IBM_PREC_FP32 &&
+      (o->arnoldi == IBM_ARNOLDI_DS || o->arnoldi == IBM_ARNOLDI_FP32) && !o->reorth &&
       ds_supported(c))
     return fgmres_solve_ds(c, b, x, o, st, x_is_zero);
   cudaStream_t s = c->stream;
@@ -361,10 +362,10 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
       if ((stt = schur_apply(c, zj, w)) != IBM_OK) return stt;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
       launch_multidot(w, V, m, j + 1, m, part, raw, s, nrm2, coef);
-      prof_end(c, ph);
+      prof_end(c, ph, 8.0 * (j + 2) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
       launch_axpy_norm(w, V, m, j + 1, coef, m, part, nrm2 + j + 1, s);
-      prof_end(c, ph);
+      prof_end(c, ph, 8.0 * (j + 3) * (double)m);
       if (o->reorth) {
         launch_multidot(w, V, m, j + 1, m, part, raw2, s, nrm2, coef2);
         launch_axpy_norm(w, V, m, j + 1, coef2, m, part, nrm2 + j + 1, s);

@@ -90,8 +90,10 @@ __device__ __forceinline__ dsf lap_cell(float zc, const float (&nb)[6], int nn, 
   return ds_mul(acc, ih2);
 }
 
+// (TW = float2: the pair; TW = float: rounded once to FP32)
+template <typename TW>
 __global__ void __launch_bounds__(32 * LVY) k_lap_ds(Dims d, const float* __restrict__ z,
-                                                     float2* __restrict__ w, float ih2_hi,
+                                                     TW* __restrict__ w, float ih2_hi,
                                                      float ih2_lo, int zc) {
   const int lane = threadIdx.x;
   const int i0 = 4 * (blockIdx.x * 32 + lane);
@@ -134,9 +136,13 @@ __global__ void __launch_bounds__(32 * LVY) k_lap_ds(Dims d, const float* __rest
       olo[q] = v.lo;
     }
     if (act) {
-      float4* wp = reinterpret_cast<float4*>(w + c);
-      wp[0] = make_float4(ohi[0], olo[0], ohi[1], olo[1]);
-      wp[1] = make_float4(ohi[2], olo[2], ohi[3], olo[3]);
+      if constexpr (std::is_same<TW, float2>::value) {
+        float4* wp = reinterpret_cast<float4*>(w + c);
+        wp[0] = make_float4(ohi[0], olo[0], ohi[1], olo[1]);
+        wp[1] = make_float4(ohi[2], olo[2], ohi[3], olo[3]);
+      } else {
+        *reinterpret_cast<float4*>(w + c) = make_float4(ohi[0], ohi[1], ohi[2], ohi[3]);
+      }
     }
     zp = zcur;
     zcur = zn;
@@ -145,12 +151,13 @@ __global__ void __launch_bounds__(32 * LVY) k_lap_ds(Dims d, const float* __rest
 
 // Shell cells: w[c] += scale * (G^T R t)[c] with the FP64 sum of the cell's
 // entries (interleaved layout, as k_shell_gradt), added to the pair in FP64.
+template <typename TW>
 __global__ void k_shell_gradt_ds(int64_t n_shell, const int32_t* __restrict__ shell_cell,
                                  const int32_t* __restrict__ base, const int32_t* __restrict__ len,
                                  const int32_t* __restrict__ ekey,
                                  const double* __restrict__ ecoef, int64_t n_ell, int64_t nmk,
                                  const double* __restrict__ t, double scale,
-                                 float2* __restrict__ wv) {
+                                 TW* __restrict__ wv) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n_shell) return;
   const int64_t g = q >> 5;
@@ -165,10 +172,14 @@ __global__ void k_shell_gradt_ds(int64_t n_shell, const int32_t* __restrict__ sh
     acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
   }
   const int64_t c = shell_cell[q];
-  const float2 wc = wv[c];
-  const double v = (double)wc.x + (double)wc.y + scale * acc;
-  const dsf r = d_to_ds(v);
-  wv[c] = make_float2(r.hi, r.lo);
+  if constexpr (std::is_same<TW, float2>::value) {
+    const float2 wc = wv[c];
+    const double v = (double)wc.x + (double)wc.y + scale * acc;
+    const dsf r = d_to_ds(v);
+    wv[c] = make_float2(r.hi, r.lo);
+  } else {
+    wv[c] = (float)((double)wv[c] + scale * acc);
+  }
 }
 
 // Compensated accumulation of products: the running FP32 sum S and an FP32
@@ -311,6 +322,73 @@ __global__ void __launch_bounds__(RT) k_gemv_ds(double* __restrict__ x,
   }
 }
 
+// FP32 Arnoldi process (IBM_ARNOLDI_FP32): the basis vectors are single FP32
+// numbers (half the bytes of the pairs); dot products and the axpy are still
+// accumulated with the compensated scheme, and each result is rounded once.
+
+// part[b][q] = <w, V_q> for FP32 w and V
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_multidot_sp(const float* __restrict__ w,
+                                                    const float* __restrict__ V, int64_t ld,
+                                                    int nq, int64_t n, double* __restrict__ part) {
+  Comp acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    const float wi = __ldg(w + i);
+    float v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = q < nq ? __ldg(V + q * ld + i) : 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) comp_add_prod_f(acc[q], wi, 0.f, v[q]);
+  }
+  dsf r[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) r[q] = fast_two_sum(acc[q].s, acc[q].e);
+  block_reduce_ds<NQ>(r, nq, part);
+}
+
+// w -= sum_q coef[q] V_q (coef as pairs, the sum compensated, the result
+// rounded once to FP32), part[b][0] = sum of w^2
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_axpy_norm_sp(float* __restrict__ w,
+                                                     const float* __restrict__ V, int64_t ld,
+                                                     int nq, const float2* __restrict__ coef,
+                                                     int64_t n, double* __restrict__ part) {
+  float ch[NQ], cl[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float2 v = q < nq ? coef[q] : make_float2(0.f, 0.f);
+    ch[q] = v.x;
+    cl[q] = v.y;
+  }
+  Comp nrm = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    const float wi = w[i];
+    float v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = q < nq ? __ldg(V + q * ld + i) : 0.f;
+    Comp t = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) comp_add_prod_f(t, ch[q], cl[q], v[q]);
+    const dsf d = two_sum(wi, -t.s);
+    const float wn = __fadd_rn(d.hi, __fsub_rn(d.lo, t.e));
+    w[i] = wn;
+    comp_add_prod_f(nrm, wn, 0.f, wn);
+  }
+  dsf r[1] = {fast_two_sum(nrm.s, nrm.e)};
+  block_reduce_ds<1>(r, 1, part);
+}
+
+// FP64 vector rounded to FP32
+__global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (float)x[i];
+}
+
 #define IBM_NQ_DISPATCH_DS(nq, KERNEL, ...)                                 \
   do {                                                                      \
     count_launch();                                                         \
@@ -345,7 +423,8 @@ bool ds_supported(const ibm_ctx* c) { return c->d.nx % 4 == 0 && c->n_levels > 1
 
 // w = S~ z for FP32 z, w as a hi/lo pair: double-single Laplacian, FP64 marker
 // term gathered from z and added on the shell cells.
-ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
+template <typename TW>
+ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
   cudaStream_t s = c->stream;
   const double ih2 = 1.0 / (c->h * c->h);
   const float ih2_hi = (float)ih2;
@@ -363,9 +442,9 @@ ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
   }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
   count_launch();
-  k_lap_ds<<<dim3(div_up(c->d.nx / 4, 32), div_up(c->d.ny, LVY), div_up(c->d.nz, zc)),
-             dim3(32, LVY), 0, s>>>(c->d, z, w, ih2_hi, ih2_lo, zc);
-  prof_end(c, ph);
+  k_lap_ds<TW><<<dim3(div_up(c->d.nx / 4, 32), div_up(c->d.ny, LVY), div_up(c->d.nz, zc)),
+                 dim3(32, LVY), 0, s>>>(c->d, z, w, ih2_hi, ih2_lo, zc);
+  prof_end(c, ph, (double)c->m * (4 + sizeof(TW)));
   if (m.n > 0 && m.n_shell > 0) {
     ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
     const double* t = m.t;
@@ -381,7 +460,7 @@ ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
       sign = c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0;
     }
     count_launch();
-    k_shell_gradt_ds<<<div_up(m.n_shell, 256), 256, 0, s>>>(
+    k_shell_gradt_ds<TW><<<div_up(m.n_shell, 256), 256, 0, s>>>(
         m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
         sign, w);
     prof_end(c, ph);
@@ -390,11 +469,21 @@ ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
   return IBM_OK;
 }
 
+ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
+  return schur_apply_ds_t<float2>(c, z, w);
+}
+
 ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
                            ibm_solve_stats* st, bool x_is_zero) {
   // Same flexible GMRES as fgmres_solve (unnormalised Arnoldi vectors with
-  // squared norms nrm2[i] on the device), with the vectors as FP32 pairs:
-  // Vhi/Vlo reuse the FP64 basis storage, Z holds the FP32 V-cycle outputs.
+  // squared norms nrm2[i] on the device), with the vectors as FP32 pairs
+  // (Vhi/Vlo reuse the FP64 basis storage) or, for IBM_ARNOLDI_FP32, single
+  // FP32 numbers; Z holds the FP32 V-cycle outputs.  A single-precision cycle
+  // stops once its residual estimate has fallen by kSingleCycle (the FP32
+  // basis cannot resolve more) and the next cycle starts from the FP64
+  // residual.
+  const bool single = o->arnoldi == IBM_ARNOLDI_FP32;
+  constexpr double kSingleCycle = 4e-6;
   cudaStream_t s = c->stream;
   const int64_t m = c->m;
   const int restart = o->restart;
@@ -407,8 +496,10 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   double* sdev = c->red_out + 6 * kOutStride;
   double* hr = c->host_red;
   float2* V2 = reinterpret_cast<float2*>(c->V);
+  float* V1 = reinterpret_cast<float*>(c->V);
   float* Zf = reinterpret_cast<float*>(c->Z);
   // leading parts of the newest basis vector, contiguous: the V-cycle input
+  // (the vector itself in the single-precision form)
   float* vin = c->lv[0].b32;
   double* r64 = c->c1;
   ibm_status stt;
@@ -452,8 +543,14 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     if (relres <= o->rtol) { converged = true; break; }
     if (total >= o->maxit) break;
     count_launch();
-    k_split<<<kRedBlocks, RT, 0, s>>>(r0, V2, vin, m);
+    if (single) {
+      k_round_f32<<<kRedBlocks, RT, 0, s>>>(r0, V1, m);
+      vin = V1;
+    } else {
+      k_split<<<kRedBlocks, RT, 0, s>>>(r0, V2, vin, m);
+    }
     rn[0] = beta;
+    const double cycle_stop = single ? kSingleCycle * beta : 0.0;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jused = 0;
@@ -461,22 +558,34 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     for (int j = 0; j < restart && total < o->maxit; ++j) {
       float* zj = Zf + (int64_t)j * m;
       float2* w = V2 + (int64_t)(j + 1) * m;
+      float* w1 = V1 + (int64_t)(j + 1) * m;
       int ph = prof_begin(c, IBM_PROF_VCYCLE);
-      if ((stt = mg_vcycle_f32(c, vin, zj, o->mg_pre, o->mg_post)) != IBM_OK) return stt;
+      if ((stt = mg_vcycle_f32(c, single ? V1 + (int64_t)j * m : vin, zj, o->mg_pre,
+                               o->mg_post)) != IBM_OK)
+        return stt;
       prof_end(c, ph);
-      if ((stt = schur_apply_ds(c, zj, w)) != IBM_OK) return stt;
+      if ((stt = single ? schur_apply_ds_t<float>(c, zj, w1) : schur_apply_ds_t<float2>(c, zj, w)) !=
+          IBM_OK)
+        return stt;
       const int nq = j + 1;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
-      IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
+      if (single)
+        IBM_NQ_DISPATCH_DS(nq, k_multidot_sp, w1, V1, m, nq, m, part);
+      else
+        IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
       count_launch();
       k_final_reduce_ds<<<nq, RT, 0, s>>>(part, kRedBlocks, raw, nrm2, coef, coef_ds);
-      prof_end(c, ph);
+      prof_end(c, ph, (single ? 4.0 : 8.0) * (nq + 1) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
-      IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);
+      if (single)
+        IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_sp, w1, V1, m, nq, coef_ds, m, part);
+      else
+        IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);
       count_launch();
       k_final_reduce_ds<<<1, RT, 0, s>>>(part, kRedBlocks, nrm2 + j + 1, nullptr, nullptr,
                                           nullptr);
-      prof_end(c, ph);
+      // V_0..V_j and w read, w written (and its leading parts for the pair form)
+      prof_end(c, ph, single ? 4.0 * (nq + 2) * (double)m : (8.0 * (nq + 2) + 4.0) * (double)m);
       IBM_LAUNCH_CHECK(c);
       IBM_CUDA(c, cudaMemcpyAsync(hr, raw, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
       IBM_CUDA(c, cudaMemcpyAsync(hr + 4 * kOutStride + j + 1, nrm2 + j + 1, sizeof(double),
@@ -504,6 +613,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       jused = j + 1;
       if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = std::fabs(g[j + 1]) / bnorm;
       if (std::fabs(g[j + 1]) / bnorm <= o->rtol || hn == 0.0) break;
+      if (std::fabs(g[j + 1]) <= cycle_stop) break;   // FP32 basis exhausted
     }
     if (jused > 0) {
       for (int i = jused - 1; i >= 0; --i) {

@@ -908,7 +908,7 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
       k_first<T, TB><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(
           L.d, b, bcopy, x, w_over_n<T>(w[0] * h2), w_over_n<T>(two ? w[1] : 0.0), (T)h2, two);
   }
-  prof_end(c, ph);
+  prof_end(c, ph, (double)L.m * (sizeof(TB) + sizeof(T) + (bcopy ? sizeof(T) : 0)));
   const T* bb = bcopy ? bcopy : reinterpret_cast<const T*>(b);
   T* cur = x;
   T* nxt = t;
@@ -966,12 +966,12 @@ void post_smooth(ibm_ctx* c, int l, const T* b, T* x, T* t, int p, TO* out, cuda
     const int ph = l == 0 ? prof_begin(c, IBM_PROF_MG_SMOOTH_FINE) : -1;
     if (last && (const void*)out != (const void*)src) {
       sweep_step<T, TO>(c, l, src, b, out, w[q], s);
-      prof_end(c, ph);
+      prof_end(c, ph, (double)L.m * (2 * sizeof(T) + sizeof(TO)));
       return;
     }
     T* dst = (src == x) ? t : x;
     sweep_step<T, T>(c, l, src, b, dst, w[q], s);
-    prof_end(c, ph);
+    prof_end(c, ph, (double)L.m * 3 * sizeof(T));
     src = dst;
   }
   // the last step landed in t or x while out aliases the other: copy

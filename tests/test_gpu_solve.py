@@ -33,8 +33,9 @@ def setup(request, cuda_device):
     torch.cuda.synchronize()
 
 
-MODES = [(0, 0), (1, 1), (1, 0)]
-MODE_IDS = ["fp64_vcycle", "fp32_vcycle_ds_arnoldi", "fp32_vcycle_fp64_arnoldi"]
+MODES = [(0, 0), (1, 1), (1, 0), (1, 2)]
+MODE_IDS = ["fp64_vcycle", "fp32_vcycle_ds_arnoldi", "fp32_vcycle_fp64_arnoldi",
+            "fp32_vcycle_fp32_arnoldi"]
 
 
 @pytest.mark.parametrize("prec,arnoldi", MODES, ids=MODE_IDS)
