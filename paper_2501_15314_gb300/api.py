@@ -104,6 +104,20 @@ class IBMSolver:
         except Exception:
             pass
 
+    def _call(self, name, *args):
+        """One library call on the solver's stream.  When the caller's current
+        stream is another one, the call is ordered after it (where the inputs
+        and the freshly allocated outputs were written) and the current
+        stream after the call (where the results are read)."""
+        cur = torch.cuda.current_stream()
+        other = cur != self.stream
+        if other:
+            self.stream.wait_stream(cur)
+        status = getattr(self.lib, name)(self.ctx, *args)
+        if other:
+            cur.wait_stream(self.stream)
+        return status
+
     def _cells(self, **kw):
         return torch.empty(self.m, dtype=torch.float64, device="cuda", **kw)
 
@@ -114,14 +128,14 @@ class IBMSolver:
     def set_markers(self, X: torch.Tensor):
         X = X.reshape(3, -1) if X.numel() else X
         n = X.shape[1] if X.numel() else 0
-        check(self.lib.ibm_set_markers(self.ctx, n, _ptr(X, name="X") if n else None), self.ctx)
+        check(self._call("ibm_set_markers", n, _ptr(X, name="X") if n else None), self.ctx)
         self.n_markers = n
         self._X = X
 
     # -- operators --------------------------------------------------------
     def apply_laplacian(self, v, out=None):
         out = self._cells() if out is None else out
-        check(self.lib.ibm_apply_laplacian(self.ctx, _ptr(v, numel=self.m, name="v"),
+        check(self._call("ibm_apply_laplacian", _ptr(v, numel=self.m, name="v"),
                                            _ptr(out, numel=self.m, name="out")), self.ctx)
         return out
 
@@ -130,12 +144,12 @@ class IBMSolver:
         c_rtol, c_maxit) the form they select."""
         out = self._cells() if out is None else out
         if not kw:
-            check(self.lib.ibm_apply_schur(self.ctx, _ptr(v, numel=self.m, name="v"),
+            check(self._call("ibm_apply_schur", _ptr(v, numel=self.m, name="v"),
                                            _ptr(out, numel=self.m, name="out")), self.ctx)
             return out
         o = self.opts(**kw)
         it = C.c_int64(0)
-        check(self.lib.ibm_apply_schur_opts(self.ctx, _ptr(v, numel=self.m, name="v"),
+        check(self._call("ibm_apply_schur_opts", _ptr(v, numel=self.m, name="v"),
                                             _ptr(out, numel=self.m, name="out"), C.byref(o),
                                             C.byref(it)), self.ctx)
         self.last_c_iters = it.value
@@ -147,15 +161,15 @@ class IBMSolver:
         out = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda") if out is None else out
         it = C.c_int32(0)
         if nmk:
-            check(self.lib.ibm_apply_c_inverse(self.ctx, _ptr(t, numel=nmk, name="t"),
+            check(self._call("ibm_apply_c_inverse", _ptr(t, numel=nmk, name="t"),
                                                _ptr(out, name="s"), c_rtol, c_maxit,
                                                C.byref(it)), self.ctx)
         return out[:nmk], it.value
 
     def precond(self, r, prec=IBM_PREC_FP32, pre=2, post=2, out=None):
         out = self._cells() if out is None else out
-        check(self.lib.ibm_apply_laplacian_precond(
-            self.ctx, _ptr(r, numel=self.m, name="r"), _ptr(out, numel=self.m, name="z"),
+        check(self._call("ibm_apply_laplacian_precond",
+            _ptr(r, numel=self.m, name="r"), _ptr(out, numel=self.m, name="z"),
             prec, pre, post), self.ctx)
         return out
 
@@ -163,25 +177,25 @@ class IBMSolver:
         out = torch.zeros(3 * self.n_markers, dtype=torch.float64, device="cuda") \
             if out is None else out
         if self.n_markers:
-            check(self.lib.ibm_interp(self.ctx, _ptr(u, numel=self.nf, name="u"),
+            check(self._call("ibm_interp", _ptr(u, numel=self.nf, name="u"),
                                       _ptr(out, name="U")), self.ctx)
         return out
 
     def spread(self, F, out=None):
         out = self._faces() if out is None else out
-        check(self.lib.ibm_spread(self.ctx, _ptr(F, name="F") if self.n_markers else None,
+        check(self._call("ibm_spread", _ptr(F, name="F") if self.n_markers else None,
                                   _ptr(out, numel=self.nf, name="u")), self.ctx)
         return out
 
     def gradient(self, p, out=None):
         out = self._faces() if out is None else out
-        check(self.lib.ibm_gradient(self.ctx, _ptr(p, numel=self.m, name="p"),
+        check(self._call("ibm_gradient", _ptr(p, numel=self.m, name="p"),
                                     _ptr(out, numel=self.nf, name="u")), self.ctx)
         return out
 
     def gradient_t(self, u, out=None):
         out = self._cells() if out is None else out
-        check(self.lib.ibm_gradient_t(self.ctx, _ptr(u, numel=self.nf, name="u"),
+        check(self._call("ibm_gradient_t", _ptr(u, numel=self.nf, name="u"),
                                       _ptr(out, numel=self.m, name="out")), self.ctx)
         return out
 
@@ -189,7 +203,7 @@ class IBMSolver:
         out = torch.zeros(3 * self.n_markers, dtype=torch.float64, device="cuda") \
             if out is None else out
         if self.n_markers:
-            check(self.lib.ibm_force_correction(self.ctx, _ptr(p, numel=self.m, name="p"),
+            check(self._call("ibm_force_correction", _ptr(p, numel=self.m, name="p"),
                                                 _ptr(rhs_F, name="rhs_F"),
                                                 _ptr(out, name="F")), self.ctx)
         return out
@@ -208,7 +222,7 @@ class IBMSolver:
             else x0.clone()
         o = self.opts(**kw)
         st = _lib.ibm_solve_stats()
-        status = self.lib.ibm_solve_schur(self.ctx, _ptr(b, numel=self.m, name="b"),
+        status = self._call("ibm_solve_schur", _ptr(b, numel=self.m, name="b"),
                                           _ptr(p, numel=self.m, name="p"), C.byref(o),
                                           C.byref(st))
         if raise_on_error:
@@ -225,8 +239,8 @@ class IBMSolver:
                        F=torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda"))
         o = self.opts(**kw)
         st = _lib.ibm_solve_stats()
-        status = self.lib.ibm_step(
-            self.ctx, _ptr(u_n, numel=self.nf, name="u_n"),
+        status = self._call("ibm_step",
+            _ptr(u_n, numel=self.nf, name="u_n"),
             _ptr(u_nm1, numel=self.nf, name="u_nm1"), _ptr(p_n, numel=self.m, name="p_n"),
             _ptr(F_n, name="F_n") if nmk else None,
             _ptr(U_gamma, name="U_gamma") if nmk else None,
@@ -257,8 +271,8 @@ class IBMSolver:
             fo.gravity[e] = float(gravity[e])
         fo.xi, fo.tol, fo.max_inner = float(xi), float(tol), int(max_inner)
         st = _lib.ibm_fsi_stats()
-        status = self.lib.ibm_fsi_step(
-            self.ctx, spheres.n, spheres.arr, n, _ptr(L0, numel=nmk, name="L0"),
+        status = self._call("ibm_fsi_step",
+            spheres.n, spheres.arr, n, _ptr(L0, numel=nmk, name="L0"),
             _ptr(body_id, dtype=torch.int32, numel=n, name="body_id"),
             _ptr(u_n, numel=self.nf, name="u_n"), _ptr(u_nm1, numel=self.nf, name="u_nm1"),
             _ptr(p_n, numel=self.m, name="p_n"), _ptr(F_n, numel=nmk, name="F_n"),
@@ -273,11 +287,11 @@ class IBMSolver:
                          helm_iters=st.helm_iters, helm_relres=st.helm_relres, status=status)
 
     def profile_enable(self, on=True):
-        check(self.lib.ibm_profile_enable(self.ctx, 1 if on else 0), self.ctx)
+        check(self._call("ibm_profile_enable", 1 if on else 0), self.ctx)
 
     def profile_read(self) -> dict:
         p = _lib.ibm_profile()
-        check(self.lib.ibm_profile_read(self.ctx, C.byref(p)), self.ctx)
+        check(self._call("ibm_profile_read", C.byref(p)), self.ctx)
         return {name: dict(ms=p.ms[i], launches=p.launches[i], bytes=p.bytes[i])
                 for i, name in enumerate(_lib.PROF_NAMES)}
 
@@ -290,8 +304,8 @@ class IBMSolver:
         X_bar = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda")
         o = self.opts(**kw)
         st = _lib.ibm_solve_stats()
-        status = self.lib.ibm_adjoint_step(
-            self.ctx, _ptr(u_np1, numel=self.nf, name="u_np1"),
+        status = self._call("ibm_adjoint_step",
+            _ptr(u_np1, numel=self.nf, name="u_np1"),
             _ptr(F_n, numel=nmk, name="F_n") if (nmk and F_n is not None) else None,
             _ptr(F_np1, numel=nmk, name="F_np1") if nmk else None,
             _ptr(F_bar, numel=nmk, name="F_bar") if nmk else None,
@@ -317,8 +331,8 @@ class IBMSolver:
         X_bar = torch.zeros(max(nmk, 1), dtype=torch.float64, device="cuda")
         c_bar = np.zeros((nb, 3))
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
-        check(self.lib.ibm_body_forces_adjoint(
-            self.ctx, _ptr(F, name="F") if nmk else None, _ptr(X, name="X") if nmk else None,
+        check(self._call("ibm_body_forces_adjoint",
+            _ptr(F, name="F") if nmk else None, _ptr(X, name="X") if nmk else None,
             _ptr(body_id, dtype=torch.int32, name="body_id") if nmk else None, nb,
             dp(centers), dp(w), dp(out), _ptr(F_bar, name="F_bar") if nmk else None,
             _ptr(X_bar, name="X_bar") if nmk else None, dp(c_bar)), self.ctx)
@@ -329,8 +343,8 @@ class IBMSolver:
         centers = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, 3))
         nb = centers.shape[0]
         out = np.zeros((nb, 6))
-        check(self.lib.ibm_body_forces(
-            self.ctx, _ptr(F, name="F"), _ptr(X, name="X"),
+        check(self._call("ibm_body_forces",
+            _ptr(F, name="F"), _ptr(X, name="X"),
             _ptr(body_id, dtype=torch.int32, name="body_id"), nb,
             centers.ctypes.data_as(C.POINTER(C.c_double)),
             out.ctypes.data_as(C.POINTER(C.c_double))), self.ctx)

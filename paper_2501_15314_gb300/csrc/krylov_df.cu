@@ -382,6 +382,93 @@ __global__ void __launch_bounds__(RT) k_axpy_norm_sp(float* __restrict__ w,
   block_reduce_ds<1>(r, 1, part);
 }
 
+// The same two kernels on float4 (four consecutive elements per thread and
+// array, 16-byte loads: more bytes in flight per thread), for m a multiple of
+// 4 and nq <= 16.  Each element is accumulated exactly as in the scalar
+// kernels; only the order of the additions within a thread differs.
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_multidot_sp4(const float4* __restrict__ w,
+                                                     const float4* __restrict__ V, int64_t ld4,
+                                                     int nq, int64_t n4,
+                                                     double* __restrict__ part) {
+  Comp acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n4; i += (int64_t)gridDim.x * RT) {
+    const float4 wi = __ldg(w + i);
+    float4 v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      v[q] = q < nq ? __ldg(V + q * ld4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (q < nq) {
+        comp_add_prod_f(acc[q], wi.x, 0.f, v[q].x);
+        comp_add_prod_f(acc[q], wi.y, 0.f, v[q].y);
+        comp_add_prod_f(acc[q], wi.z, 0.f, v[q].z);
+        comp_add_prod_f(acc[q], wi.w, 0.f, v[q].w);
+      }
+    }
+  }
+  dsf r[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) r[q] = fast_two_sum(acc[q].s, acc[q].e);
+  block_reduce_ds<NQ>(r, nq, part);
+}
+
+template <int NQ>
+__device__ __forceinline__ float axpy_elem(float wi, const float (&ch)[NQ], const float (&cl)[NQ],
+                                           const float (&v)[NQ], int nq) {
+  Comp t = {0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    if (q < nq) comp_add_prod_f(t, ch[q], cl[q], v[q]);
+  const dsf d = two_sum(wi, -t.s);
+  return __fadd_rn(d.hi, __fsub_rn(d.lo, t.e));
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_axpy_norm_sp4(float4* __restrict__ w,
+                                                      const float4* __restrict__ V, int64_t ld4,
+                                                      int nq, const float2* __restrict__ coef,
+                                                      int64_t n4, double* __restrict__ part) {
+  float ch[NQ], cl[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float2 c = q < nq ? coef[q] : make_float2(0.f, 0.f);
+    ch[q] = c.x;
+    cl[q] = c.y;
+  }
+  Comp nrm = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n4; i += (int64_t)gridDim.x * RT) {
+    const float4 wi = w[i];
+    float4 v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      v[q] = q < nq ? __ldg(V + q * ld4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float vx[NQ], vy[NQ], vz[NQ], vw[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      vx[q] = v[q].x;
+      vy[q] = v[q].y;
+      vz[q] = v[q].z;
+      vw[q] = v[q].w;
+    }
+    float4 o;
+    o.x = axpy_elem<NQ>(wi.x, ch, cl, vx, nq);
+    o.y = axpy_elem<NQ>(wi.y, ch, cl, vy, nq);
+    o.z = axpy_elem<NQ>(wi.z, ch, cl, vz, nq);
+    o.w = axpy_elem<NQ>(wi.w, ch, cl, vw, nq);
+    w[i] = o;
+    comp_add_prod_f(nrm, o.x, 0.f, o.x);
+    comp_add_prod_f(nrm, o.y, 0.f, o.y);
+    comp_add_prod_f(nrm, o.z, 0.f, o.z);
+    comp_add_prod_f(nrm, o.w, 0.f, o.w);
+  }
+  dsf r[1] = {fast_two_sum(nrm.s, nrm.e)};
+  block_reduce_ds<1>(r, 1, part);
+}
+
 // FP64 vector rounded to FP32
 __global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -401,6 +488,17 @@ __global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ v,
     else if ((nq) <= 32) KERNEL<32><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
     else if ((nq) <= 48) KERNEL<48><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
     else KERNEL<kMaxRestart + 1><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);    \
+  } while (0)
+
+// the float4 FP32 kernels, for nq <= 16
+#define IBM_NQ_DISPATCH_SP4(nq, KERNEL, ...)                                \
+  do {                                                                      \
+    count_launch();                                                         \
+    if ((nq) <= 2) KERNEL<2><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);        \
+    else if ((nq) <= 4) KERNEL<4><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
+    else if ((nq) <= 8) KERNEL<8><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
+    else if ((nq) <= 12) KERNEL<12><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
+    else KERNEL<16><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);                 \
   } while (0)
 
 int lap_zc(Dims d) {
@@ -483,6 +581,8 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   // basis cannot resolve more) and the next cycle starts from the FP64
   // residual.
   const bool single = o->arnoldi == IBM_ARNOLDI_FP32;
+  // float4 Gram-Schmidt kernels: every basis vector starts on a 16-byte boundary
+  const bool vec4 = single && c->m % 4 == 0;
   constexpr double kSingleCycle = 4e-6;
   cudaStream_t s = c->stream;
   const int64_t m = c->m;
@@ -569,7 +669,10 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         return stt;
       const int nq = j + 1;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
-      if (single)
+      if (vec4 && nq <= 16)
+        IBM_NQ_DISPATCH_SP4(nq, k_multidot_sp4, reinterpret_cast<const float4*>(w1),
+                            reinterpret_cast<const float4*>(V1), m / 4, nq, m / 4, part);
+      else if (single)
         IBM_NQ_DISPATCH_DS(nq, k_multidot_sp, w1, V1, m, nq, m, part);
       else
         IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
@@ -577,7 +680,10 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       k_final_reduce_ds<<<nq, RT, 0, s>>>(part, kRedBlocks, raw, nrm2, coef, coef_ds);
       prof_end(c, ph, (single ? 4.0 : 8.0) * (nq + 1) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
-      if (single)
+      if (vec4 && nq <= 16)
+        IBM_NQ_DISPATCH_SP4(nq, k_axpy_norm_sp4, reinterpret_cast<float4*>(w1),
+                            reinterpret_cast<const float4*>(V1), m / 4, nq, coef_ds, m / 4, part);
+      else if (single)
         IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_sp, w1, V1, m, nq, coef_ds, m, part);
       else
         IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);

@@ -118,3 +118,26 @@ def test_edge_cases(cuda_device):
     # a grid that does not coarsen to <= 512 cells is rejected at creation
     with pytest.raises(_lib.IBMError):
         IBMSolver(50, 50, 75)
+
+
+def test_fp32_arnoldi_cell_count_not_multiple_of_4(cuda_device):
+    """FP32 Arnoldi on a 10 x 9 x 5 grid (450 cells, not a multiple of 4, so
+    the scalar Gram-Schmidt kernels run instead of the float4 ones, which
+    need every basis vector on a 16-byte boundary): parity with the oracle's
+    solve at rtol 1e-13."""
+    from oracle import mac, schur
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+    nx, ny, nz, h = 10, 9, 5, 0.1
+    g = mac.Grid(nx, ny, nz, h)
+    X = wl.fibonacci_sphere(10, 0.06, [0.5, 0.45, 0.25])
+    rng = np.random.default_rng(3)
+    sysm = schur.SchurSystem(g, X)
+    u = rng.standard_normal(g.n_faces) * g.interior_face_mask_packed()
+    b = sysm.rhs_scalar(mac.apply_GT(g, u), rng.standard_normal(sysm.k))
+    ref, _, _, _ = schur.solve_schur(sysm, b, rtol=1e-13)
+    s = IBMSolver(nx, ny, nz, h)
+    s.set_markers(dev(X))
+    p, st = s.solve_schur(dev(b), rtol=1e-13, precond_prec=1, arnoldi=2, maxit=300)
+    assert rel(host(p), ref) < PARITY, (rel(host(p), ref), st)
+    s.close()

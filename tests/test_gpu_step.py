@@ -61,3 +61,35 @@ def test_step_with_history_ragged(cuda_device):
     ref, out, st = _run(case, u_n, u_nm1, p_n, F_n)
     for k in ("u", "p", "F"):
         assert rel(out[k], ref[k]) < 1e-10, (k, rel(out[k], ref[k]))
+
+
+def test_solver_on_its_own_stream_orders_against_caller(cuda_device):
+    """A solver created on a stream other than the caller's: the inputs are
+    written on the caller's stream behind a long busy kernel, the step runs
+    on the solver's stream and the results are read back on the caller's
+    stream.  The step must see the inputs and the caller the results: the
+    same answer as a solver on the caller's stream."""
+    import torch
+    from paper_2501_15314_gb300.api import IBMSolver
+    case = _with_inputs(gc.sphere16())
+    g = case.grid()
+    src = {k: dev(v) for k, v in dict(X=case.X, U=case.U_gamma, f=case.f_body).items()}
+    outs = []
+    for side in (False, True):
+        s = IBMSolver(case.nx, case.ny, case.nz, case.h, Re=case.Re, dt=case.dt,
+                      stream=torch.cuda.Stream() if side else None)
+        torch.cuda.synchronize()
+        inp = {k: torch.empty_like(v) for k, v in src.items()}
+        torch.cuda._sleep(20_000_000)          # keeps the caller's stream busy for ~10 ms
+        for k in inp:
+            inp[k].copy_(src[k])
+        s.set_markers(inp["X"])
+        zf = torch.zeros(g.n_faces, dtype=torch.float64, device="cuda")
+        out, st = s.step(zf, zf, torch.zeros(g.m, dtype=torch.float64, device="cuda"),
+                         torch.zeros(3 * case.N, dtype=torch.float64, device="cuda"), inp["U"],
+                         inp["f"], precond_prec=0, rtol=1e-12)
+        outs.append({k: host(v) for k, v in out.items()})
+        s.close()
+    for k in ("u", "p", "F"):
+        assert rel(outs[1][k], outs[0][k]) < 1e-13, (k, rel(outs[1][k], outs[0][k]))
+        assert np.linalg.norm(outs[0][k]) > 0
