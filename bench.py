@@ -50,7 +50,14 @@ SAMPLE_ITERS = 3           # FGMRES iterations in the CPU oracle's bounded sampl
 # cells x vectors).  profiles/ncu_traffic_step_spheres8_192.md has the
 # command and the per-kernel numbers.  A class whose kernel changes after the
 # capture must be removed here (its traffic then reads null).
-NCU_TRAFFIC_RATIO = {}
+NCU_TRAFFIC_RATIO = {
+    # mode-1 launches of the predictor's Chebyshev step (the class's launches)
+    "helm_sweep": 0.957,
+    # FP32 Gram-Schmidt (float4 kernels): at 192^3 the new vector w (28 MB)
+    # is partly L2-resident, as at 256^3 (67 MB)
+    "multidot": 1.001,
+    "axpy_norm": 0.912,
+}
 
 
 def env_rank():
@@ -308,9 +315,10 @@ def run_ours(args):
 
     # ---- end to end through the public API with host buffers ----
     # Every step copies its inputs from pinned host memory and its results
-    # back.  The copies run on a second stream, pipelined with the steps:
-    # step k+1's inputs go in and step k-1's results come out while step k
-    # computes (two device buffer sets, ordered by events).
+    # back.  The copies run on two more streams, one per direction (the link
+    # is full duplex), pipelined with the steps: step k+1's inputs go in and
+    # step k-1's results come out while step k computes (two device buffer
+    # sets, ordered by events).
     pin = lambda t: t.cpu().pin_memory()  # noqa: E731
     h_in = dict(X=pin(X), U=pin(U), f=pin(f), u_n=pin(zf), u_nm1=pin(zf), p_n=pin(zc),
                 F_n=pin(zk))
@@ -320,7 +328,8 @@ def run_ours(args):
              for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
     d2h = sum(v.numel() * v.element_size() for v in h_out[0].values())
-    cstream = torch.cuda.Stream()
+    cstream = torch.cuda.Stream()           # host to device
+    ostream = torch.cuda.Stream()           # device to host
     ev = lambda: torch.cuda.Event()  # noqa: E731
     ev_in, ev_done, ev_outc = [ev(), ev()], [ev(), ev()], [ev(), ev()]
     for q in range(2):
@@ -335,11 +344,11 @@ def run_ours(args):
             ev_in[b].record(cstream)
 
     def copy_out(b):
-        with torch.cuda.stream(cstream):
-            cstream.wait_event(ev_done[b])
+        with torch.cuda.stream(ostream):
+            ostream.wait_event(ev_done[b])
             for kk in h_out[b]:
                 h_out[b][kk].copy_(d_out[b][kk], non_blocking=True)
-            ev_outc[b].record(cstream)
+            ev_outc[b].record(ostream)
 
     def e2e_run(K):
         copy_in(0)
@@ -408,11 +417,12 @@ def run_ours(args):
     kern = {
         "k_helm_cheb_v4 (predictor FP32 Chebyshev step: read e, e_old, r; write e_new)":
             ("helm_sweep", prof["helm_sweep"]["bytes"]),
-        "k_multidot_sp (Gram-Schmidt multi-dot on FP32 vectors: w and V_0..V_j)":
+        "k_multidot_sp4 (Gram-Schmidt multi-dot on FP32 vectors, float4: w and V_0..V_j)":
             ("multidot", prof["multidot"]["bytes"]),
-        "k_axpy_norm_sp (Gram-Schmidt axpy+norm on FP32 vectors: V_0..V_j, w in/out)":
+        "k_axpy_norm_sp4 (Gram-Schmidt axpy+norm on FP32 vectors, float4: V_0..V_j, w in/out)":
             ("axpy_norm", prof["axpy_norm"]["bytes"]),
-        "k_lap_ds<float> (Schur Laplacian, FP32 z in, exact product rounded to FP32 out)":
+        ("Schur Laplacian class: k_lap_ds<float> (FP32 z in, exact product rounded to FP32 "
+         "out) per iteration and k_laplacian<double> of the FP64 true residuals"):
             ("laplacian_f64", prof["laplacian_f64"]["bytes"]),
         "k_first_v4 + k_sweep_v4 (finest V-cycle smoothing)":
             ("mg_smooth_fine", prof["mg_smooth_fine"]["bytes"]),
@@ -459,8 +469,8 @@ def run_ours(args):
             "clocks": clk,
             "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
-                    "copies": "pinned host buffers, H2D/D2H on a second stream pipelined "
-                              "with the steps (double-buffered)",
+                    "copies": "pinned host buffers; H2D and D2H each on a stream of its "
+                              "own, pipelined with the steps (double-buffered)",
                     "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, det = oracle_sample(W, oracle_iterations(args.config))

@@ -297,6 +297,51 @@ int prof_begin(ibm_ctx* c, int cls);
 // written once), summed per class by ibm_profile_read
 void prof_end(ibm_ctx* c, int handle, double bytes = 0.0);
 
+// Sum over one shell cell's entries of the interleaved layout (entry p of the
+// cell at idx + 32 p): sum_p sum_e coef_e[p] t_e[marker(p)], FP64 FMAs in
+// entry order.  Four entries' loads are issued before their FMAs (the marker
+// index of an entry must arrive before its t can be gathered, so one entry at
+// a time leaves the thread waiting on two dependent loads per entry); the
+// order of the FMAs, and so the result, is that of the plain loop.
+__device__ __forceinline__ double ell_gradt_sum(const int32_t* __restrict__ ekey,
+                                                const double* __restrict__ ecoef, int64_t n_ell,
+                                                int64_t nmk, const double* __restrict__ t,
+                                                int64_t idx, int L) {
+  double acc = 0.0;
+  int p = 0;
+  for (; p + 4 <= L; p += 4, idx += 128) {
+    int64_t k[4];
+    double c0[4], c1[4], c2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      k[u] = ekey[idx + 32 * u] >> 6;
+      c0[u] = ecoef[idx + 32 * u];
+      c1[u] = ecoef[n_ell + idx + 32 * u];
+      c2[u] = ecoef[2 * n_ell + idx + 32 * u];
+    }
+    double t0[4], t1[4], t2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      t0[u] = t[k[u]];
+      t1[u] = t[nmk + k[u]];
+      t2[u] = t[2 * nmk + k[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc = fma(c0[u], t0[u], acc);
+      acc = fma(c1[u], t1[u], acc);
+      acc = fma(c2[u], t2[u], acc);
+    }
+  }
+  for (; p < L; ++p, idx += 32) {
+    const int64_t k = ekey[idx] >> 6;
+    acc = fma(ecoef[idx], t[k], acc);
+    acc = fma(ecoef[n_ell + idx], t[nmk + k], acc);
+    acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
+  }
+  return acc;
+}
+
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace ibm

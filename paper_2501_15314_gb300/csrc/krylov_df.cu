@@ -162,15 +162,7 @@ __global__ void k_shell_gradt_ds(int64_t n_shell, const int32_t* __restrict__ sh
   if (q >= n_shell) return;
   const int64_t g = q >> 5;
   const int lane = (int)(q & 31);
-  const int32_t L = len[g];
-  int64_t idx = base[g] + lane;
-  double acc = 0.0;
-  for (int p = 0; p < L; ++p, idx += 32) {
-    const int64_t k = ekey[idx] >> 6;
-    acc = fma(ecoef[idx], t[k], acc);
-    acc = fma(ecoef[n_ell + idx], t[nmk + k], acc);
-    acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
-  }
+  const double acc = ell_gradt_sum(ekey, ecoef, n_ell, nmk, t, base[g] + lane, len[g]);
   const int64_t c = shell_cell[q];
   if constexpr (std::is_same<TW, float2>::value) {
     const float2 wc = wv[c];

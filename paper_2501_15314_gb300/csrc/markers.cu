@@ -13,6 +13,7 @@
 // deterministic and use no atomics.  The list is built once per marker set by
 // a counting sort (atomics only in the counting, followed by a per-segment
 // sort so that the final order does not depend on scheduling).
+#include "ds.cuh"
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -181,6 +182,12 @@ __device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcom
   return c;
 }
 
+// FP32 values widened to FP64 with integer operations (the conversion
+// instruction runs on the FP64 pipe, which this kernel also needs for its
+// FMAs); FP64 values pass through.
+__device__ __forceinline__ double widen(float x) { return f2d_exact(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // t[d][k] = scale * (R^T G v)_{k,d} using the tensor-product form of the
 // footprint: sum_a cw_d[a] sum_b w_e1[b] sum_c w_e2[c] v.  Four consecutive
 // threads hold a = 0..3 of one (marker, component) and combine in a fixed
@@ -213,7 +220,7 @@ __global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v
       for (int q2 = 0; q2 < 3; ++q2) {
         g[e2] = b2 + q2;
         const int64_t cell = g[0] + g[1] * sy + (int64_t)g[2] * sz;
-        acc2 = fma(mk.wc[(e2 * 3 + q2) * mk.n + k], (double)__ldg(v + cell), acc2);
+        acc2 = fma(mk.wc[(e2 * 3 + q2) * mk.n + k], widen(__ldg(v + cell)), acc2);
       }
       acc1 = fma(mk.wc[(e1 * 3 + q1) * mk.n + k], acc2, acc1);
     }
@@ -280,15 +287,7 @@ __global__ void k_shell_gradt(int64_t n_shell, const int32_t* __restrict__ shell
   if (q >= n_shell) return;
   const int64_t w = q >> 5;
   const int lane = (int)(q & 31);
-  const int32_t L = len[w];
-  int64_t idx = base[w] + lane;
-  double acc = 0.0;
-  for (int p = 0; p < L; ++p, idx += 32) {
-    const int64_t k = ekey[idx] >> 6;
-    acc = fma(ecoef[idx], t[k], acc);
-    acc = fma(ecoef[n_ell + idx], t[nmk + k], acc);
-    acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
-  }
+  const double acc = ell_gradt_sum(ekey, ecoef, n_ell, nmk, t, base[w] + lane, len[w]);
   const int64_t c = shell_cell[q];
   out[c] = fma(scale, acc, out[c]);
 }

@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     if (mode == 2) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (val[q] && !wallx[q] && !wally && !wallz) u[f64 + q] = fma(us, (double)out[q], u[f64 + q]);
+        if (val[q] && !wallx[q] && !wally && !wallz)
+          u[f64 + q] = fma(us, f2d_exact(out[q]), u[f64 + q]);   // widened without the FP64 pipe
     }
     ep = ec;
     ec = ez;
