@@ -342,6 +342,33 @@ __device__ __forceinline__ double ell_gradt_sum(const int32_t* __restrict__ ekey
   return acc;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while its predecessor in the stream is still finishing, and
+// pdl_wait() (first statement of such a kernel) blocks until that
+// predecessor has completed and its memory is visible; pdl_trigger() lets the
+// next kernel be scheduled once every block of this one has started.  This
+// hides the launch latency between the short dependent kernels of a V-cycle.
+// Without the launch attribute both instructions have no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);   // errors: last error
+}
+
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace ibm

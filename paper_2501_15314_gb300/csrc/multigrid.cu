@@ -348,6 +348,8 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
                                                       const float* __restrict__ b,
                                                       TO* __restrict__ xo, float w, float h2,
                                                       int zc) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x;
   const int i0 = 4 * (blockIdx.x * 32 + lane);
   const int j = blockIdx.y * VY + threadIdx.y;
@@ -410,6 +412,8 @@ __global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restri
                                                       float* __restrict__ bcopy,
                                                       float* __restrict__ xo, float w0h2,
                                                       float w1, float h2, int two, int zc) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float4 sb[VY + 2][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int i0 = 4 * (blockIdx.x * 32 + lane);
@@ -550,6 +554,8 @@ __global__ void __launch_bounds__(32 * VY) k_restrict_v4(Dims d, Dims dc,
                                                          const float* __restrict__ b,
                                                          float* __restrict__ bcoarse, float inv_h2,
                                                          int zcc) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x;
   const int i0 = 4 * (blockIdx.x * 32 + lane);
   const int J = blockIdx.y * VY + threadIdx.y;
@@ -625,6 +631,8 @@ __global__ void __launch_bounds__(32 * VY) k_prolong_v4(Dims d, Dims dc,
                                                         const float* __restrict__ xc,
                                                         float* __restrict__ x, int overwrite,
                                                         int zc) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x;
   const int q = blockIdx.x * 32 + lane;
   const int i0 = 4 * q;
@@ -739,6 +747,8 @@ __device__ void chain_smooth(const CoarseChain& ch, int l, float* x, float* t, c
 __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
                                                                 const float* __restrict__ b_in,
                                                                 float* __restrict__ x_out) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ float sm[];
   const int tot = ch.off[ch.nlev];
   float* xs = sm;
@@ -900,8 +910,8 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
   count_launch();
   if constexpr (std::is_same<T, float>::value) {
     if (vec)
-      k_first_v4<TB><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(
-          L.d, b, bcopy, x, (float)(w[0] * h2), (float)(two ? w[1] : 0.0), (float)h2, two, zc);
+      launch_pdl(k_first_v4<TB>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, b, bcopy, x,
+                 (float)(w[0] * h2), (float)(two ? w[1] : 0.0), (float)h2, two, zc);
   }
   if constexpr (!std::is_same<TB, float2>::value) {
     if (!vec)
@@ -916,8 +926,8 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
     count_launch();
     if constexpr (std::is_same<T, float>::value) {
       if (vec)
-        k_sweep_v4<float><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(L.d, cur, bb, nxt,
-                                                                      (float)w[q], (float)h2, zc);
+        launch_pdl(k_sweep_v4<float>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d,
+                   (const float*)cur, (const float*)bb, nxt, (float)w[q], (float)h2, zc);
     }
     if (!vec)
       k_sweep<T, T, T><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(L.d, cur, bb, nxt,
@@ -936,8 +946,8 @@ void sweep_step(ibm_ctx* c, int l, const T* src, const T* b, TO* dst, double w, 
   if constexpr (std::is_same<T, float>::value) {
     if (vec_ok(L.d)) {
       const int zc = vec_zc(L.d);
-      k_sweep_v4<TO><<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(L.d, src, b, dst, (float)w,
-                                                               (float)h2, zc);
+      launch_pdl(k_sweep_v4<TO>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, (const float*)src,
+                 (const float*)b, dst, (float)w, (float)h2, zc);
       return;
     }
   }
@@ -994,9 +1004,10 @@ void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cuda
   if constexpr (std::is_same<T, float>::value) {
     if (vec_ok(L.d)) {
       const int zcc = std::max(1, vec_zc(L.d) / 2);
-      k_restrict_v4<<<dim3(div_up(L.d.nx / 4, 32), div_up(C.d.ny, VY), div_up(C.d.nz, zcc)),
-                      dim3(32, VY), 0, s>>>(L.d, C.d, xin, b, cp.b, (float)(1.0 / (L.h * L.h)),
-                                            zcc);
+      launch_pdl(k_restrict_v4,
+                 dim3(div_up(L.d.nx / 4, 32), div_up(C.d.ny, VY), div_up(C.d.nz, zcc)),
+                 dim3(32, VY), 0, s, L.d, C.d, (const float*)xin, (const float*)b, cp.b,
+                 (float)(1.0 / (L.h * L.h)), zcc);
       done = true;
     }
   }
@@ -1009,8 +1020,8 @@ void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cuda
   if constexpr (std::is_same<T, float>::value) {
     if (vec_ok(L.d)) {
       const int zc = vec_zc(L.d);
-      k_prolong_v4<<<vec_grid(L.d, zc), dim3(32, VY), 0, s>>>(L.d, C.d, cp.x, x, pre > 0 ? 0 : 1,
-                                                              zc);
+      launch_pdl(k_prolong_v4, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, C.d,
+                 (const float*)cp.x, x, pre > 0 ? 0 : 1, zc);
       done = true;
     }
   }
@@ -1054,7 +1065,7 @@ bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post
     attr_set[dev] = true;
   }
   count_launch();
-  k_coarse_chain<<<1, kChainThreads, smem, s>>>(ch, b, x);
+  launch_pdl(k_coarse_chain, dim3(1), dim3(kChainThreads), smem, s, ch, b, x);
   return true;
 }
 

@@ -67,3 +67,13 @@ def config_case(index, secondary=False):
     c.U_gamma = W.U_gamma.ravel()
     c.f_body = W.f_body
     return c
+
+
+def wide_grid():
+    """160 x 24 x 40 cells: two 128-face blocks along x (the second one
+    ragged), ragged y and z tiles, one sphere of radius 0.03 at spacing h."""
+    h = 1.0 / 160
+    c = np.array([0.52, 0.075, 0.12])
+    X = wl.fibonacci_sphere(wl.markers_for_spacing(0.03, h), 0.03, c)
+    return Case("wide160x24x40", 160, 24, 40, h, X, None, c[None, :], Re=100.0, dt=0.004,
+                seed=4)

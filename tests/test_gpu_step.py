@@ -93,3 +93,22 @@ def test_solver_on_its_own_stream_orders_against_caller(cuda_device):
     for k in ("u", "p", "F"):
         assert rel(outs[1][k], outs[0][k]) < 1e-13, (k, rel(outs[1][k], outs[0][k]))
         assert np.linalg.norm(outs[0][k]) > 0
+
+
+def test_step_with_history_wide_grid(cuda_device):
+    """A grid wider than one 128-face block of the predictor kernels along
+    x (the second block ragged), with ragged y and z tiles: neighbours across
+    every block edge.  FP64 form against the oracle, every term of
+    Eq. (ustar) active."""
+    case = _with_inputs(gc.wide_grid())
+    g = case.grid()
+    rng = np.random.default_rng(9)
+    mask = g.interior_face_mask_packed()
+    u_n = 0.3 * rng.standard_normal(g.n_faces) * mask
+    u_nm1 = 0.3 * rng.standard_normal(g.n_faces) * mask
+    p_n = rng.standard_normal(g.m)
+    F_n = rng.standard_normal(3 * case.N)
+    ref, out, st = _run(case, u_n, u_nm1, p_n, F_n)
+    for k in ("u", "p", "F"):
+        assert rel(out[k], ref[k]) < 1e-10, (k, rel(out[k], ref[k]))
+    assert st["helm_iters"] >= 2, st
