@@ -268,6 +268,8 @@ __global__ void __launch_bounds__(RT) k_final_reduce_ds(const double* __restrict
                                                         const double* __restrict__ div,
                                                         double* __restrict__ quot,
                                                         float2* __restrict__ quot_ds) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.x;
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * kOutStride + q];
@@ -383,6 +385,8 @@ __global__ void __launch_bounds__(RT) k_multidot_sp4(const float4* __restrict__ 
                                                      const float4* __restrict__ V, int64_t ld4,
                                                      int nq, int64_t n4,
                                                      double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   Comp acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = {0.f, 0.f};
@@ -424,6 +428,8 @@ __global__ void __launch_bounds__(RT) k_axpy_norm_sp4(float4* __restrict__ w,
                                                       const float4* __restrict__ V, int64_t ld4,
                                                       int nq, const float2* __restrict__ coef,
                                                       int64_t n4, double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   float ch[NQ], cl[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -483,14 +489,15 @@ __global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ v,
   } while (0)
 
 // the float4 FP32 kernels, for nq <= 16
-#define IBM_NQ_DISPATCH_SP4(nq, KERNEL, ...)                                \
-  do {                                                                      \
-    count_launch();                                                         \
-    if ((nq) <= 2) KERNEL<2><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);        \
-    else if ((nq) <= 4) KERNEL<4><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
-    else if ((nq) <= 8) KERNEL<8><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);   \
-    else if ((nq) <= 12) KERNEL<12><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__); \
-    else KERNEL<16><<<kRedBlocks, RT, 0, s>>>(__VA_ARGS__);                 \
+#define IBM_NQ_DISPATCH_SP4(nq, KERNEL, ...)                                       \
+  do {                                                                             \
+    count_launch();                                                                \
+    const dim3 g_(kRedBlocks), b_(RT);                                             \
+    if ((nq) <= 2) launch_pdl(KERNEL<2>, g_, b_, 0, s, __VA_ARGS__);               \
+    else if ((nq) <= 4) launch_pdl(KERNEL<4>, g_, b_, 0, s, __VA_ARGS__);          \
+    else if ((nq) <= 8) launch_pdl(KERNEL<8>, g_, b_, 0, s, __VA_ARGS__);          \
+    else if ((nq) <= 12) launch_pdl(KERNEL<12>, g_, b_, 0, s, __VA_ARGS__);        \
+    else launch_pdl(KERNEL<16>, g_, b_, 0, s, __VA_ARGS__);                        \
   } while (0)
 
 int lap_zc(Dims d) {
@@ -669,7 +676,8 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       else
         IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
       count_launch();
-      k_final_reduce_ds<<<nq, RT, 0, s>>>(part, kRedBlocks, raw, nrm2, coef, coef_ds);
+      launch_pdl(k_final_reduce_ds, dim3(nq), dim3(RT), 0, s, (const double*)part, kRedBlocks,
+                 raw, (const double*)nrm2, coef, coef_ds);
       prof_end(c, ph, (single ? 4.0 : 8.0) * (nq + 1) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
       if (vec4 && nq <= 16)
@@ -680,8 +688,8 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       else
         IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);
       count_launch();
-      k_final_reduce_ds<<<1, RT, 0, s>>>(part, kRedBlocks, nrm2 + j + 1, nullptr, nullptr,
-                                          nullptr);
+      launch_pdl(k_final_reduce_ds, dim3(1), dim3(RT), 0, s, (const double*)part, kRedBlocks,
+                 nrm2 + j + 1, (const double*)nullptr, (double*)nullptr, (float2*)nullptr);
       // V_0..V_j and w read, w written (and its leading parts for the pair form)
       prof_end(c, ph, single ? 4.0 * (nq + 2) * (double)m : (8.0 * (nq + 2) + 4.0) * (double)m);
       IBM_LAUNCH_CHECK(c);

@@ -303,6 +303,8 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     const float* __restrict__ eo, float* __restrict__ r32, float* __restrict__ rlo,
     const double* __restrict__ r64, float rs_hi, float rs_lo, float a, float nu_h2, float alpha,
     float beta, float* __restrict__ en, double* __restrict__ u, double us, int mode) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.z / zchunks;
   const int zc = blockIdx.z - c * zchunks;
   const int lane = threadIdx.x;
@@ -580,9 +582,9 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float
   const FaceGeom32 p = make_face_geom32(d);
   const float rs_hi = (float)rs, rs_lo = (float)(rs - (double)rs_hi);
   count_launch();
-  k_helm_cheb_v4<<<helm_v4_grid(d), dim3(32, HVY), 0, s>>>(
-      make_face_geom(d), p, helm_zchunks(d), e, eo, r32, rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha,
-      beta, en, u, us, mode);
+  launch_pdl(k_helm_cheb_v4, helm_v4_grid(d), dim3(32, HVY), 0, s, make_face_geom(d), p,
+             helm_zchunks(d), e, eo, r32, rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us,
+             mode);
 }
 
 int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, double a,
