@@ -89,10 +89,10 @@ ibm_status ibm_adjoint_step(ibm_ctx* c, const double* u_np1, const double* F_n,
   const double inv_h = 1.0 / c->h;
 
   // lambda = S~^+ (2 B^T F_bar): the transposed (= same) Schur solve
-  IBM_CUDA(c, cudaMemsetAsync(c->c2, 0, sizeof(double) * c->m, str));
+  launch_zero(c->c2, sizeof(double) * c->m, str);
   launch_shell_gradt_spread(c, F_bar, 2.0, c->c2);
   double* lam = c->c3;
-  IBM_CUDA(c, cudaMemsetAsync(lam, 0, sizeof(double) * c->m, str));
+  launch_zero(lam, sizeof(double) * c->m, str);
   IBM_LAUNCH_CHECK(c);
   s = fgmres_solve(c, c->c2, lam, o, st, true);
   if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) { prof_end(c, ph); return s; }
@@ -105,7 +105,7 @@ ibm_status ibm_adjoint_step(ibm_ctx* c, const double* u_np1, const double* F_n,
   if (F_n)
     launch_axpby(F_np1, 1.0, F_n, -1.0, mk.t, 3 * n, str);
   else
-    IBM_CUDA(c, cudaMemcpyAsync(mk.t, F_np1, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, str));
+    launch_copy(mk.t, F_np1, sizeof(double) * 3 * n, str);
 
   // X_bar = (R F' - a u^{n+1})^T dR (U_bar / a)
   launch_axpby(u_np1, -a, u_np1, 0.0, c->f1, c->nf, str);

@@ -141,10 +141,9 @@ ibm_status ensure_krylov(ibm_ctx* c, int restart) {
 }
 
 ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out) {
-  launch_dot(x, x, n, c->red_part, c->red_out + 7 * (kMaxRestart + 2), c->stream);
+  launch_dot(x, x, n, c->red_part, c->red_out + 7 * (kMaxRestart + 2), c->stream,
+             c->host_red_dev);
   IBM_LAUNCH_CHECK(c);
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, c->red_out + 7 * (kMaxRestart + 2),
-                              sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   IBM_CUDA(c, cudaStreamSynchronize(c->stream));
   *out = std::sqrt(c->host_red[0]);
   return IBM_OK;
@@ -204,7 +203,7 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   ibm_status st = norm2_host(c, rhs, nf, &rnorm0);
   if (st != IBM_OK) return st;
   if (!std::isfinite(rnorm0)) return set_err(c, IBM_ERR_NAN, "non-finite predictor RHS");
-  IBM_CUDA(c, cudaMemsetAsync(u, 0, sizeof(double) * nf, s));
+  launch_zero(u, sizeof(double) * nf, s);
   *iters = 0;
   *relres = 0.0;
   if (rnorm0 == 0.0) return IBM_OK;
@@ -217,9 +216,8 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
       // (g1, g5) = r^ - A e_K; ||r_new|| = ||r|| * ||r^ - A e_K||
       const int64_t nb = launch_helm_resid_ds(c->d, eK, c->g1, c->g5, a, nu_h2, c->helm_part,
                                               kMaxRestart + 2, s);
-      launch_final_reduce(c->helm_part, (int)nb, sdev, s);
+      launch_final_reduce(c->helm_part, (int)nb, sdev, s, c->host_red_dev);
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaMemcpyAsync(c->host_red, sdev, sizeof(double), cudaMemcpyDeviceToHost, s));
       IBM_CUDA(c, cudaStreamSynchronize(s));
       qn = std::sqrt(c->host_red[0]);
       rn *= qn;
@@ -236,7 +234,7 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
     float* eo = c->g2;
     float* e = c->g3;
     float* en = c->g4;
-    IBM_CUDA(c, cudaMemsetAsync(eo, 0, sizeof(float) * helm_fp32_size(c->d), s));
+    launch_zero(eo, sizeof(float) * helm_fp32_size(c->d), s);
     // r^ = r / ||r||: from the FP64 right-hand side first, then from the pair
     launch_helm_cheb(c->d, nullptr, nullptr, c->g1, c->g5, it == 0 ? rhs : nullptr, 1.0 / qn,
                      (float)a, (float)nu_h2, (float)(1.0 / theta), 0.f, e, nullptr, 0.0, 0, s);
@@ -310,7 +308,9 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
             cudaMalloc(&c->cell_flag, sizeof(int32_t) * (m + 1)) == cudaSuccess &&
             cudaMalloc(&c->scan_tmp, sizeof(int32_t) * nscan) == cudaSuccess &&
             cudaMalloc(&c->dev_flag, sizeof(int32_t) * 4) == cudaSuccess &&
-            cudaMallocHost(&c->host_flag, sizeof(int32_t) * 4) == cudaSuccess &&
+            cudaHostAlloc(&c->host_flag, sizeof(int32_t) * 4, cudaHostAllocMapped) ==
+                cudaSuccess &&
+            cudaHostGetDevicePointer(&c->host_flag_dev, c->host_flag, 0) == cudaSuccess &&
             cudaMalloc(&c->c1, sizeof(double) * m) == cudaSuccess &&
             cudaMalloc(&c->c2, sizeof(double) * m) == cudaSuccess &&
             cudaMalloc(&c->c3, sizeof(double) * (m + 1)) == cudaSuccess &&
@@ -327,7 +327,9 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
                 cudaSuccess &&
             cudaMalloc(&c->red_out, sizeof(double) * 8 * (kMaxRestart + 2)) ==
                 cudaSuccess &&
-            cudaMallocHost(&c->host_red, sizeof(double) * 8 * (kMaxRestart + 2)) == cudaSuccess &&
+            cudaHostAlloc(&c->host_red, sizeof(double) * 8 * (kMaxRestart + 2),
+                          cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer(&c->host_red_dev, c->host_red, 0) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
@@ -432,7 +434,7 @@ ibm_status ibm_interp(ibm_ctx* c, const double* u, double* U) {
 ibm_status ibm_spread(ibm_ctx* c, const double* F, double* u) {
   if (check_ctx(c) != IBM_OK) return IBM_ERR_ARG;
   if (bad_ptr(u) || (c->mk.n > 0 && bad_ptr(F))) return set_err(c, IBM_ERR_ARG, "bad F/u");
-  IBM_CUDA(c, cudaMemsetAsync(u, 0, sizeof(double) * c->nf, c->stream));
+  launch_zero(u, sizeof(double) * c->nf, c->stream);
   launch_shell_spread_faces(c, F, 1.0, u);
   IBM_LAUNCH_CHECK(c);
   return IBM_OK;
@@ -523,7 +525,7 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
 
   // 2. RHS_p = a G^T u*, RHS_F = a (R^T u* - U), b = RHS_p + 2 B^T RHS_F
   launch_gradt_axpby(c->d, u_star, a * inv_h, nullptr, 0.0, c->c1, str);
-  IBM_CUDA(c, cudaMemcpyAsync(c->c2, c->c1, sizeof(double) * c->m, cudaMemcpyDeviceToDevice, str));
+  launch_copy(c->c2, c->c1, sizeof(double) * c->m, str);
   if (n > 0) {
     launch_interp(c, u_star, mk.t2);
     count_launch();
@@ -532,8 +534,7 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
       launch_shell_gradt_spread(c, mk.t2, 2.0, c->c2);
     } else {
       // RHS_F kept in t3 (the Schur products use t and t2); b = RHS_p +- B^T C^{-1} RHS_F
-      IBM_CUDA(c, cudaMemcpyAsync(mk.t3, mk.t2, sizeof(double) * 3 * n,
-                                  cudaMemcpyDeviceToDevice, str));
+      launch_copy(mk.t3, mk.t2, sizeof(double) * 3 * n, str);
       if ((s = c_solve(c, mk.t3, mk.t2, c->c_rtol, c->c_maxit, nullptr)) != IBM_OK) return s;
       launch_shell_gradt_spread(c, mk.t2, csign, c->c2);
     }
@@ -542,7 +543,7 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
 
   // 3. Schur solve for p' (into c3, zero initial guess)
   double* pc = c->c3;
-  IBM_CUDA(c, cudaMemsetAsync(pc, 0, sizeof(double) * c->m, str));
+  launch_zero(pc, sizeof(double) * c->m, str);
   ph = prof_begin(c, IBM_PROF_SOLVE);
   s = fgmres_solve(c, c->c2, pc, o, st, true);
   prof_end(c, ph);

@@ -81,12 +81,11 @@ ibm_status c_solve(ibm_ctx* c, const double* t, double* s, double rtol, int maxi
   double* p = mk.cg + n;
   double* q = mk.cg + 2 * n;
   double* sc = c->cg_scal;   // [0] rr, [1] <p, q>, [2] alpha, [3] rr_new
-  IBM_CUDA(c, cudaMemsetAsync(s, 0, sizeof(double) * n, str));
-  IBM_CUDA(c, cudaMemcpyAsync(r, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, str));
-  IBM_CUDA(c, cudaMemcpyAsync(p, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, str));
-  launch_dot(t, t, n, c->red_part, sc, str);
+  launch_zero(s, sizeof(double) * n, str);
+  launch_copy(r, t, sizeof(double) * n, str);
+  launch_copy(p, t, sizeof(double) * n, str);
+  launch_dot(t, t, n, c->red_part, sc, str, c->host_red_dev);
   IBM_LAUNCH_CHECK(c);
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, sc, sizeof(double), cudaMemcpyDeviceToHost, str));
   IBM_CUDA(c, cudaStreamSynchronize(str));
   const double tt = c->host_red[0];
   if (!std::isfinite(tt)) return set_err(c, IBM_ERR_NAN, "non-finite right-hand side of C s = t");
@@ -109,8 +108,8 @@ ibm_status c_solve(ibm_ctx* c, const double* t, double* s, double rtol, int maxi
     k_copy_scalar<<<1, 1, 0, str>>>(sc + 3, sc);
     ++it;
     if (it % kCheck == 0 || it == maxit) {
+      launch_to_host(sc, c->host_red_dev, sizeof(double), str);
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaMemcpyAsync(c->host_red, sc, sizeof(double), cudaMemcpyDeviceToHost, str));
       IBM_CUDA(c, cudaStreamSynchronize(str));
       rr = c->host_red[0];
       if (!std::isfinite(rr)) return set_err(c, IBM_ERR_NAN, "non-finite CG residual on C");

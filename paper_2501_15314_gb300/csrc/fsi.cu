@@ -307,13 +307,13 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
   }
   IBM_CUDA(c, cudaMemcpyAsync(d_par, pose.data(), sizeof(double) * pose.size(),
                               cudaMemcpyHostToDevice, str));
-  IBM_CUDA(c, cudaMemsetAsync(c->dev_flag, 0, sizeof(int32_t), str));
+  launch_zero(c->dev_flag, sizeof(int32_t), str);
   count_launch();
   k_rigid_positions<<<div_up(n, TPB), TPB, 0, str>>>(n, L0, body_id, d_par, nb, X_np1,
                                                      c->dev_flag);
   IBM_LAUNCH_CHECK(c);
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->dev_flag, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                              str));
+  launch_to_host(c->dev_flag, c->host_flag_dev, sizeof(int32_t), str);
+  IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(str));
   if (c->host_flag[0]) { prof_end(c, ph); return set_err(c, IBM_ERR_ARG, "body_id out of range"); }
   if ((s = ibm_set_markers(c, n, X_np1)) != IBM_OK) { prof_end(c, ph); return s; }
@@ -376,8 +376,8 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
   IBM_LAUNCH_CHECK(c);
   s = helmholtz_solve(c, c->f1, u_np1, o, &fst->helm_iters, &fst->helm_relres);
   if (s != IBM_OK) { prof_end(c, ph); return s; }
-  IBM_CUDA(c, cudaMemcpyAsync(p_np1, p_n, sizeof(double) * c->m, cudaMemcpyDeviceToDevice, str));
-  IBM_CUDA(c, cudaMemcpyAsync(F_np1, F_n, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, str));
+  launch_copy(p_np1, p_n, sizeof(double) * c->m, str);
+  launch_copy(F_np1, F_n, sizeof(double) * 3 * n, str);
 
   // ---- Step 3: corrections ----
   std::vector<double> lin, ang, vel(9 * nb), loads((size_t)6 * kLoadBlocks * nb),
@@ -425,7 +425,7 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
     launch_interp(c, u_np1, mk.t2);
     launch_axpby(mk.t2, a, Ugam, -a, mk.t2, 3 * n, str);
     launch_shell_gradt_spread(c, mk.t2, 2.0, c->c2);
-    IBM_CUDA(c, cudaMemsetAsync(pc, 0, sizeof(double) * c->m, str));
+    launch_zero(pc, sizeof(double) * c->m, str);
     IBM_LAUNCH_CHECK(c);
     ibm_solve_stats sst;
     memset(&sst, 0, sizeof(sst));

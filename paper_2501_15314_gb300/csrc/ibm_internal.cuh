@@ -107,7 +107,8 @@ struct ibm_ctx {
   int32_t* cell_flag = nullptr;    // [m + 1]
   int32_t* scan_tmp = nullptr;     // block sums of the scans
   int32_t* dev_flag = nullptr;     // device error word(s)
-  int32_t* host_flag = nullptr;    // pinned mirror
+  int32_t* host_flag = nullptr;    // mapped pinned mirror (host address)
+  int32_t* host_flag_dev = nullptr; // its device address
   double* c1 = nullptr;            // [m] cell temporaries
   double* c2 = nullptr;
   double* c3 = nullptr;
@@ -122,7 +123,8 @@ struct ibm_ctx {
   float* g5 = nullptr;             // low parts of the predictor's residual
   double* red_part = nullptr;      // [kRedBlocks][kMaxRestart + 2] partials
   double* red_out = nullptr;       // [8][kMaxRestart + 2] reduced values
-  double* host_red = nullptr;      // pinned mirror of red_out
+  double* host_red = nullptr;      // mapped pinned mirror of red_out (host address)
+  double* host_red_dev = nullptr;  // its device address
   double* helm_part = nullptr;     // per-block partials of the predictor norm
 
   // Krylov bases
@@ -243,22 +245,35 @@ void set_cmode(ibm_ctx* c, const ibm_solve_opts* o);
 // ---- reductions and vector kernels (krylov.cu) ----
 // red_out[q] = <w, V_q>, q < nq (two-stage, fixed order)
 // (with div != null also quot[q] = out[q] / div[q])
+// (with hout != null, the device address of a place in the mapped host
+// mirror, the reduced values are also written there: the host reads them
+// after synchronising the stream, with no copy-engine transfer that bulk
+// copies queued by the caller on other streams could hold up)
 void launch_multidot(const double* w, const double* V, int64_t ld, int nq, int64_t n,
                      double* part, double* out, cudaStream_t s, const double* div = nullptr,
-                     double* quot = nullptr);
+                     double* quot = nullptr, double* hout = nullptr);
 // w -= sum_q coef[q] V_q  (coef on device), out = ||w||^2 (two-stage)
 void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const double* coef,
-                      int64_t n, double* part, double* out, cudaStream_t s);
+                      int64_t n, double* part, double* out, cudaStream_t s,
+                      double* hout = nullptr);
 void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out,
-                cudaStream_t s);
+                cudaStream_t s, double* hout = nullptr);
+// zero nbytes / copy nbytes device to device (multiples of 4), by kernels
+void launch_zero(void* p, int64_t nbytes, cudaStream_t s);
+void launch_copy(void* dst, const void* src, int64_t nbytes, cudaStream_t s);
+// nbytes (a multiple of 4) from device memory to dst_dev, the device address
+// of a place in a mapped host mirror (host_red_dev, host_flag_dev)
+void launch_to_host(const void* src, void* dst_dev, int nbytes, cudaStream_t s);
 void launch_scale(double* x, int64_t n, const double* inv, double scale, cudaStream_t s);
 void launch_scale_to(const double* x, int64_t n, double a, double* y, cudaStream_t s);
 void launch_axpby(const double* x, double a, const double* y, double b, double* out,
                   int64_t n, cudaStream_t s);
+// x += sum_q y[q] Z_q, y = the first nq host values (passed by value)
 void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const double* y,
                      int64_t n, cudaStream_t s);
 // out[0] = sum of part[b * (kMaxRestart + 2)], b < nb (fixed order)
-void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s);
+void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s,
+                         double* hout = nullptr);
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s);
 void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
                            cudaStream_t s);
@@ -370,5 +385,20 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Solution coefficients of one FGMRES cycle, passed to the update kernel by
+// value (kernel parameters need no host-to-device copy).
+struct CoefF64 {
+  double v[kMaxRestart + 1];
+};
+struct CoefDS {
+  float2 v[kMaxRestart + 1];
+};
+
+// Device address of a place in the mapped host mirror host_red (kernels write
+// small results there; the host reads them after synchronising the stream).
+inline double* hmirror(ibm_ctx* c, const double* hp) {
+  return c->host_red_dev + (hp - c->host_red);
+}
 
 }  // namespace ibm

@@ -88,11 +88,13 @@ __global__ void __launch_bounds__(RT) k_axpy_norm(double* __restrict__ w,
 }
 
 // out[q] = sum_b part[b][q], fixed-order tree (one block per q); with div
-// != null also quot[q] = out[q] / div[q]
+// != null also quot[q] = out[q] / div[q]; with hout != null also hout[q] =
+// out[q] (the device address of the mapped host mirror)
 __global__ void __launch_bounds__(RT) k_final_reduce(const double* __restrict__ part, int nb,
                                                      double* __restrict__ out,
                                                      const double* __restrict__ div = nullptr,
-                                                     double* __restrict__ quot = nullptr) {
+                                                     double* __restrict__ quot = nullptr,
+                                                     double* hout = nullptr) {
   const int q = blockIdx.x;
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * kOutStride + q];
@@ -105,7 +107,29 @@ __global__ void __launch_bounds__(RT) k_final_reduce(const double* __restrict__ 
     for (int w = 0; w < RT / 32; ++w) t += sh[w];
     out[q] = t;
     if (div) quot[q] = t / div[q];
+    if (hout) hout[q] = t;
   }
+}
+
+// Zeroing and device-to-device copies by kernels, so that the copy engines
+// serve only the caller's transfers: 16-byte words where both ends allow it,
+// else 4-byte words.
+template <typename W>
+__global__ void k_zero_words(W* __restrict__ p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = W{};
+}
+template <typename W>
+__global__ void k_copy_words(W* __restrict__ dst, const W* __restrict__ src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// n 32-bit words from device memory to the mapped host mirror
+__global__ void k_to_host(const uint32_t* __restrict__ src, uint32_t* dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
 __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
@@ -139,14 +163,14 @@ __global__ void k_axpby(const double* __restrict__ x, double a, const double* __
     out[i] = fma(a, x[i], b * y[i]);
 }
 
-// x += sum_q y[q] Z_q  (y on device)
+// x += sum_q y[q] Z_q  (y by value)
 template <int NQ>
 __global__ void __launch_bounds__(RT) k_gemv_acc(double* __restrict__ x,
                                                  const double* __restrict__ Z, int64_t ld, int nq,
-                                                 const double* __restrict__ y, int64_t n) {
+                                                 const CoefF64 y, int64_t n) {
   double cf[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) cf[q] = q < nq ? y[q] : 0.0;
+  for (int q = 0; q < NQ; ++q) cf[q] = q < nq ? y.v[q] : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
     double xi = x[i];
 #pragma unroll
@@ -182,30 +206,67 @@ __global__ void k_add_scalar(double* __restrict__ x, int64_t n, const double* __
 
 void launch_multidot(const double* w, const double* V, int64_t ld, int nq, int64_t n,
                      double* part, double* out, cudaStream_t s, const double* div,
-                     double* quot) {
+                     double* quot, double* hout) {
   IBM_NQ_DISPATCH(nq, k_multidot, w, V, ld, nq, n, part);
   count_launch();
-  k_final_reduce<<<nq, RT, 0, s>>>(part, kRedBlocks, out, div, quot);
+  k_final_reduce<<<nq, RT, 0, s>>>(part, kRedBlocks, out, div, quot, hout);
 }
 
 void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const double* coef,
-                      int64_t n, double* part, double* out, cudaStream_t s) {
+                      int64_t n, double* part, double* out, cudaStream_t s, double* hout) {
   IBM_NQ_DISPATCH(nq, k_axpy_norm, w, V, ld, nq, coef, n, part);
   count_launch();
-  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out);
+  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out, nullptr, nullptr, hout);
 }
 
-void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s) {
+void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s,
+                         double* hout) {
   count_launch();
-  k_final_reduce<<<1, RT, 0, s>>>(part, nb, out);
+  k_final_reduce<<<1, RT, 0, s>>>(part, nb, out, nullptr, nullptr, hout);
 }
 
 void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out,
-                cudaStream_t s) {
+                cudaStream_t s, double* hout) {
   count_launch();
   k_dot<<<kRedBlocks, RT, 0, s>>>(a, b, n, part);
   count_launch();
-  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out);
+  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out, nullptr, nullptr, hout);
+}
+
+namespace {
+int word_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 4 * kRedBlocks ? 4 * kRedBlocks : b));
+}
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+}  // namespace
+
+void launch_zero(void* p, int64_t nbytes, cudaStream_t s) {
+  if (nbytes <= 0) return;
+  count_launch();
+  if (al16(p) && nbytes % 16 == 0)
+    k_zero_words<uint4><<<word_blocks(nbytes / 16), 256, 0, s>>>(static_cast<uint4*>(p),
+                                                                 nbytes / 16);
+  else
+    k_zero_words<uint32_t><<<word_blocks(nbytes / 4), 256, 0, s>>>(static_cast<uint32_t*>(p),
+                                                                   nbytes / 4);
+}
+
+void launch_copy(void* dst, const void* src, int64_t nbytes, cudaStream_t s) {
+  if (nbytes <= 0) return;
+  count_launch();
+  if (al16(dst) && al16(src) && nbytes % 16 == 0)
+    k_copy_words<uint4><<<word_blocks(nbytes / 16), 256, 0, s>>>(
+        static_cast<uint4*>(dst), static_cast<const uint4*>(src), nbytes / 16);
+  else
+    k_copy_words<uint32_t><<<word_blocks(nbytes / 4), 256, 0, s>>>(
+        static_cast<uint32_t*>(dst), static_cast<const uint32_t*>(src), nbytes / 4);
+}
+
+void launch_to_host(const void* src, void* dst_dev, int nbytes, cudaStream_t s) {
+  count_launch();
+  k_to_host<<<1, 64, 0, s>>>(static_cast<const uint32_t*>(src), static_cast<uint32_t*>(dst_dev),
+                             nbytes / 4);
 }
 
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s) {
@@ -230,7 +291,9 @@ void launch_axpby(const double* x, double a, const double* y, double b, double* 
 
 void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const double* y, int64_t n,
                      cudaStream_t s) {
-  IBM_NQ_DISPATCH(nq, k_gemv_acc, x, Z, ld, nq, y, n);
+  CoefF64 cy;
+  for (int q = 0; q <= kMaxRestart; ++q) cy.v[q] = q < nq ? y[q] : 0.0;
+  IBM_NQ_DISPATCH(nq, k_gemv_acc, x, Z, ld, nq, cy, n);
 }
 
 void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
@@ -272,8 +335,8 @@ ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
 namespace {
 
 ibm_status fetch(ibm_ctx* c, const double* dev, int n) {
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, dev, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                              c->stream));
+  launch_to_host(dev, c->host_red_dev, (int)sizeof(double) * n, c->stream);
+  IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return IBM_OK;
 }
@@ -300,7 +363,6 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   double* raw2 = c->red_out + 2 * kOutStride;    // second Gram-Schmidt pass
   double* coef2 = c->red_out + 3 * kOutStride;
   double* nrm2 = c->red_out + 4 * kOutStride;    // ||V_i||^2
-  double* ydev = c->red_out + 5 * kOutStride;    // solution coefficients
   double* sdev = c->red_out + 6 * kOutStride;    // scalars
   double* hr = c->host_red;                      // host mirror (same offsets)
   ibm_status stt;
@@ -314,7 +376,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   int total = 0, cycles = 0;
   double relres = 0.0;
   if (bnorm == 0.0) {
-    IBM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * m, s));
+    launch_zero(x, sizeof(double) * m, s);
     if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; }
     return IBM_OK;
   }
@@ -330,8 +392,8 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
     // V_0 = r0 = b - S x, nrm2[0] = ||r0||^2 (r0 = b for a zero first guess)
     double beta;
     if (first && x_is_zero) {
-      IBM_CUDA(c, cudaMemcpyAsync(V, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-      IBM_CUDA(c, cudaMemcpyAsync(nrm2, sdev, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      launch_copy(V, b, sizeof(double) * m, s);
+      launch_copy(nrm2, sdev, sizeof(double), s);
       beta = bnorm;
     } else {
       if ((stt = schur_apply(c, x, V)) != IBM_OK) return stt;
@@ -361,22 +423,19 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
       prof_end(c, ph);
       if ((stt = schur_apply(c, zj, w)) != IBM_OK) return stt;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
-      launch_multidot(w, V, m, j + 1, m, part, raw, s, nrm2, coef);
+      launch_multidot(w, V, m, j + 1, m, part, raw, s, nrm2, coef, hmirror(c, hr));
       prof_end(c, ph, 8.0 * (j + 2) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
-      launch_axpy_norm(w, V, m, j + 1, coef, m, part, nrm2 + j + 1, s);
+      launch_axpy_norm(w, V, m, j + 1, coef, m, part, nrm2 + j + 1, s,
+                       hmirror(c, hr + 4 * kOutStride + j + 1));
       prof_end(c, ph, 8.0 * (j + 3) * (double)m);
       if (o->reorth) {
-        launch_multidot(w, V, m, j + 1, m, part, raw2, s, nrm2, coef2);
-        launch_axpy_norm(w, V, m, j + 1, coef2, m, part, nrm2 + j + 1, s);
+        launch_multidot(w, V, m, j + 1, m, part, raw2, s, nrm2, coef2,
+                        hmirror(c, hr + 2 * kOutStride));
+        launch_axpy_norm(w, V, m, j + 1, coef2, m, part, nrm2 + j + 1, s,
+                         hmirror(c, hr + 4 * kOutStride + j + 1));
       }
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaMemcpyAsync(hr, raw, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
-      IBM_CUDA(c, cudaMemcpyAsync(hr + 4 * kOutStride + j + 1, nrm2 + j + 1, sizeof(double),
-                                  cudaMemcpyDeviceToHost, s));
-      if (o->reorth)
-        IBM_CUDA(c, cudaMemcpyAsync(hr + 2 * kOutStride, raw2, sizeof(double) * (j + 1),
-                                    cudaMemcpyDeviceToHost, s));
       IBM_CUDA(c, cudaStreamSynchronize(s));
       for (int i = 0; i <= j; ++i)
         Hm(i, j) = (hr[i] + (o->reorth ? hr[2 * kOutStride + i] : 0.0)) / rn[i];
@@ -408,10 +467,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
         for (int q = i + 1; q < jused; ++q) acc -= Hm(i, q) * y[q];
         y[i] = acc / Hm(i, i);
       }
-      double* hy = hr + 5 * kOutStride;
-      for (int i = 0; i < jused; ++i) hy[i] = y[i];
-      IBM_CUDA(c, cudaMemcpyAsync(ydev, hy, sizeof(double) * jused, cudaMemcpyHostToDevice, s));
-      launch_gemv_acc(x, Z, m, jused, ydev, m, s);
+      launch_gemv_acc(x, Z, m, jused, y.data(), m, s);
       IBM_LAUNCH_CHECK(c);
     }
     ++cycles;

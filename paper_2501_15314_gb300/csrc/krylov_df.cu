@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(RT) k_final_reduce_ds(const double* __restrict
                                                         double* __restrict__ out,
                                                         const double* __restrict__ div,
                                                         double* __restrict__ quot,
-                                                        float2* __restrict__ quot_ds) {
+                                                        float2* __restrict__ quot_ds,
+                                                        double* hout) {
   pdl_wait();
   pdl_trigger();
   const int q = blockIdx.x;
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(RT) k_final_reduce_ds(const double* __restrict
     double t = 0.0;
     for (int w = 0; w < RT / 32; ++w) t += sh[w];
     out[q] = t;
+    if (hout) hout[q] = t;   // mapped host mirror
     if (div) {
       const double qv = t / div[q];
       quot[q] = qv;
@@ -296,11 +298,11 @@ __global__ void __launch_bounds__(RT) k_final_reduce_ds(const double* __restrict
 template <int NQ>
 __global__ void __launch_bounds__(RT) k_gemv_ds(double* __restrict__ x,
                                                 const float* __restrict__ Z, int64_t ld, int nq,
-                                                const float2* __restrict__ y, int64_t n) {
+                                                const CoefDS y, int64_t n) {
   float yh[NQ], yl[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const float2 v = q < nq ? y[q] : make_float2(0.f, 0.f);
+    const float2 v = q < nq ? y.v[q] : make_float2(0.f, 0.f);
     yh[q] = v.x;
     yl[q] = v.y;
   }
@@ -508,8 +510,8 @@ int lap_zc(Dims d) {
 }
 
 ibm_status fetch(ibm_ctx* c, const double* dev, int n) {
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_red, dev, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                              c->stream));
+  launch_to_host(dev, c->host_red_dev, (int)sizeof(double) * n, c->stream);
+  IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return IBM_OK;
 }
@@ -591,7 +593,6 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   double* coef = c->red_out + kOutStride;
   float2* coef_ds = reinterpret_cast<float2*>(c->red_out + 2 * kOutStride);
   double* nrm2 = c->red_out + 4 * kOutStride;
-  float2* y_ds = reinterpret_cast<float2*>(c->red_out + 5 * kOutStride);
   double* sdev = c->red_out + 6 * kOutStride;
   double* hr = c->host_red;
   float2* V2 = reinterpret_cast<float2*>(c->V);
@@ -611,7 +612,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   int total = 0, cycles = 0;
   double relres = 0.0;
   if (bnorm == 0.0) {
-    IBM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * m, s));
+    launch_zero(x, sizeof(double) * m, s);
     if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; }
     return IBM_OK;
   }
@@ -625,7 +626,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     double beta;
     const double* r0 = b;
     if (first && x_is_zero) {
-      IBM_CUDA(c, cudaMemcpyAsync(nrm2, sdev, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      launch_copy(nrm2, sdev, sizeof(double), s);
       beta = bnorm;
     } else {
       if ((stt = schur_apply(c, x, r64)) != IBM_OK) return stt;
@@ -677,7 +678,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
       count_launch();
       launch_pdl(k_final_reduce_ds, dim3(nq), dim3(RT), 0, s, (const double*)part, kRedBlocks,
-                 raw, (const double*)nrm2, coef, coef_ds);
+                 raw, (const double*)nrm2, coef, coef_ds, hmirror(c, hr));
       prof_end(c, ph, (single ? 4.0 : 8.0) * (nq + 1) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
       if (vec4 && nq <= 16)
@@ -689,13 +690,11 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);
       count_launch();
       launch_pdl(k_final_reduce_ds, dim3(1), dim3(RT), 0, s, (const double*)part, kRedBlocks,
-                 nrm2 + j + 1, (const double*)nullptr, (double*)nullptr, (float2*)nullptr);
+                 nrm2 + j + 1, (const double*)nullptr, (double*)nullptr, (float2*)nullptr,
+                 hmirror(c, hr + 4 * kOutStride + j + 1));
       // V_0..V_j and w read, w written (and its leading parts for the pair form)
       prof_end(c, ph, single ? 4.0 * (nq + 2) * (double)m : (8.0 * (nq + 2) + 4.0) * (double)m);
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaMemcpyAsync(hr, raw, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
-      IBM_CUDA(c, cudaMemcpyAsync(hr + 4 * kOutStride + j + 1, nrm2 + j + 1, sizeof(double),
-                                  cudaMemcpyDeviceToHost, s));
       IBM_CUDA(c, cudaStreamSynchronize(s));
       for (int i = 0; i <= j; ++i) Hm(i, j) = hr[i] / rn[i];
       const double hn = std::sqrt(hr[4 * kOutStride + j + 1]);
@@ -727,14 +726,13 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         for (int q = i + 1; q < jused; ++q) acc -= Hm(i, q) * y[q];
         y[i] = acc / Hm(i, i);
       }
-      float* hy = reinterpret_cast<float*>(hr + 5 * kOutStride);
-      for (int i = 0; i < jused; ++i) {
-        const float yh = (float)y[i];
-        hy[2 * i] = yh;
-        hy[2 * i + 1] = (float)(y[i] - (double)yh);
+      CoefDS cy;
+      for (int i = 0; i <= kMaxRestart; ++i) {
+        const double yi = i < jused ? y[i] : 0.0;
+        const float yh = (float)yi;
+        cy.v[i] = make_float2(yh, (float)(yi - (double)yh));
       }
-      IBM_CUDA(c, cudaMemcpyAsync(y_ds, hy, sizeof(float2) * jused, cudaMemcpyHostToDevice, s));
-      IBM_NQ_DISPATCH_DS(jused, k_gemv_ds, x, Zf, m, jused, y_ds, m);
+      IBM_NQ_DISPATCH_DS(jused, k_gemv_ds, x, Zf, m, jused, cy, m);
       IBM_LAUNCH_CHECK(c);
     }
     ++cycles;

@@ -455,7 +455,7 @@ __global__ void k_scan_add(int32_t* out, int64_t n, const int32_t* __restrict__ 
 ibm_status exclusive_scan(ibm_ctx* c, const int32_t* in, int32_t* out, int64_t n) {
   const int64_t nb = (n + SCAN_T * SCAN_E - 1) / (SCAN_T * SCAN_E);
   if (nb == 0) {
-    IBM_CUDA(c, cudaMemsetAsync(out, 0, sizeof(int32_t), c->stream));
+    launch_zero(out, sizeof(int32_t), c->stream);
     return IBM_OK;
   }
   int32_t* sums = c->scan_tmp;
@@ -549,12 +549,13 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   ibm_status st = grow_markers(c, n);
   if (st != IBM_OK) return st;
   cudaStream_t s = c->stream;
-  IBM_CUDA(c, cudaMemsetAsync(c->dev_flag, 0, sizeof(int32_t), s));
+  launch_zero(c->dev_flag, sizeof(int32_t), s);
   count_launch();
   k_marker_setup<<<div_up(n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org, m.wf,
                                                  m.wc, m.cw, m.dwf, m.dwc, c->dev_flag);
   IBM_LAUNCH_CHECK(c);
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->dev_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  launch_to_host(c->dev_flag, c->host_flag_dev, sizeof(int32_t), s);
+  IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(s));
   if (c->host_flag[0] != 0)
     return set_err(c, IBM_ERR_MARKER_DOMAIN,
@@ -562,7 +563,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   m.n = n;
   const MkView mv = view(m);
   // counting sort of (marker, slot) pairs by cell
-  IBM_CUDA(c, cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->m, s));
+  launch_zero(c->cell_count, sizeof(int32_t) * c->m, s);
   count_launch();
   k_count<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_count);
   IBM_LAUNCH_CHECK(c);
@@ -577,10 +578,9 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   st = exclusive_scan(c, c->cell_flag, fpos, c->m);
   if (st != IBM_OK) return st;
   int32_t tot[2];
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, c->cell_start + c->m, sizeof(int32_t),
-                              cudaMemcpyDeviceToHost, s));
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag + 1, fpos + c->m, sizeof(int32_t),
-                              cudaMemcpyDeviceToHost, s));
+  launch_to_host(c->cell_start + c->m, c->host_flag_dev, sizeof(int32_t), s);
+  launch_to_host(fpos + c->m, c->host_flag_dev + 1, sizeof(int32_t), s);
+  IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(s));
   tot[0] = c->host_flag[0];
   tot[1] = c->host_flag[1];
@@ -591,9 +591,8 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   k_shell_list<<<div_up(c->m, TPB), TPB, 0, s>>>(c->cell_count, c->cell_start, fpos, c->m,
                                                  m.shell_cell, m.shell_off);
   IBM_LAUNCH_CHECK(c);
-  IBM_CUDA(c, cudaMemcpyAsync(m.shell_off + ns, c->cell_start + c->m, sizeof(int32_t),
-                              cudaMemcpyDeviceToDevice, s));
-  IBM_CUDA(c, cudaMemsetAsync(c->cell_flag, 0, sizeof(int32_t) * c->m, s));
+  launch_copy(m.shell_off + ns, c->cell_start + c->m, sizeof(int32_t), s);
+  launch_zero(c->cell_flag, sizeof(int32_t) * c->m, s);
   count_launch();
   k_fill<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_start, c->cell_flag, m.entry_key);
   IBM_LAUNCH_CHECK(c);
@@ -608,8 +607,8 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   IBM_LAUNCH_CHECK(c);
   st = exclusive_scan(c, cnt, m.ell_base, ng);
   if (st != IBM_OK) return st;
-  IBM_CUDA(c, cudaMemcpyAsync(c->host_flag, m.ell_base + ng, sizeof(int32_t),
-                              cudaMemcpyDeviceToHost, s));
+  launch_to_host(m.ell_base + ng, c->host_flag_dev, sizeof(int32_t), s);
+  IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(s));
   const int64_t n_ell = c->host_flag[0];
   if ((st = grow_ell(c, n_ell)) != IBM_OK) return st;

@@ -934,7 +934,7 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
                                                             w_over_n<T>(w[q]), (T)h2);
     T* tmp = cur; cur = nxt; nxt = tmp;
   }
-  if (cur != x) cudaMemcpyAsync(x, cur, sizeof(T) * L.m, cudaMemcpyDeviceToDevice, s);
+  if (cur != x) launch_copy(x, cur, sizeof(T) * L.m, s);
 }
 
 // one smoothing step src -> dst on level l
@@ -986,7 +986,7 @@ void post_smooth(ibm_ctx* c, int l, const T* b, T* x, T* t, int p, TO* out, cuda
   }
   // the last step landed in t or x while out aliases the other: copy
   if ((const void*)src != (const void*)out)
-    cudaMemcpyAsync(out, src, sizeof(T) * L.m, cudaMemcpyDeviceToDevice, s);
+    launch_copy(out, src, sizeof(T) * L.m, s);
 }
 
 // V-cycle on level l >= 1 (or level 0 in the FP64 form): x_l ~ L_l^{-1} b_l.
