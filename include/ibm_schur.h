@@ -34,10 +34,15 @@
  *   (int32 where stated), contiguous, 8-byte aligned; the library never frees
  *   it.  The library owns only the workspace it allocates in ibm_create /
  *   ibm_set_markers and frees in ibm_destroy.
- * Streams: all work is enqueued on the stream given to ibm_create.  Entry
- *   points that return statistics or detect errors on the device synchronise
- *   that stream before returning (stated per call); the others are
- *   asynchronous.
+ * Streams: all work is enqueued on the stream given to ibm_create (the Schur
+ *   product forks its marker interpolation onto an internal stream and joins
+ *   it back before the product completes).  Entry points that return
+ *   statistics or detect errors on the device synchronise that stream before
+ *   returning (stated per call); the others are asynchronous.  Every step is a
+ *   kernel: zeroing, device-to-device copies and the scalars the host reads
+ *   (written by kernels into mapped pinned host memory) use no copy engine,
+ *   so host transfers the caller queues on other streams run alongside
+ *   without delaying the library's own control flow.
  * Errors: every call returns an ibm_status; ibm_last_error gives a message.
  *   No exception crosses the ABI and no kernel traps or asserts.  Arguments are
  *   validated before any work is enqueued.
