@@ -38,11 +38,12 @@
  *   product forks its marker interpolation onto an internal stream and joins
  *   it back before the product completes).  Entry points that return
  *   statistics or detect errors on the device synchronise that stream before
- *   returning (stated per call); the others are asynchronous.  Every step is a
- *   kernel: zeroing, device-to-device copies and the scalars the host reads
- *   (written by kernels into mapped pinned host memory) use no copy engine,
- *   so host transfers the caller queues on other streams run alongside
- *   without delaying the library's own control flow.
+ *   returning (stated per call); the others are asynchronous.
+ *   ibm_set_markers, ibm_solve_schur and ibm_step use no copy engine: their
+ *   zeroing and device-to-device copies are kernels, and the scalars the host
+ *   reads (residual norms, Hessenberg entries, counts, error flags) are
+ *   written by kernels into mapped pinned host memory, so host transfers the
+ *   caller queues on other streams run alongside without delaying them.
  * Errors: every call returns an ibm_status; ibm_last_error gives a message.
  *   No exception crosses the ABI and no kernel traps or asserts.  Arguments are
  *   validated before any work is enqueued.
