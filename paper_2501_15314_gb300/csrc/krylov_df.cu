@@ -318,6 +318,45 @@ __global__ void __launch_bounds__(RT) k_gemv_ds(double* __restrict__ x,
   }
 }
 
+// The same update four elements per thread (float4 loads of Z, two double2
+// read-modify-writes of x), for m a multiple of 4 and nq <= 16; the FP32 sum
+// and its error term are widened with integer operations, so the FP64 pipe
+// only adds.
+template <int NQ>
+__global__ void __launch_bounds__(RT) k_gemv_ds4(double2* __restrict__ x,
+                                                 const float4* __restrict__ Z, int64_t ld4,
+                                                 int nq, const CoefDS y, int64_t n4) {
+  pdl_wait();
+  pdl_trigger();
+  float yh[NQ], yl[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float2 v = q < nq ? y.v[q] : make_float2(0.f, 0.f);
+    yh[q] = v.x;
+    yl[q] = v.y;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n4; i += (int64_t)gridDim.x * RT) {
+    Comp a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, a2 = {0.f, 0.f}, a3 = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (q < nq) {
+        const float4 zq = __ldg(Z + q * ld4 + i);
+        comp_add_prod_f(a0, yh[q], yl[q], zq.x);
+        comp_add_prod_f(a1, yh[q], yl[q], zq.y);
+        comp_add_prod_f(a2, yh[q], yl[q], zq.z);
+        comp_add_prod_f(a3, yh[q], yl[q], zq.w);
+      }
+    }
+    double2 u0 = x[2 * i], u1 = x[2 * i + 1];
+    u0.x += f2d_exact(a0.s) + f2d_exact(a0.e);
+    u0.y += f2d_exact(a1.s) + f2d_exact(a1.e);
+    u1.x += f2d_exact(a2.s) + f2d_exact(a2.e);
+    u1.y += f2d_exact(a3.s) + f2d_exact(a3.e);
+    x[2 * i] = u0;
+    x[2 * i + 1] = u1;
+  }
+}
+
 // FP32 Arnoldi process (IBM_ARNOLDI_FP32): the basis vectors are single FP32
 // numbers (half the bytes of the pairs); dot products and the axpy are still
 // accumulated with the compensated scheme, and each result is rounded once.
@@ -732,7 +771,11 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         const float yh = (float)yi;
         cy.v[i] = make_float2(yh, (float)(yi - (double)yh));
       }
-      IBM_NQ_DISPATCH_DS(jused, k_gemv_ds, x, Zf, m, jused, cy, m);
+      if (m % 4 == 0 && jused <= 16 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0)
+        IBM_NQ_DISPATCH_SP4(jused, k_gemv_ds4, reinterpret_cast<double2*>(x),
+                            reinterpret_cast<const float4*>(Zf), m / 4, jused, cy, m / 4);
+      else
+        IBM_NQ_DISPATCH_DS(jused, k_gemv_ds, x, Zf, m, jused, cy, m);
       IBM_LAUNCH_CHECK(c);
     }
     ++cycles;
