@@ -297,12 +297,15 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // and e_new = alpha r^.hi.  mode 1: e_new = e + beta (e - e_old) +
 // alpha (r - A e) with r = r32; mode 2: the same step, accumulated into the
 // FP64 iterate, u += us * e_new, and stored in e_new (the next residual
-// reads it).
+// reads it).  The mode is a template parameter: each instance carries only
+// its own registers (mode 2 loads the FP64 iterate with the plane's other
+// inputs, so that its latency overlaps theirs).
+template <int mode>
 __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     FaceGeom g, FaceGeom32 p, int zchunks, const float* __restrict__ e,
     const float* __restrict__ eo, float* __restrict__ r32, float* __restrict__ rlo,
     const double* __restrict__ r64, float rs_hi, float rs_lo, float a, float nu_h2, float alpha,
-    float beta, float* __restrict__ en, double* __restrict__ u, double us, int mode) {
+    float beta, float* __restrict__ en, double* __restrict__ u, double us) {
   pdl_wait();
   pdl_trigger();
   const int c = blockIdx.z / zchunks;
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     wallx[q] = c == 0 && (x0 + q == 0 || x0 + q == n0 - 1);
   }
   const bool wally = c == 1 && (j == 0 || j == n1 - 1);
-  if (mode == 0) {
+  if constexpr (mode == 0) {
     const dsf rs = {rs_hi, rs_lo};
     for (int z = z0; z < z1; ++z, f += sz, f64 += sz64) {
       const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
@@ -381,6 +384,12 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     if (lane == 31) right = (act && x0 + 4 < n0) ? e[f + 4] : 0.f;
     const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
     const int gz = (c != 2) ? ((z == 0) + (z == n2 - 1)) : 0;
+    double uo[4] = {0.0, 0.0, 0.0, 0.0};
+    if constexpr (mode == 2) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (val[q] && !wallx[q] && !wally && !wallz) uo[q] = u[f64 + q];
+    }
     const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
     const float evp[4] = {ep.x, ep.y, ep.z, ep.w};
     const float evn[4] = {ez.x, ez.y, ez.z, ez.w};
@@ -405,11 +414,11 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
       out[q] = live ? ev[q] + beta * (ev[q] - vo[q]) + alpha * res : 0.f;
     }
     if (act) *reinterpret_cast<float4*>(en + f) = make_float4(out[0], out[1], out[2], out[3]);
-    if (mode == 2) {
+    if constexpr (mode == 2) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (val[q] && !wallx[q] && !wally && !wallz)
-          u[f64 + q] = fma(us, f2d_exact(out[q]), u[f64 + q]);   // widened without the FP64 pipe
+          u[f64 + q] = fma(us, f2d_exact(out[q]), uo[q]);   // widened without the FP64 pipe
     }
     ep = ec;
     ec = ez;
@@ -582,9 +591,17 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float
   const FaceGeom32 p = make_face_geom32(d);
   const float rs_hi = (float)rs, rs_lo = (float)(rs - (double)rs_hi);
   count_launch();
-  launch_pdl(k_helm_cheb_v4, helm_v4_grid(d), dim3(32, HVY), 0, s, make_face_geom(d), p,
-             helm_zchunks(d), e, eo, r32, rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us,
-             mode);
+  const FaceGeom g = make_face_geom(d);
+  const int zch = helm_zchunks(d);
+  if (mode == 0)
+    launch_pdl(k_helm_cheb_v4<0>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us);
+  else if (mode == 1)
+    launch_pdl(k_helm_cheb_v4<1>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us);
+  else
+    launch_pdl(k_helm_cheb_v4<2>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us);
 }
 
 int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, double a,
