@@ -165,6 +165,8 @@ static void free_all(ibm_ctx* c) {
   cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (cudaEvent_t& e : c->ev_iter)
+    if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
@@ -332,7 +334,9 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
             cudaHostGetDevicePointer(&c->host_red_dev, c->host_red, 0) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_iter[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_iter[1], cudaEventDisableTiming) == cudaSuccess;
   {
     // partial sums of the fused predictor residual norm (one per block)
     const int64_t nb = (int64_t)div_up(g->nx + 1, 32) * div_up(g->ny + 1, 8) * 3 *

@@ -99,6 +99,7 @@ struct ibm_ctx {
   // runs on it concurrently with the Laplacian
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_iter[2] = {nullptr, nullptr};   // ends of Krylov iterations (by parity)
   std::string err;
 
   // grid-sized scratch (FP64)

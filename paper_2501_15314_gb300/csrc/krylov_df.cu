@@ -694,19 +694,24 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     g[0] = beta;
     int jused = 0;
     bool breakdown = false;
-    for (int j = 0; j < restart && total < o->maxit; ++j) {
-      float* zj = Zf + (int64_t)j * m;
-      float2* w = V2 + (int64_t)(j + 1) * m;
-      float* w1 = V1 + (int64_t)(j + 1) * m;
+    // Iteration j's kernels: V-cycle, Schur product, Gram-Schmidt; the
+    // Hessenberg column goes to the host mirror (raw part in one of two
+    // buffers by the parity of j, apart from the scalar slot at the mirror's
+    // start that other reads use) and an event marks the iteration's end.
+    auto launch_iter = [&](int jj) -> ibm_status {
+      float* zj = Zf + (int64_t)jj * m;
+      float2* w = V2 + (int64_t)(jj + 1) * m;
+      float* w1 = V1 + (int64_t)(jj + 1) * m;
       int ph = prof_begin(c, IBM_PROF_VCYCLE);
-      if ((stt = mg_vcycle_f32(c, single ? V1 + (int64_t)j * m : vin, zj, o->mg_pre,
-                               o->mg_post)) != IBM_OK)
-        return stt;
+      ibm_status sv;
+      if ((sv = mg_vcycle_f32(c, single ? V1 + (int64_t)jj * m : vin, zj, o->mg_pre,
+                              o->mg_post)) != IBM_OK)
+        return sv;
       prof_end(c, ph);
-      if ((stt = single ? schur_apply_ds_t<float>(c, zj, w1) : schur_apply_ds_t<float2>(c, zj, w)) !=
+      if ((sv = single ? schur_apply_ds_t<float>(c, zj, w1) : schur_apply_ds_t<float2>(c, zj, w)) !=
           IBM_OK)
-        return stt;
-      const int nq = j + 1;
+        return sv;
+      const int nq = jj + 1;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
       if (vec4 && nq <= 16)
         IBM_NQ_DISPATCH_SP4(nq, k_multidot_sp4, reinterpret_cast<const float4*>(w1),
@@ -717,7 +722,8 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         IBM_NQ_DISPATCH_DS(nq, k_multidot_ds, w, V2, m, nq, m, part);
       count_launch();
       launch_pdl(k_final_reduce_ds, dim3(nq), dim3(RT), 0, s, (const double*)part, kRedBlocks,
-                 raw, (const double*)nrm2, coef, coef_ds, hmirror(c, hr));
+                 raw, (const double*)nrm2, coef, coef_ds,
+                 hmirror(c, hr + (2 + (jj & 1)) * kOutStride));
       prof_end(c, ph, (single ? 4.0 : 8.0) * (nq + 1) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
       if (vec4 && nq <= 16)
@@ -729,13 +735,42 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
         IBM_NQ_DISPATCH_DS(nq, k_axpy_norm_ds, w, V2, m, nq, coef_ds, m, part, vin);
       count_launch();
       launch_pdl(k_final_reduce_ds, dim3(1), dim3(RT), 0, s, (const double*)part, kRedBlocks,
-                 nrm2 + j + 1, (const double*)nullptr, (double*)nullptr, (float2*)nullptr,
-                 hmirror(c, hr + 4 * kOutStride + j + 1));
+                 nrm2 + jj + 1, (const double*)nullptr, (double*)nullptr, (float2*)nullptr,
+                 hmirror(c, hr + 4 * kOutStride + jj + 1));
       // V_0..V_j and w read, w written (and its leading parts for the pair form)
       prof_end(c, ph, single ? 4.0 * (nq + 2) * (double)m : (8.0 * (nq + 2) + 4.0) * (double)m);
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaStreamSynchronize(s));
-      for (int i = 0; i <= j; ++i) Hm(i, j) = hr[i] / rn[i];
+      IBM_CUDA(c, cudaEventRecord(c->ev_iter[jj & 1], s));
+      return IBM_OK;
+    };
+    // The host stays one iteration behind the device where that is safe:
+    // iteration j+1 (which needs nothing from the host) is launched before
+    // iteration j's column is read whenever the residual estimate, shrinking
+    // at the fastest rate seen so far, cannot reach the stopping threshold at
+    // iteration j; so the device does not idle during the host's read and
+    // Givens update.  A wrong guess costs the unused iteration j+1; the
+    // iterates and the iteration count do not depend on the guesses.  The
+    // exact and sign-consistent forms, whose Schur product waits on the host
+    // (inner conjugate gradients), run one iteration at a time.
+    const double thresh = std::max(o->rtol * bnorm, cycle_stop);
+    const bool ahead = c->cmode == IBM_CMODE_SCALAR;
+    double prev = beta, rate = 0.05;   // assumed until a ratio has been seen
+    bool have_rate = false;
+    bool next_launched = false;
+    if (restart > 0 && total < o->maxit) {
+      if ((stt = launch_iter(0)) != IBM_OK) return stt;
+      next_launched = true;
+    }
+    for (int j = 0; next_launched; ++j) {
+      const bool can_next = j + 1 < restart && total + 1 < o->maxit;
+      next_launched = false;
+      if (ahead && can_next && prev * rate > 4.0 * thresh) {
+        if ((stt = launch_iter(j + 1)) != IBM_OK) return stt;
+        next_launched = true;
+      }
+      IBM_CUDA(c, cudaEventSynchronize(c->ev_iter[j & 1]));
+      const double* hraw = hr + (2 + (j & 1)) * kOutStride;
+      for (int i = 0; i <= j; ++i) Hm(i, j) = hraw[i] / rn[i];
       const double hn = std::sqrt(hr[4 * kOutStride + j + 1]);
       if (!std::isfinite(hn)) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
       Hm(j + 1, j) = hn;
@@ -755,9 +790,19 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       g[j] = cs[j] * g[j];
       ++total;
       jused = j + 1;
-      if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = std::fabs(g[j + 1]) / bnorm;
-      if (std::fabs(g[j + 1]) / bnorm <= o->rtol || hn == 0.0) break;
-      if (std::fabs(g[j + 1]) <= cycle_stop) break;   // FP32 basis exhausted
+      const double res = std::fabs(g[j + 1]);
+      if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = res / bnorm;
+      if (res / bnorm <= o->rtol || hn == 0.0) break;
+      if (res <= cycle_stop) break;   // FP32 basis exhausted
+      if (prev > 0.0) {
+        rate = have_rate ? std::min(rate, res / prev) : res / prev;
+        have_rate = true;
+      }
+      prev = res;
+      if (!next_launched && can_next) {
+        if ((stt = launch_iter(j + 1)) != IBM_OK) return stt;
+        next_launched = true;
+      }
     }
     if (jused > 0) {
       for (int i = jused - 1; i >= 0; --i) {
