@@ -60,6 +60,23 @@ NCU_TRAFFIC_RATIO = {
 }
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time per step (the job ends with it); ms itself
+    without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, ms):
+    """Whole-job solves/s: each of the world ranks (replicas, no collective on
+    the data path) completes one solve per step of ms milliseconds."""
+    return world * 1000.0 / ms
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -269,11 +286,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / K
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / K, dist, "cuda")
         return ms, stats
 
     # ---- mixed form (headline) ----
@@ -310,7 +323,7 @@ def run_ours(args):
         kw = dict(precond_prec=prec, arnoldi=arn, rtol=1e-8)
         s.solve_schur(b, **kw)
         msq, stq = timed(lambda: s.solve_schur(b, **kw)[1], k64)
-        solve_only[name] = {"solves_per_s": world * 1000.0 / msq, "ms": msq,
+        solve_only[name] = {"solves_per_s": job_rate(world, msq), "ms": msq,
                             "iters": stq[-1]["iters"], "relres": stq[-1]["relres_true"]}
 
     # ---- end to end through the public API with host buffers ----
@@ -394,11 +407,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
 
     # ---- adjoint of the step (transposed Schur solve) ----
     adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
@@ -447,7 +456,7 @@ def run_ours(args):
     breakdown = {kk: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
                  for kk, v in prof.items() if v["launches"]}
 
-    value = world * 1000.0 / ms_mixed
+    value = job_rate(world, ms_mixed)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -455,7 +464,7 @@ def run_ours(args):
                      "double-single predictor, f64 markers and true residual",
             "data": "synthetic",
             "config": workload_config(W),
-            "fp64_form": {"value": world * 1000.0 / ms_fp64, "unit": UNIT, "ms_per_step": ms_fp64,
+            "fp64_form": {"value": job_rate(world, ms_fp64), "unit": UNIT, "ms_per_step": ms_fp64,
                           "iters": st_fp64[-1]["iters"],
                           "what": "FP64 V-cycle + FP64 Arnoldi, same step"},
             "solve_only": solve_only,
@@ -467,7 +476,7 @@ def run_ours(args):
             "multistep": multistep,
             "gpu_launches": int(launches),
             "clocks": clk,
-            "e2e": {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                     "copies": "pinned host buffers; H2D and D2H each on a stream of its "
                               "own, pipelined with the steps (double-buffered)",
