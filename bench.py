@@ -47,8 +47,8 @@ SAMPLE_ITERS = 3           # FGMRES iterations in the CPU oracle's bounded sampl
 # step) of the same kernels on the eight-sphere workload at 192^3, where the
 # capture fits the profiling size rule; the traffic of a 256^3 launch is this
 # ratio times its algorithmic bytes (traffic grows with the units processed:
-# cells x vectors).  profiles/ncu_traffic_step_spheres8_192.md has the
-# command and the per-kernel numbers.  A class whose kernel changes after the
+# cells x vectors).  The profile summaries keep the capture's command and
+# the per-kernel numbers.  A class whose kernel changes after the
 # capture must be removed here (its traffic then reads null).
 NCU_TRAFFIC_RATIO = {
     # mode-1 launches of the predictor's Chebyshev step (the class's launches)
