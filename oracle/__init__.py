@@ -42,9 +42,11 @@ Modules:
                  torque sums with respect to U^Gamma and the marker positions
                  (through phi', the derivative of Eq. (delta)); the paper has
                  no adjoint, so this differentiates the step as written.
+* ``step_convergence``  a measurement, run by hand: the observed grid orders
+                 of one step between 32^3, 64^3 and 128^3.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` except the full-step convergence order, which the
 paper does not fix (its delta is first order, Sec. 2.3 footnote): "parity
-unpinned" for that property only.
+unpinned" for that property only (``step_convergence`` measures it).
 """
