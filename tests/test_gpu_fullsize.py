@@ -1,0 +1,81 @@
+"""Full-size checks on the 256^3 workload that bench.py times: eight spheres,
+60000 markers, Re 200, dt 1e-3, FP32 V-cycle and FP32 Arnoldi cycles refined
+by the FP64 residual, rtol 1e-8.  The oracle cannot afford the whole step at
+this size in a test, so the checks are properties that hold at any size,
+evaluated with the oracle's own operators (its G, G^T, R and C at 256^3) on
+the GPU's outputs:
+
+* the Schur solve: the residual ||b - S~ p|| / ||b|| recomputed by the
+  oracle meets 1e-8 and equals the solver's own FP64 residual;
+* one step from rest: the slip identity R^T u^{n+1} - U = (dt/3)(2C - I) F'
+  (exact algebra of the force recovery and the update), the divergence
+  identity G^T u^{n+1} = (4 dt/3) B^T F' up to (2 dt/3) times the solve
+  residual, a mean-zero pressure correction, and the per-body force and
+  torque sums."""
+import numpy as np
+import pytest
+
+from gpu_cases import dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full(cuda_device):
+    from oracle import mac, schur
+    from paper_2501_15314_gb300 import workloads as wl
+    from paper_2501_15314_gb300.api import IBMSolver
+    W = wl.config(3, secondary=True)
+    g = mac.Grid(W.n)
+    sysm = schur.SchurSystem(g, W.X)
+    s = IBMSolver(W.n, Re=W.Re, dt=W.dt)
+    s.set_markers(dev(W.X))
+    yield W, g, sysm, s
+    s.close()
+
+
+def test_schur_solve_residual_256(full):
+    from oracle import mac
+    W, g, sysm, s = full
+    rng = np.random.default_rng(31)
+    u = rng.standard_normal(g.n_faces) * g.interior_face_mask_packed()
+    b = sysm.rhs_scalar(mac.apply_GT(g, u), rng.standard_normal(sysm.k))
+    p, st = s.solve_schur(dev(b), precond_prec=1, rtol=1e-8)
+    ph = host(p)
+    r = rel(sysm.apply_S_tilde(ph), b)
+    print(f"256^3 solve: {st['iters']} iterations, oracle residual {r:.3e}, "
+          f"solver residual {st['relres_true']:.3e}")
+    assert r <= 1.01e-8
+    assert abs(r - st["relres_true"]) <= 1e-3 * r + 1e-14
+    assert abs(ph.sum()) <= 1e-10 * np.abs(ph).sum()
+    assert st["iters"] <= 20
+
+
+def test_step_identities_256(full):
+    import torch
+    from oracle import mac, step
+    W, g, sysm, s = full
+    z = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda")  # noqa: E731
+    out, st = s.step(z(g.n_faces), z(g.n_faces), z(g.m), z(sysm.k), dev(W.U_gamma.ravel()),
+                     dev(W.f_body), precond_prec=1, rtol=1e-8)
+    u1, p1, F1 = host(out["u"]), host(out["p"]), host(out["F"])   # F^n = 0: F' = F^{n+1}
+    U = W.U_gamma.ravel()
+    dt = W.dt
+    # slip: exact algebra of the force recovery and the update
+    slip = sysm.R.T @ u1 - U
+    slip_ref = (dt / 3.0) * (2.0 * (sysm.C @ F1) - F1)
+    assert rel(slip, slip_ref) < 1e-9, rel(slip, slip_ref)
+    # divergence: up to (2 dt/3) times the solve residual (||b|| ~ ||S~ p'||)
+    div = mac.apply_GT(g, u1)
+    div_ref = (4.0 * dt / 3.0) * sysm.apply_BT(F1)
+    bnorm = np.linalg.norm(sysm.apply_S_tilde(p1))
+    gap = np.linalg.norm(div - div_ref)
+    print(f"256^3 step: {st['iters']} iterations, |div - (4dt/3) B^T F'| = {gap:.3e}, "
+          f"bound (2dt/3) 1e-8 |b| = {(2 * dt / 3) * 1e-8 * bnorm:.3e}")
+    assert gap <= (2.0 * dt / 3.0) * 1.05e-8 * bnorm + 1e-12 * np.linalg.norm(div_ref)
+    assert st["relres_true"] <= 1e-8
+    assert abs(p1.sum()) <= 1e-10 * np.abs(p1).sum()
+    # per-body force and torque: the oracle's sums of the GPU's force
+    ref = step.body_force_torque(g, W.X, F1, W.body_id, W.centers)
+    got = s.body_forces(out["F"], dev(W.X.ravel()), dev(W.body_id.astype(np.int32)), W.centers)
+    assert rel(got, ref) < 1e-12
