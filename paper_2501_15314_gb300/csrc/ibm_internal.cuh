@@ -265,8 +265,6 @@ void launch_copy(void* dst, const void* src, int64_t nbytes, cudaStream_t s);
 // nbytes (a multiple of 4) from device memory to dst_dev, the device address
 // of a place in a mapped host mirror (host_red_dev, host_flag_dev)
 void launch_to_host(const void* src, void* dst_dev, int nbytes, cudaStream_t s);
-void launch_scale(double* x, int64_t n, const double* inv, double scale, cudaStream_t s);
-void launch_scale_to(const double* x, int64_t n, double a, double* y, cudaStream_t s);
 void launch_axpby(const double* x, double a, const double* y, double b, double* out,
                   int64_t n, cudaStream_t s);
 // x += sum_q y[q] Z_q, y = the first nq host values (passed by value)
@@ -278,8 +276,6 @@ void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s);
 void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
                            cudaStream_t s);
-void launch_copy_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
-void launch_copy_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t s);
 
 // ---- scans (markers.cu) ----
 ibm_status exclusive_scan(ibm_ctx* c, const int32_t* in, int32_t* out, int64_t n);

@@ -140,22 +140,6 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
   block_reduce_store<1>(acc, 1, part);
 }
 
-// x *= scale / sqrt(*inv) when inv != null, else x *= scale
-__global__ void k_scale(double* __restrict__ x, int64_t n, const double* __restrict__ nrm2,
-                        double scale) {
-  const double f = nrm2 ? scale / sqrt(*nrm2) : scale;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] *= f;
-}
-
-__global__ void k_scale_to(const double* __restrict__ x, int64_t n, double a,
-                           double* __restrict__ y) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i];
-}
-
 __global__ void k_axpby(const double* __restrict__ x, double a, const double* __restrict__ y,
                         double b, double* __restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -271,16 +255,6 @@ void launch_to_host(const void* src, void* dst_dev, int nbytes, cudaStream_t s) 
 
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s) {
   launch_dot(x, nullptr, n, part, out, s);
-}
-
-void launch_scale(double* x, int64_t n, const double* nrm2, double scale, cudaStream_t s) {
-  count_launch();
-  k_scale<<<kRedBlocks, RT, 0, s>>>(x, n, nrm2, scale);
-}
-
-void launch_scale_to(const double* x, int64_t n, double a, double* y, cudaStream_t s) {
-  count_launch();
-  k_scale_to<<<kRedBlocks, RT, 0, s>>>(x, n, a, y);
 }
 
 void launch_axpby(const double* x, double a, const double* y, double b, double* out, int64_t n,

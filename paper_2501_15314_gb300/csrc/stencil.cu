@@ -569,10 +569,6 @@ void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c, 
 
 int helm_zchunks(Dims d) { return div_up(d.nz + 1, ZH); }
 
-dim3 helm_grid(Dims d) {
-  return dim3(div_up(d.nx + 1, BX), div_up(d.ny + 1, BY), 3 * helm_zchunks(d));
-}
-
 int64_t helm_fp32_size(Dims d) {
   const FaceGeom32 p = make_face_geom32(d);
   return p.off[2] + p.sz[2] * p.n[2][2];
