@@ -70,8 +70,15 @@ class RigidSpheres:
 
 
 class IBMSolver:
-    """One MAC grid (nx, ny, nz, h) with its workspace on the current device
-    and stream."""
+    """One MAC grid (nx, ny, nz, h) with its workspace on the current device.
+
+    The library runs on ``stream`` (default: the current stream at creation).
+    Every call is ordered after the caller's current stream at the time of the
+    call (where its inputs and freshly allocated outputs were written), and
+    the caller's current stream after the call (where the results are read),
+    so tensors can be produced and consumed on any stream.  Inputs are
+    contiguous CUDA float64 tensors (int32 for body ids) in the layouts of
+    include/ibm_schur.h."""
 
     def __init__(self, nx: int, ny: int | None = None, nz: int | None = None,
                  h: float | None = None, Re: float = 100.0, dt: float = 0.01,
