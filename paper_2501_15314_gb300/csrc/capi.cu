@@ -574,17 +574,20 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   }
   IBM_LAUNCH_CHECK(c);
 
-  // 6. diagnostics
+  // 6. diagnostics: both squared norms go to the host mirror, one round trip
+  double* dslot = c->red_out + 7 * (kMaxRestart + 2);
   launch_gradient_t(c->d, u_np1, c->c1, inv_h, str);
-  IBM_LAUNCH_CHECK(c);
-  if ((s = norm2_host(c, c->c1, c->m, &st->div_l2)) != IBM_OK) return s;
+  launch_dot(c->c1, c->c1, c->m, c->red_part, dslot, str, c->host_red_dev);
   if (n > 0) {
     launch_interp(c, u_np1, mk.t2);
     count_launch();
     k_axpby_small<<<div_up(3 * n, TPB), TPB, 0, str>>>(mk.t2, 1.0, U_gamma, -1.0, mk.t2, 3 * n);
-    IBM_LAUNCH_CHECK(c);
-    if ((s = norm2_host(c, mk.t2, 3 * n, &st->slip_l2)) != IBM_OK) return s;
+    launch_dot(mk.t2, mk.t2, 3 * n, c->red_part, dslot + 1, str, c->host_red_dev + 1);
   }
+  IBM_LAUNCH_CHECK(c);
+  IBM_CUDA(c, cudaStreamSynchronize(str));
+  st->div_l2 = std::sqrt(c->host_red[0]);
+  if (n > 0) st->slip_l2 = std::sqrt(c->host_red[1]);
   st->c_iters = c->c_iters;
   set_cmode(c, nullptr);
   return solve_status;
