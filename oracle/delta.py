@@ -23,7 +23,9 @@ with ``ValueError``.
 Pins (tests/test_oracle_delta.py): closed-form values and the zeroth, first
 and squared-sum moments of phi; R^T computed by an independent brute-force
 double loop over all faces and markers; partition of unity; force
-conservation; the average row sum of R^T R against Table A1 (RtR_spacing).  phi_prime
+conservation; exact interpolation of linear fields and second-order
+interpolation of a smooth field; the average row sum of R^T R against Table
+A1 (RtR_spacing).  phi_prime
 and ``regularization_derivative`` are pinned to central differences of phi
 and R, the values -1 and 0 at the breakpoints and the differentiated moment
 identities (tests/test_oracle_adjoint.py).

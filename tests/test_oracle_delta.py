@@ -1,5 +1,5 @@
 """Pins of oracle.delta (Roma delta, R, R^T) to closed forms, brute force and
-the paper's Table A1 (RtR_spacing)."""
+the paper's Table A1 (RtR_spacing), and the O(h^2) accuracy of interpolation."""
 import numpy as np
 import pytest
 
@@ -114,3 +114,26 @@ def test_support_outside_interior_rejected():
     X = np.array([[0.5], [0.5], [1.2 / 16]])   # z within 1.5h of the wall face
     with pytest.raises(ValueError):
         delta.regularization_matrix(g, X)
+
+
+def test_smooth_field_interpolated_to_second_order():
+    # zeroth and first moments vanish beyond order one, so interpolating a
+    # smooth field leaves an O(h^2) error (Sec. 3.2: the kernel's moment
+    # conditions); halving h divides the error by about 4
+    errs = []
+    for n in (16, 32, 64):
+        g = mac.Grid(n)
+        W = _sphere(n, 0.3, center=(0.48, 0.51, 0.53))
+        R = delta.regularization_matrix(g, W.X)
+        err = 0.0
+        for d in range(3):
+            x, y, z = g.face_coords(d)
+            f = lambda a, b, c: np.sin(2 * np.pi * a + d) * np.cos(2 * np.pi * b) * np.cos(np.pi * c)  # noqa: E731
+            u = np.zeros(g.n_faces)
+            o, s = g.face_offsets[d], g.face_sizes[d]
+            u[o:o + s] = f(x, y, z).ravel()
+            U = (R.T @ u).reshape(3, -1)[d]
+            err = max(err, np.abs(U - f(*W.X)).max())
+        errs.append(err)
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((orders > 1.8) & (orders < 2.3)), (errs, orders)
