@@ -4,6 +4,7 @@ compute call (no GPU needed)."""
 import ctypes as C
 import re
 import subprocess
+import sys
 from pathlib import Path
 
 import pytest
@@ -74,3 +75,22 @@ def test_product_path_does_not_import_oracle():
         for line in bench.read_text().splitlines():
             if "import oracle" in line or "from oracle" in line:
                 assert line.startswith("    "), line
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # with the shared library absent, the first call into the package raises;
+    # nothing falls back to a CPU implementation
+    code = ("import sys; from pathlib import Path\n"
+            f"sys.path.insert(0, {str(ROOT)!r})\n"
+            "from paper_2501_15314_gb300 import _lib\n"
+            f"_lib.LIB_PATH = Path({str(tmp_path / 'libibmschur.so')!r})\n"
+            "from paper_2501_15314_gb300.api import IBMSolver\n"
+            "try:\n"
+            "    IBMSolver(16)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "is not built" in r.stdout
