@@ -195,15 +195,21 @@ def cpu_model():
 
 
 def workload_config(W):
-    return {"workload": f"{W.name}: {W.n}^3 MAC grid, {len(W.radii)} spheres r in "
-                        f"[0.05,0.1], {W.n_markers} markers (spacing ratio "
-                        f"{W.info['spacing_ratio']:.2f}), Re {W.Re:g}, dt {W.dt:g}, first "
-                        f"step from rest, FGMRES rtol 1e-8",
-            "grid": [W.n, W.n, W.n], "markers": W.n_markers, "bodies": len(W.radii),
-            "Re": W.Re, "dt": W.dt, "rtol": 1e-8,
-            "l2": ("no flush: one step streams tens of GB (FP64 fields 134-403 MB, Krylov "
-                   "basis GBs) through the 129 MB L2, so no step starts with the previous "
-                   "step's data resident"),
+    nb = len(W.radii)
+    bodies = (f"1 sphere r {W.radii[0]:g}" if nb == 1 else
+              f"{nb} spheres r {W.info.get('radius_law', 'in [%.3f,%.3f]' % (W.radii.min(), W.radii.max()))}")
+    cell_mb = 8.0 * W.n ** 3 / 1e6
+    if cell_mb > 129.0:
+        l2 = (f"no flush: one step streams tens of GB (FP64 fields {cell_mb:.0f}-"
+              f"{3 * cell_mb:.0f} MB, Krylov basis GBs) through the 129 MB L2, so no step "
+              f"starts with the previous step's data resident")
+    else:
+        l2 = f"small case: an FP64 cell field ({cell_mb:.1f} MB) fits in the 129 MB L2"
+    return {"workload": f"{W.name}: {W.n}^3 MAC grid, {bodies}, {W.n_markers} markers "
+                        f"(spacing ratio {W.info['spacing_ratio']:.2f}), Re {W.Re:g}, "
+                        f"dt {W.dt:g}, first step from rest, FGMRES rtol 1e-8",
+            "grid": [W.n, W.n, W.n], "markers": W.n_markers, "bodies": nb,
+            "Re": W.Re, "dt": W.dt, "rtol": 1e-8, "l2": l2,
             "parallelism": "replicas"}
 
 

@@ -182,8 +182,10 @@ def config(index: int, secondary: bool = False) -> Workload:
     if index == 3:
         n = 256
         centers, radii = place_spheres(8, 0.05, 0.1, 1.0 / n, rng)
-        return spheres_workload("spheres8_256", n, 200.0, 1e-3, centers, radii,
-                                60000 if secondary else None, index, rng=rng)
+        W = spheres_workload("spheres8_256", n, 200.0, 1e-3, centers, radii,
+                             60000 if secondary else None, index, rng=rng)
+        W.info["radius_law"] = "in [0.05,0.1]"
+        return W
     if index == 5:
         return spheres_workload("sediment384", 384, 50.0, 5e-4,
                                 [[0.5, 0.5, 0.7]], [0.08],

@@ -1,0 +1,44 @@
+"""bench.py's reference arm: the oracle timed on the host cores on a bounded
+sample of one step, printed as one JSON line with the fields of the bench
+contract.  Run here on the 32^3 one-sphere workload, which takes well under a
+second; only rank 0 prints."""
+import json
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _run(extra_env=None):
+    env = dict(os.environ)
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference",
+                           "--config", "1", "--steps", "2", "--warmup", "1"],
+                          capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+
+
+def test_reference_line():
+    r = _run()
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["unit"] == "solves/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1000.0 / d["value"]) < 1e-9 * d["ms_per_step"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert "FGMRES iterations" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["grid"] == [32, 32, 32] and d["config"]["markers"] == 1000
+    assert "1 sphere r 0.2" in d["config"]["workload"]
+
+
+def test_reference_arm_prints_only_on_rank_0():
+    r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
