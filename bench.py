@@ -90,6 +90,51 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# Kernel classes reported in the bench line: label -> the library's profile
+# class.  The library counts each class's algorithmic bytes per launch (every
+# array read or written once; Gram-Schmidt from the actual basis length of each
+# launch and the element size of the Arnoldi form).
+ROOFLINE_CLASSES = {
+    "k_helm_cheb_v4 (predictor FP32 Chebyshev step: read e, e_old, r; write e_new)":
+        "helm_sweep",
+    "k_multidot_sp4 (Gram-Schmidt multi-dot on FP32 vectors, float4: w and V_0..V_j)":
+        "multidot",
+    "k_axpy_norm_sp4 (Gram-Schmidt axpy+norm on FP32 vectors, float4: V_0..V_j, w in/out)":
+        "axpy_norm",
+    ("Schur Laplacian class: k_lap_ds<float> (FP32 z in, exact product rounded to FP32 "
+     "out) per iteration and k_laplacian<double> of the FP64 true residuals"):
+        "laplacian_f64",
+    "k_first_v4 + k_sweep_v4 (finest V-cycle smoothing)": "mg_smooth_fine",
+}
+
+
+def roofline(prof, steps, hbm, peak_kind):
+    """Per-class achieved bandwidth (algorithmic bytes over the class's
+    event-timed duration) and the roofline record of the class that takes the
+    most time.  prof: class -> {"ms", "launches", "bytes"} summed over the
+    timed steps."""
+    classes = {}
+    for name, cls in ROOFLINE_CLASSES.items():
+        t_ms = prof[cls]["ms"]
+        tot_bytes = prof[cls]["bytes"]
+        n_l = max(1, prof[cls]["launches"])
+        gbs = tot_bytes / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+        classes[name] = {"ms_per_step": t_ms / steps, "launches_per_step": n_l / steps,
+                         "achieved_gbs": gbs, "frac": gbs / hbm,
+                         "bytes_per_launch": tot_bytes / n_l, "avg_launch_ms": t_ms / n_l}
+    best = max(classes, key=lambda kk: classes[kk]["ms_per_step"])
+    cb = classes[best]
+    cls = ROOFLINE_CLASSES[best]
+    roof = {"bound": "hbm", "kernel": best, "achieved": cb["achieved_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": cb["frac"], "peak_kind": peak_kind,
+            "traffic": (NCU_TRAFFIC_RATIO[cls] * cb["bytes_per_launch"]
+                        if cls in NCU_TRAFFIC_RATIO else None),
+            "traffic_source": "ncu DRAM bytes per algorithmic byte at 192^3, scaled to this "
+                              "launch's units", "avg_launch_ms": cb["avg_launch_ms"],
+            "bytes_per_launch": cb["bytes_per_launch"]}
+    return roof, classes
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
@@ -423,42 +468,8 @@ def run_ours(args):
     multistep = multistep_bench()
 
     # ---- roofline of the dominant kernel class ----
-    # algorithmic bytes per launch (DRAM traffic the kernel must move at
-    # least once), summed over the timed region's launches of each class
     hbm, peak_kind = measured_peaks()
-    # algorithmic bytes of each timed class as the library counts them per
-    # launch (every array read or written once; Gram-Schmidt from the actual
-    # basis length of each launch and the element size of the Arnoldi form)
-    kern = {
-        "k_helm_cheb_v4 (predictor FP32 Chebyshev step: read e, e_old, r; write e_new)":
-            ("helm_sweep", prof["helm_sweep"]["bytes"]),
-        "k_multidot_sp4 (Gram-Schmidt multi-dot on FP32 vectors, float4: w and V_0..V_j)":
-            ("multidot", prof["multidot"]["bytes"]),
-        "k_axpy_norm_sp4 (Gram-Schmidt axpy+norm on FP32 vectors, float4: V_0..V_j, w in/out)":
-            ("axpy_norm", prof["axpy_norm"]["bytes"]),
-        ("Schur Laplacian class: k_lap_ds<float> (FP32 z in, exact product rounded to FP32 "
-         "out) per iteration and k_laplacian<double> of the FP64 true residuals"):
-            ("laplacian_f64", prof["laplacian_f64"]["bytes"]),
-        "k_first_v4 + k_sweep_v4 (finest V-cycle smoothing)":
-            ("mg_smooth_fine", prof["mg_smooth_fine"]["bytes"]),
-    }
-    classes = {}
-    for name, (cls, tot_bytes) in kern.items():
-        t_ms = prof[cls]["ms"]
-        n_l = max(1, prof[cls]["launches"])
-        gbs = tot_bytes / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
-        classes[name] = {"ms_per_step": t_ms / args.steps, "launches_per_step":
-                         n_l / args.steps, "achieved_gbs": gbs, "frac": gbs / hbm,
-                         "bytes_per_launch": tot_bytes / n_l, "avg_launch_ms": t_ms / n_l}
-    best = max(classes, key=lambda kk: classes[kk]["ms_per_step"])
-    cb = classes[best]
-    roof = {"bound": "hbm", "kernel": best, "achieved": cb["achieved_gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": cb["frac"], "peak_kind": peak_kind,
-            "traffic": (NCU_TRAFFIC_RATIO[kern[best][0]] * cb["bytes_per_launch"]
-                        if kern[best][0] in NCU_TRAFFIC_RATIO else None),
-            "traffic_source": "ncu DRAM bytes per algorithmic byte at 192^3, scaled to this "
-                              "launch's units", "avg_launch_ms": cb["avg_launch_ms"],
-            "bytes_per_launch": cb["bytes_per_launch"]}
+    roof, classes = roofline(prof, args.steps, hbm, peak_kind)
     breakdown = {kk: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
                  for kk, v in prof.items() if v["launches"]}
 
