@@ -120,11 +120,11 @@ def test_edge_cases(cuda_device):
         IBMSolver(50, 50, 75)
 
 
-def test_fp32_arnoldi_cell_count_not_multiple_of_4(cuda_device):
-    """FP32 Arnoldi on a 10 x 9 x 5 grid (450 cells, not a multiple of 4, so
-    the scalar Gram-Schmidt kernels run instead of the float4 ones, which
-    need every basis vector on a 16-byte boundary): parity with the oracle's
-    solve at rtol 1e-13."""
+def test_fp32_arnoldi_request_with_nx_not_multiple_of_4(cuda_device):
+    """FP32 Arnoldi requested on a 10 x 9 x 5 grid: nx is not a multiple of 4,
+    so the float4 V-cycle and the single-precision Arnoldi forms do not apply
+    and the solver runs the FP64 Arnoldi process with the scalar FP32 V-cycle
+    (as the header states); parity with the oracle's solve at rtol 1e-13."""
     from oracle import mac, schur
     from paper_2501_15314_gb300 import workloads as wl
     from paper_2501_15314_gb300.api import IBMSolver
