@@ -195,7 +195,7 @@ def test_finite_differences_oscillating_sphere_128(cuda_device):
         fd = (J_at(Xc.detach(), Ut.detach() + e * dU)
               - J_at(Xc.detach(), Ut.detach() - e * dU)) / (2 * e)
         errs_U.append(abs(float(np.dot(gU, host(dU))) - fd) / abs(fd))
-    print(f"J {float(J):.12g} centre gradient {gc_ad}; centre FD rel error: single steps "
+    print(f"J {float(J.detach()):.12g} centre gradient {gc_ad}; centre FD rel error: single steps "
           f"{single}, mean over steps 5e-8..8.5e-8 {err_mean:.3e}; "
           f"U directions rel error (step 1e-6) {errs_U}")
     assert err_mean < 1e-6
