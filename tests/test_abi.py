@@ -94,3 +94,14 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "is not built" in r.stdout
+
+
+@pytest.mark.parametrize("compiler,std,ext", [("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")])
+def test_header_is_strict_c_and_cpp(tmp_path, compiler, std, ext):
+    # the boundary is plain C: the header compiles warning-free as ISO C99 and C++11
+    src = tmp_path / f"h.{ext}"
+    src.write_text('#include "ibm_schur.h"\nint main(void) { ibm_solve_opts o; '
+                   'ibm_default_opts(&o); return o.restart > 0 ? 0 : 1; }\n')
+    subprocess.run([compiler, std, "-pedantic", "-Wall", "-Wextra", "-Werror",
+                    f"-I{ROOT / 'include'}", "-c", str(src), "-o", str(tmp_path / "h.o")],
+                   check=True)
