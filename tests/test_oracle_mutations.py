@@ -11,7 +11,7 @@ import textwrap
 
 import pytest
 
-from oracle import delta, fsi, helmholtz, mac, schur, step
+from oracle import adjoint, delta, fsi, helmholtz, mac, schur, step
 
 # (case, owner of the function, function, text in its source, planted text,
 #  pin module, pin function, pin arguments)
@@ -84,6 +84,37 @@ MUTATIONS = [
     ("rigid update: buoyancy factor dropped", fsi, "rigid_velocities",
      "(th - 1.0) / th * g", "g", "test_oracle_fsi", "test_rigid_update_free_fall_is_exact",
      ()),
+    ("volume fraction: outside counted", fsi, "volume_fraction",
+     "num += np.maximum(-phi, 0.0)", "num += np.maximum(phi, 0.0)",
+     "test_oracle_fsi", "test_volume_fraction_second_order", ()),
+    ("enclosed angular momentum: z sign", fsi, "fluid_momentum",
+     "ang[2] += np.sum(r[0] * w * e[1] - r[1] * w * e[0])",
+     "ang[2] += np.sum(r[1] * w * e[0] - r[0] * w * e[1])",
+     "test_oracle_fsi", "test_fluid_momentum_uniform_and_rotating_fields", ()),
+    ("FGMRES: update from V in place of Z", schur, "fgmres", "x = x + Z[:j_used].T @ y",
+     "x = x + V[:j_used].T @ y",
+     "test_oracle_schur", "test_fgmres_matches_dense_bruteforce", ()),
+    ("FGMRES: projection on V_0 only", schur, "fgmres", "H[i, j] = np.dot(w, V[i])",
+     "H[i, j] = np.dot(w, V[0])",
+     "test_oracle_schur", "test_fgmres_matches_dense_bruteforce", ()),
+    ("Helmholtz solve: sign of the viscous term", helmholtz, "solve",
+     "r = r / (a + nu * lam)", "r = r / (a - nu * lam)",
+     "test_oracle_helmholtz", "test_solve_matches_sparse_direct", ()),
+    ("torque: lever and force swapped", step, "body_force_torque", "np.cross(r.T, f.T)",
+     "np.cross(f.T, r.T)", "test_oracle_step", "test_body_force_torque_closed_form", ()),
+    ("adjoint: a term of the chain dropped", adjoint, "step_vjp",
+     "pairs.append((Gp, -2.0 * sys.apply_B(lam)))",
+     "pairs.append((Gp, 0.0 * sys.apply_B(lam)))",
+     "test_oracle_adjoint", "test_center_gradient_central_difference", (False,)),
+    ("adjoint: sign of dJ/dU", adjoint, "step_vjp", "U_bar = -a * rhsF_bar",
+     "U_bar = a * rhsF_bar", "test_oracle_adjoint", "test_U_gradient_exact_by_linearity",
+     (False,)),
+    ("adjoint: factor 2 of B lambda dropped", adjoint, "step_vjp",
+     "rhsF_bar = rhsF_bar + 2.0 * sys.apply_B(lam)", "rhsF_bar = rhsF_bar + sys.apply_B(lam)",
+     "test_oracle_adjoint", "test_U_gradient_exact_by_linearity", (False,)),
+    ("force/torque VJP: cross product order", adjoint, "body_force_torque_vjp",
+     "np.cross(wT, r.T).T", "np.cross(r.T, wT).T",
+     "test_oracle_adjoint", "test_body_force_torque_vjp_central_difference", ()),
 ]
 
 

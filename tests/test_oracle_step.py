@@ -89,3 +89,23 @@ def test_zero_forcing_zero_velocity_gives_zero_step():
     g = mac.Grid(12)
     out = step.step(g, W.Re, W.dt, W.X, np.zeros_like(W.U_gamma), np.zeros(g.n_faces))
     assert np.abs(out["u"]).max() == 0.0 and np.abs(out["p"]).max() == 0.0
+
+
+def test_body_force_torque_closed_form():
+    # per body h^3 sum F_k and h^3 sum (X_k - X_c) x F_k (Eq. (IBM_force)),
+    # written out for three markers with axis-aligned lever arms and forces
+    g = mac.Grid(10)                                  # h^3 = 1e-3
+    c = np.array([[0.5, 0.5, 0.5], [0.2, 0.3, 0.4]])
+    X = np.array([[0.5, 0.5, 0.3],                    # columns: markers
+                  [0.7, 0.5, 0.3],
+                  [0.5, 0.6, 0.4]])
+    F = np.array([[1.0, 0.0, 0.0],
+                  [0.0, 2.0, 0.0],
+                  [0.0, 0.0, 3.0]])
+    body_id = np.array([0, 0, 1])
+    out = step.body_force_torque(g, X, F, body_id, c)
+    # body 0: r = (0, 0.2, 0) with F = (1, 0, 0), r = (0, 0, 0.1) with F = (0, 2, 0)
+    # body 1: r = (0.1, 0, 0) with F = (0, 0, 3)
+    expect = 1e-3 * np.array([[1.0, 2.0, 0.0, -0.2, 0.0, -0.2],
+                              [0.0, 0.0, 3.0, 0.0, -0.3, 0.0]])
+    np.testing.assert_allclose(out, expect, rtol=0, atol=1e-15)
