@@ -49,4 +49,6 @@ Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` except the full-step convergence order, which the
 paper does not fix (its delta is first order, Sec. 2.3 footnote): "parity
 unpinned" for that property only (``step_convergence`` measures it).
+``tests/test_oracle_mutations.py`` plants mistakes in these modules' source
+(on the CPU) and checks that a pin fails for each.
 """
