@@ -40,7 +40,8 @@ def test_achieved_bandwidth_and_dominant_class():
     assert roof["frac"] == pytest.approx(expect / 6787.9, rel=1e-12)
     assert roof["avg_launch_ms"] == pytest.approx(2.522462 / 18, rel=1e-12)
     assert roof["bytes_per_launch"] == pytest.approx(808452096.0)
-    assert roof["traffic"] == pytest.approx(bench.NCU_TRAFFIC_RATIO["helm_sweep"] * 808452096.0)
+    # no ncu ratio taken on the current build of the Chebyshev step: traffic null
+    assert "helm_sweep" not in bench.NCU_TRAFFIC_RATIO and roof["traffic"] is None
     assert len(classes) == 5
     for v in classes.values():
         assert v["achieved_gbs"] == pytest.approx(
@@ -53,6 +54,7 @@ def test_class_without_launches_reads_zero():
     prof["multidot"] = _prof(4.0, 8, 1e8)
     roof, classes = bench.roofline(prof, 2, 1000.0, "fallback")
     assert roof["kernel"].startswith("k_multidot_sp4")
+    assert roof["traffic"] == pytest.approx(bench.NCU_TRAFFIC_RATIO["multidot"] * 1e8)
     assert roof["achieved"] == pytest.approx(8 * 1e8 / 4e-3 / 1e9)
     assert roof["peak_kind"] == "fallback"
     zero = [v for v in classes.values() if v["ms_per_step"] == 0.0]
