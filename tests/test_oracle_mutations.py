@@ -91,6 +91,14 @@ MUTATIONS = [
      "ang[2] += np.sum(r[0] * w * e[1] - r[1] * w * e[0])",
      "ang[2] += np.sum(r[1] * w * e[0] - r[0] * w * e[1])",
      "test_oracle_fsi", "test_fluid_momentum_uniform_and_rotating_fields", ()),
+    ("skew matrix: one sign", fsi, "skew", "[v[2], 0.0, -v[0]]", "[-v[2], 0.0, -v[0]]",
+     "test_oracle_fsi", "test_rodrigues_increment_rotates_by_the_ab2_angle", ()),
+    ("two-way correction: half the update", fsi, "fsi_step",
+     "u = u + xi * (1.0 / a) *", "u = u + xi * (0.5 / a) *",
+     "test_oracle_fsi", "test_fixed_body_one_correction_equals_one_way_step", ()),
+    ("body position: Euler step in place of BDF2", fsi, "fsi_step",
+     "(2.0 / 3.0) * dt * b.us", "dt * b.us",
+     "test_oracle_fsi", "test_corrections_approach_the_constrained_fixed_point", ()),
     ("FGMRES: update from V in place of Z", schur, "fgmres", "x = x + Z[:j_used].T @ y",
      "x = x + V[:j_used].T @ y",
      "test_oracle_schur", "test_fgmres_matches_dense_bruteforce", ()),
