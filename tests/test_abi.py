@@ -105,3 +105,40 @@ def test_header_is_strict_c_and_cpp(tmp_path, compiler, std, ext):
     subprocess.run([compiler, std, "-pedantic", "-Wall", "-Wextra", "-Werror",
                     f"-I{ROOT / 'include'}", "-c", str(src), "-o", str(tmp_path / "h.o")],
                    check=True)
+
+
+def test_noalloc_argument_checks_need_no_gpu(built_lib):
+    # the checks that precede any CUDA call: body count, cell width, missing
+    # outputs; zero markers give zero sums without touching a device
+    from paper_2501_15314_gb300 import _lib
+    fn = built_lib.ibm_body_forces_noalloc
+    centers = (C.c_double * (3 * 1025))()
+    out = (C.c_double * (6 * 1025))(*([7.0] * (6 * 1025)))
+    assert fn(None, None, None, 0, 0, centers, 0.1, None, out) == _lib.IBM_ERR_ARG
+    assert fn(None, None, None, 0, 1025, centers, 0.1, None, out) == _lib.IBM_ERR_ARG
+    assert fn(None, None, None, 0, 2, centers, 0.0, None, out) == _lib.IBM_ERR_ARG
+    assert fn(None, None, None, 0, 2, None, 0.1, None, out) == _lib.IBM_ERR_ARG
+    assert fn(None, None, None, 0, 2, centers, 0.1, None, None) == _lib.IBM_ERR_ARG
+    assert fn(None, None, None, -1, 2, centers, 0.1, None, out) == _lib.IBM_ERR_ARG
+    assert fn(None, None, None, 5, 2, centers, 0.1, None, out) == _lib.IBM_ERR_ARG  # no F, X
+    assert fn(None, None, None, 0, 3, centers, 0.1, None, out) == _lib.IBM_OK
+    assert list(out[:18]) == [0.0] * 18 and out[18] == 7.0
+
+
+def test_every_context_call_rejects_a_null_context(built_lib):
+    # every entry point taking an ibm_ctx returns IBM_ERR_ARG for NULL before
+    # any CUDA call (all other arguments zero or NULL)
+    from paper_2501_15314_gb300 import _lib
+    no_ctx = {"ibm_create", "ibm_destroy", "ibm_last_error", "ibm_num_cells", "ibm_num_faces",
+              "ibm_default_opts", "ibm_default_fsi_opts", "ibm_kernel_launches",
+              "ibm_body_forces_noalloc"}
+    checked = 0
+    for name, _, args in _lib.SIGNATURES:
+        if name in no_ctx:
+            continue
+        vals = [0 if a in (C.c_int, C.c_int32, C.c_int64) else 0.0 if a is C.c_double else None
+                for a in args]
+        assert getattr(built_lib, name)(*vals) == _lib.IBM_ERR_ARG, name
+        checked += 1
+    assert checked >= 19
+    assert built_lib.ibm_num_cells(None) == 0 and built_lib.ibm_num_faces(None) == 0
