@@ -65,8 +65,11 @@ class RigidSpheres:
         self.n = nb
 
     def get(self, name):
+        """One field of every sphere: (n,) for a scalar field, (n, k) for an
+        array field."""
         import numpy as np
-        return np.array([list(getattr(self.arr[b], name)) for b in range(self.n)])
+        vals = [getattr(self.arr[b], name) for b in range(self.n)]
+        return np.array([list(v) if hasattr(v, "__len__") else v for v in vals])
 
 
 class IBMSolver:

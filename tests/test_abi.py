@@ -142,3 +142,21 @@ def test_every_context_call_rejects_a_null_context(built_lib):
         checked += 1
     assert checked >= 19
     assert built_lib.ibm_num_cells(None) == 0 and built_lib.ibm_num_faces(None) == 0
+
+
+def test_binding_rejects_host_tensors():
+    # the binding passes device pointers only: a CPU tensor (or a wrong dtype,
+    # a strided view, a wrong size) is refused before any library call, so no
+    # call can silently run on host memory
+    import torch
+    from paper_2501_15314_gb300.api import RigidSpheres, _ptr
+    with pytest.raises(ValueError, match="CUDA"):
+        _ptr(torch.zeros(8, dtype=torch.float64), name="u")
+    with pytest.raises(TypeError):
+        _ptr([0.0] * 8, name="u")
+    # host state of the two-way spheres is a plain ctypes array
+    rs = RigidSpheres([0.1, 0.2], 2.0, [[0.3, 0.3, 0.3], [0.7, 0.6, 0.5]],
+                      velocities=[[1, 2, 3], [4, 5, 6]])
+    assert rs.n == 2 and rs.get("radius").tolist() == [0.1, 0.2]
+    assert rs.get("us").tolist() == [[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]]
+    assert rs.get("rot").tolist() == [[1, 0, 0, 0, 1, 0, 0, 0, 1]] * 2
