@@ -55,7 +55,7 @@ import numpy as np
 
 from . import helmholtz, mac
 from .schur import SchurSystem, solve_schur
-from .step import advection
+from .step import predictor_rhs
 
 
 @dataclass
@@ -185,17 +185,15 @@ def fsi_step(g: mac.Grid, Re: float, dt: float, bodies, L0, body_id, u_n, u_nm1,
         xc_new.append(x1)
     lever = X - np.stack([xc_new[i] for i in body_id], axis=1) if N else X
     sys = SchurSystem(g, X)
-    mask = g.interior_face_mask_packed()
     # Step 2: predictor
     u_n = np.asarray(u_n, dtype=np.float64)
     u_nm1 = np.asarray(u_nm1, dtype=np.float64)
     p = np.asarray(p_n, dtype=np.float64).copy()
     F = np.asarray(F_n, dtype=np.float64).ravel().copy()
-    rhs = ((4.0 * u_n - u_nm1) / (2.0 * dt) - mac.apply_G(g, p) + sys.R @ F
-           + (0.0 if f_body is None else np.asarray(f_body, dtype=np.float64)))
-    if with_advection:
-        rhs = rhs - advection(g, u_n)
-    u = helmholtz.solve(g, np.where(mask, rhs, 0.0), a, nu, workers=workers)
+    rhs = predictor_rhs(g, dt, u_n, u_nm1, p, sys.R @ F,
+                        0.0 if f_body is None else np.asarray(f_body, dtype=np.float64),
+                        with_advection)
+    u = helmholtz.solve(g, rhs, a, nu, workers=workers)
     # Step 3: corrections
     h3 = g.h ** 3
     iters, ratio, inner = [], np.inf, 0

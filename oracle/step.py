@@ -97,6 +97,24 @@ def advection(g: mac.Grid, u):
     return out
 
 
+def predictor_rhs(g: mac.Grid, dt: float, u_n, u_nm1, p_n, RF_n, f_body,
+                  with_advection=True):
+    """Right-hand side of the BDF2 momentum predictor, Eq. (ustar), on the
+    interior faces (0 on the wall faces): moving the u^n and u^{n-1} parts of
+    the BDF2 time derivative (3 u* - 4 u^n + u^{n-1})/(2 dt) to the right and
+    keeping the explicit terms at time level n,
+
+        rhs = (4 u^n - u^{n-1})/(2 dt) - G p^n + R F^n + f - A(u^n),
+
+    with R F^n the spread force density (passed in as RF_n), f the prescribed
+    body force on the faces and A the convective term (``advection``).  Shared
+    by the one-way step and the two-way predictor of Eq. (ustar_two_way)."""
+    rhs = (4.0 * u_n - u_nm1) / (2.0 * dt) - mac.apply_G(g, p_n) + RF_n + f_body
+    if with_advection:
+        rhs = rhs - advection(g, u_n)
+    return np.where(g.interior_face_mask_packed(), rhs, 0.0)
+
+
 def step(g: mac.Grid, Re: float, dt: float, X, U_gamma, f_body,
          u_n=None, u_nm1=None, p_n=None, F_n=None, mode="scalar",
          rtol=1e-13, with_advection=True, workers=None):
@@ -111,13 +129,9 @@ def step(g: mac.Grid, Re: float, dt: float, X, U_gamma, f_body,
     a = 3.0 / (2.0 * dt)
     nu = 1.0 / Re
     sys = SchurSystem(g, X)
-    mask = g.interior_face_mask_packed()
 
-    rhs_u = ((4.0 * u_n - u_nm1) / (2.0 * dt) - mac.apply_G(g, p_n) + sys.R @ F_n
-             + np.asarray(f_body, dtype=np.float64))
-    if with_advection:
-        rhs_u = rhs_u - advection(g, u_n)
-    rhs_u = np.where(mask, rhs_u, 0.0)
+    rhs_u = predictor_rhs(g, dt, u_n, u_nm1, p_n, sys.R @ F_n,
+                          np.asarray(f_body, dtype=np.float64), with_advection)
     u_star = helmholtz.solve(g, rhs_u, a, nu, workers=workers)
 
     rhs_p = a * mac.apply_GT(g, u_star)

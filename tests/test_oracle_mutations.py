@@ -69,6 +69,33 @@ MUTATIONS = [
     ("RHS_F: U^Gamma added", step, "step", "sys.R.T @ u_star - U_gamma",
      "sys.R.T @ u_star + U_gamma", "test_oracle_step", "test_post_update_identities",
      ("exact",)),
+    ("predictor: BDF2 weight of u^n", step, "predictor_rhs", "(4.0 * u_n - u_nm1)",
+     "(3.0 * u_n - u_nm1)", "test_oracle_step", "test_linear_in_time_solution_is_reproduced",
+     (False,)),
+    ("predictor: BDF2 weight of u^{n-1} dropped", step, "predictor_rhs",
+     "(4.0 * u_n - u_nm1)", "(4.0 * u_n - 0.0 * u_nm1)",
+     "test_oracle_step", "test_linear_in_time_solution_is_reproduced", (False,)),
+    ("predictor: history levels swapped", step, "predictor_rhs", "(4.0 * u_n - u_nm1)",
+     "(4.0 * u_nm1 - u_n)", "test_oracle_step", "test_linear_in_time_solution_is_reproduced",
+     (False,)),
+    ("predictor: dt in place of 2 dt", step, "predictor_rhs", "/ (2.0 * dt)", "/ dt",
+     "test_oracle_step", "test_linear_in_time_solution_is_reproduced", (False,)),
+    ("predictor: sign of G p^n", step, "predictor_rhs", "- mac.apply_G(g, p_n)",
+     "+ mac.apply_G(g, p_n)", "test_oracle_step", "test_linear_in_time_solution_is_reproduced",
+     (False,)),
+    ("predictor: sign of R F^n", step, "predictor_rhs", "+ RF_n +", "- RF_n +",
+     "test_oracle_step", "test_linear_in_time_solution_is_reproduced", (False,)),
+    ("predictor: body force dropped", step, "predictor_rhs", "+ f_body", "+ 0.0 * f_body",
+     "test_oracle_step", "test_linear_in_time_solution_is_reproduced", (False,)),
+    ("predictor: sign of the convective term", step, "predictor_rhs",
+     "rhs = rhs - advection(g, u_n)", "rhs = rhs + advection(g, u_n)",
+     "test_oracle_step", "test_linear_in_time_solution_is_reproduced", (True,)),
+    ("predictor: sign of the convective term (analytic pin)", step, "predictor_rhs",
+     "rhs = rhs - advection(g, u_n)", "rhs = rhs + advection(g, u_n)",
+     "test_oracle_step", "test_convective_term_drives_the_step_with_minus_sign", ()),
+    ("predictor: convective term at u^{n-1}", step, "predictor_rhs",
+     "rhs = rhs - advection(g, u_n)", "rhs = rhs - advection(g, u_nm1)",
+     "test_oracle_step", "test_linear_in_time_solution_is_reproduced", (True,)),
     ("advection: one-sided centre value", step, "advection",
      "cc = 0.5 * (ud[tuple(lo)] + ud[tuple(hi)])", "cc = ud[tuple(hi)]",
      "test_oracle_step", "test_advection_conserves_energy_for_divergence_free_fields", ()),

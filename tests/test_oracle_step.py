@@ -109,3 +109,85 @@ def test_body_force_torque_closed_form():
     expect = 1e-3 * np.array([[1.0, 2.0, 0.0, -0.2, 0.0, -0.2],
                               [0.0, 0.0, 3.0, 0.0, -0.3, 0.0]])
     np.testing.assert_allclose(out, expect, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("with_advection", [False, True])
+def test_linear_in_time_solution_is_reproduced(with_advection):
+    # A state that moves linearly in time, u(t) = u_s + t w with u_s and w
+    # discretely divergence-free, constant p_s and F_s, is an exact solution of
+    # the discrete momentum equation u_t - nu Lap_h u + G p - R F + A = f when
+    # f is defined by it: BDF2 differentiates linear functions exactly, and
+    # with U^Gamma = R^T u^{n+1} and G^T u^{n+1} = 0 the correction system has
+    # a zero right-hand side.  So one step from (u^n, u^{n-1}) = (u_s, u_s - dt w),
+    # p^n = p_s, F^n = F_s must return u^{n+1} = u_s + dt w with p' = F' = 0.
+    # The forcing is built from the momentum equation (Sec. 2.1, Eq. (IBM_eq)
+    # form: time derivative, viscous term, pressure gradient, IB force,
+    # convective term), not from the predictor's right-hand side, so a wrong
+    # BDF2 weight, a flipped -G p^n, +R F^n or -A(u^n), or a dropped f fails.
+    W = wl.spheres_workload("t", 12, 100, 0.01, [[0.5] * 3], [0.25], None, 5)
+    g = mac.Grid(12)
+    from oracle import helmholtz
+    from oracle.schur import SchurSystem
+    rng = np.random.default_rng(11)
+    dt, nu = W.dt, 1.0 / W.Re
+    u_s = _curl_field(g, rng) * 0.05
+    w = _curl_field(g, rng) * 0.5
+    p_s = mac.remove_mean(rng.standard_normal(g.m))
+    F_s = rng.standard_normal(3 * W.X.shape[1])
+    u_nm1, u_n, u_np1 = u_s - dt * w, u_s, u_s + dt * w
+    sys = SchurSystem(g, W.X)
+    mask = g.interior_face_mask_packed()
+    conv = step.advection(g, u_n) if with_advection else 0.0
+    f = np.where(mask, w + helmholtz.apply(g, u_np1, 0.0, nu) + mac.apply_G(g, p_s)
+                 - sys.R @ F_s + conv, 0.0)
+    U = sys.R.T @ u_np1
+    assert np.abs(mac.apply_GT(g, u_np1)).max() < 1e-10 * np.abs(w).max()
+    out = step.step(g, W.Re, dt, W.X, U, f, u_n=u_n, u_nm1=u_nm1, p_n=p_s, F_n=F_s,
+                    with_advection=with_advection)
+    np.testing.assert_allclose(out["u"], u_np1, rtol=0, atol=1e-11 * np.abs(u_np1).max())
+    assert np.abs(out["p_corr"]).max() <= 1e-11 * np.abs(p_s).max()
+    assert np.abs(out["F_corr"]).max() <= 1e-11 * np.abs(F_s).max()
+    np.testing.assert_allclose(out["p"], p_s, rtol=0, atol=1e-11 * np.abs(p_s).max())
+    np.testing.assert_allclose(out["F"], F_s, rtol=0, atol=1e-11 * np.abs(F_s).max())
+
+
+def test_convective_term_drives_the_step_with_minus_sign():
+    # Inviscid limit, no markers, no pressure or forcing, equal history
+    # u^n = u^{n-1} = u0 discretely divergence-free: the predictor gives
+    # u* = u0 - A(u0)/a and the projection removes its gradient part, so
+    # (u^{n+1} - u0)/dt = -(2/3) P[(u.grad)u] with a = 3/(2 dt) and
+    # P v = v - G L^+ G^T v.  Compared with the analytic (u.grad)u of the
+    # field u = curl(0, 0, psi) (second-order agreement of the discrete field
+    # and the discrete convective term), a sign error is off by 200%.
+    sympy = pytest.importorskip("sympy")
+    x, y, z = sympy.symbols("x y z")
+    psi = sympy.sin(sympy.pi * x) ** 2 * sympy.sin(sympy.pi * y) ** 2 * (
+        1 + sympy.sin(sympy.pi * z) / 2)
+    uvec = [sympy.diff(psi, y), -sympy.diff(psi, x), sympy.Integer(0)]
+    conv = [sum(uvec[e] * sympy.diff(uvec[d], v) for e, v in enumerate((x, y, z)))
+            for d in range(3)]
+    conv_f = [sympy.lambdify((x, y, z), c, "numpy") for c in conv]
+    psi_f = sympy.lambdify((x, y, z), psi, "numpy")
+    rel = []
+    for n in (16, 32):
+        g = mac.Grid(n)
+        h = g.h
+        # psi on the z-edges (i h, j h, (k + 1/2) h); its discrete curl
+        kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n + 1), np.arange(n + 1),
+                                 indexing="ij")
+        Az = psi_f(ii * h, jj * h, (kk + 0.5) * h)
+        ux = (Az[:, 1:, :] - Az[:, :-1, :]) / h
+        uy = -(Az[:, :, 1:] - Az[:, :, :-1]) / h
+        uz = np.zeros((n + 1, n, n))
+        u0 = g.pack_faces(ux, uy, uz)
+        assert np.abs(mac.apply_GT(g, u0)).max() < 1e-10
+        A = g.pack_faces(*[np.broadcast_to(conv_f[d](*g.face_coords(d)), s.shape)
+                           for d, s in enumerate((ux, uy, uz))])
+        A = A * g.interior_face_mask_packed()
+        PA = A - mac.apply_G(g, mac.laplacian_pinv(g, mac.apply_GT(g, A)))
+        dt = 1e-3
+        out = step.step(g, 1e12, dt, np.zeros((3, 0)), np.zeros(0), np.zeros(g.n_faces),
+                        u_n=u0)
+        du = (out["u"] - u0) / dt
+        rel.append(np.linalg.norm(du + (2.0 / 3.0) * PA) / np.linalg.norm(PA))
+    assert rel[1] < 0.02 and rel[1] < 0.4 * rel[0], rel
