@@ -290,17 +290,25 @@ ibm_status ibm_body_forces(ibm_ctx* ctx, const double* F, const double* X,
  * [n_bodies][3], out host [n_bodies][6]; h the cell width; stream a
  * cudaStream_t (NULL = legacy default stream).  Synchronises the stream.
  *
- * Scratch: the device staging buffer is a fixed array inside the library of
- * IBM_NOALLOC_MAX_BODIES * 6 doubles (48 KiB) that every GPU loading the
- * library holds until the process exits.  No call allocates or frees memory.
- * The first call on each device looks up that device's address of the array
- * (with the device current), so make the first call on a device outside any
- * stream capture.  All calls share the array: calls whose work overlaps on the
- * GPU (different streams, or different host threads on one device) race and
- * must be serialised by the caller.  Every output slot is overwritten by each
- * call, so no clearing is needed between calls.
+ * Scratch: the device staging buffer (the centres going in, the sums coming
+ * out) is a fixed array inside the library of IBM_NOALLOC_MAX_BODIES * 9
+ * doubles (72 KiB) that every GPU loading the library holds until the process
+ * exits.  No call allocates or frees memory.  A call looks up the current
+ * device's address of that array (with the device current) the first time it
+ * runs on that device, and again after the device's context has changed (for
+ * example after cudaDeviceReset), so make the first call on a device outside
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls whose work overlaps on the GPU (different streams,
+ * or different host threads on one device) race and must be serialised by
+ * the caller.  Every centre and sum slot a call uses is written by that call,
+ * so no clearing is needed between calls.  One kernel launch, one block per
+ * body.  The call clears the calling thread's last CUDA runtime error before
+ * it launches, so that its own check sees only its own launch.
  * Returns IBM_ERR_ARG when n_bodies < 1 or n_bodies > IBM_NOALLOC_MAX_BODIES,
- * or a pointer is missing; IBM_ERR_CUDA on a CUDA failure. */
+ * h <= 0, a pointer is missing, F or X is not 8-byte aligned, body_id not
+ * 4-byte aligned, or F, X or body_id is not device (or managed) memory of the
+ * current device -- all before anything is launched; IBM_ERR_CUDA on a CUDA
+ * failure. */
 #define IBM_NOALLOC_MAX_BODIES 1024
 ibm_status ibm_body_forces_noalloc(const double* F, const double* X, const int32_t* body_id,
                                    int64_t n_markers, int32_t n_bodies, const double* centers,

@@ -53,9 +53,17 @@ namespace {
 
 constexpr int TPB = 256;
 
-__global__ void k_body_forces(const double* __restrict__ F, const double* __restrict__ X,
-                              const int32_t* __restrict__ bid, int64_t n, double cx, double cy,
-                              double cz, int body, double h3, double* __restrict__ out) {
+// Per body b (block b): out[6b..6b+2] = h^3 sum_{k in b} F_k and
+// out[6b+3..6b+5] = h^3 sum_{k in b} (X_k - c_b) x F_k (Eq. (IBM_force)),
+// c_b = cen[3b..3b+2].  Each block scans every marker and keeps its body's;
+// a fixed-order block reduction makes the sums reproducible.
+__global__ void __launch_bounds__(TPB) k_body_sums(const double* __restrict__ F,
+                                                   const double* __restrict__ X,
+                                                   const int32_t* __restrict__ bid, int64_t n,
+                                                   const double* __restrict__ cen, double h3,
+                                                   double* __restrict__ out) {
+  const int body = blockIdx.x;
+  const double cx = cen[3 * body], cy = cen[3 * body + 1], cz = cen[3 * body + 2];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
     if (bid[k] != body) continue;
@@ -74,7 +82,7 @@ __global__ void k_body_forces(const double* __restrict__ F, const double* __rest
       for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x < 6) out[threadIdx.x] = h3 * sh[threadIdx.x][0];
+  if (threadIdx.x < 6) out[6 * body + threadIdx.x] = h3 * sh[threadIdx.x][0];
 }
 
 __global__ void k_axpby_small(const double* __restrict__ x, double a, const double* __restrict__ y,
@@ -86,6 +94,12 @@ __global__ void k_axpby_small(const double* __restrict__ x, double a, const doub
 }  // namespace
 
 bool bad_ptr(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 7) != 0; }
+
+void launch_body_sums(const double* F, const double* X, const int32_t* bid, int64_t n,
+                      int n_bodies, const double* cen, double h3, double* out, cudaStream_t s) {
+  count_launch();
+  k_body_sums<<<n_bodies, TPB, 0, s>>>(F, X, bid, n, cen, h3, out);
+}
 
 ibm_status check_ctx(ibm_ctx* c) {
   if (!c) return IBM_ERR_ARG;
@@ -639,17 +653,17 @@ ibm_status ibm_body_forces(ibm_ctx* c, const double* F, const double* X, const i
     return set_err(c, IBM_ERR_ARG, "bad body arguments");
   if (n > 0 && (bad_ptr(F) || bad_ptr(X) || body_id == nullptr))
     return set_err(c, IBM_ERR_ARG, "bad marker pointers");
-  double* dout = c->red_part;   // n_bodies * 6 <= kRedBlocks * (kMaxRestart + 2)
+  // sums, then the centres: n_bodies * 9 <= kRedBlocks * (kMaxRestart + 2)
+  double* dout = c->red_part;
+  double* dcen = c->red_part + 6 * (int64_t)n_bodies;
   const double h3 = c->h * c->h * c->h;
   if (n == 0) {
     for (int q = 0; q < 6 * n_bodies; ++q) out[q] = 0.0;
     return IBM_OK;
   }
-  for (int b = 0; b < n_bodies; ++b) {
-    count_launch();
-    k_body_forces<<<1, TPB, 0, c->stream>>>(F, X, body_id, n, centers[3 * b], centers[3 * b + 1],
-                                             centers[3 * b + 2], b, h3, dout + 6 * b);
-  }
+  IBM_CUDA(c, cudaMemcpyAsync(dcen, centers, sizeof(double) * 3 * n_bodies,
+                              cudaMemcpyHostToDevice, c->stream));
+  launch_body_sums(F, X, body_id, n, n_bodies, dcen, h3, dout, c->stream);
   IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaMemcpyAsync(out, dout, sizeof(double) * 6 * n_bodies, cudaMemcpyDeviceToHost,
                               c->stream));

@@ -302,6 +302,13 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
 // Counts one kernel launch (process-wide counter, ibm_kernel_launches).
 void count_launch();
 
+// Per-body force and torque sums (Eq. (IBM_force)) in one launch of n_bodies
+// blocks: out[6b..6b+5] = h3 (sum F, sum (X - c_b) x F) over the markers with
+// bid == b; cen: device [n_bodies][3].  Shared by ibm_body_forces and its
+// allocation-free variant.
+void launch_body_sums(const double* F, const double* X, const int32_t* bid, int64_t n,
+                      int n_bodies, const double* cen, double h3, double* out, cudaStream_t s);
+
 // Records a start event for class cls (returns a handle, -1 when off) and the
 // matching end event.
 int prof_begin(ibm_ctx* c, int cls);

@@ -125,6 +125,24 @@ def test_noalloc_argument_checks_need_no_gpu(built_lib):
     assert list(out[:18]) == [0.0] * 18 and out[18] == 7.0
 
 
+def test_noalloc_refuses_misaligned_and_host_pointers_before_any_launch(built_lib):
+    # F, X must be 8-byte aligned, body_id 4-byte aligned, and all three
+    # device memory of the current device; otherwise IBM_ERR_ARG comes back
+    # before anything is launched (here without a GPU: the pointer checks
+    # themselves need no device)
+    from paper_2501_15314_gb300 import _lib
+    fn = built_lib.ibm_body_forces_noalloc
+    centers = (C.c_double * 3)()
+    out = (C.c_double * 6)()
+    host = (C.c_double * 64)()
+    a = C.addressof(host)
+    assert a % 8 == 0
+    launches = built_lib.ibm_kernel_launches()
+    for F, X, bid in ((a + 4, a, a), (a, a + 2, a), (a, a, a + 2), (a, a, a)):
+        assert fn(F, X, bid, 5, 1, centers, 0.1, None, out) == _lib.IBM_ERR_ARG
+    assert built_lib.ibm_kernel_launches() == launches
+
+
 def test_every_context_call_rejects_a_null_context(built_lib):
     # every entry point taking an ibm_ctx returns IBM_ERR_ARG for NULL before
     # any CUDA call (all other arguments zero or NULL)

@@ -59,3 +59,52 @@ def test_noalloc_rejects_too_many_bodies(cuda_device):
                                      centers.ctypes.data_as(C.POINTER(C.c_double)), 0.1, None,
                                      out.ctypes.data_as(C.POINTER(C.c_double)))
     assert st == _lib.IBM_ERR_ARG
+
+
+def test_noalloc_refuses_misaligned_and_host_pointers(cuda_device):
+    # refused with IBM_ERR_ARG before any launch: a device pointer off its
+    # 8-byte alignment, and host memory the kernel must not be given
+    import torch
+    from paper_2501_15314_gb300 import _lib
+    lib = _lib.load()
+    n = 8
+    F = torch.zeros(3 * n + 1, dtype=torch.float64, device="cuda")
+    X = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    bid = torch.zeros(n, dtype=torch.int32, device="cuda")
+    Fh = torch.zeros(3 * n, dtype=torch.float64)
+    centers = np.zeros((1, 3))
+    out = np.zeros((1, 6))
+    cp = centers.ctypes.data_as(C.POINTER(C.c_double))
+    op = out.ctypes.data_as(C.POINTER(C.c_double))
+    l0 = lib.ibm_kernel_launches()
+    for f, x, b in ((F.data_ptr() + 4, X.data_ptr(), bid.data_ptr()),
+                    (F.data_ptr(), X.data_ptr(), bid.data_ptr() + 2),
+                    (Fh.data_ptr(), X.data_ptr(), bid.data_ptr())):
+        assert lib.ibm_body_forces_noalloc(f, x, b, n, 1, cp, 0.1, None, op) == _lib.IBM_ERR_ARG
+    assert lib.ibm_kernel_launches() == l0
+    torch.cuda.synchronize()
+
+
+def test_noalloc_at_the_body_limit(cuda_device):
+    # IBM_NOALLOC_MAX_BODIES bodies, markers assigned at random, against the
+    # context call on the same inputs, twice in a row
+    import torch
+    from paper_2501_15314_gb300 import _lib
+    from paper_2501_15314_gb300.api import IBMSolver
+    rng = np.random.default_rng(7)
+    nb, nm = 1024, 5000
+    case = gc.ragged_multi()
+    s = IBMSolver(case.nx, case.ny, case.nz, case.h, Re=case.Re, dt=case.dt)
+    Xh = case.X[:, rng.integers(0, case.N, nm)] + 1e-3 * rng.standard_normal((3, nm))
+    s.set_markers(dev(np.ascontiguousarray(Xh)))
+    X = dev(np.ascontiguousarray(Xh).ravel())
+    bid = dev(rng.integers(0, nb, nm).astype(np.int32))
+    centers = rng.uniform(0.3, 0.7, (nb, 3))
+    for call in range(2):
+        F = dev(rng.standard_normal(3 * nm) * (3.0 ** call))
+        ref = s.body_forces(F, X, bid, centers)
+        st, out = _noalloc(s.lib, F, X, bid, nm, centers, case.h, s.stream)
+        assert st == _lib.IBM_OK
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-300)
+    s.close()
+    torch.cuda.synchronize()
