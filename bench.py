@@ -11,16 +11,18 @@ FGMRES to a relative residual of 1e-8.
 A step = marker binning (ibm_set_markers) + ibm_step (predictor, correction
 right-hand sides, Schur solve, force recovery, update, diagnostics): every
 row of the hot path, one Schur solve per step, so steps/s = Schur solves/s.
-The headline `value` uses the mixed form (FP32 V-cycle, double-single Arnoldi
-process, FP64 true residual); the plain FP64 form (FP64 V-cycle and Arnoldi)
-and the solve alone are reported beside it.
+The headline `value` uses the mixed form (FP32 V-cycle, FP32 Arnoldi cycles
+refined by the FP64 true residual); beside it the same step with the FP64
+outer iteration and the FP32 V-cycle, the plain FP64 form (FP64 V-cycle and
+Arnoldi), the solve alone, and (from the oracle leg) each form's error
+against the oracle's step solved to 1e-13.
 
 `--profile-step` runs one warm-up step and then one step bracketed by
 cudaProfilerStart/Stop (for `ncu --profile-from-start off`), and exits.
 
 Multi-GPU: replicas only (one independent workload per rank, no collective on
 the data path); `value` sums the ranks' step rates over the slowest rank's
-time.  `--impl reference` times the CPU oracle on a bounded sample of the same
+time.  `--impl reference` times whole steps of the CPU oracle on the same
 workload (rank 0 only).
 """
 from __future__ import annotations
@@ -40,8 +42,6 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "Schur solves/s at 256^3 to 1e-8 residual, FP32-precond vs FP64; HBM fraction"
 UNIT = "solves/s"
-SAMPLE_ITERS = 3           # FGMRES iterations per step of the reference arm's sample
-BASELINE_SAMPLE_ITERS = 6  # FGMRES iterations in the cpu_baseline sample (10-20 s of work)
 
 # DRAM traffic / algorithmic bytes of each timed kernel class, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of every launch of one
@@ -194,39 +194,49 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_sample(W, n_iters_full, sample_iters=SAMPLE_ITERS):
-    """Bounded CPU sample of one oracle step: setup, predictor and right-hand
-    sides, sample_iters FGMRES iterations (exact L^+ by DCT), force recovery
-    and update.  Returns (estimated seconds per full step, detail)."""
-    import numpy as np
-    from oracle import helmholtz, mac, schur
+def oracle_step(W, rtol=1e-8):
+    """One whole oracle step of the workload on the host cores (marker
+    operators, predictor, right-hand sides, FGMRES with the exact L^+ to rtol,
+    force recovery, update, diagnostics), timed on the wall clock.  Returns
+    (seconds, the oracle's step dict, worker threads)."""
+    from oracle import mac, step
     workers = len(os.sched_getaffinity(0))
     t0 = time.perf_counter()
     g = mac.Grid(W.n)
-    sysm = schur.SchurSystem(g, W.X)
-    a = 1.5 / W.dt
-    rhs = W.f_body * g.interior_face_mask_packed()
-    us = helmholtz.solve(g, rhs, a, 1.0 / W.Re, workers=workers)
-    rhs_F = a * (sysm.R.T @ us - W.U_gamma.ravel())
-    b = sysm.rhs_scalar(a * mac.apply_GT(g, us), rhs_F)
-    t1 = time.perf_counter()
-    x, it, rel, _ = schur.fgmres(sysm.apply_S_tilde, b,
-                                 lambda r: mac.laplacian_pinv(g, r, workers=workers),
-                                 rtol=1e-8, restart=60, maxit=sample_iters)
-    t2 = time.perf_counter()
-    Fc = sysm.force_scalar(x, rhs_F)
-    u = us + (2.0 * W.dt / 3.0) * (-mac.apply_G(g, x) + sysm.R @ Fc)
-    t3 = time.perf_counter()
-    est = (t1 - t0) + (t2 - t1) / sample_iters * n_iters_full + (t3 - t2)
-    return est, dict(setup_predictor_s=t1 - t0, sample_iters=sample_iters,
-                     sample_solve_s=t2 - t1, update_s=t3 - t2, sample_wall_s=t3 - t0,
-                     workers=workers, est_step_s=est, iters_full=n_iters_full, _u=float(u[0]))
+    out = step.step(g, W.Re, W.dt, W.X, W.U_gamma, W.f_body, rtol=rtol, workers=workers)
+    return time.perf_counter() - t0, out, workers
 
 
-def oracle_iterations(cfg):
-    p = ROOT / "oracle" / "iteration_counts.json"
-    d = json.loads(p.read_text())
-    return int(d[f"config{cfg}_stated_markers_rtol1e-8"])
+def oracle_errors(ref, got):
+    """Errors of a GPU step's (u, p, F) against the oracle's: relative 2-norm
+    of the difference, the largest element difference relative to the
+    largest element of the oracle's field, and the same on the shell cells
+    (cells coupled to the markers through B = R^T G) and shell faces (faces
+    in the support of R), where the marker terms act."""
+    import numpy as np
+    sysm = ref["sys"]
+    g = sysm.g
+    shell_f = np.unique(sysm.R.tocoo().row)
+    ind = np.zeros(g.n_faces)
+    ind[shell_f] = 1.0
+    cells = np.zeros((g.nz, g.ny, g.nx), dtype=bool)
+    for d, comp in enumerate(g.split_faces(ind)):
+        ax = 2 - d
+        nd = comp.shape[ax] - 1
+        cells |= np.take(comp, np.arange(nd), axis=ax) > 0
+        cells |= np.take(comp, np.arange(1, nd + 1), axis=ax) > 0
+    shell_c = np.flatnonzero(cells.ravel())
+    res = {}
+    for key, sel in (("u", shell_f), ("p", shell_c), ("F", None)):
+        a = np.asarray(got[key], dtype=np.float64)
+        b = np.asarray(ref[key], dtype=np.float64)
+        d = np.abs(a - b)
+        e = {"rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+             "max_abs_rel": float(d.max() / np.abs(b).max())}
+        if sel is not None and sel.size:
+            e["shell_max_abs_rel"] = float(d[sel].max() / np.abs(b).max())
+        res[key] = e
+    return res
 
 
 def cpu_model():
@@ -265,19 +275,20 @@ def run_reference(args):
         return 0
     from paper_2501_15314_gb300 import workloads as wl
     W = wl.config(args.config, secondary=True)
-    n_it = oracle_iterations(args.config)
     for _ in range(args.warmup):
-        oracle_sample(W, n_it)
-    ests, details = [], []
+        oracle_step(W)
+    secs, iters = [], []
     for _ in range(args.steps):
-        e, d = oracle_sample(W, n_it)
-        ests.append(e)
-        details.append(d)
-    value = len(ests) / sum(ests)
-    cores = details[-1]["workers"]
-    sample = (f"per step: oracle setup + predictor + RHS, {SAMPLE_ITERS} of {n_it} FGMRES "
-              f"iterations (exact L^+ by DCT), force recovery and update at the full workload; "
-              f"solve time scaled by {n_it}/{SAMPLE_ITERS}")
+        t, out, cores = oracle_step(W)
+        secs.append(t)
+        iters.append(int(out["iters"]))
+        del out
+    value = len(secs) / sum(secs)
+    sample = (f"whole oracle steps at the full workload, each timed on the wall clock: "
+              f"marker operators, predictor, right-hand sides, FGMRES with the exact L^+ "
+              f"(DCT) to rtol 1e-8 ({min(iters)}-{max(iters)} iterations, all run), force "
+              f"recovery, update, diagnostics; scipy.fft workers = {cores}, sparse products "
+              f"single-threaded")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -353,11 +364,21 @@ def run_ours(args):
     launches = lib.ibm_kernel_launches() - l0
     s.profile_enable(False)
     clk = clocks.stop()
+    # each form's step result (every timed step repeats the same step), kept
+    # on the host for the comparison with the oracle's solution
+    to_host = lambda: {kk: v.cpu().numpy().copy() for kk, v in out.items()}  # noqa: E731
+    results = {"headline_fp32_vcycle_fp32_arnoldi": to_host()}
+
+    # ---- FP64 outer iteration with the FP32 V-cycle (FP64 Arnoldi) ----
+    k64 = max(1, args.steps // 2)
+    step(_lib.IBM_PREC_FP32, _lib.IBM_ARNOLDI_FP64)
+    ms_ns, st_ns = timed(lambda: step(_lib.IBM_PREC_FP32, _lib.IBM_ARNOLDI_FP64), k64)
+    results["fp32_vcycle_fp64_arnoldi"] = to_host()
 
     # ---- FP64 form (FP64 V-cycle, FP64 Arnoldi) ----
-    k64 = max(1, args.steps // 2)
     step(_lib.IBM_PREC_FP64, _lib.IBM_ARNOLDI_FP64)
     ms_fp64, st_fp64 = timed(lambda: step(_lib.IBM_PREC_FP64, _lib.IBM_ARNOLDI_FP64), k64)
+    results["fp64_form"] = to_host()
 
     # ---- the solve alone, on a right-hand side of the step's form ----
     a = 1.5 / W.dt
@@ -484,7 +505,13 @@ def run_ours(args):
             "config": workload_config(W),
             "fp64_form": {"value": job_rate(world, ms_fp64), "unit": UNIT, "ms_per_step": ms_fp64,
                           "iters": st_fp64[-1]["iters"],
+                          "relres_true": st_fp64[-1]["relres_true"],
                           "what": "FP64 V-cycle + FP64 Arnoldi, same step"},
+            "fp32_vcycle_fp64_arnoldi": {
+                "value": job_rate(world, ms_ns), "unit": UNIT, "ms_per_step": ms_ns,
+                "iters": st_ns[-1]["iters"], "relres_true": st_ns[-1]["relres_true"],
+                "what": ("same step; outer FGMRES, residuals and Schur products in FP64, "
+                         "V-cycle preconditioner in FP32 with FP32 accumulation")},
             "solve_only": solve_only,
             "iters": st_mixed[-1]["iters"], "relres_true": st_mixed[-1]["relres_true"],
             "helm_iters": st_mixed[-1]["helm_iters"],
@@ -500,14 +527,29 @@ def run_ours(args):
                               "own, pipelined with the steps (double-buffered)",
                     "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, det = oracle_sample(W, oracle_iterations(args.config), BASELINE_SAMPLE_ITERS)
+        # the oracle on the host cores: one whole step at the metric's
+        # tolerance, timed; then (untimed) the same step solved to 1e-13, the
+        # reference each GPU form's result is compared with
+        t8, o8, cores = oracle_step(W, 1e-8)
+        it8 = int(o8["iters"])
+        del o8
+        t13, o13, _ = oracle_step(W, 1e-13)
         line["cpu_baseline"] = {
-            "value": 1.0 / est, "unit": UNIT, "cores": det["workers"], "kind": "oracle",
-            "sample": (f"one oracle step at the full workload with {det['sample_iters']} of "
-                       f"{det['iters_full']} FGMRES iterations run (scipy.fft workers = "
-                       f"{det['workers']}, sparse products single-threaded), solve time "
-                       f"scaled to the full count; {det['sample_wall_s']:.1f} s of CPU work"),
+            "value": 1.0 / t8, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one whole oracle step at the full workload, timed on the wall clock "
+                       f"({t8:.1f} s): marker operators, predictor, right-hand sides, FGMRES "
+                       f"with the exact L^+ (DCT) to rtol 1e-8 ({it8} iterations, all run), "
+                       f"force recovery, update, diagnostics; scipy.fft workers = {cores}, "
+                       f"sparse products single-threaded"),
             "cpu": cpu_model()}
+        line["oracle_error"] = {
+            "reference": (f"oracle step solved to rtol 1e-13 ({int(o13['iters'])} FGMRES "
+                          f"iterations, {t13:.1f} s); errors of each GPU form's step result "
+                          f"(rtol 1e-8): relative 2-norm, and the largest element difference "
+                          f"over the largest oracle element, over all and on the shell "
+                          f"cells/faces"),
+            **{name: oracle_errors(o13, r) for name, r in results.items()}}
+        del o13
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()

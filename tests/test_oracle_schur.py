@@ -103,13 +103,3 @@ def test_unpreconditioned_needs_many_more_iterations():
                                  maxit=400)
     assert it_u > 8 * it_p
 
-
-def test_stored_iteration_count_is_the_oracles():
-    # oracle/iteration_counts.json is written by oracle/iteration_count.py;
-    # the 32^3 entry is recomputed here (the 256^3 one takes a minute)
-    import json
-    from pathlib import Path
-    from oracle import iteration_count
-    stored = json.loads((Path(iteration_count.__file__).parent
-                         / "iteration_counts.json").read_text())
-    assert iteration_count.count(1) == stored["config1_stated_markers_rtol1e-8"]
