@@ -261,7 +261,15 @@ ibm_status ibm_apply_c_inverse(ibm_ctx* ctx, const double* t, double* s, double 
  *   6. diagnostics ||G^T u^{n+1}||, ||R^T u^{n+1} - U_gamma|| into stats.
  * Inputs u_n, u_nm1 (faces), p_n (cells), F_n, U_gamma ([3][n_markers]),
  * f_body (faces; may be NULL for none).  Outputs u_np1, p_np1, F_np1 must not
- * alias the inputs.  Synchronises like ibm_solve_schur. */
+ * alias the inputs.  Synchronises like ibm_solve_schur.
+ * Input range: the predictor reads u_n, u_nm1, p_n and f_body as pairs of
+ * FP32 numbers (hi + lo, within 2^-46 relative), split with integer
+ * operations; an entry with |x| < 2^-80 (about 8.3e-25) is read as 0 and one
+ * with |x| >= 2^101 (about 2.5e30) as +-infinity (then IBM_ERR_NAN).  So an
+ * entry is lost only where it is below 2^-80 in absolute value: a field whose
+ * entries that matter are all above that (any flow in units where velocities
+ * and pressures are not below about 1e-20) is read to 2^-46 relative.  The
+ * same holds for ibm_fsi_step and the predictor solve of ibm_adjoint_step. */
 ibm_status ibm_step(ibm_ctx* ctx, const double* u_n, const double* u_nm1,
                     const double* p_n, const double* F_n, const double* U_gamma,
                     const double* f_body, double* u_np1, double* p_np1,

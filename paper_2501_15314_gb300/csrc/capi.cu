@@ -46,7 +46,25 @@ int prof_begin(ibm_ctx* c, int cls) {
 void prof_end(ibm_ctx* c, int h, double bytes) {
   if (h < 0) return;
   c->prof[h].bytes = bytes;
+  c->prof_acc += bytes;
   cudaEventRecord(c->prof[h].b, c->stream);
+}
+
+void prof_note(ibm_ctx* c, double bytes) {
+  if (c->prof_on) c->prof_acc += bytes;
+}
+
+double prof_mark(const ibm_ctx* c) { return c->prof_acc; }
+
+void prof_end_span(ibm_ctx* c, int h, double mark) {
+  if (h < 0) return;
+  c->prof[h].bytes = c->prof_acc - mark;
+  cudaEventRecord(c->prof[h].b, c->stream);
+}
+
+void prof_end_or_note(ibm_ctx* c, int h, double bytes) {
+  if (h >= 0) prof_end(c, h, bytes);
+  else prof_note(c, bytes);
 }
 
 namespace {
@@ -186,7 +204,7 @@ static void free_all(ibm_ctx* c) {
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
   cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc); cudaFree(m.cg);
   cudaFree(m.t3); cudaFree(c->cg_scal);
-  cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off);
+  cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_cell);
   cudaFree(m.ell_base); cudaFree(m.ell_len); cudaFree(m.ell_key); cudaFree(m.ell_coef);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
@@ -483,9 +501,10 @@ ibm_status ibm_solve_schur(ibm_ctx* c, const double* b, double* p, const ibm_sol
   if ((s = ensure_krylov(c, o->restart)) != IBM_OK) return s;
   if (st) memset(st, 0, sizeof(*st));
   set_cmode(c, o);
+  const double mk0 = prof_mark(c);
   const int ph = prof_begin(c, IBM_PROF_SOLVE);
   s = fgmres_solve(c, b, p, o, st);
-  prof_end(c, ph);
+  prof_end_span(c, ph, mk0);
   if (st) st->c_iters = c->c_iters;
   set_cmode(c, nullptr);
   return s;
@@ -562,9 +581,10 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   // 3. Schur solve for p' (into c3, zero initial guess)
   double* pc = c->c3;
   launch_zero(pc, sizeof(double) * c->m, str);
+  const double mk0 = prof_mark(c);
   ph = prof_begin(c, IBM_PROF_SOLVE);
   s = fgmres_solve(c, c->c2, pc, o, st, true);
-  prof_end(c, ph);
+  prof_end_span(c, ph, mk0);
   if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
   const ibm_status solve_status = s;
 
@@ -625,6 +645,7 @@ ibm_status ibm_profile_enable(ibm_ctx* c, int32_t on) {
   IBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->prof_on = on != 0;
   c->prof_used = 0;
+  c->prof_acc = 0.0;
   return IBM_OK;
 }
 

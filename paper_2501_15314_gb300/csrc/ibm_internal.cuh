@@ -72,9 +72,10 @@ struct MarkerData {
   // cell-sorted (marker, slot) list for the atomic-free gathers
   int64_t n_entries = 0, entries_cap = 0;
   int32_t* entry_key = nullptr;   // marker * 64 + slot, sorted within a cell
-  // the same entries re-laid out for the B^T t gather: shell cells in groups
-  // of 32 (one warp), group w padded to its longest segment L_w and stored
-  // interleaved, entry p of lane l at ell_base[w] + 32 p + l
+  // the same entries re-laid out for the B^T t gather: shell cells (in the
+  // order of ell_cell) in groups of 32 (one warp), group w padded to its
+  // longest segment L_w and stored interleaved, entry p of lane l at
+  // ell_base[w] + 32 p + l
   int64_t n_ell = 0, ell_cap = 0;
   int32_t* ell_key = nullptr;
   double* ell_coef = nullptr;     // [3][n_ell] G^T R coefficients (0 on padding)
@@ -83,6 +84,10 @@ struct MarkerData {
   int64_t n_shell = 0;
   int32_t* shell_cell = nullptr;  // [n_shell] cells touched by any marker
   int32_t* shell_off = nullptr;   // [n_shell + 1] segment offsets
+  // the shell cells in the order of the interleaved layout: within each
+  // window of 1024 (32 groups) sorted by entry count, longest first, so that
+  // the cells of a group have nearly equal counts and little padding
+  int32_t* ell_cell = nullptr;    // [n_shell]
   double* t = nullptr;            // [3][n] per-marker scratch
   double* t2 = nullptr;           // [3][n] per-marker scratch
 };
@@ -152,6 +157,7 @@ struct ibm_ctx {
 
   // event timing of kernel classes (ibm_profile_enable)
   bool prof_on = false;
+  double prof_acc = 0.0;   // algorithmic bytes counted while profiling
   struct ProfRec {
     int cls;
     cudaEvent_t a, b;
@@ -162,6 +168,16 @@ struct ibm_ctx {
 };
 
 namespace ibm {
+
+// Algorithmic bytes of the marker term of one Schur product (each array read
+// or written once): per marker its tap bases, Roma weights and G-weighted
+// weights (192 B), t written and read back (24 + 24 B); per cell-sorted entry
+// its key and three G^T R coefficients (28 B); per shell cell the input value
+// (sz_in), the cell index and the output read and written (2 sz_out).
+inline double marker_term_bytes(const ibm_ctx* c, int sz_in, int sz_out) {
+  return (double)c->mk.n * 240.0 + (double)c->mk.n_entries * 28.0 +
+         (double)c->mk.n_shell * (sz_in + 4 + 2 * sz_out);
+}
 
 // ---- error helpers (host) ----
 ibm_status set_err(ibm_ctx* c, ibm_status s, const std::string& msg);
@@ -315,6 +331,15 @@ int prof_begin(ibm_ctx* c, int cls);
 // bytes: the algorithmic DRAM bytes of the timed kernels (each array read or
 // written once), summed per class by ibm_profile_read
 void prof_end(ibm_ctx* c, int handle, double bytes = 0.0);
+// Algorithmic bytes of kernels outside any timed class (while profiling):
+// they count towards the enclosing span (prof_end_span).
+void prof_note(ibm_ctx* c, double bytes);
+// prof_end for a class whose bytes are those counted (prof_end, prof_note)
+// since prof_mark returned `mark`: the V-cycle, the solve, the step.
+double prof_mark(const ibm_ctx* c);
+void prof_end_span(ibm_ctx* c, int handle, double mark);
+// prof_end when the class is timed (handle >= 0), else prof_note.
+void prof_end_or_note(ibm_ctx* c, int handle, double bytes);
 
 // Sum over one shell cell's entries of the interleaved layout (entry p of the
 // cell at idx + 32 p): sum_p sum_e coef_e[p] t_e[marker(p)], FP64 FMAs in

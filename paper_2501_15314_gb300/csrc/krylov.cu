@@ -301,7 +301,7 @@ ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
     if (s != IBM_OK) { prof_end(c, ph); return s; }
     launch_shell_gradt_spread(c, c->mk.t2, c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0, out);
   }
-  prof_end(c, ph);
+  prof_end(c, ph, c->mk.n > 0 ? marker_term_bytes(c, 8, 8) : 0.0);
   IBM_LAUNCH_CHECK(c);
   return IBM_OK;
 }
@@ -343,6 +343,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
 
   // ||b||
   launch_dot(b, b, m, part, sdev, s);
+  prof_note(c, 8.0 * m);
   IBM_LAUNCH_CHECK(c);
   if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
   const double bnorm = std::sqrt(hr[0]);
@@ -368,11 +369,13 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
     if (first && x_is_zero) {
       launch_copy(V, b, sizeof(double) * m, s);
       launch_copy(nrm2, sdev, sizeof(double), s);
+      prof_note(c, 16.0 * m);
       beta = bnorm;
     } else {
       if ((stt = schur_apply(c, x, V)) != IBM_OK) return stt;
       launch_axpby(b, 1.0, V, -1.0, V, m, s);
       launch_dot(V, V, m, part, nrm2, s);
+      prof_note(c, 32.0 * m);
       IBM_LAUNCH_CHECK(c);
       if ((stt = fetch(c, nrm2, 1)) != IBM_OK) return stt;
       beta = std::sqrt(hr[0]);
@@ -391,10 +394,11 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
       double* vj = V + (int64_t)j * m;
       double* zj = Z + (int64_t)j * m;
       double* w = V + (int64_t)(j + 1) * m;
+      const double mk0 = prof_mark(c);
       int ph = prof_begin(c, IBM_PROF_VCYCLE);
       if ((stt = mg_vcycle(c, vj, zj, o->precond_prec, o->mg_pre, o->mg_post)) != IBM_OK)
         return stt;
-      prof_end(c, ph);
+      prof_end_span(c, ph, mk0);
       if ((stt = schur_apply(c, zj, w)) != IBM_OK) return stt;
       ph = prof_begin(c, IBM_PROF_MULTIDOT);
       launch_multidot(w, V, m, j + 1, m, part, raw, s, nrm2, coef, hmirror(c, hr));
@@ -442,6 +446,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
         y[i] = acc / Hm(i, i);
       }
       launch_gemv_acc(x, Z, m, jused, y.data(), m, s);
+      prof_note(c, 8.0 * (jused + 2) * (double)m);
       IBM_LAUNCH_CHECK(c);
     }
     ++cycles;
@@ -450,6 +455,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   // mean-zero projection (S~ annihilates constants)
   launch_sum(x, m, part, sdev, s);
   launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
+  prof_note(c, 24.0 * m);
   IBM_LAUNCH_CHECK(c);
   if (st) {
     st->iters = total;

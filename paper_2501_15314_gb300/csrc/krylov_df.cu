@@ -599,9 +599,9 @@ ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
     }
     count_launch();
     k_shell_gradt_ds<TW><<<div_up(m.n_shell, 256), 256, 0, s>>>(
-        m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
+        m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
         sign, w);
-    prof_end(c, ph);
+    prof_end(c, ph, marker_term_bytes(c, 4, (int)sizeof(TW)));
   }
   IBM_LAUNCH_CHECK(c);
   return IBM_OK;
@@ -644,6 +644,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   ibm_status stt;
 
   launch_dot(b, b, m, part, sdev, s);
+  prof_note(c, 8.0 * m);
   IBM_LAUNCH_CHECK(c);
   if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
   const double bnorm = std::sqrt(hr[0]);
@@ -671,6 +672,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       if ((stt = schur_apply(c, x, r64)) != IBM_OK) return stt;
       launch_axpby(b, 1.0, r64, -1.0, r64, m, s);
       launch_dot(r64, r64, m, part, nrm2, s);
+      prof_note(c, 32.0 * m);
       IBM_LAUNCH_CHECK(c);
       if ((stt = fetch(c, nrm2, 1)) != IBM_OK) return stt;
       beta = std::sqrt(hr[0]);
@@ -685,8 +687,10 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     if (single) {
       k_round_f32<<<kRedBlocks, RT, 0, s>>>(r0, V1, m);
       vin = V1;
+      prof_note(c, 12.0 * m);
     } else {
       k_split<<<kRedBlocks, RT, 0, s>>>(r0, V2, vin, m);
+      prof_note(c, 20.0 * m);
     }
     rn[0] = beta;
     const double cycle_stop = single ? kSingleCycle * beta : 0.0;
@@ -702,12 +706,13 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       float* zj = Zf + (int64_t)jj * m;
       float2* w = V2 + (int64_t)(jj + 1) * m;
       float* w1 = V1 + (int64_t)(jj + 1) * m;
+      const double mk0 = prof_mark(c);
       int ph = prof_begin(c, IBM_PROF_VCYCLE);
       ibm_status sv;
       if ((sv = mg_vcycle_f32(c, single ? V1 + (int64_t)jj * m : vin, zj, o->mg_pre,
                               o->mg_post)) != IBM_OK)
         return sv;
-      prof_end(c, ph);
+      prof_end_span(c, ph, mk0);
       if ((sv = single ? schur_apply_ds_t<float>(c, zj, w1) : schur_apply_ds_t<float2>(c, zj, w)) !=
           IBM_OK)
         return sv;
@@ -821,6 +826,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
                             reinterpret_cast<const float4*>(Zf), m / 4, jused, cy, m / 4);
       else
         IBM_NQ_DISPATCH_DS(jused, k_gemv_ds, x, Zf, m, jused, cy, m);
+      prof_note(c, (4.0 * jused + 16.0) * (double)m);
       IBM_LAUNCH_CHECK(c);
     }
     ++cycles;
@@ -828,6 +834,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   }
   launch_sum(x, m, part, sdev, s);
   launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
+  prof_note(c, 24.0 * m);
   IBM_LAUNCH_CHECK(c);
   if (st) {
     st->iters = total;

@@ -235,15 +235,57 @@ __global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v
   if (tid < nt && (lane & 3) == 0) t[dc * mk.n + k] = scale * ((p0 + p1) + (p2 + p3));
 }
 
+// Order of the shell cells in the interleaved layout: each block sorts one
+// window of 1024 consecutive shell cells by (entry count descending, index
+// ascending) with a bitonic network in shared memory -- deterministic, and
+// a window is 32 whole groups, so each group gets cells of nearly equal
+// counts.  perm[q'] = q (position q' of the layout holds shell cell q),
+// ell_cell[q'] = its cell.
+constexpr int kOrderWin = 1024;
+__global__ void __launch_bounds__(kOrderWin) k_ell_order(int64_t n_shell,
+                                                         const int32_t* __restrict__ off,
+                                                         const int32_t* __restrict__ shell_cell,
+                                                         int32_t* perm, int32_t* ell_cell) {
+  __shared__ unsigned long long key[kOrderWin];
+  const int t = threadIdx.x;
+  const int64_t q = (int64_t)blockIdx.x * kOrderWin + t;
+  key[t] = q < n_shell ? ((unsigned long long)(0x7fffffff - (off[q + 1] - off[q])) << 32) |
+                             (unsigned long long)(q - (int64_t)blockIdx.x * kOrderWin)
+                       : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= kOrderWin; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int p = t ^ j;
+      if (p > t) {
+        const unsigned long long a = key[t], b = key[p];
+        const bool up = (t & k) == 0;
+        if (up ? (a > b) : (a < b)) {
+          key[t] = b;
+          key[p] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (q < n_shell) {
+    const int64_t src = (int64_t)blockIdx.x * kOrderWin + (int64_t)(key[t] & 0xffffffffu);
+    perm[q] = (int32_t)src;
+    ell_cell[q] = shell_cell[src];
+  }
+}
+
 // Group lengths of the interleaved layout: len[w] = longest segment among the
-// 32 shell cells of group w, cnt[w] = 32 * len[w].
-__global__ void k_ell_len(int64_t n_shell, const int32_t* __restrict__ off, int32_t* len,
-                          int32_t* cnt) {
+// 32 shell cells of group w (layout order), cnt[w] = 32 * len[w].
+__global__ void k_ell_len(int64_t n_shell, const int32_t* __restrict__ off,
+                          const int32_t* __restrict__ perm, int32_t* len, int32_t* cnt) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ng = (n_shell + 31) / 32;
   if (w >= ng) return;
   int32_t L = 0;
-  for (int64_t q = 32 * w; q < min(32 * w + 32, n_shell); ++q) L = max(L, off[q + 1] - off[q]);
+  for (int64_t q = 32 * w; q < min(32 * w + 32, n_shell); ++q) {
+    const int32_t r = perm[q];
+    L = max(L, off[r + 1] - off[r]);
+  }
   len[w] = L;
   cnt[w] = 32 * L;
 }
@@ -251,14 +293,16 @@ __global__ void k_ell_len(int64_t n_shell, const int32_t* __restrict__ off, int3
 // Fills the interleaved layout with keys and G^T R coefficients (zero padding).
 __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict__ off,
                            const int32_t* __restrict__ key, const int32_t* __restrict__ base,
-                           const int32_t* __restrict__ len, const int32_t* __restrict__ shell_cell,
-                           Dims d, int64_t n_ell, int32_t* ekey, double* ecoef) {
+                           const int32_t* __restrict__ len, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ ell_cell, Dims d, int64_t n_ell,
+                           int32_t* ekey, double* ecoef) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n_shell) return;
   const int64_t w = q >> 5;
   const int lane = (int)(q & 31);
-  const int32_t a = off[q], nseg = off[q + 1] - a, L = len[w];
-  const int64_t c = shell_cell[q];
+  const int32_t r = perm[q];
+  const int32_t a = off[r], nseg = off[r + 1] - a, L = len[w];
+  const int64_t c = ell_cell[q];
   const int g[3] = {(int)(c % d.nx), (int)((c / d.nx) % d.ny), (int)(c / ((int64_t)d.nx * d.ny))};
   for (int p = 0; p < L; ++p) {
     const int64_t dst = base[w] + (int64_t)p * 32 + lane;
@@ -501,15 +545,16 @@ static ibm_status grow_entries(ibm_ctx* c, int64_t ne) {
   MarkerData& m = c->mk;
   if (ne <= m.entries_cap && m.entry_key) return IBM_OK;
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_base);
-  cudaFree(m.ell_len);
+  cudaFree(m.ell_len); cudaFree(m.ell_cell);
   m.entry_key = nullptr; m.shell_cell = nullptr; m.shell_off = nullptr; m.ell_base = nullptr;
-  m.ell_len = nullptr;
+  m.ell_len = nullptr; m.ell_cell = nullptr;
   m.entries_cap = 0;
   const int64_t cap = ne > 0 ? ne : 1;
   if (cudaMalloc(&m.entry_key, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.ell_base, sizeof(int32_t) * (cap / 32 + 2)) != cudaSuccess ||
       cudaMalloc(&m.ell_len, sizeof(int32_t) * (cap / 32 + 2)) != cudaSuccess ||
       cudaMalloc(&m.shell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
+      cudaMalloc(&m.ell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.shell_off, sizeof(int32_t) * (cap + 1)) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, IBM_ERR_NOMEM, "marker entry list allocation failed");
@@ -599,11 +644,15 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   count_launch();
   k_sort_segments<<<div_up(ns, TPB), TPB, 0, s>>>(ns, m.shell_off, m.entry_key);
   IBM_LAUNCH_CHECK(c);
-  // interleaved layout for the B^T t gather
+  // interleaved layout for the B^T t gather, in the order of ell_cell
   const int64_t ng = (ns + 31) / 32;
   int32_t* cnt = c->cell_count;   // free again: reused for the group sizes
+  int32_t* perm = c->cell_flag;   // free again (fill counters): the layout order
   count_launch();
-  k_ell_len<<<div_up(ng, TPB), TPB, 0, s>>>(ns, m.shell_off, m.ell_len, cnt);
+  k_ell_order<<<div_up(ns, kOrderWin), kOrderWin, 0, s>>>(ns, m.shell_off, m.shell_cell, perm,
+                                                          m.ell_cell);
+  count_launch();
+  k_ell_len<<<div_up(ng, TPB), TPB, 0, s>>>(ns, m.shell_off, perm, m.ell_len, cnt);
   IBM_LAUNCH_CHECK(c);
   st = exclusive_scan(c, cnt, m.ell_base, ng);
   if (st != IBM_OK) return st;
@@ -614,7 +663,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   if ((st = grow_ell(c, n_ell)) != IBM_OK) return st;
   count_launch();
   k_ell_fill<<<div_up(ns, TPB), TPB, 0, s>>>(mv, ns, m.shell_off, m.entry_key, m.ell_base,
-                                             m.ell_len, m.shell_cell, c->d, n_ell, m.ell_key,
+                                             m.ell_len, perm, m.ell_cell, c->d, n_ell, m.ell_key,
                                              m.ell_coef);
   IBM_LAUNCH_CHECK(c);
   m.n_ell = n_ell;
@@ -647,7 +696,7 @@ void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double
   if (m.n == 0 || m.n_shell == 0) return;
   count_launch();
   k_shell_gradt<<<div_up(m.n_shell, TPB), TPB, 0, c->stream>>>(
-      m.n_shell, m.shell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
+      m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
       scale, out);
 }
 

@@ -695,44 +695,61 @@ __device__ __forceinline__ void cell_ijk(Dims d, int c, int& i, int& j, int& k) 
   k = c / (d.nx * d.ny);
 }
 
-__device__ __forceinline__ float lap_nb(Dims d, const float* x, int c, int& nn) {
-  int i, j, k;
-  cell_ijk(d, c, i, j, k);
+// Per cell of the chain's levels, computed once per launch into shared
+// memory: the packed coordinates i | j << 10 | k << 20 and a mask of the
+// existing neighbours (bits x-, x+, y-, y+, z-, z+), so that the phases need
+// no integer division.
+__device__ __forceinline__ void unpack(uint32_t p, int& i, int& j, int& k) {
+  i = p & 1023;
+  j = (p >> 10) & 1023;
+  k = p >> 20;
+}
+
+__device__ __forceinline__ float lap_nb(Dims d, const float* x, int c, uint32_t mask, int& nn) {
+  const int sz = d.nx * d.ny;
   float s = 0.f;
-  nn = 0;
-  if (i > 0) { s += x[c - 1]; ++nn; }
-  if (i < d.nx - 1) { s += x[c + 1]; ++nn; }
-  if (j > 0) { s += x[c - d.nx]; ++nn; }
-  if (j < d.ny - 1) { s += x[c + d.nx]; ++nn; }
-  if (k > 0) { s += x[c - d.nx * d.ny]; ++nn; }
-  if (k < d.nz - 1) { s += x[c + d.nx * d.ny]; ++nn; }
+  if (mask & 1u) s += x[c - 1];
+  if (mask & 2u) s += x[c + 1];
+  if (mask & 4u) s += x[c - d.nx];
+  if (mask & 8u) s += x[c + d.nx];
+  if (mask & 16u) s += x[c - sz];
+  if (mask & 32u) s += x[c + sz];
+  nn = __popc(mask);
   return s;
 }
 
+struct ChainSm {
+  float* x;
+  float* b;
+  float* t;
+  const uint32_t* pk;
+  const uint8_t* nb;
+};
+
 // p Chebyshev steps on one level in shared memory; from_zero starts at x = 0.
 // Ends with the result in x (t is the ping-pong buffer).
-__device__ void chain_smooth(const CoarseChain& ch, int l, float* x, float* t, const float* b,
-                             const float* w, int p, bool from_zero) {
+__device__ void chain_smooth(const CoarseChain& ch, const ChainSm& S, int l, const float* w,
+                             int p, bool from_zero) {
   const Dims d = ch.d[l];
+  const int o = ch.off[l];
   const int m = d.nx * d.ny * d.nz;
   const float h2 = ch.h2[l];
+  float* x = S.x + o;
+  const float* b = S.b + o;
+  const uint8_t* nb = S.nb + o;
   float* cur = x;
-  float* nxt = t;
+  float* nxt = S.t + o;
   int q = 0;
   if (from_zero && p > 0) {
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      int i, j, k;
-      cell_ijk(d, c, i, j, k);
-      const int nn = (i > 0) + (i < d.nx - 1) + (j > 0) + (j < d.ny - 1) + (k > 0) + (k < d.nz - 1);
-      x[c] = w[0] * h2 * b[c] * inv_nn(nn);
-    }
+    for (int c = threadIdx.x; c < m; c += blockDim.x)
+      x[c] = w[0] * h2 * b[c] * inv_nn(__popc((uint32_t)nb[c]));
     __syncthreads();
     q = 1;
   }
   for (; q < p; ++q) {
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       int nn;
-      const float s = lap_nb(d, cur, c, nn);
+      const float s = lap_nb(d, cur, c, nb[c], nn);
       nxt[c] = fmaf(w[q] * inv_nn(nn), fmaf(h2, b[c], s - (float)nn * cur[c]), cur[c]);
     }
     __syncthreads();
@@ -751,45 +768,68 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
   pdl_trigger();
   extern __shared__ float sm[];
   const int tot = ch.off[ch.nlev];
-  float* xs = sm;
-  float* bs = sm + tot;
-  float* ts = sm + 2 * tot;
+  ChainSm S;
+  S.x = sm;
+  S.b = sm + tot;
+  S.t = sm + 2 * tot;
+  uint32_t* pk = reinterpret_cast<uint32_t*>(sm + 3 * tot);
+  uint8_t* nbm = reinterpret_cast<uint8_t*>(pk + tot);
+  S.pk = pk;
+  S.nb = nbm;
+  for (int l = 0; l < ch.nlev; ++l) {
+    const Dims d = ch.d[l];
+    const int m = d.nx * d.ny * d.nz;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      int i, j, k;
+      cell_ijk(d, c, i, j, k);
+      pk[ch.off[l] + c] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
+      nbm[ch.off[l] + c] = (uint8_t)((i > 0) | ((i < d.nx - 1) << 1) | ((j > 0) << 2) |
+                                     ((j < d.ny - 1) << 3) | ((k > 0) << 4) |
+                                     ((k < d.nz - 1) << 5));
+    }
+  }
   const int m0 = ch.off[1];
-  for (int c = threadIdx.x; c < m0; c += blockDim.x) bs[c] = b_in[c];
+  for (int c = threadIdx.x; c < m0; c += blockDim.x) S.b[c] = b_in[c];
   __syncthreads();
   // descend
   for (int l = 0; l < ch.nlev - 1; ++l) {
-    float* x = xs + ch.off[l];
-    float* b = bs + ch.off[l];
-    float* t = ts + ch.off[l];
-    chain_smooth(ch, l, x, t, b, ch.wpre, ch.pre, true);
+    chain_smooth(ch, S, l, ch.wpre, ch.pre, true);
     const Dims d = ch.d[l], dc = ch.d[l + 1];
     const int mcl = dc.nx * dc.ny * dc.nz;
     const float ih2 = 1.f / ch.h2[l];
-    float* bc = bs + ch.off[l + 1];
-    for (int C = threadIdx.x; C < mcl; C += blockDim.x) {
-      int I, J, K;
-      cell_ijk(dc, C, I, J, K);
-      float acc = 0.f;
-      for (int q = 0; q < 8; ++q) {
+    const float* x = S.x + ch.off[l];
+    const float* b = S.b + ch.off[l];
+    const uint8_t* nb = nbm + ch.off[l];
+    float* bc = S.b + ch.off[l + 1];
+    // eight threads per coarse cell (one child each), summed by shuffles
+    for (int base = 0; base < 8 * mcl; base += blockDim.x) {
+      const int t = base + threadIdx.x;
+      const bool act = t < 8 * mcl;
+      float r = 0.f;
+      if (act) {
+        const int C = t >> 3, q = t & 7;
+        int I, J, K;
+        unpack(pk[ch.off[l + 1] + C], I, J, K);
         const int c = ((2 * K + (q >> 2)) * d.ny + 2 * J + ((q >> 1) & 1)) * d.nx + 2 * I + (q & 1);
-        float r = b[c];
+        r = b[c];
         if (ch.pre > 0) {
           int nn;
-          const float s = lap_nb(d, x, c, nn);
-          r -= ((float)nn * x[c] - s) * ih2;
+          const float sn = lap_nb(d, x, c, nb[c], nn);
+          r -= ((float)nn * x[c] - sn) * ih2;
         }
-        acc += r;
       }
-      bc[C] = acc * 0.125f;
+      r += __shfl_xor_sync(0xffffffffu, r, 1);
+      r += __shfl_xor_sync(0xffffffffu, r, 2);
+      r += __shfl_xor_sync(0xffffffffu, r, 4);
+      if (act && (t & 7) == 0) bc[t >> 3] = r * 0.125f;
     }
     __syncthreads();
   }
   // coarsest: dense pseudo-inverse
   {
     const int l = ch.nlev - 1;
-    float* x = xs + ch.off[l];
-    const float* b = bs + ch.off[l];
+    float* x = S.x + ch.off[l];
+    const float* b = S.b + ch.off[l];
     for (int r = threadIdx.x; r < ch.mc; r += blockDim.x) {
       float acc = 0.f;
       for (int q = 0; q < ch.mc; ++q) acc = fmaf(__ldg(ch.pinv + r * ch.mc + q), b[q], acc);
@@ -799,15 +839,13 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
   }
   // ascend
   for (int l = ch.nlev - 2; l >= 0; --l) {
-    float* x = xs + ch.off[l];
-    float* b = bs + ch.off[l];
-    float* t = ts + ch.off[l];
-    const float* xc = xs + ch.off[l + 1];
+    float* x = S.x + ch.off[l];
+    const float* xc = S.x + ch.off[l + 1];
     const Dims d = ch.d[l], dc = ch.d[l + 1];
     const int m = d.nx * d.ny * d.nz;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       int i, j, k;
-      cell_ijk(d, c, i, j, k);
+      unpack(pk[ch.off[l] + c], i, j, k);
       const int I = i >> 1, J = j >> 1, K = k >> 1;
       const int In = (i & 1) ? min(I + 1, dc.nx - 1) : max(I - 1, 0);
       const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
@@ -821,9 +859,9 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
       x[c] = ch.pre > 0 ? x[c] + v : v;
     }
     __syncthreads();
-    chain_smooth(ch, l, x, t, b, ch.wpost, ch.post, false);
+    chain_smooth(ch, S, l, ch.wpost, ch.post, false);
   }
-  for (int c = threadIdx.x; c < m0; c += blockDim.x) x_out[c] = xs[c];
+  for (int c = threadIdx.x; c < m0; c += blockDim.x) x_out[c] = S.x[c];
 }
 
 // x = P b on the coarsest level: one block, dense pseudo-inverse.
@@ -918,12 +956,13 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
       k_first<T, TB><<<zm_grid(L.d), dim3(BX, BY), 0, s>>>(
           L.d, b, bcopy, x, w_over_n<T>(w[0] * h2), w_over_n<T>(two ? w[1] : 0.0), (T)h2, two);
   }
-  prof_end(c, ph, (double)L.m * (sizeof(TB) + sizeof(T) + (bcopy ? sizeof(T) : 0)));
+  prof_end_or_note(c, ph, (double)L.m * (sizeof(TB) + sizeof(T) + (bcopy ? sizeof(T) : 0)));
   const T* bb = bcopy ? bcopy : reinterpret_cast<const T*>(b);
   T* cur = x;
   T* nxt = t;
   for (int q = two ? 2 : 1; q < p; ++q) {
     count_launch();
+    prof_note(c, (double)L.m * 3 * sizeof(T));
     if constexpr (std::is_same<T, float>::value) {
       if (vec)
         launch_pdl(k_sweep_v4<float>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d,
@@ -934,7 +973,10 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
                                                             w_over_n<T>(w[q]), (T)h2);
     T* tmp = cur; cur = nxt; nxt = tmp;
   }
-  if (cur != x) launch_copy(x, cur, sizeof(T) * L.m, s);
+  if (cur != x) {
+    launch_copy(x, cur, sizeof(T) * L.m, s);
+    prof_note(c, 2.0 * sizeof(T) * L.m);
+  }
 }
 
 // one smoothing step src -> dst on level l
@@ -965,6 +1007,7 @@ void post_smooth(ibm_ctx* c, int l, const T* b, T* x, T* t, int p, TO* out, cuda
     if ((const void*)out != (const void*)x) {
       count_launch();
       k_convert<T, TO><<<kRedBlocks, 256, 0, s>>>(x, out, L.m);
+      prof_note(c, (double)L.m * (sizeof(T) + sizeof(TO)));
     }
     return;
   }
@@ -976,17 +1019,19 @@ void post_smooth(ibm_ctx* c, int l, const T* b, T* x, T* t, int p, TO* out, cuda
     const int ph = l == 0 ? prof_begin(c, IBM_PROF_MG_SMOOTH_FINE) : -1;
     if (last && (const void*)out != (const void*)src) {
       sweep_step<T, TO>(c, l, src, b, out, w[q], s);
-      prof_end(c, ph, (double)L.m * (2 * sizeof(T) + sizeof(TO)));
+      prof_end_or_note(c, ph, (double)L.m * (2 * sizeof(T) + sizeof(TO)));
       return;
     }
     T* dst = (src == x) ? t : x;
     sweep_step<T, T>(c, l, src, b, dst, w[q], s);
-    prof_end(c, ph, (double)L.m * 3 * sizeof(T));
+    prof_end_or_note(c, ph, (double)L.m * 3 * sizeof(T));
     src = dst;
   }
   // the last step landed in t or x while out aliases the other: copy
-  if ((const void*)src != (const void*)out)
+  if ((const void*)src != (const void*)out) {
     launch_copy(out, src, sizeof(T) * L.m, s);
+    prof_note(c, 2.0 * sizeof(T) * L.m);
+  }
 }
 
 // V-cycle on level l >= 1 (or level 0 in the FP64 form): x_l ~ L_l^{-1} b_l.
@@ -1014,6 +1059,7 @@ void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cuda
   if (!done)
     k_restrict<T><<<dim3(div_up(C.d.nx, BX), div_up(C.d.ny, BY), div_up(C.d.nz, ZC / 2)),
                     dim3(BX, BY), 0, s>>>(L.d, C.d, xin, b, cp.b, (T)(1.0 / (L.h * L.h)));
+  prof_note(c, (double)L.m * ((xin ? 2 : 1) * sizeof(T)) + (double)C.m * sizeof(T));
   vcycle<T>(c, l + 1, cp.b, cp.x, cp.t, pre, post, s);
   done = false;
   count_launch();
@@ -1028,6 +1074,7 @@ void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cuda
   if (!done)
     k_prolong<T><<<dim3(div_up(C.d.nx, BX), div_up(L.d.ny, BY), div_up(L.d.nz, ZC)),
                    dim3(BX, BY), 0, s>>>(L.d, C.d, cp.x, x, pre > 0 ? 0 : 1);
+  prof_note(c, (double)C.m * sizeof(T) + (double)L.m * ((pre > 0 ? 2 : 1) * sizeof(T)));
 }
 
 // Launches the one-CTA cycle from level l down; false if it does not apply.
@@ -1052,7 +1099,8 @@ bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post
   ch.post = post;
   ch.pinv = c->coarse_pinv32;
   ch.mc = c->coarse_m;
-  const size_t smem = sizeof(float) * 3 * ch.off[nlev];
+  // x, b, t (FP32), packed coordinates (4 B) and neighbour masks (1 B) per cell
+  const size_t smem = (sizeof(float) * 3 + 4 + 1) * ch.off[nlev];
   if (smem > 200 * 1024) return false;
   // the shared-memory limit is raised once per device
   static bool attr_set[64] = {false};
@@ -1066,6 +1114,7 @@ bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post
   }
   count_launch();
   launch_pdl(k_coarse_chain, dim3(1), dim3(kChainThreads), smem, s, ch, b, x);
+  prof_note(c, 8.0 * ch.off[1] + 4.0 * (double)ch.mc * ch.mc);
   return true;
 }
 
@@ -1077,6 +1126,7 @@ void vcycle(ibm_ctx* c, int l, const T* b, T* x, T* t, int pre, int post, cudaSt
   if (l == c->n_levels - 1) {
     count_launch();
     k_coarse_solve<T><<<1, 256, 0, s>>>(pinv_of<T>(c), b, x, c->coarse_m);
+    prof_note(c, (double)c->coarse_m * (c->coarse_m + 2) * sizeof(T));
     return;
   }
   if (pre > 0) pre_smooth<T, T>(c, l, b, nullptr, x, t, pre, s);
@@ -1165,6 +1215,17 @@ ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, 
     // the whole grid is the coarsest level: the cycle is the exact pseudo-inverse
     count_launch();
     k_coarse_solve<double><<<1, 256, 0, s>>>(c->coarse_pinv64, r, z, c->coarse_m);
+    IBM_LAUNCH_CHECK(c);
+    return IBM_OK;
+  }
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (prec == IBM_PREC_FP32 && vec_ok(L0.d) && (!al16(r) || !al16(z))) {
+    // the four-cell kernels load and store FP64 pairs (16 bytes): a caller's
+    // vector on an 8-byte boundary goes through the level's aligned buffers
+    launch_copy(L0.b64, r, sizeof(double) * L0.m, s);
+    ibm_status st = mg_vcycle(c, L0.b64, L0.t64, prec, pre, post);
+    if (st != IBM_OK) return st;
+    launch_copy(z, L0.t64, sizeof(double) * L0.m, s);
     IBM_LAUNCH_CHECK(c);
     return IBM_OK;
   }

@@ -156,3 +156,36 @@ def test_step_unchanged_by_concurrent_bulk_copies(cuda_device):
     torch.cuda.synchronize()
     assert float(h_dst[-1]) == 1.0 and float(d_buf[0]) == 1.0
     s.close()
+
+
+def _scaled_step(case, s_f, s_U):
+    from paper_2501_15314_gb300.api import IBMSolver
+    g = case.grid()
+    s = IBMSolver(case.nx, case.ny, case.nz, case.h, Re=case.Re, dt=case.dt)
+    s.set_markers(dev(case.X))
+    z = lambda n: dev(np.zeros(n))  # noqa: E731
+    out, _ = s.step(z(g.n_faces), z(g.n_faces), z(g.m), z(3 * case.N), dev(s_U * case.U_gamma),
+                    dev(s_f * case.f_body), precond_prec=0, arnoldi=0, rtol=1e-13,
+                    helm_rtol=1e-14, helm_maxit=12)
+    s.close()
+    return {k: host(v) for k, v in out.items()}
+
+
+def test_predictor_input_range(cuda_device):
+    # The step from rest is linear in (U^Gamma, f).  The predictor reads f as
+    # FP32 pairs: above 2^-80 in magnitude the scaled inputs give the scaled
+    # results (here 2^-40: every entry that matters stays above the floor);
+    # every entry below 2^-80 is read as 0 (here 2^-100: the result is that of
+    # the same step without body force).
+    case = _with_inputs(gc.sphere16())
+    base = _scaled_step(case, 1.0, 1.0)
+    s = 2.0 ** -40
+    small = _scaled_step(case, s, s)
+    for k in ("u", "p", "F"):
+        assert rel(small[k], s * base[k]) < 1e-10, (k, rel(small[k], s * base[k]))
+    t = 2.0 ** -100
+    assert np.abs(t * case.f_body).max() < 2.0 ** -80
+    tiny = _scaled_step(case, t, 1.0)
+    no_force = _scaled_step(case, 0.0, 1.0)
+    for k in ("u", "p", "F"):
+        np.testing.assert_array_equal(tiny[k], no_force[k])
