@@ -503,7 +503,9 @@ def run_ours(args):
     adjoint = adjoint_bench(s, W, X, U, f, out, zf, zc, zk, timed, k64)
     c_modes = cmode_bench(timed, max(1, k64 // 2))
     porous = porous_bench(timed, k64)
-    fsi = fsi_bench(timed, 3, 2)
+    fsi = ({"spread_force_criterion": fsi_bench(args.fsi_steps, args.fsi_xi, 1),
+            "marker_force_criterion": fsi_bench(args.fsi_steps, args.fsi_xi, 0)}
+           if args.fsi_steps > 0 else None)
     multistep = multistep_bench()
 
     # ---- roofline of the dominant kernel class ----
@@ -675,12 +677,16 @@ def multistep_bench(steps=10):
             "mixed_vs_fp64_per_step": diff}
 
 
-def fsi_bench(timed, K, W, n=384):
-    """Two-way coupled step (Sec. 3.2) of the sedimenting sphere: r = 0.08,
-    density ratio 1.05, Re 50, dt 5e-4, gravity 10 along -z, released from
-    rest at (0.5, 0.5, 0.7), markers at spacing h; FP32 V-cycle, inner Schur
-    solves to 1e-2, corrections until ||F'||_1/||F||_1 < 1e-3 (xi = 1).  W
-    untimed steps from rest, then K timed steps."""
+def fsi_bench(steps=200, xi=1.0, criterion=0, n=384):
+    """The sedimentation workload (Sec. 3.2 two-way coupling; Model problem 3
+    of Sec. 6.1.3): a sphere r = 0.08 of density ratio 1.05 released from
+    rest at (0.5, 0.5, 0.7) in the 384^3 unit box, Re 50, dt 5e-4, gravity
+    10 along -z, markers at spacing h; FP32 V-cycle, inner Schur solves to
+    1e-2, relaxation xi, corrections until ||F'||_1/||F||_1 < 1e-3.  `steps`
+    consecutive steps from release, each timed with CUDA events (every step
+    synchronises for its correction count).  criterion: the norm of the
+    stopping test, on the marker force densities (0, as Eq.
+    (convergence_criterion) is written) or on the spread ones (1)."""
     import numpy as np
     import torch
     from paper_2501_15314_gb300 import workloads as wl
@@ -694,28 +700,35 @@ def fsi_bench(timed, K, W, n=384):
     z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")  # noqa: E731
     st_ = dict(u=z(s.nf), um1=z(s.nf), p=z(s.m), F=z(3 * nm))
     outs = [dict(X=z(3 * nm), u=z(s.nf), p=z(s.m), F=z(3 * nm)) for _ in range(3)]
-    cnt = [0]
-
-    def one():
-        o = outs[cnt[0] % 3]
-        cnt[0] += 1
+    ms, inner, fg, usz = [], [], [], []
+    torch.cuda.synchronize()
+    for k in range(steps):
+        o = outs[k % 3]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
         out, st = s.fsi_step(sp, L0, bid, st_["u"], st_["um1"], st_["p"], st_["F"], None,
-                             out=o, gravity=(0.0, 0.0, -10.0), xi=1.0, tol=1e-3, max_inner=200,
-                             rtol=1e-2, raise_on_error=False)
+                             out=o, gravity=(0.0, 0.0, -10.0), xi=xi, tol=1e-3, max_inner=200,
+                             rtol=1e-2, criterion=criterion, raise_on_error=False)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
         st_["um1"], st_["u"], st_["p"], st_["F"] = st_["u"], out["u"], out["p"], out["F"]
-        return st
-    for _ in range(W):
-        one()
-    ms, sts = timed(one, K)
-    res = {"workload": (f"sediment{n}: {n}^3, sphere r {r} density ratio {th}, Re 50, dt {dt}, "
-                        f"g 10, {nm} markers, steps {W + 1}..{W + K} after release"),
-           "ms_per_step": ms, "steps_per_s": 1000.0 / ms,
-           "corrections_per_step": [st["inner"] for st in sts],
-           "fgmres_iters_per_step": [st["fgmres_iters"] for st in sts],
-           "ratio": [st["ratio"] for st in sts],
-           "u_s_z": float(sp.get("us")[0, 2])}
+        ms.append(e0.elapsed_time(e1))
+        inner.append(int(st["inner"]))
+        fg.append(int(st["fgmres_iters"]))
+        usz.append(float(sp.get("us")[0, 2]))
     s.close()
-    return res
+    last = slice(steps // 2, steps)
+    return {"workload": (f"sediment{n}: {n}^3, sphere r {r} density ratio {th}, Re 50, dt {dt}, "
+                         f"g 10, {nm} markers, {steps} steps from release, xi {xi}, stopping "
+                         f"test on the {'spread' if criterion else 'marker'} force densities"),
+            "steps": steps, "wall_s": sum(ms) / 1e3, "ms_per_step": sum(ms) / steps,
+            "ms_per_step_second_half": float(np.mean(ms[last])),
+            "corrections_mean": float(np.mean(inner)),
+            "corrections_second_half_mean": float(np.mean(inner[last])),
+            "corrections_max": int(max(inner)),
+            "corrections_per_step": inner, "fgmres_iters_per_step": fg,
+            "ms_per_step_each": [round(v, 2) for v in ms],
+            "u_s_z_every_10": usz[9::10]}
 
 
 def porous_bench(timed, K):
@@ -842,6 +855,9 @@ def main():
     ap.add_argument("--fp64", action="store_true", help="profile the plain FP64 form")
     ap.add_argument("--grid", type=int, default=0, help="profile step: grid size override")
     ap.add_argument("--restart", type=int, default=40, help="profile step: FGMRES restart")
+    ap.add_argument("--fsi-steps", type=int, default=200,
+                    help="two-way sedimentation steps at 384^3 (0: skip the record)")
+    ap.add_argument("--fsi-xi", type=float, default=1.0, help="two-way relaxation factor")
     args = ap.parse_args()
     if args.profile_step:
         return run_profile_step(args)

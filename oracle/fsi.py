@@ -163,11 +163,13 @@ def rigid_velocities(b: RigidSphere, dt, F_sum, T_sum, lin, ang, gravity):
 
 def fsi_step(g: mac.Grid, Re: float, dt: float, bodies, L0, body_id, u_n, u_nm1, p_n, F_n,
              f_body=None, gravity=(0.0, 0.0, 0.0), xi=1.0, tol=1e-3, max_inner=50,
-             rtol=1e-13, with_advection=True, workers=None):
+             rtol=1e-13, with_advection=True, workers=None, criterion="lagrangian"):
     """One two-way step.  bodies: list of RigidSphere (updated in place to
     t^{n+1}); L0 (3, N) body-frame marker offsets; body_id (N,).  Returns a
     dict with u, p, F, X (markers at t^{n+1}), inner (correction count),
-    iters (FGMRES iterations per correction), ratio (last ||F'||_1/||F||_1)."""
+    iters (FGMRES iterations per correction), ratio (last ||F'||_1/||F||_1,
+    or ||R F'||_1/||R F||_1 with criterion="eulerian": the stopping test of
+    Eq. (convergence_criterion) on the force densities spread to the faces)."""
     L0 = np.asarray(L0, dtype=np.float64).reshape(3, -1)
     body_id = np.asarray(body_id)
     N = L0.shape[1]
@@ -218,8 +220,14 @@ def fsi_step(g: mac.Grid, Re: float, dt: float, bodies, L0, body_id, u_n, u_nm1,
         u = u + xi * (1.0 / a) * (-mac.apply_G(g, pc) + sys.R @ Fc)
         iters.append(it)
         inner = k + 1
-        nF = np.abs(F).sum()
-        ratio = np.abs(Fc).sum() / nF if nF > 0 else 0.0
+        # Eq. (convergence_criterion) on the marker force densities, or on
+        # the force densities spread to the faces (what the fluid receives)
+        if criterion == "eulerian":
+            nF = np.abs(sys.R @ F).sum()
+            ratio = np.abs(sys.R @ Fc).sum() / nF if nF > 0 else 0.0
+        else:
+            nF = np.abs(F).sum()
+            ratio = np.abs(Fc).sum() / nF if nF > 0 else 0.0
         if ratio < tol:
             break
     # advance the bodies to t^{n+1}

@@ -26,6 +26,8 @@ IBM_PREC_FP32 = 1
 IBM_ARNOLDI_FP64 = 0
 IBM_ARNOLDI_DS = 1
 IBM_ARNOLDI_FP32 = 2
+IBM_FSI_CRIT_LAGRANGIAN = 0
+IBM_FSI_CRIT_EULERIAN = 1
 IBM_CMODE_SCALAR = 0
 IBM_CMODE_EXACT = 1
 IBM_CMODE_CONSISTENT = 2
@@ -70,7 +72,7 @@ class ibm_rigid_sphere(C.Structure):
 
 class ibm_fsi_opts(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("xi", C.c_double), ("tol", C.c_double),
-                ("max_inner", C.c_int32)]
+                ("max_inner", C.c_int32), ("criterion", C.c_int32)]
 
 
 class ibm_fsi_stats(C.Structure):

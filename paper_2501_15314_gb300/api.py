@@ -265,6 +265,7 @@ class IBMSolver:
 
     def fsi_step(self, spheres: "RigidSpheres", L0, body_id, u_n, u_nm1, p_n, F_n, f_body=None,
                  out=None, gravity=(0.0, 0.0, 0.0), xi=1.0, tol=1e-3, max_inner=50,
+                 criterion=_lib.IBM_FSI_CRIT_LAGRANGIAN,
                  raise_on_error=True, **kw):
         """One two-way coupled step (Sec. 3.2); spheres advance in place.
         Returns (dict(X, u, p, F), stats)."""
@@ -280,6 +281,7 @@ class IBMSolver:
         for e in range(3):
             fo.gravity[e] = float(gravity[e])
         fo.xi, fo.tol, fo.max_inner = float(xi), float(tol), int(max_inner)
+        fo.criterion = int(criterion)
         st = _lib.ibm_fsi_stats()
         status = self._call("ibm_fsi_step",
             spheres.n, spheres.arr, n, _ptr(L0, numel=nmk, name="L0"),

@@ -244,6 +244,7 @@ void ibm_default_fsi_opts(ibm_fsi_opts* f) {
   f->xi = 1.0;
   f->tol = 1e-3;
   f->max_inner = 50;
+  f->criterion = IBM_FSI_CRIT_LAGRANGIAN;
 }
 
 ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_t n,
@@ -262,8 +263,9 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
     return set_err(c, IBM_ERR_ARG, "bad field pointer");
   if (u_np1 == u_n || u_np1 == u_nm1 || p_np1 == p_n || F_np1 == F_n || X_np1 == L0)
     return set_err(c, IBM_ERR_ARG, "outputs must not alias inputs");
-  if (!(fo->xi > 0.0) || !(fo->tol >= 0.0) || fo->max_inner < 1)
-    return set_err(c, IBM_ERR_ARG, "need xi > 0, tol >= 0, max_inner >= 1");
+  if (!(fo->xi > 0.0) || !(fo->tol >= 0.0) || fo->max_inner < 1 ||
+      (fo->criterion != IBM_FSI_CRIT_LAGRANGIAN && fo->criterion != IBM_FSI_CRIT_EULERIAN))
+    return set_err(c, IBM_ERR_ARG, "need xi > 0, tol >= 0, max_inner >= 1 and a known criterion");
   for (int b = 0; b < nb; ++b)
     if (!(bodies[b].radius > 0.0) || !(bodies[b].theta > 0.0))
       return set_err(c, IBM_ERR_ARG, "sphere radius and density ratio must be positive");
@@ -440,14 +442,20 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
     launch_axpby(F_np1, 1.0, mk.t, fo->xi, F_np1, 3 * n, str);
     launch_grad_axpy(c->d, u_np1, pc, -fo->xi * (2.0 * dt / 3.0) * inv_h, u_np1, str);
     launch_shell_spread_faces(c, mk.t, fo->xi * (2.0 * dt / 3.0), u_np1);
-    count_launch();
-    k_asum2<<<kAsumBlocks, TPB, 0, str>>>(3 * n, mk.t, F_np1, d_asum);
+    int nblk = kAsumBlocks;
+    if (fo->criterion == IBM_FSI_CRIT_EULERIAN) {
+      nblk = launch_shell_spread_asum2(c, mk.t, F_np1, d_asum);   // <= kAsumBlocks partials
+      if (nblk > kAsumBlocks) { prof_end(c, ph); return set_err(c, IBM_ERR_ARG, "asum grid"); }
+    } else {
+      count_launch();
+      k_asum2<<<kAsumBlocks, TPB, 0, str>>>(3 * n, mk.t, F_np1, d_asum);
+    }
     IBM_LAUNCH_CHECK(c);
-    IBM_CUDA(c, cudaMemcpyAsync(asum.data(), d_asum, sizeof(double) * asum.size(),
+    IBM_CUDA(c, cudaMemcpyAsync(asum.data(), d_asum, sizeof(double) * 2 * nblk,
                                 cudaMemcpyDeviceToHost, str));
     IBM_CUDA(c, cudaStreamSynchronize(str));
     double na = 0.0, nf = 0.0;
-    for (int q = 0; q < kAsumBlocks; ++q) { na += asum[2 * q]; nf += asum[2 * q + 1]; }
+    for (int q = 0; q < nblk; ++q) { na += asum[2 * q]; nf += asum[2 * q + 1]; }
     if (!std::isfinite(na) || !std::isfinite(nf)) {
       prof_end(c, ph);
       return set_err(c, IBM_ERR_NAN, "non-finite force correction");
@@ -484,8 +492,8 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
   if (solve_status != IBM_OK) return solve_status;
   if (ratio >= fo->tol && fo->tol > 0.0) {
     char buf[160];
-    snprintf(buf, sizeof buf, "two-way corrections stopped at ||F'||_1/||F||_1 = %.3g > tol %.3g",
-             ratio, fo->tol);
+    snprintf(buf, sizeof buf, "two-way corrections stopped at ratio %.3g > tol %.3g (%s norm)",
+             ratio, fo->tol, fo->criterion == IBM_FSI_CRIT_EULERIAN ? "spread" : "marker");
     return set_err(c, IBM_ERR_NOT_CONVERGED, buf);
   }
   return IBM_OK;

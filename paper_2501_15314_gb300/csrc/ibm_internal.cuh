@@ -73,19 +73,19 @@ struct MarkerData {
   int64_t n_entries = 0, entries_cap = 0;
   int32_t* entry_key = nullptr;   // marker * 64 + slot, sorted within a cell
   // the same entries re-laid out for the B^T t gather: shell cells (in the
-  // order of ell_cell) in groups of 32 (one warp), group w padded to its
-  // longest segment L_w and stored interleaved, entry p of lane l at
-  // ell_base[w] + 32 p + l
+  // order of ell_cell) in groups of kEllCells (one warp, kEllLanes lanes per
+  // cell), group w padded to its longest cell and stored interleaved, entry
+  // kEllLanes r + j of the group's cell c at ell_base[w] + 32 r + kEllLanes c + j
   int64_t n_ell = 0, ell_cap = 0;
   int32_t* ell_key = nullptr;
   double* ell_coef = nullptr;     // [3][n_ell] G^T R coefficients (0 on padding)
   int32_t* ell_base = nullptr;    // [n_groups + 1]
-  int32_t* ell_len = nullptr;     // [n_groups]
+  int32_t* ell_len = nullptr;     // [n_groups] rounds (entries per lane)
   int64_t n_shell = 0;
   int32_t* shell_cell = nullptr;  // [n_shell] cells touched by any marker
   int32_t* shell_off = nullptr;   // [n_shell + 1] segment offsets
   // the shell cells in the order of the interleaved layout: within each
-  // window of 1024 (32 groups) sorted by entry count, longest first, so that
+  // window of 1024 (128 groups) sorted by entry count, longest first, so that
   // the cells of a group have nearly equal counts and little padding
   int32_t* ell_cell = nullptr;    // [n_shell]
   double* t = nullptr;            // [3][n] per-marker scratch
@@ -253,6 +253,9 @@ void launch_interp_dpos(ibm_ctx* c, const double* f, const double* m, double sca
 void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double* u);
 // u = R F on the shell faces only (written, not accumulated)
 void launch_shell_spread_faces_set(ibm_ctx* c, const double* F, double* u);
+// Per-block partial L1 norms of R A and R B (2 doubles per block into part);
+// returns the number of blocks (0 without markers).
+int launch_shell_spread_asum2(ibm_ctx* c, const double* A, const double* B, double* part);
 // ---- C = R^T R (cmode.cu) ----
 void apply_C(ibm_ctx* c, const double* v, double* out);
 ibm_status c_solve(ibm_ctx* c, const double* t, double* s, double rtol, int maxit, int* iters);
@@ -341,9 +344,26 @@ void prof_end_span(ibm_ctx* c, int handle, double mark);
 // prof_end when the class is timed (handle >= 0), else prof_note.
 void prof_end_or_note(ibm_ctx* c, int handle, double bytes);
 
-// Sum over one shell cell's entries of the interleaved layout (entry p of the
-// cell at idx + 32 p): sum_p sum_e coef_e[p] t_e[marker(p)], FP64 FMAs in
-// entry order.  Four entries' loads are issued before their FMAs (the marker
+// Interleaved layout of the B^T t gather: a group (one warp) holds kEllCells
+// shell cells, kEllLanes lanes per cell; lane l takes the entries
+// p = kEllLanes r + l % kEllLanes of its cell, stored at base + 32 r + l.
+constexpr int kEllLanes = 4;
+constexpr int kEllCells = 32 / kEllLanes;
+__host__ __device__ inline int64_t ell_groups(int64_t n_shell) {
+  return (n_shell + kEllCells - 1) / kEllCells;
+}
+
+// Sum of the kEllLanes lanes of a cell, in a fixed order (all 32 lanes of
+// the warp take part).
+__device__ __forceinline__ double ell_combine(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
+// One lane's share of a shell cell's entries in the interleaved layout
+// (round p at idx + 32 p): sum_p sum_e coef_e[p] t_e[marker(p)], FP64 FMAs
+// in round order.  Four entries' loads are issued before their FMAs (the marker
 // index of an entry must arrive before its t can be gathered, so one entry at
 // a time leaves the thread waiting on two dependent loads per entry); the
 // order of the FMAs, and so the result, is that of the plain loop.

@@ -158,11 +158,14 @@ __global__ void k_shell_gradt_ds(int64_t n_shell, const int32_t* __restrict__ sh
                                  const double* __restrict__ ecoef, int64_t n_ell, int64_t nmk,
                                  const double* __restrict__ t, double scale,
                                  TW* __restrict__ wv) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n_shell) return;
-  const int64_t g = q >> 5;
-  const int lane = (int)(q & 31);
-  const double acc = ell_gradt_sum(ekey, ecoef, n_ell, nmk, t, base[g] + lane, len[g]);
+  const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = tq >> 5;
+  const int lane = (int)(tq & 31);
+  const int64_t q = g * kEllCells + lane / kEllLanes;
+  const bool live = g < ell_groups(n_shell) && q < n_shell;
+  double acc = live ? ell_gradt_sum(ekey, ecoef, n_ell, nmk, t, base[g] + lane, len[g]) : 0.0;
+  acc = ell_combine(acc);
+  if (!live || lane % kEllLanes != 0) return;
   const int64_t c = shell_cell[q];
   if constexpr (std::is_same<TW, float2>::value) {
     const float2 wc = wv[c];
@@ -598,7 +601,7 @@ ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
       sign = c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0;
     }
     count_launch();
-    k_shell_gradt_ds<TW><<<div_up(m.n_shell, 256), 256, 0, s>>>(
+    k_shell_gradt_ds<TW><<<div_up(32 * ell_groups(m.n_shell), 256), 256, 0, s>>>(
         m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
         sign, w);
     prof_end(c, ph, marker_term_bytes(c, 4, (int)sizeof(TW)));

@@ -274,20 +274,24 @@ __global__ void __launch_bounds__(kOrderWin) k_ell_order(int64_t n_shell,
   }
 }
 
-// Group lengths of the interleaved layout: len[w] = longest segment among the
-// 32 shell cells of group w (layout order), cnt[w] = 32 * len[w].
+// Group lengths of the interleaved layout.  A group is one warp: kEllCells
+// shell cells (layout order) with kEllLanes lanes each; lane l of the group
+// holds the entries p = kEllLanes r + (l % kEllLanes), r = 0, 1, ..., of cell
+// l / kEllLanes at slot base[w] + 32 r + l.  len[w] = rounds of group w (the
+// longest cell's count over kEllLanes, rounded up), cnt[w] = 32 * len[w].
 __global__ void k_ell_len(int64_t n_shell, const int32_t* __restrict__ off,
                           const int32_t* __restrict__ perm, int32_t* len, int32_t* cnt) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t ng = (n_shell + 31) / 32;
+  const int64_t ng = (n_shell + kEllCells - 1) / kEllCells;
   if (w >= ng) return;
   int32_t L = 0;
-  for (int64_t q = 32 * w; q < min(32 * w + 32, n_shell); ++q) {
+  for (int64_t q = kEllCells * w; q < min(kEllCells * w + kEllCells, n_shell); ++q) {
     const int32_t r = perm[q];
     L = max(L, off[r + 1] - off[r]);
   }
-  len[w] = L;
-  cnt[w] = 32 * L;
+  const int32_t rounds = (L + kEllLanes - 1) / kEllLanes;
+  len[w] = rounds;
+  cnt[w] = 32 * rounds;
 }
 
 // Fills the interleaved layout with keys and G^T R coefficients (zero padding).
@@ -298,14 +302,14 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
                            int32_t* ekey, double* ecoef) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n_shell) return;
-  const int64_t w = q >> 5;
-  const int lane = (int)(q & 31);
+  const int64_t w = q / kEllCells;
+  const int cl = (int)(q % kEllCells);
   const int32_t r = perm[q];
-  const int32_t a = off[r], nseg = off[r + 1] - a, L = len[w];
+  const int32_t a = off[r], nseg = off[r + 1] - a, L = kEllLanes * len[w];
   const int64_t c = ell_cell[q];
   const int g[3] = {(int)(c % d.nx), (int)((c / d.nx) % d.ny), (int)(c / ((int64_t)d.nx * d.ny))};
   for (int p = 0; p < L; ++p) {
-    const int64_t dst = base[w] + (int64_t)p * 32 + lane;
+    const int64_t dst = base[w] + (int64_t)(p / kEllLanes) * 32 + kEllLanes * cl + p % kEllLanes;
     if (p < nseg) {
       const int32_t kk = key[a + p];
       ekey[dst] = kk;
@@ -320,20 +324,26 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
   }
 }
 
-// out[c] += scale * sum over the entries of shell cell c (in marker order) of
-// sum_d coef_d t[d][k]; coalesced loads through the interleaved layout.
+// out[c] += scale * sum over the entries of shell cell c of sum_d coef_d
+// t[d][k]; coalesced loads through the interleaved layout, kEllLanes lanes
+// per cell (each its own share of the entries), their sums combined in a
+// fixed order.  One warp per group: launch 32 threads per group.
 __global__ void k_shell_gradt(int64_t n_shell, const int32_t* __restrict__ shell_cell,
                               const int32_t* __restrict__ base, const int32_t* __restrict__ len,
                               const int32_t* __restrict__ ekey, const double* __restrict__ ecoef,
                               int64_t n_ell, int64_t nmk, const double* __restrict__ t,
                               double scale, double* __restrict__ out) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n_shell) return;
-  const int64_t w = q >> 5;
-  const int lane = (int)(q & 31);
-  const double acc = ell_gradt_sum(ekey, ecoef, n_ell, nmk, t, base[w] + lane, len[w]);
-  const int64_t c = shell_cell[q];
-  out[c] = fma(scale, acc, out[c]);
+  const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t w = tq >> 5;
+  const int lane = (int)(tq & 31);
+  const int64_t q = w * kEllCells + lane / kEllLanes;
+  const bool live = w < ell_groups(n_shell) && q < n_shell;
+  double acc = live ? ell_gradt_sum(ekey, ecoef, n_ell, nmk, t, base[w] + lane, len[w]) : 0.0;
+  acc = ell_combine(acc);
+  if (live && lane % kEllLanes == 0) {
+    const int64_t c = shell_cell[q];
+    out[c] = fma(scale, acc, out[c]);
+  }
 }
 
 // U[d][k] = sum over the 27 taps of component d of w * u_d  (R^T u)
@@ -371,14 +381,14 @@ __global__ void k_interp(Dims d, MkView mk, const double* __restrict__ u, double
 // Face spread R F on the shell: every tap face of a marker is the lower face
 // (along its own normal) of a cell of the marker's box, so one thread per
 // (shell cell, component) owns that face and gathers its markers in order.
-__global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
-                                     const int32_t* __restrict__ shell_cell,
-                                     const int32_t* __restrict__ off,
-                                     const int32_t* __restrict__ key,
-                                     const double* __restrict__ F, double scale, int set,
-                                     double* __restrict__ u) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= 3 * n_shell) return;
+// spread_face: the gathered value (any = false when no tap of the cell's
+// markers lands on that face) and the face's index in the packed vector.
+__device__ __forceinline__ double spread_face(Dims d, const MkView& mk, int64_t n_shell,
+                                              const int32_t* __restrict__ shell_cell,
+                                              const int32_t* __restrict__ off,
+                                              const int32_t* __restrict__ key,
+                                              const double* __restrict__ F, int64_t tid,
+                                              bool& any, int64_t& f) {
   const int dc = (int)(tid / n_shell);
   const int64_t q = tid - dc * n_shell;
   const int64_t c = shell_cell[q];
@@ -388,7 +398,7 @@ __global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
   const int g[3] = {ci, cj, ck};
   const int32_t a = off[q], b = off[q + 1];
   double acc = 0.0;
-  bool any = false;
+  any = false;
   for (int32_t x = a; x < b; ++x) {
     const int64_t k = key[x] >> 6;
     double w = 1.0;
@@ -402,13 +412,61 @@ __global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
     }
     if (in) { acc = fma(w, F[dc * mk.n + k], acc); any = true; }
   }
-  if (!any) return;
   const FaceDims fd = face_dims(d);
   const int64_t foff = dc == 0 ? 0 : (dc == 1 ? fd.nfx : fd.nfx + fd.nfy);
   const int64_t sy = d.nx + (dc == 0 ? 1 : 0);
   const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
-  const int64_t f = foff + ck * sz + cj * sy + ci;
+  f = foff + ck * sz + cj * sy + ci;
+  return acc;
+}
+
+__global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
+                                     const int32_t* __restrict__ shell_cell,
+                                     const int32_t* __restrict__ off,
+                                     const int32_t* __restrict__ key,
+                                     const double* __restrict__ F, double scale, int set,
+                                     double* __restrict__ u) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= 3 * n_shell) return;
+  bool any;
+  int64_t f;
+  const double acc = spread_face(d, mk, n_shell, shell_cell, off, key, F, tid, any, f);
+  if (!any) return;
   u[f] = set ? scale * acc : fma(scale, acc, u[f]);
+}
+
+// L1 norms of the spread forces R A and R B over the faces (every face of the
+// support is owned by one (shell cell, component) task): per block the sums
+// of |(R A)_f| and |(R B)_f| over its tasks (fixed grid and order),
+// part[2 blk], part[2 blk + 1].
+constexpr int kSpreadAsumBlocks = 256;
+__global__ void __launch_bounds__(TPB) k_shell_spread_asum2(
+    Dims d, MkView mk, int64_t n_shell, const int32_t* __restrict__ shell_cell,
+    const int32_t* __restrict__ off, const int32_t* __restrict__ key,
+    const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ part) {
+  double sa = 0.0, sb = 0.0;
+  for (int64_t tid = blockIdx.x * (int64_t)TPB + threadIdx.x; tid < 3 * n_shell;
+       tid += (int64_t)kSpreadAsumBlocks * TPB) {
+    bool any;
+    int64_t f;
+    sa += fabs(spread_face(d, mk, n_shell, shell_cell, off, key, A, tid, any, f));
+    sb += fabs(spread_face(d, mk, n_shell, shell_cell, off, key, B, tid, any, f));
+  }
+  __shared__ double sh[2][TPB];
+  sh[0][threadIdx.x] = sa;
+  sh[1][threadIdx.x] = sb;
+  __syncthreads();
+  for (int w = TPB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sh[0][0];
+    part[2 * blockIdx.x + 1] = sh[1][0];
+  }
 }
 
 // ---- exclusive scan of int32 (three phases, 4096 elements per block) ----
@@ -551,8 +609,8 @@ static ibm_status grow_entries(ibm_ctx* c, int64_t ne) {
   m.entries_cap = 0;
   const int64_t cap = ne > 0 ? ne : 1;
   if (cudaMalloc(&m.entry_key, sizeof(int32_t) * cap) != cudaSuccess ||
-      cudaMalloc(&m.ell_base, sizeof(int32_t) * (cap / 32 + 2)) != cudaSuccess ||
-      cudaMalloc(&m.ell_len, sizeof(int32_t) * (cap / 32 + 2)) != cudaSuccess ||
+      cudaMalloc(&m.ell_base, sizeof(int32_t) * (cap / kEllCells + 2)) != cudaSuccess ||
+      cudaMalloc(&m.ell_len, sizeof(int32_t) * (cap / kEllCells + 2)) != cudaSuccess ||
       cudaMalloc(&m.shell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.ell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.shell_off, sizeof(int32_t) * (cap + 1)) != cudaSuccess) {
@@ -645,7 +703,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   k_sort_segments<<<div_up(ns, TPB), TPB, 0, s>>>(ns, m.shell_off, m.entry_key);
   IBM_LAUNCH_CHECK(c);
   // interleaved layout for the B^T t gather, in the order of ell_cell
-  const int64_t ng = (ns + 31) / 32;
+  const int64_t ng = ell_groups(ns);
   int32_t* cnt = c->cell_count;   // free again: reused for the group sizes
   int32_t* perm = c->cell_flag;   // free again (fill counters): the layout order
   count_launch();
@@ -695,7 +753,7 @@ void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double
   const MarkerData& m = c->mk;
   if (m.n == 0 || m.n_shell == 0) return;
   count_launch();
-  k_shell_gradt<<<div_up(m.n_shell, TPB), TPB, 0, c->stream>>>(
+  k_shell_gradt<<<div_up(32 * ell_groups(m.n_shell), TPB), TPB, 0, c->stream>>>(
       m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
       scale, out);
 }
@@ -787,6 +845,15 @@ void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double
   count_launch();
   k_shell_spread_faces<<<div_up(3 * m.n_shell, TPB), TPB, 0, c->stream>>>(
       c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, scale, 0, u);
+}
+
+int launch_shell_spread_asum2(ibm_ctx* c, const double* A, const double* B, double* part) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0 || m.n_shell == 0) return 0;
+  count_launch();
+  k_shell_spread_asum2<<<kSpreadAsumBlocks, TPB, 0, c->stream>>>(
+      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, A, B, part);
+  return kSpreadAsumBlocks;
 }
 
 void launch_shell_spread_faces_set(ibm_ctx* c, const double* F, double* u) {

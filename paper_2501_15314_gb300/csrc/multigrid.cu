@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
 // between lanes by shuffles, the block's rows (and the two y-halo rows) are
 // staged as float4 in shared memory for the y-neighbours, z by the march.
 template <typename TB>
-__global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restrict__ b,
+__global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __restrict__ b,
                                                       float* __restrict__ bcopy,
                                                       float* __restrict__ xo, float w0h2,
                                                       float w1, float h2, int two, int zc) {
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(32 * VY) k_first_v4(Dims d, const TB* __restri
 
 // Residual restriction, four fine cells (two coarse cells) per thread and
 // two fine rows (one coarse row); the march runs over fine planes.
-__global__ void __launch_bounds__(32 * VY) k_restrict_v4(Dims d, Dims dc,
+__global__ void __launch_bounds__(32 * VY, 4) k_restrict_v4(Dims d, Dims dc,
                                                          const float* __restrict__ x,
                                                          const float* __restrict__ b,
                                                          float* __restrict__ bcoarse, float inv_h2,

@@ -180,3 +180,54 @@ def test_heavy_sphere_falls_slower_than_in_vacuum():
     assert vacuum < b.us[2] < 0.0                  # falls, but slower than in vacuum
     assert abs(b.us[0]) + abs(b.us[1]) < 1e-3 * abs(b.us[2])
     assert b.xc[2] < 0.55
+
+
+def test_spread_norm_sees_little_of_the_weak_modes_of_C():
+    # C = R^T R at marker spacing h: its weakest eigenvectors are force
+    # patterns that R spreads to almost nothing (||R v||_2^2 = lambda), which
+    # the scalar C^{-1} ~ 2 I corrections damp only by |1 - 2 lambda| each
+    from oracle import mac, schur
+    from paper_2501_15314_gb300 import workloads as wl
+    n, r = 20, 0.2
+    g = mac.Grid(n)
+    X = wl.fibonacci_sphere(wl.markers_for_spacing(r, 1.0 / n), r, [0.5, 0.5, 0.5])
+    S = schur.SchurSystem(g, X)
+    lam, V = np.linalg.eigh(S.C.toarray())
+    assert lam[0] < 0.02 and lam[-1] < 0.6
+    weak, strong = V[:, 0], V[:, -1]
+    assert np.linalg.norm(S.R @ weak) ** 2 == pytest.approx(lam[0], rel=1e-8)
+    assert abs(1 - 2 * lam[0]) > 0.96
+    ratio = lambda v: np.abs(S.R @ v).sum() / np.abs(v).sum()  # noqa: E731
+    assert ratio(weak) < 0.1 * ratio(strong)
+
+
+def test_spread_criterion_stops_early_with_the_same_body_motion():
+    # a sedimenting sphere (r 0.15 on 32^3, markers at spacing h, density
+    # ratio 1.5: at 1.05 this coarse sphere's rotational update is unstable
+    # by itself) one step after release: the marker norm of
+    # Eq. (convergence_criterion) stalls above 1e-3 on the weak modes of C,
+    # while the spread norm reaches it within a few corrections; the body's
+    # velocity differs by far less than the step changes it
+    import copy
+    from oracle import fsi, mac
+    from paper_2501_15314_gb300 import workloads as wl
+    n, r, th, dt = 32, 0.15, 1.5, 5e-4
+    g = mac.Grid(n)
+    nm = wl.markers_for_spacing(r, 1.0 / n)
+    L0 = wl.fibonacci_sphere(nm, r, [0.0, 0.0, 0.0])
+    bid = np.zeros(nm, dtype=int)
+    b = fsi.RigidSphere(r, th, np.array([0.5, 0.5, 0.55]), np.array([0.5, 0.5, 0.55]))
+    u = np.zeros(g.n_faces)
+    kw = dict(gravity=(0, 0, -10.0), tol=1e-3, rtol=1e-10)
+    out = fsi.fsi_step(g, 50.0, dt, [b], L0, bid, u, u, np.zeros(g.m), np.zeros(3 * nm),
+                       max_inner=60, criterion="eulerian", **kw)
+    state = (out["u"], u, out["p"], out["F"])
+    res = {}
+    for crit, cap in (("lagrangian", 25), ("eulerian", 25)):
+        bc = copy.deepcopy(b)
+        o = fsi.fsi_step(g, 50.0, dt, [bc], L0, bid, *state, max_inner=cap, criterion=crit, **kw)
+        res[crit] = (o["inner"], o["ratio"], bc.us.copy())
+    (nl, rl, ul), (ne, re_, ue) = res["lagrangian"], res["eulerian"]
+    assert ne <= 8 and re_ < 1e-3, res
+    assert nl == 25 and rl > 1e-3, res
+    assert abs(ue[2] - ul[2]) < 1e-2 * abs(ul[2] - b.us[2]), (res, b.us)

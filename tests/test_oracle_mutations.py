@@ -120,6 +120,9 @@ MUTATIONS = [
      "test_oracle_fsi", "test_fluid_momentum_uniform_and_rotating_fields", ()),
     ("skew matrix: one sign", fsi, "skew", "[v[2], 0.0, -v[0]]", "[-v[2], 0.0, -v[0]]",
      "test_oracle_fsi", "test_rodrigues_increment_rotates_by_the_ab2_angle", ()),
+    ("spread criterion: norm of F in place of F'", fsi, "fsi_step",
+     "ratio = np.abs(sys.R @ Fc).sum() / nF", "ratio = np.abs(sys.R @ F).sum() / nF",
+     "test_oracle_fsi", "test_spread_criterion_stops_early_with_the_same_body_motion", ()),
     ("two-way correction: half the update", fsi, "fsi_step",
      "u = u + xi * (1.0 / a) *", "u = u + xi * (0.5 / a) *",
      "test_oracle_fsi", "test_fixed_body_one_correction_equals_one_way_step", ()),
