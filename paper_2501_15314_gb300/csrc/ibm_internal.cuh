@@ -230,9 +230,11 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float
                       float* en, double* u, double us, int mode, cudaStream_t s);
 // predictor RHS with the convective term of u_n fused in (with_adv != 0),
 // evaluated in double-single arithmetic (see k_predictor_rhs_ds)
+// (u_hi, u_lo: FP32 face scratch of nf values each, receiving u^n as pairs)
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,
                               const double* p_n, const double* f_body, int with_adv,
-                              double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
+                              double inv_2dt, double inv_h, double* rhs, float* u_hi,
+                              float* u_lo, cudaStream_t s);
 
 // ---- markers (markers.cu) ----
 ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);
@@ -347,7 +349,10 @@ void prof_end_or_note(ibm_ctx* c, int handle, double bytes);
 // Interleaved layout of the B^T t gather: a group (one warp) holds kEllCells
 // shell cells, kEllLanes lanes per cell; lane l takes the entries
 // p = kEllLanes r + l % kEllLanes of its cell, stored at base + 32 r + l.
-constexpr int kEllLanes = 4;
+#ifndef IBM_ELL_LANES
+#define IBM_ELL_LANES 4
+#endif
+constexpr int kEllLanes = IBM_ELL_LANES;
 constexpr int kEllCells = 32 / kEllLanes;
 __host__ __device__ inline int64_t ell_groups(int64_t n_shell) {
   return (n_shell + kEllCells - 1) / kEllCells;
@@ -356,8 +361,8 @@ __host__ __device__ inline int64_t ell_groups(int64_t n_shell) {
 // Sum of the kEllLanes lanes of a cell, in a fixed order (all 32 lanes of
 // the warp take part).
 __device__ __forceinline__ double ell_combine(double v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
+#pragma unroll
+  for (int o = 1; o < kEllLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 

@@ -329,10 +329,17 @@ __device__ __forceinline__ float inv_nn(int nn) {
 }
 __device__ __forceinline__ float w_over(float w, int nn) { return w * inv_nn(nn); }
 
+// Planes per thread of the four-cell kernels: about four blocks per SM over
+// the grid, at most kVecZcMax (each thread loads the planes above and below
+// its first and last ones once more, and sets up its weights once).
+#ifndef IBM_VEC_ZC_MAX
+#define IBM_VEC_ZC_MAX 4
+#endif
+constexpr int kVecZcMax = IBM_VEC_ZC_MAX;
 int vec_zc(Dims d) {
   const int64_t bxy = (int64_t)div_up(d.nx / 4, 32) * div_up(d.ny, VY);
   int64_t zc = (int64_t)d.nz * bxy / (152 * 4);
-  zc = zc < 1 ? 1 : (zc > 4 ? 4 : zc);
+  zc = zc < 1 ? 1 : (zc > kVecZcMax ? kVecZcMax : zc);
   return (int)zc;
 }
 
@@ -458,16 +465,35 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
     nyp[q] = nrow(j + 1, q);
   }
   // per-thread weights away from the y and z walls (neighbour count 4 + x-count)
-  int ax[4];
   float r_own[4], w1_own[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    ax[q] = (i0 + q > 0) + (i0 + q < d.nx - 1);
-    r_own[q] = w_over(w0h2, ax[q] + 4);
-    w1_own[q] = w_over(w1, ax[q] + 4);
+    const int ax = (i0 + q > 0) + (i0 + q < d.nx - 1);
+    r_own[q] = w_over(w0h2, ax + 4);
+    w1_own[q] = w_over(w1, ax + 4);
   }
   const float r_l = w_over(w0h2, ((i0 - 1 > 0) + 1) + 4);
   const float r_r = w_over(w0h2, (1 + (i0 + 4 < d.nx - 1)) + 4);
+  // Away from the y and z walls the two steps are one 7-point stencil on b
+  // with per-thread weights: x1 = r b (r = w0 h^2 / nn), and with
+  // nn x1 = w0 h^2 b,
+  //   x2 = x1 + (w1/nn)(h^2 b - nn x1 + sum_nb x1)
+  //      = c0 b + cl b_left + cr b_right + cy (b_y- + b_y+ + b_z- + b_z+),
+  // c0 = r + (w1/nn) h^2 (1 - w0), cl = (w1/nn) r_left, cr = (w1/nn) r_right,
+  // cy = (w1/nn) r (the y and z neighbours share the cell's x-count).
+  float k0[4], kl[4], kr[4], ky[4];
+  {
+    const float h2w = h2 - w0h2;   // h^2 (1 - w0)
+    const float rl4[4] = {r_l, r_own[0], r_own[1], r_own[2]};
+    const float rr4[4] = {r_own[1], r_own[2], r_own[3], r_r};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      k0[q] = fmaf(w1_own[q], h2w, r_own[q]);
+      kl[q] = w1_own[q] * rl4[q];
+      kr[q] = w1_own[q] * rr4[q];
+      ky[q] = w1_own[q] * r_own[q];
+    }
+  }
   float4 bp = (act && z0 > 0) ? ld4_any(b + c - sz) : Z4;
   float4 bc = act ? ld4_any(b + c) : Z4;
   for (int z = z0; z < z1; ++z, c += sz) {
@@ -506,15 +532,10 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
       // constants
       const float xl[4] = {left, bcv[0], bcv[1], bcv[2]};
       const float xr[4] = {bcv[1], bcv[2], bcv[3], right};
-      const float rl[4] = {r_l, r_own[0], r_own[1], r_own[2]};
-      const float rr[4] = {r_own[1], r_own[2], r_own[3], r_r};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int nn = ax[q] + 4;
-        const float x1q = r_own[q] * bcv[q];
-        const float s = fmaf(rl[q], xl[q], rr[q] * xr[q]) +
-                        r_own[q] * ((ymv[q] + ypv[q]) + (bpv[q] + bnv[q]));
-        o[q] = fmaf(w1_own[q], fmaf(h2, bcv[q], s - (float)nn * x1q), x1q);
+        const float s4 = (ymv[q] + ypv[q]) + (bpv[q] + bnv[q]);
+        o[q] = fmaf(k0[q], bcv[q], fmaf(kl[q], xl[q], fmaf(kr[q], xr[q], ky[q] * s4)));
       }
     } else {
       // x1 = w0 h^2 b / nn at the own cells and the two x-halo cells

@@ -98,9 +98,10 @@ def test_free_and_held_bodies_ragged_grid(cuda_device):
 def test_stopping_test_matches_oracle(cuda_device, criterion):
     # the corrections stop where the oracle's do, on the marker norm of
     # Eq. (convergence_criterion) or on the spread (face) norm, with the
-    # same ratio and the same state
-    specs = [((0.5, 0.52, 0.55), 0.2, 1.2, (0.0, 0.0, -0.1), (0.0, 0.5, 0.0), True)]
-    errs = _run(16, 16, 16, specs, 3, 50.0, 0.01, (0.0, 0.0, -1.0), 1.0, 40, tol=1e-3,
+    # same ratio and the same state (a coarse sphere under a random body
+    # force: the oracle stops after 28 to 37 corrections at tol 2e-2)
+    specs = [((0.5, 0.52, 0.55), 0.2, 1.5, (0.0, 0.0, -0.1), (0.0, 0.5, 0.0), True)]
+    errs = _run(16, 16, 16, specs, 3, 50.0, 0.01, (0.0, 0.0, -1.0), 0.8, 40, tol=2e-2,
                 criterion=criterion)
     for e in errs:
         for k, v in e.items():
