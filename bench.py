@@ -43,21 +43,26 @@ sys.path.insert(0, str(ROOT))
 METRIC = "Schur solves/s at 256^3 to 1e-8 residual, FP32-precond vs FP64; HBM fraction"
 UNIT = "solves/s"
 
-# DRAM traffic / algorithmic bytes of each timed kernel class, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum of every launch of one
-# step) of the same kernels on the eight-sphere workload at 192^3, where the
-# capture fits the profiling size rule; the traffic of a 256^3 launch is this
-# ratio times its algorithmic bytes (traffic grows with the units processed:
-# cells x vectors).  The profile summaries keep the capture's command and
-# the per-kernel numbers.  A class whose kernel changes after the
-# capture must be removed here (its traffic then reads null).
+# DRAM traffic / algorithmic bytes of each timed kernel class: ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum of the class's kernels, each
+# captured alone (one launch, one pass) in one step of the 256^3 eight-sphere
+# workload, over the algorithmic bytes of those launches.  The profile
+# summary keeps the commands and the per-launch numbers.  A class whose kernel
+# changes after the capture must be removed here (its traffic then reads
+# null).  Below 1: part of a launch's output is still in the 129 MB L2 when
+# it ends (written back later, often never: the next kernel reads it there).
 NCU_TRAFFIC_RATIO = {
-    # (the predictor's Chebyshev step, 0.958 in that capture, is left out: the
-    # kernel was made a template on its mode after the capture)
-    # FP32 Gram-Schmidt (float4 kernels): at 192^3 the new vector w (28 MB)
-    # is partly L2-resident, as at 256^3 (67 MB)
-    "multidot": 1.001,
-    "axpy_norm": 0.913,
+    # predictor FP32 Chebyshev step (mode 1): 631.8 + 182.2 MB for 808.5 MB
+    "helm_sweep": 1.0067,
+    # finest-level smoothing, one V-cycle: k_first_v4 67.1 + 25.8 MB and the
+    # two k_sweep_v4 134.2 + 39.0 and 134.2 + 36.8 MB, for 134.2 + 2 x 201.3 MB
+    "mg_smooth_fine": 0.8144,
+    # FP32 Gram-Schmidt at basis lengths 6 and 7
+    "multidot": 1.0042,
+    "axpy_norm": 0.9744,
+    # marker terms of one Schur product: k_marker_grad_interp 13.8 MB and
+    # k_shell_gradt_ds 120.6 + 3.0 MB for 125.0 MB
+    "schur_markers": 1.099,
 }
 
 
@@ -138,8 +143,10 @@ def roofline(prof, steps, hbm, peak_kind):
             "unit": "GB/s", "frac": cb["frac"], "peak_kind": peak_kind,
             "traffic": (NCU_TRAFFIC_RATIO[cls] * cb["bytes_per_launch"]
                         if cls in NCU_TRAFFIC_RATIO else None),
-            "traffic_source": "ncu DRAM bytes per algorithmic byte at 192^3, scaled to this "
-                              "launch's units", "avg_launch_ms": cb["avg_launch_ms"],
+            "traffic_source": ("ncu DRAM bytes per algorithmic byte of the class's kernels, "
+                               "each captured alone in one step at 256^3, times this "
+                               "launch's algorithmic bytes"),
+            "avg_launch_ms": cb["avg_launch_ms"],
             "bytes_per_launch": cb["bytes_per_launch"]}
     sv = prof["solve"]
     n_sv = max(1, sv["launches"])

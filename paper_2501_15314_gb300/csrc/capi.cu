@@ -551,7 +551,7 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
 
   // 1. predictor (Eq. (ustar))
   launch_predictor_rhs_adv(c->d, u_n, u_nm1, p_n, f_body, o->with_advection, 1.0 / (2.0 * c->dt),
-                           inv_h, c->f1, c->g1, c->g2, str);
+                           inv_h, c->f1, str);
   if (n > 0) launch_shell_spread_faces(c, F_n, 1.0, c->f1);
   IBM_LAUNCH_CHECK(c);
   double* u_star = c->f2;

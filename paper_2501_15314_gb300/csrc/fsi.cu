@@ -373,7 +373,7 @@ ibm_status ibm_fsi_step(ibm_ctx* c, int32_t nb, ibm_rigid_sphere* bodies, int64_
 
   // ---- Step 2: predictor (Eq. (ustar_two_way)) into u_np1 ----
   launch_predictor_rhs_adv(c->d, u_n, u_nm1, p_n, f_body, o->with_advection, 1.0 / (2.0 * dt),
-                           inv_h, c->f1, c->g1, c->g2, str);
+                           inv_h, c->f1, str);
   launch_shell_spread_faces(c, F_n, 1.0, c->f1);
   IBM_LAUNCH_CHECK(c);
   s = helmholtz_solve(c, c->f1, u_np1, o, &fst->helm_iters, &fst->helm_relres);

@@ -230,11 +230,9 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float
                       float* en, double* u, double us, int mode, cudaStream_t s);
 // predictor RHS with the convective term of u_n fused in (with_adv != 0),
 // evaluated in double-single arithmetic (see k_predictor_rhs_ds)
-// (u_hi, u_lo: FP32 face scratch of nf values each, receiving u^n as pairs)
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,
                               const double* p_n, const double* f_body, int with_adv,
-                              double inv_2dt, double inv_h, double* rhs, float* u_hi,
-                              float* u_lo, cudaStream_t s);
+                              double inv_2dt, double inv_h, double* rhs, cudaStream_t s);
 
 // ---- markers (markers.cu) ----
 ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);

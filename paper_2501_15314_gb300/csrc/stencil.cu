@@ -142,32 +142,11 @@ __device__ __forceinline__ T sel3(int c, T a, T b, T d) {
 
 constexpr int ZH = 16;
 
-// u^n split once into FP32 pairs, hi and lo in the packed face layout (each
-// value of u^n is read by up to nine fluxes of the three launches below).
-__global__ void k_split_faces(const double* __restrict__ u, float* __restrict__ hi,
-                              float* __restrict__ lo, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const dsf v = split_exact(__ldg(u + i));
-    hi[i] = v.hi;
-    lo[i] = v.lo;
-  }
-}
-
-// The split u^n as pairs: (hi, lo) of one face.
-struct SplitU {
-  const float* __restrict__ hi;
-  const float* __restrict__ lo;
-};
-
-__device__ __forceinline__ dsf ldp(const SplitU& u, int64_t f) {
-  return dsf{__ldg(u.hi + f), __ldg(u.lo + f)};
-}
-
-// u_E at (x, y, z) of its own face grid, as its FP32 pair
+// u_E at (x, y, z) of its own face grid, split into an FP32 pair
 template <int E>
-__device__ __forceinline__ dsf ldu(const FaceGeom& g, const SplitU& u, int x, int y, int z) {
-  return ldp(u, g.off[E] + (int64_t)z * g.sz[E] + (int64_t)y * g.sy[E] + x);
+__device__ __forceinline__ dsf ldu(const FaceGeom& g, const double* __restrict__ u, int x, int y,
+                                   int z) {
+  return split_exact(__ldg(u + g.off[E] + (int64_t)z * g.sz[E] + (int64_t)y * g.sy[E] + x));
 }
 
 // Convective flux on the edge between the C-face at (x, y, z) and the E-face
@@ -175,8 +154,8 @@ __device__ __forceinline__ dsf ldu(const FaceGeom& g, const SplitU& u, int x, in
 // (sum of the two u_C adjacent along E); 0 on the walls (q = 0 or the last
 // E-face).  For an interior C-face every value read is an interior face.
 template <int C, int E>
-__device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const SplitU& u, int x, int y,
-                                            int z, int q) {
+__device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const double* __restrict__ u,
+                                            int x, int y, int z, int q) {
   if (q <= 0 || q >= g.n[E][E] - 1) return dsf{0.f, 0.f};
   const int ax = E == 0 ? q : x, ay = E == 1 ? q : y, az = E == 2 ? q : z;
   const dsf ue = ds_add(ldu<E>(g, u, ax - (C == 0), ay - (C == 1), az - (C == 2)),
@@ -204,7 +183,7 @@ __device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const SplitU& u, 
 // Templating on C makes every stride and boundary test a compile-time case.
 template <int C>
 __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
-    Dims d, FaceGeom g, SplitU un, const double* __restrict__ unm1,
+    Dims d, FaceGeom g, const double* __restrict__ un, const double* __restrict__ unm1,
     const double* __restrict__ pn, const double* __restrict__ fb, int with_adv, dsf c4, dsf c1,
     dsf cp_h, dsf ca, double* __restrict__ rhs) {
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -246,7 +225,7 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
       continue;
     }
     const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
-    const dsf u0 = ldp(un, f);
+    const dsf u0 = split_exact(__ldg(un + f));
     // 4/(2dt) u^n - 1/(2dt) u^{n-1} - (p_+ - p_-)/h (+ f)
     dsf v = ds_add(ds_mul(c4, u0), ds_neg(ds_mul(c1, split_exact(__ldg(unm1 + f)))));
     const dsf dp = ds_add(split_exact(__ldg(pn + cp)), ds_neg(split_exact(__ldg(pn + cp - cstr))));
@@ -640,25 +619,20 @@ dsf host_ds(double x) {
 
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1, const double* p_n,
                               const double* f_body, int with_adv, double inv_2dt, double inv_h,
-                              double* rhs, float* u_hi, float* u_lo, cudaStream_t s) {
+                              double* rhs, cudaStream_t s) {
   const FaceGeom g = make_face_geom(d);
-  const FaceDims fd = face_dims(d);
-  const int64_t nf = fd.nfx + fd.nfy + fd.nfz;
   const dsf c4 = host_ds(4.0 * inv_2dt), c1 = host_ds(inv_2dt), cph = host_ds(inv_h),
             ca = host_ds(0.25 * inv_h);
-  count_launch();
-  k_split_faces<<<kRedBlocks, 256, 0, s>>>(u_n, u_hi, u_lo, nf);
-  const SplitU un{u_hi, u_lo};
   const dim3 b(BX, BY);
   count_launch();
   k_predictor_rhs_ds<0><<<dim3(div_up(d.nx + 1, BX), div_up(d.ny, BY), div_up(d.nz, ZH)), b, 0,
-                          s>>>(d, g, un, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
+                          s>>>(d, g, u_n, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
   count_launch();
   k_predictor_rhs_ds<1><<<dim3(div_up(d.nx, BX), div_up(d.ny + 1, BY), div_up(d.nz, ZH)), b, 0,
-                          s>>>(d, g, un, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
+                          s>>>(d, g, u_n, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
   count_launch();
   k_predictor_rhs_ds<2><<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz + 1, ZH)), b, 0,
-                          s>>>(d, g, un, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
+                          s>>>(d, g, u_n, u_nm1, p_n, f_body, with_adv, c4, c1, cph, ca, rhs);
 }
 
 }  // namespace ibm

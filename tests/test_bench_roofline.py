@@ -44,6 +44,7 @@ def test_achieved_bandwidth_and_dominant_class():
     assert roof["frac"] == pytest.approx(expect / 6787.9, rel=1e-12)
     assert roof["avg_launch_ms"] == pytest.approx(1.838854 / 42, rel=1e-12)
     assert roof["bytes_per_launch"] == pytest.approx(178956971.0)
+    assert roof["traffic"] == pytest.approx(bench.NCU_TRAFFIC_RATIO["mg_smooth_fine"] * 178956971.0)
     assert len(classes) == len(bench.ROOFLINE_CLASSES)
     for v in classes.values():
         assert v["achieved_gbs"] == pytest.approx(
