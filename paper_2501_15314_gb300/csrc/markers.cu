@@ -295,22 +295,36 @@ __global__ void k_ell_len(int64_t n_shell, const int32_t* __restrict__ off,
 }
 
 // Fills the interleaved layout with keys and G^T R coefficients (zero padding).
+// One warp per group: round r, lane l fills slot base[w] + 32 r + l, entry
+// p = kEllLanes r + l % kEllLanes of the group's cell l / kEllLanes (zeros
+// past the cell's count or for a cell past the last shell cell).
 __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict__ off,
                            const int32_t* __restrict__ key, const int32_t* __restrict__ base,
                            const int32_t* __restrict__ len, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ ell_cell, Dims d, int64_t n_ell,
                            int32_t* ekey, double* ecoef) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n_shell) return;
-  const int64_t w = q / kEllCells;
-  const int cl = (int)(q % kEllCells);
-  const int32_t r = perm[q];
-  const int32_t a = off[r], nseg = off[r + 1] - a, L = kEllLanes * len[w];
-  const int64_t c = ell_cell[q];
-  const int g[3] = {(int)(c % d.nx), (int)((c / d.nx) % d.ny), (int)(c / ((int64_t)d.nx * d.ny))};
-  for (int p = 0; p < L; ++p) {
-    const int64_t dst = base[w] + (int64_t)(p / kEllLanes) * 32 + kEllLanes * cl + p % kEllLanes;
-    if (p < nseg) {
+  const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t w = tq >> 5;
+  if (w >= ell_groups(n_shell)) return;
+  const int lane = (int)(tq & 31);
+  const int64_t q = w * kEllCells + lane / kEllLanes;
+  const bool live = q < n_shell;
+  int32_t a = 0, nseg = 0;
+  int g[3] = {0, 0, 0};
+  if (live) {
+    const int32_t r = perm[q];
+    a = off[r];
+    nseg = off[r + 1] - a;
+    const int64_t c = ell_cell[q];
+    g[0] = (int)(c % d.nx);
+    g[1] = (int)((c / d.nx) % d.ny);
+    g[2] = (int)(c / ((int64_t)d.nx * d.ny));
+  }
+  const int32_t rounds = len[w];
+  for (int32_t rr = 0; rr < rounds; ++rr) {
+    const int64_t dst = base[w] + (int64_t)rr * 32 + lane;
+    const int p = kEllLanes * rr + lane % kEllLanes;
+    if (live && p < nseg) {
       const int32_t kk = key[a + p];
       ekey[dst] = kk;
       const int64_t k = kk >> 6;
@@ -720,7 +734,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   const int64_t n_ell = c->host_flag[0];
   if ((st = grow_ell(c, n_ell)) != IBM_OK) return st;
   count_launch();
-  k_ell_fill<<<div_up(ns, TPB), TPB, 0, s>>>(mv, ns, m.shell_off, m.entry_key, m.ell_base,
+  k_ell_fill<<<div_up(32 * ng, TPB), TPB, 0, s>>>(mv, ns, m.shell_off, m.entry_key, m.ell_base,
                                              m.ell_len, perm, m.ell_cell, c->d, n_ell, m.ell_key,
                                              m.ell_coef);
   IBM_LAUNCH_CHECK(c);
