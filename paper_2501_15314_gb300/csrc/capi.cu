@@ -194,7 +194,7 @@ static void free_all(ibm_ctx* c) {
     cudaFree(L.x32); cudaFree(L.b32); cudaFree(L.t32);
     cudaFree(L.x64); cudaFree(L.b64); cudaFree(L.t64);
   }
-  cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32);
+  cudaFree(c->coarse_pinv64); cudaFree(c->coarse_pinv32); cudaFree(c->chain_tab);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (cudaEvent_t& e : c->ev_iter)

@@ -144,6 +144,10 @@ struct ibm_ctx {
   double* coarse_pinv64 = nullptr; // dense [mc][mc]
   float* coarse_pinv32 = nullptr;
   int coarse_m = 0;
+  // one-CTA chain of the coarse levels: its first level (-1: none), and the
+  // packed coordinates and neighbour masks of its cells, built at setup
+  int chain_l = -1;
+  void* chain_tab = nullptr;
 
   ibm::MarkerData mk;
   bool markers_set = false;

@@ -329,16 +329,22 @@ __device__ __forceinline__ float inv_nn(int nn) {
 }
 __device__ __forceinline__ float w_over(float w, int nn) { return w * inv_nn(nn); }
 
-// Planes per thread of the four-cell kernels: about four blocks per SM over
-// the grid, at most kVecZcMax (each thread loads the planes above and below
-// its first and last ones once more, and sets up its weights once).
+// Planes per thread of the four-cell kernels: about IBM_VEC_ZC_BLOCKS blocks
+// per SM over the grid, at most kVecZcMax (each thread loads the planes
+// above and below its first and last ones once more, and sets up its weights
+// once).  With eight, levels of 128^3 cells and below get one plane per
+// thread: there the kernels wait on memory latency rather than on bandwidth
+// or instruction issue, and more blocks in flight hide more of it.
 #ifndef IBM_VEC_ZC_MAX
 #define IBM_VEC_ZC_MAX 4
 #endif
 constexpr int kVecZcMax = IBM_VEC_ZC_MAX;
+#ifndef IBM_VEC_ZC_BLOCKS
+#define IBM_VEC_ZC_BLOCKS 8
+#endif
 int vec_zc(Dims d) {
   const int64_t bxy = (int64_t)div_up(d.nx / 4, 32) * div_up(d.ny, VY);
-  int64_t zc = (int64_t)d.nz * bxy / (152 * 4);
+  int64_t zc = (int64_t)d.nz * bxy / (152 * IBM_VEC_ZC_BLOCKS);
   zc = zc < 1 ? 1 : (zc > kVecZcMax ? kVecZcMax : zc);
   return (int)zc;
 }
@@ -349,7 +355,10 @@ dim3 vec_grid(Dims d, int zc) {
 
 bool vec_ok(Dims d) { return d.nx % 4 == 0; }
 
-// xo = x + w D^{-1} (b - L x) for four cells per thread.
+// xo = x + w D^{-1} (b - L x) for four cells per thread.  Rows and planes
+// away from the y and z walls (a warp-uniform test) take a path whose
+// weights and neighbour counts are per-thread constants and whose loads
+// need no wall test.
 template <typename TO>
 __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __restrict__ x,
                                                       const float* __restrict__ b,
@@ -371,23 +380,36 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
   int ax[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) ax[q] = (i0 + q > 0) + (i0 + q < d.nx - 1);
-  float wi[4];
+  float wi[4], nni[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) wi[q] = w_over(w, ax[q] + 4);
+  for (int q = 0; q < 4; ++q) {
+    wi[q] = w_over(w, ax[q] + 4);
+    nni[q] = (float)(ax[q] + 4);
+  }
   const int ny_c = (j > 0) + (j < d.ny - 1);
+  const bool yin = ny_c == 2;
   float4 xp = (act && z0 > 0) ? ld4(x + c - sz) : Z4;
   float4 xc = act ? ld4(x + c) : Z4;
   for (int z = z0; z < z1; ++z, c += sz) {
-    const float4 xn = (act && z + 1 < d.nz) ? ld4(x + c + sz) : Z4;
-    const float4 ym = (act && j > 0) ? ld4(x + c - sy) : Z4;
-    const float4 yp = (act && j < d.ny - 1) ? ld4(x + c + sy) : Z4;
-    const float4 bb = act ? ld4(b + c) : Z4;
+    const bool inner = yin && z > 0 && z < d.nz - 1;
+    float4 xn = Z4, ym = Z4, yp = Z4, bb = Z4;
+    if (inner) {
+      if (act) {
+        xn = ld4(x + c + sz);
+        ym = ld4(x + c - sy);
+        yp = ld4(x + c + sy);
+        bb = ld4(b + c);
+      }
+    } else if (act) {
+      if (z + 1 < d.nz) xn = ld4(x + c + sz);
+      if (j > 0) ym = ld4(x + c - sy);
+      if (j < d.ny - 1) yp = ld4(x + c + sy);
+      bb = ld4(b + c);
+    }
     float left = __shfl_up_sync(kFull, xc.w, 1);
     float right = __shfl_down_sync(kFull, xc.x, 1);
     if (lane == 0) left = (act && i0 > 0) ? __ldg(x + c - 1) : 0.f;
     if (lane == 31) right = (act && i0 + 4 < d.nx) ? __ldg(x + c + 4) : 0.f;
-    const int zn = (z > 0) + (z < d.nz - 1);
-    const bool inner = ny_c == 2 && zn == 2;
     const float xv[4] = {xc.x, xc.y, xc.z, xc.w};
     const float xl[4] = {left, xc.x, xc.y, xc.z};
     const float xr[4] = {xc.y, xc.z, xc.w, right};
@@ -397,12 +419,20 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
     const float vzn[4] = {xn.x, xn.y, xn.z, xn.w};
     const float vb[4] = {bb.x, bb.y, bb.z, bb.w};
     float o[4];
+    if (inner) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int nn = ax[q] + ny_c + zn;
-      const float s = (xl[q] + xr[q]) + (vym[q] + vyp[q]) + (vzp[q] + vzn[q]);
-      const float wq = inner ? wi[q] : w_over(w, nn);
-      o[q] = fmaf(wq, fmaf(h2, vb[q], s - (float)nn * xv[q]), xv[q]);
+      for (int q = 0; q < 4; ++q) {
+        const float s = (xl[q] + xr[q]) + (vym[q] + vyp[q]) + (vzp[q] + vzn[q]);
+        o[q] = fmaf(wi[q], fmaf(h2, vb[q], s - nni[q] * xv[q]), xv[q]);
+      }
+    } else {
+      const int zn = (z > 0) + (z < d.nz - 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int nn = ax[q] + ny_c + zn;
+        const float s = (xl[q] + xr[q]) + (vym[q] + vyp[q]) + (vzp[q] + vzn[q]);
+        o[q] = fmaf(w_over(w, nn), fmaf(h2, vb[q], s - (float)nn * xv[q]), xv[q]);
+      }
     }
     if (act) st4(xo + c, make_float4(o[0], o[1], o[2], o[3]));
     xp = xc;
@@ -432,9 +462,9 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
   int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i0;
   const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   const int ny_c = (j > 0) + (j < d.ny - 1);
-  const int n0 = ny_c + (i0 > 0) + 1, n3 = ny_c + 1 + (i0 + 3 < d.nx - 1);
-  const int n12 = ny_c + 2;
   if (!two) {
+    const int n0 = ny_c + (i0 > 0) + 1, n3 = ny_c + 1 + (i0 + 3 < d.nx - 1);
+    const int n12 = ny_c + 2;
     for (int z = z0; z < z1; ++z, c += sz) {
       if (!act) continue;
       const float4 bv = ld4_any(b + c);
@@ -449,43 +479,25 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
     }
     return;
   }
-  // in-plane neighbour counts: own cells, x-neighbours at i0-1 and i0+4, and
-  // the rows j-1, j+1 (same x)
-  const int cx_m = (i0 - 1 > 0) + 1 + (j > 0) + (j < d.ny - 1);            // cell i0-1
-  const int cx_p = 1 + (i0 + 4 < d.nx - 1) + (j > 0) + (j < d.ny - 1);      // cell i0+4
-  auto nrow = [&](int jj, int q) {
-    const int ii = i0 + q;
-    return (ii > 0) + (ii < d.nx - 1) + (jj > 0) + (jj < d.ny - 1);
-  };
-  int nown[4], nym[4], nyp[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    nown[q] = nrow(j, q);
-    nym[q] = nrow(j - 1, q);
-    nyp[q] = nrow(j + 1, q);
-  }
-  // per-thread weights away from the y and z walls (neighbour count 4 + x-count)
-  float r_own[4], w1_own[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ax = (i0 + q > 0) + (i0 + q < d.nx - 1);
-    r_own[q] = w_over(w0h2, ax + 4);
-    w1_own[q] = w_over(w1, ax + 4);
-  }
-  const float r_l = w_over(w0h2, ((i0 - 1 > 0) + 1) + 4);
-  const float r_r = w_over(w0h2, (1 + (i0 + 4 < d.nx - 1)) + 4);
   // Away from the y and z walls the two steps are one 7-point stencil on b
   // with per-thread weights: x1 = r b (r = w0 h^2 / nn), and with
   // nn x1 = w0 h^2 b,
   //   x2 = x1 + (w1/nn)(h^2 b - nn x1 + sum_nb x1)
   //      = c0 b + cl b_left + cr b_right + cy (b_y- + b_y+ + b_z- + b_z+),
   // c0 = r + (w1/nn) h^2 (1 - w0), cl = (w1/nn) r_left, cr = (w1/nn) r_right,
-  // cy = (w1/nn) r (the y and z neighbours share the cell's x-count).
+  // cy = (w1/nn) r (the y and z neighbours share the cell's x-count).  There
+  // nn = 4 + x-count, the x-count is 2 except at an x-wall cell (1), so 1/nn
+  // is 1/6 or 1/5.
   float k0[4], kl[4], kr[4], ky[4];
   {
+    auto inv = [](bool two_x) { return two_x ? (1.f / 6.f) : 0.2f; };
+    const float f0 = inv(i0 > 0), f3 = inv(i0 + 3 < d.nx - 1);
+    const float fl = inv(i0 - 1 > 0), fr = inv(i0 + 4 < d.nx - 1);
+    const float r_own[4] = {w0h2 * f0, w0h2 * (1.f / 6.f), w0h2 * (1.f / 6.f), w0h2 * f3};
+    const float w1_own[4] = {w1 * f0, w1 * (1.f / 6.f), w1 * (1.f / 6.f), w1 * f3};
+    const float rl4[4] = {w0h2 * fl, r_own[0], r_own[1], r_own[2]};
+    const float rr4[4] = {r_own[1], r_own[2], r_own[3], w0h2 * fr};
     const float h2w = h2 - w0h2;   // h^2 (1 - w0)
-    const float rl4[4] = {r_l, r_own[0], r_own[1], r_own[2]};
-    const float rr4[4] = {r_own[1], r_own[2], r_own[3], r_r};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       k0[q] = fmaf(w1_own[q], h2w, r_own[q]);
@@ -494,16 +506,28 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
       ky[q] = w1_own[q] * r_own[q];
     }
   }
+  const bool yin = j >= 2 && j <= d.ny - 3;
   float4 bp = (act && z0 > 0) ? ld4_any(b + c - sz) : Z4;
   float4 bc = act ? ld4_any(b + c) : Z4;
   for (int z = z0; z < z1; ++z, c += sz) {
-    const float4 bn = (act && z + 1 < d.nz) ? ld4_any(b + c + sz) : Z4;
-    float4 ym, yp;
+    // rows and planes two cells away from the y and z walls (warp-uniform)
+    const bool inner = yin && z >= 2 && z <= d.nz - 3;
+    float4 bn = Z4, ym = Z4, yp = Z4;
     if constexpr (std::is_same<TB, float>::value) {
       // FP32 input: the y-neighbour rows come straight through L1
-      ym = (act && j > 0) ? ld4_any(b + c - sy) : Z4;
-      yp = (act && j < d.ny - 1) ? ld4_any(b + c + sy) : Z4;
+      if (inner) {
+        if (act) {
+          bn = ld4_any(b + c + sz);
+          ym = ld4_any(b + c - sy);
+          yp = ld4_any(b + c + sy);
+        }
+      } else if (act) {
+        if (z + 1 < d.nz) bn = ld4_any(b + c + sz);
+        if (j > 0) ym = ld4_any(b + c - sy);
+        if (j < d.ny - 1) yp = ld4_any(b + c + sy);
+      }
     } else {
+      bn = (act && z + 1 < d.nz) ? ld4_any(b + c + sz) : Z4;
       // rounded once, shared through shared memory
       sb[ty + 1][lane] = bc;
       if (ty == 0) sb[0][lane] = (act && j > 0) ? ld4_any(b + c - sy) : Z4;
@@ -517,19 +541,13 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
     float right = __shfl_down_sync(kFull, bc.x, 1);
     if (lane == 0) left = (act && i0 > 0) ? ld1_any(b + c - 1) : 0.f;
     if (lane == 31) right = (act && i0 + 4 < d.nx) ? ld1_any(b + c + 4) : 0.f;
-    const int zn = (z > 0) + (z < d.nz - 1);
-    const int znm = (z - 1 > 0) + (z - 1 < d.nz - 1);
-    const int znp = (z + 1 > 0) + (z + 1 < d.nz - 1);
     const float bcv[4] = {bc.x, bc.y, bc.z, bc.w};
     const float bpv[4] = {bp.x, bp.y, bp.z, bp.w};
     const float bnv[4] = {bn.x, bn.y, bn.z, bn.w};
     const float ymv[4] = {ym.x, ym.y, ym.z, ym.w};
     const float ypv[4] = {yp.x, yp.y, yp.z, yp.w};
     float o[4];
-    if (j >= 2 && j <= d.ny - 3 && z >= 2 && z <= d.nz - 3) {
-      // rows and planes two cells away from the y and z walls: every
-      // neighbour count is 4 + its x-count, so the weights are per-thread
-      // constants
+    if (inner) {
       const float xl[4] = {left, bcv[0], bcv[1], bcv[2]};
       const float xr[4] = {bcv[1], bcv[2], bcv[3], right};
 #pragma unroll
@@ -538,23 +556,34 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
         o[q] = fmaf(k0[q], bcv[q], fmaf(kl[q], xl[q], fmaf(kr[q], xr[q], ky[q] * s4)));
       }
     } else {
-      // x1 = w0 h^2 b / nn at the own cells and the two x-halo cells
+      // the two steps as written: x1 = w0 h^2 b / nn at the own cells, the
+      // two x-halo cells and the y and z neighbours, then the second step
+      auto nrow = [&](int jj, int q) {
+        const int ii = i0 + q;
+        return (ii > 0) + (ii < d.nx - 1) + (jj > 0) + (jj < d.ny - 1);
+      };
+      const int zn = (z > 0) + (z < d.nz - 1);
+      const int znm = (z - 1 > 0) + (z - 1 < d.nz - 1);
+      const int znp = (z + 1 > 0) + (z + 1 < d.nz - 1);
+      const int cx_m = (i0 - 1 > 0) + 1 + ny_c;          // cell i0-1
+      const int cx_p = 1 + (i0 + 4 < d.nx - 1) + ny_c;   // cell i0+4
       float x1[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) x1[q] = w_over(w0h2, nown[q] + zn) * bcv[q];
+      for (int q = 0; q < 4; ++q) x1[q] = w_over(w0h2, nrow(j, q) + zn) * bcv[q];
       const float x1l = w_over(w0h2, cx_m + zn) * left;
       const float x1r = w_over(w0h2, cx_p + zn) * right;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int ii = i0 + q;
+        const int nown = nrow(j, q);
         float s = 0.f;
         if (ii > 0) s += (q == 0) ? x1l : x1[q - 1];
         if (ii < d.nx - 1) s += (q == 3) ? x1r : x1[q + 1];
-        if (j > 0) s += w_over(w0h2, nym[q] + zn) * ymv[q];
-        if (j < d.ny - 1) s += w_over(w0h2, nyp[q] + zn) * ypv[q];
-        if (z > 0) s += w_over(w0h2, nown[q] + znm) * bpv[q];
-        if (z < d.nz - 1) s += w_over(w0h2, nown[q] + znp) * bnv[q];
-        const int nn = nown[q] + zn;
+        if (j > 0) s += w_over(w0h2, nrow(j - 1, q) + zn) * ymv[q];
+        if (j < d.ny - 1) s += w_over(w0h2, nrow(j + 1, q) + zn) * ypv[q];
+        if (z > 0) s += w_over(w0h2, nown + znm) * bpv[q];
+        if (z < d.nz - 1) s += w_over(w0h2, nown + znp) * bnv[q];
+        const int nn = nown + zn;
         o[q] = fmaf(w_over(w1, nn), fmaf(h2, bcv[q], s - (float)nn * x1[q]), x1[q]);
       }
     }
@@ -695,9 +724,15 @@ __global__ void __launch_bounds__(32 * VY) k_prolong_v4(Dims d, Dims dc,
 // level's x, b and a ping-pong buffer live in shared memory, phases are
 // separated by __syncthreads, so the five to eight launches per coarse level
 // (each a few microseconds of latency for a few thousand cells) become one.
+// The packed coordinates i | j << 10 | k << 20 and the masks of existing
+// neighbours (bits x-, x+, y-, y+, z-, z+) of the chain's cells are built
+// once at setup and copied into shared memory by each launch, so that no
+// phase needs an integer division; the coarsest level's dense
+// pseudo-inverse is staged in shared memory as well when it is small.
 constexpr int kChainCells = 4096;
 constexpr int kChainMax = 6;
 constexpr int kChainThreads = 1024;
+constexpr int kChainPinvStage = 128;   // largest coarsest level staged in shared memory
 
 struct CoarseChain {
   int nlev;                    // levels in the chain (the last is the coarsest)
@@ -708,18 +743,11 @@ struct CoarseChain {
   int pre, post;
   const float* pinv;           // dense pseudo-inverse of the coarsest level
   int mc;
+  int stage_pinv;              // pinv copied into shared memory
+  const uint32_t* pk;          // packed coordinates of the chain's cells
+  const uint8_t* nb;           // neighbour masks of the chain's cells
 };
 
-__device__ __forceinline__ void cell_ijk(Dims d, int c, int& i, int& j, int& k) {
-  i = c % d.nx;
-  j = (c / d.nx) % d.ny;
-  k = c / (d.nx * d.ny);
-}
-
-// Per cell of the chain's levels, computed once per launch into shared
-// memory: the packed coordinates i | j << 10 | k << 20 and a mask of the
-// existing neighbours (bits x-, x+, y-, y+, z-, z+), so that the phases need
-// no integer division.
 __device__ __forceinline__ void unpack(uint32_t p, int& i, int& j, int& k) {
   i = p & 1023;
   j = (p >> 10) & 1023;
@@ -743,9 +771,69 @@ struct ChainSm {
   float* x;
   float* b;
   float* t;
-  const uint32_t* pk;
-  const uint8_t* nb;
+  uint32_t* pk;
+  uint8_t* nb;
+  const float* pinv;
 };
+
+__host__ __device__ inline int round4(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline int round16(int n) { return (n + 15) & ~15; }
+
+// floats of shared memory the chain needs: x, b, t and the coordinates
+// (round4(tot) each, so that every array starts on a 16-byte boundary), the
+// masks (round16(tot) bytes) and the staged pseudo-inverse
+__host__ __device__ inline int chain_smem_floats(int tot, int mc, int stage) {
+  return 4 * round4(tot) + round16(tot) / 4 + (stage ? round4(mc * mc) : 0);
+}
+
+__device__ ChainSm chain_layout(float* base, const CoarseChain& ch) {
+  const int t4 = round4(ch.off[ch.nlev]);
+  ChainSm S;
+  S.x = base;
+  S.b = base + t4;
+  S.t = base + 2 * t4;
+  S.pk = reinterpret_cast<uint32_t*>(base + 3 * t4);
+  S.nb = reinterpret_cast<uint8_t*>(base + 4 * t4);
+  S.pinv = ch.stage_pinv ? base + 4 * t4 + round16(ch.off[ch.nlev]) / 4 : ch.pinv;
+  return S;
+}
+
+// Copies n 16-byte words from global to shared memory; each thread issues
+// its R loads of a round before its stores, so a round costs one memory
+// latency.
+template <int R>
+__device__ __forceinline__ void copy_words(uint4* dst, const uint4* __restrict__ src, int n) {
+  for (int base = 0; base < n; base += R * (int)blockDim.x) {
+    uint4 v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int e = base + (int)threadIdx.x + q * (int)blockDim.x;
+      if (e < n) v[q] = __ldg(src + e);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int e = base + (int)threadIdx.x + q * (int)blockDim.x;
+      if (e < n) dst[e] = v[q];
+    }
+  }
+}
+
+// Copies the coordinate and mask tables and the staged pseudo-inverse into
+// shared memory (the caller synchronises before they are used).  The tables
+// are padded to whole 16-byte words at setup.
+__device__ void chain_load(const CoarseChain& ch, const ChainSm& S) {
+  const int tot = ch.off[ch.nlev];
+  copy_words<2>(reinterpret_cast<uint4*>(S.pk), reinterpret_cast<const uint4*>(ch.pk),
+                round4(tot) / 4);
+  copy_words<1>(reinterpret_cast<uint4*>(S.nb), reinterpret_cast<const uint4*>(ch.nb),
+                round16(tot) / 16);
+  if (ch.stage_pinv) {
+    const int n = ch.mc * ch.mc;
+    float* pv = const_cast<float*>(S.pinv);
+    copy_words<4>(reinterpret_cast<uint4*>(pv), reinterpret_cast<const uint4*>(ch.pinv), n / 4);
+    for (int q = (n & ~3) + threadIdx.x; q < n; q += blockDim.x) pv[q] = __ldg(ch.pinv + q);
+  }
+}
 
 // p Chebyshev steps on one level in shared memory; from_zero starts at x = 0.
 // Ends with the result in x (t is the ping-pong buffer).
@@ -782,36 +870,9 @@ __device__ void chain_smooth(const CoarseChain& ch, const ChainSm& S, int l, con
   }
 }
 
-__global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
-                                                                const float* __restrict__ b_in,
-                                                                float* __restrict__ x_out) {
-  pdl_wait();
-  pdl_trigger();
-  extern __shared__ float sm[];
-  const int tot = ch.off[ch.nlev];
-  ChainSm S;
-  S.x = sm;
-  S.b = sm + tot;
-  S.t = sm + 2 * tot;
-  uint32_t* pk = reinterpret_cast<uint32_t*>(sm + 3 * tot);
-  uint8_t* nbm = reinterpret_cast<uint8_t*>(pk + tot);
-  S.pk = pk;
-  S.nb = nbm;
-  for (int l = 0; l < ch.nlev; ++l) {
-    const Dims d = ch.d[l];
-    const int m = d.nx * d.ny * d.nz;
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      int i, j, k;
-      cell_ijk(d, c, i, j, k);
-      pk[ch.off[l] + c] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
-      nbm[ch.off[l] + c] = (uint8_t)((i > 0) | ((i < d.nx - 1) << 1) | ((j > 0) << 2) |
-                                     ((j < d.ny - 1) << 3) | ((k > 0) << 4) |
-                                     ((k < d.nz - 1) << 5));
-    }
-  }
-  const int m0 = ch.off[1];
-  for (int c = threadIdx.x; c < m0; c += blockDim.x) S.b[c] = b_in[c];
-  __syncthreads();
+// The cycle on the chain's levels: b of its first level in S.b, the tables
+// loaded and synchronised; leaves x of its first level in S.x.
+__device__ void chain_run(const CoarseChain& ch, const ChainSm& S) {
   // descend
   for (int l = 0; l < ch.nlev - 1; ++l) {
     chain_smooth(ch, S, l, ch.wpre, ch.pre, true);
@@ -820,7 +881,7 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
     const float ih2 = 1.f / ch.h2[l];
     const float* x = S.x + ch.off[l];
     const float* b = S.b + ch.off[l];
-    const uint8_t* nb = nbm + ch.off[l];
+    const uint8_t* nb = S.nb + ch.off[l];
     float* bc = S.b + ch.off[l + 1];
     // eight threads per coarse cell (one child each), summed by shuffles
     for (int base = 0; base < 8 * mcl; base += blockDim.x) {
@@ -830,7 +891,7 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
       if (act) {
         const int C = t >> 3, q = t & 7;
         int I, J, K;
-        unpack(pk[ch.off[l + 1] + C], I, J, K);
+        unpack(S.pk[ch.off[l + 1] + C], I, J, K);
         const int c = ((2 * K + (q >> 2)) * d.ny + 2 * J + ((q >> 1) & 1)) * d.nx + 2 * I + (q & 1);
         r = b[c];
         if (ch.pre > 0) {
@@ -846,15 +907,19 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
     }
     __syncthreads();
   }
-  // coarsest: dense pseudo-inverse
+  // coarsest: dense pseudo-inverse, one warp per row (lanes split the row,
+  // summed by shuffles in a fixed order)
   {
     const int l = ch.nlev - 1;
     float* x = S.x + ch.off[l];
     const float* b = S.b + ch.off[l];
-    for (int r = threadIdx.x; r < ch.mc; r += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < ch.mc; r += nw) {
       float acc = 0.f;
-      for (int q = 0; q < ch.mc; ++q) acc = fmaf(__ldg(ch.pinv + r * ch.mc + q), b[q], acc);
-      x[r] = acc;
+      for (int q = lane; q < ch.mc; q += 32) acc = fmaf(S.pinv[r * ch.mc + q], b[q], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) x[r] = acc;
     }
     __syncthreads();
   }
@@ -866,7 +931,7 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
     const int m = d.nx * d.ny * d.nz;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       int i, j, k;
-      unpack(pk[ch.off[l] + c], i, j, k);
+      unpack(S.pk[ch.off[l] + c], i, j, k);
       const int I = i >> 1, J = j >> 1, K = k >> 1;
       const int In = (i & 1) ? min(I + 1, dc.nx - 1) : max(I - 1, 0);
       const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
@@ -882,7 +947,22 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
     __syncthreads();
     chain_smooth(ch, S, l, ch.wpost, ch.post, false);
   }
-  for (int c = threadIdx.x; c < m0; c += blockDim.x) x_out[c] = S.x[c];
+}
+
+__global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
+                                                                const float* __restrict__ b_in,
+                                                                float* __restrict__ x_out) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) float sm[];
+  const ChainSm S = chain_layout(sm, ch);
+  chain_load(ch, S);
+  const int m0 = ch.off[1];   // a multiple of 8 (the level has a level below it)
+  copy_words<1>(reinterpret_cast<uint4*>(S.b), reinterpret_cast<const uint4*>(b_in), m0 / 4);
+  __syncthreads();
+  chain_run(ch, S);
+  for (int c = threadIdx.x; c < m0 / 4; c += blockDim.x)
+    reinterpret_cast<float4*>(x_out)[c] = reinterpret_cast<const float4*>(S.x)[c];
 }
 
 // x = P b on the coarsest level: one block, dense pseudo-inverse.
@@ -1098,12 +1178,11 @@ void coarse_correct(ibm_ctx* c, int l, const T* b, T* x, int pre, int post, cuda
   prof_note(c, (double)C.m * sizeof(T) + (double)L.m * ((pre > 0 ? 2 : 1) * sizeof(T)));
 }
 
-// Launches the one-CTA cycle from level l down; false if it does not apply.
-bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post,
-                  cudaStream_t s) {
+constexpr size_t kChainSmemMax = 200 * 1024;
+
+// The chain from level l (its first level, c->chain_l) down.
+void chain_desc(ibm_ctx* c, int l, int pre, int post, CoarseChain& ch) {
   const int nlev = c->n_levels - l;
-  if (nlev < 2 || nlev > kChainMax || c->lv[l].m > kChainCells) return false;
-  CoarseChain ch;
   ch.nlev = nlev;
   ch.off[0] = 0;
   for (int q = 0; q < nlev; ++q) {
@@ -1120,21 +1199,69 @@ bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post
   ch.post = post;
   ch.pinv = c->coarse_pinv32;
   ch.mc = c->coarse_m;
-  // x, b, t (FP32), packed coordinates (4 B) and neighbour masks (1 B) per cell
-  const size_t smem = (sizeof(float) * 3 + 4 + 1) * ch.off[nlev];
-  if (smem > 200 * 1024) return false;
-  // the shared-memory limit is raised once per device
-  static bool attr_set[64] = {false};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-  if (!attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_coarse_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
-      return false;
-    attr_set[dev] = true;
+  ch.stage_pinv = ch.mc <= kChainPinvStage;
+  const int tot = ch.off[nlev];
+  ch.pk = static_cast<const uint32_t*>(c->chain_tab);
+  ch.nb = reinterpret_cast<const uint8_t*>(ch.pk + round4(tot));
+}
+
+size_t chain_smem_bytes(const CoarseChain& ch) {
+  return sizeof(float) * (size_t)chain_smem_floats(ch.off[ch.nlev], ch.mc, ch.stage_pinv);
+}
+
+// Setup of the coarse end of the FP32 V-cycle: the chain's first level (the
+// first level below the finest with at most kChainCells cells and a level
+// below it) and the coordinate and mask tables of its cells.
+ibm_status coarse_end_setup(ibm_ctx* c) {
+  c->chain_l = -1;
+  int l0 = -1;
+  for (int l = 1; l < c->n_levels - 1; ++l)
+    if (c->lv[l].m <= kChainCells) {
+      l0 = l;
+      break;
+    }
+  if (l0 < 0 || c->n_levels - l0 > kChainMax) return IBM_OK;
+  CoarseChain ch;
+  c->chain_tab = nullptr;
+  chain_desc(c, l0, 2, 2, ch);
+  if (chain_smem_bytes(ch) > kChainSmemMax) return IBM_OK;
+  const int tot = ch.off[ch.nlev];
+  // coordinates padded to whole 16-byte words, then the masks likewise
+  std::vector<uint32_t> pk(round4(tot), 0u);
+  std::vector<uint8_t> nb(round16(tot), 0u);
+  for (int q = 0; q < ch.nlev; ++q) {
+    const Dims d = ch.d[q];
+    for (int k = 0; k < d.nz; ++k)
+      for (int j = 0; j < d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) {
+          const int e = ch.off[q] + (k * d.ny + j) * d.nx + i;
+          pk[e] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
+          nb[e] = (uint8_t)((i > 0) | ((i < d.nx - 1) << 1) | ((j > 0) << 2) |
+                            ((j < d.ny - 1) << 3) | ((k > 0) << 4) | ((k < d.nz - 1) << 5));
+        }
   }
+  if (cudaMalloc(&c->chain_tab, pk.size() * 4 + nb.size()) != cudaSuccess) {
+    cudaGetLastError();
+    c->chain_tab = nullptr;
+    return set_err(c, IBM_ERR_NOMEM, "multigrid allocation failed");
+  }
+  IBM_CUDA(c, cudaMemcpy(c->chain_tab, pk.data(), pk.size() * 4, cudaMemcpyHostToDevice));
+  IBM_CUDA(c, cudaMemcpy(static_cast<char*>(c->chain_tab) + pk.size() * 4, nb.data(),
+                         nb.size(), cudaMemcpyHostToDevice));
+  IBM_CUDA(c, cudaFuncSetAttribute(k_coarse_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kChainSmemMax));
+  c->chain_l = l0;
+  return IBM_OK;
+}
+
+// Launches the one-CTA cycle from level l down; false if it does not apply.
+bool chain_vcycle(ibm_ctx* c, int l, const float* b, float* x, int pre, int post,
+                  cudaStream_t s) {
+  if (l != c->chain_l) return false;
+  CoarseChain ch;
+  chain_desc(c, l, pre, post, ch);
   count_launch();
-  launch_pdl(k_coarse_chain, dim3(1), dim3(kChainThreads), smem, s, ch, b, x);
+  launch_pdl(k_coarse_chain, dim3(1), dim3(kChainThreads), chain_smem_bytes(ch), s, ch, b, x);
   prof_note(c, 8.0 * ch.off[1] + 4.0 * (double)ch.mc * ch.mc);
   return true;
 }
@@ -1226,7 +1353,7 @@ ibm_status mg_setup(ibm_ctx* c) {
                          cudaMemcpyHostToDevice));
   IBM_CUDA(c, cudaMemcpy(c->coarse_pinv32, A32.data(), sizeof(float) * mc * mc,
                          cudaMemcpyHostToDevice));
-  return IBM_OK;
+  return coarse_end_setup(c);
 }
 
 ibm_status mg_vcycle(ibm_ctx* c, const double* r, double* z, int prec, int pre, int post) {
