@@ -6,6 +6,10 @@
 // Thread layout: one thread per grid point, blocks of 32 x 8 in (x, y) and one
 // z-plane per blockIdx.z, so that a warp reads 32 consecutive x values of each
 // neighbour row (coalesced; the y/z neighbours hit L1/L2).
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+
 #include "ds.cuh"
 #include "ibm_internal.cuh"
 
@@ -82,6 +86,102 @@ __global__ void __launch_bounds__(BX * BY) k_laplacian(Dims d, const T* __restri
     r = fma((T)nn, vc, -s);
   }
   out[c] = r * inv_h2;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Laplacian with the stencil sum formed exactly in integers.  GB300
+// issues FP64 arithmetic at about 1/58 of its FP32 rate, so the seven-term
+// FP64 sum bounds k_laplacian<double> far below the HBM rate.  Here each
+// value v = m 2^(e - 1075) (m the signed 53-bit significand, e the biased
+// exponent; a subnormal has e = 1 and no implicit bit) is aligned to the
+// largest exponent E of the seven with kLapGuard extra low bits, and
+// S = nn m_c - sum_nb m_nb is summed in 64-bit integers: the bits dropped
+// below 2^(E - 1075 - kLapGuard) amount to at most 7 2^-kLapGuard units in
+// the last place of the largest term, less than the rounding error of the
+// FP64 sum.  Then out = (double)S 2^(E - 1075 - kLapGuard) / h^2 with two
+// roundings (the conversion and one multiplication; the scale is 1/h^2 with
+// E - 1080 added to its exponent field).  Non-finite values, and sums whose
+// scale would leave the normal range, take the FP64 formula.
+constexpr int kLapGuard = 5;
+
+struct FxVal {
+  int e;
+  long long m;
+};
+
+__device__ __forceinline__ FxVal fx_unpack(double v) {
+  const long long u = __double_as_longlong(v);
+  int e = (int)((u >> 52) & 0x7ff);
+  long long m = u & 0xFFFFFFFFFFFFFLL;
+  if (e != 0)
+    m |= 1LL << 52;
+  else
+    e = 1;
+  return {e, u < 0 ? -m : m};
+}
+
+// m 2^kLapGuard shifted down to exponent E (|m| < 2^56, so no overflow)
+__device__ __forceinline__ long long fx_align(long long m, int e, int E) {
+  return (m * (1LL << kLapGuard)) >> min(E - e, 63);
+}
+
+// (nn v_c - sum of the six neighbour values) / h^2; an absent neighbour is 0
+__device__ __forceinline__ double lap_fx(double vc, double xm, double xp, double ym, double yp,
+                                         double zm, double zp, int nn, long long inv_h2_bits,
+                                         int e_min, int e_max) {
+  const FxVal c = fx_unpack(vc), a0 = fx_unpack(xm), a1 = fx_unpack(xp), a2 = fx_unpack(ym),
+              a3 = fx_unpack(yp), a4 = fx_unpack(zm), a5 = fx_unpack(zp);
+  const int E = max(max(max(c.e, a0.e), max(a1.e, a2.e)), max(max(a3.e, a4.e), a5.e));
+  if (E < e_min || E > e_max) {
+    const double s = ((xm + xp) + (ym + yp)) + (zm + zp);
+    return fma((double)nn, vc, -s) * __longlong_as_double(inv_h2_bits);
+  }
+  long long S = fx_align(c.m * nn, c.e, E);
+  S -= fx_align(a0.m, a0.e, E) + fx_align(a1.m, a1.e, E);
+  S -= fx_align(a2.m, a2.e, E) + fx_align(a3.m, a3.e, E);
+  S -= fx_align(a4.m, a4.e, E) + fx_align(a5.m, a5.e, E);
+  const double scale =
+      __longlong_as_double(inv_h2_bits + (long long)(E - 1075 - kLapGuard) * (1LL << 52));
+  return __ll2double_rn(S) * scale;
+}
+
+// One cell per thread, blocks of 32 x 8 cells over zc z-planes: x-neighbours
+// by shuffles (loads at the warp edges), z-neighbours from the registers of
+// the march, y-neighbours through L1.
+__global__ void __launch_bounds__(BX * BY) k_laplacian_fx(Dims d, const double* __restrict__ v,
+                                                          double* __restrict__ out,
+                                                          long long inv_h2_bits, int e_min,
+                                                          int e_max, int zc) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * BX + lane;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool act = i < d.nx && j < d.ny;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz);
+  const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+  int64_t c = (int64_t)z0 * sz + (int64_t)j * sy + i;
+  const bool hxm = i > 0, hxp = i < d.nx - 1, hym = j > 0, hyp = j < d.ny - 1;
+  const int nxy = (int)hxm + (int)hxp + (int)hym + (int)hyp;
+  double vp = (act && z0 > 0) ? __ldg(v + c - sz) : 0.0;
+  double vc = act ? __ldg(v + c) : 0.0;
+  for (int z = z0; z < z1; ++z, c += sz) {
+    double vn = 0.0, ym = 0.0, yp = 0.0;
+    if (act) {
+      if (z + 1 < d.nz) vn = __ldg(v + c + sz);
+      if (hym) ym = __ldg(v + c - sy);
+      if (hyp) yp = __ldg(v + c + sy);
+    }
+    double xm = __shfl_up_sync(0xffffffffu, vc, 1);
+    double xp = __shfl_down_sync(0xffffffffu, vc, 1);
+    if (lane == 0) xm = (act && hxm) ? __ldg(v + c - 1) : 0.0;
+    if (lane == 31) xp = (act && hxp) ? __ldg(v + c + 1) : 0.0;
+    if (!hxm) xm = 0.0;
+    if (!hxp) xp = 0.0;
+    const int nn = nxy + (z > 0) + (z < d.nz - 1);
+    if (act) out[c] = lap_fx(vc, xm, xp, ym, yp, vp, vn, nn, inv_h2_bits, e_min, e_max);
+    vp = vc;
+    vc = vn;
+  }
 }
 
 // u = u_in + alpha * G p on interior faces, 0 on wall faces (u_in may be null).
@@ -538,7 +638,25 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
 template <typename T>
 void launch_laplacian(Dims d, const T* v, T* out, double inv_h2, cudaStream_t s) {
   count_launch();
-  k_laplacian<T><<<cell_grid(d), dim3(BX, BY), 0, s>>>(d, v, out, (T)inv_h2);
+  if constexpr (std::is_same<T, double>::value) {
+    // planes per thread: about eight blocks per SM over the grid, at most 4
+    const int64_t bxy = (int64_t)div_up(d.nx, BX) * div_up(d.ny, BY);
+    const int zc = (int)std::min<int64_t>(4, std::max<int64_t>(1, d.nz * bxy / (152 * 8)));
+    long long bits;
+    std::memcpy(&bits, &inv_h2, sizeof(bits));
+    // the scale 2^(E - 1075 - kLapGuard) / h^2 is formed by adding E - 1075 -
+    // kLapGuard to the exponent field e_h of 1/h^2, which must stay in
+    // [1, 2046]; E = 2047 (a non-finite value) always takes the FP64 formula
+    const int e_h = (int)((bits >> 52) & 0x7ff);
+    int e_min = 1075 + kLapGuard + 1 - e_h, e_max = 2046 + 1075 + kLapGuard - e_h;
+    e_min = std::max(e_min, 1);
+    e_max = std::min(e_max, 2046);
+    if (e_h == 0 || e_h == 0x7ff || bits < 0) e_min = 2047;   // 1/h^2 not normal and positive
+    k_laplacian_fx<<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0,
+                     s>>>(d, v, out, bits, e_min, e_max, zc);
+  } else {
+    k_laplacian<T><<<cell_grid(d), dim3(BX, BY), 0, s>>>(d, v, out, (T)inv_h2);
+  }
 }
 template void launch_laplacian<float>(Dims, const float*, float*, double, cudaStream_t);
 template void launch_laplacian<double>(Dims, const double*, double*, double, cudaStream_t);
