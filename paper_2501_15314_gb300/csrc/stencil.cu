@@ -286,17 +286,23 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
     Dims d, FaceGeom g, const double* __restrict__ un, const double* __restrict__ unm1,
     const double* __restrict__ pn, const double* __restrict__ fb, int with_adv, dsf c4, dsf c1,
     dsf cp_h, dsf ca, double* __restrict__ rhs) {
-  const int i = blockIdx.x * BX + threadIdx.x;
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * BX + lane;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int n0 = g.n[C][0], n1 = g.n[C][1], n2 = g.n[C][2];
   const int z0 = blockIdx.z * ZH;
-  if (i >= n0 || j >= n1) return;
+  // u_y and u_z faces share their x-edge fluxes between neighbouring lanes,
+  // so lanes past the last face stay in the march (without loads or stores);
+  // a row past the last one leaves as a whole warp
+  const bool act = i < n0;
+  if (j >= n1 || (C == 0 && !act)) return;
   const int z1 = min(z0 + ZH, n2);
   const int64_t sy = g.sy[C], sz = g.sz[C];
   int64_t f = g.off[C] + (int64_t)z0 * sz + (int64_t)j * sy + i;
   const bool col_wall = (C == 0 && (i == 0 || i == n0 - 1)) || (C == 1 && (j == 0 || j == n1 - 1));
   if (col_wall) {
-    for (int z = z0; z < z1; ++z, f += sz) rhs[f] = 0.0;
+    if (act)
+      for (int z = z0; z < z1; ++z, f += sz) rhs[f] = 0.0;
     return;
   }
   const int64_t csy = d.nx, csz = (int64_t)d.nx * d.ny;
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
   auto sq = [](dsf x) { return ds_mul(x, x); };
   // lower z-flux (C = 0, 1) or lower cell-centred square (C = 2)
   dsf carry = Z;
-  if (with_adv) {
+  if (with_adv && act) {
     if (C == 2) {
       const dsf lo = (z0 - 1 >= 1) ? ldu<2>(g, un, i, j, z0 - 1) : Z;
       const dsf mid = (z0 >= 1 && z0 <= n2 - 2) ? ldu<2>(g, un, i, j, z0) : Z;
@@ -314,8 +320,19 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
       carry = edge_flux_ds<C, 2>(g, un, i, j, z0, z0);
     }
   }
+  // the flux through the x-edge at q = i + 1 of this lane is the flux
+  // through the x-edge at q = i of the next lane (the same values, the same
+  // operations); lane 0 forms its lower one itself
+  auto xflux_pair = [&](auto fn, dsf& lower) {
+    const dsf up = act ? fn(i + 1) : Z;
+    lower.hi = __shfl_up_sync(0xffffffffu, up.hi, 1);
+    lower.lo = __shfl_up_sync(0xffffffffu, up.lo, 1);
+    if (lane == 0) lower = act ? fn(i) : Z;
+    return up;
+  };
   for (int z = z0; z < z1; ++z, f += sz) {
     if (C == 2 && (z == 0 || z == n2 - 1)) {
+      if (!act) continue;
       rhs[f] = 0.0;
       if (with_adv) {
         const dsf mid = (z >= 1 && z <= n2 - 2) ? ldu<2>(g, un, i, j, z) : Z;
@@ -324,6 +341,13 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
       }
       continue;
     }
+    // x-edge fluxes (shared between lanes: every lane takes part)
+    dsf fx_lo = Z, fx_up = Z;
+    if (with_adv && C != 0) {
+      constexpr int CC = C == 0 ? 1 : C;   // (no x-edge flux for u_x itself)
+      fx_up = xflux_pair([&](int q) { return edge_flux_ds<CC, 0>(g, un, i, j, z, q); }, fx_lo);
+    }
+    if (!act) continue;
     const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
     const dsf u0 = split_exact(__ldg(un + f));
     // 4/(2dt) u^n - 1/(2dt) u^{n-1} - (p_+ - p_-)/h (+ f)
@@ -338,8 +362,7 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
         const dsf up2 = sq(ds_add(u0, up));
         acc = ds_add(up2, ds_neg(carry));
         carry = up2;
-        acc = ds_add(acc, ds_add(edge_flux_ds<2, 0>(g, un, i, j, z, i + 1),
-                                 ds_neg(edge_flux_ds<2, 0>(g, un, i, j, z, i))));
+        acc = ds_add(acc, ds_add(fx_up, ds_neg(fx_lo)));
         acc = ds_add(acc, ds_add(edge_flux_ds<2, 1>(g, un, i, j, z, j + 1),
                                  ds_neg(edge_flux_ds<2, 1>(g, un, i, j, z, j))));
       } else {
@@ -350,9 +373,12 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
         const dsf um = (pc - 1 >= 1) ? ldu<C>(g, un, i - (C == 0), j - (C == 1), z) : Z;
         const dsf two_u0 = {2.f * u0.hi, 2.f * u0.lo};
         acc = ds_mul(ds_add(up, ds_neg(um)), ds_add(ds_add(up, um), two_u0));
-        const int po = O == 0 ? i : j;
-        acc = ds_add(acc, ds_add(edge_flux_ds<C, O>(g, un, i, j, z, po + 1),
-                                 ds_neg(edge_flux_ds<C, O>(g, un, i, j, z, po))));
+        if (O == 0) {
+          acc = ds_add(acc, ds_add(fx_up, ds_neg(fx_lo)));
+        } else {
+          acc = ds_add(acc, ds_add(edge_flux_ds<C, O>(g, un, i, j, z, j + 1),
+                                   ds_neg(edge_flux_ds<C, O>(g, un, i, j, z, j))));
+        }
         const dsf fz = edge_flux_ds<C, 2>(g, un, i, j, z, z + 1);
         acc = ds_add(acc, ds_add(fz, ds_neg(carry)));
         carry = fz;
