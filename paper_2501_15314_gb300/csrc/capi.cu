@@ -202,10 +202,12 @@ static void free_all(ibm_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
-  cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc); cudaFree(m.cg);
+  cudaFree(m.t); cudaFree(m.t2); cudaFree(m.t32); cudaFree(m.dwf); cudaFree(m.dwc);
+  cudaFree(m.cg);
   cudaFree(m.t3); cudaFree(c->cg_scal);
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_cell);
   cudaFree(m.ell_base); cudaFree(m.ell_len); cudaFree(m.ell_key); cudaFree(m.ell_coef);
+  cudaFree(m.ell_coef32);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

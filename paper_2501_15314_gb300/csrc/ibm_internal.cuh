@@ -79,6 +79,7 @@ struct MarkerData {
   int64_t n_ell = 0, ell_cap = 0;
   int32_t* ell_key = nullptr;
   double* ell_coef = nullptr;     // [3][n_ell] G^T R coefficients (0 on padding)
+  float* ell_coef32 = nullptr;    // [3][n_ell] the same rounded to FP32 (FP32 Arnoldi cycles)
   int32_t* ell_base = nullptr;    // [n_groups + 1]
   int32_t* ell_len = nullptr;     // [n_groups] rounds (entries per lane)
   int64_t n_shell = 0;
@@ -90,6 +91,7 @@ struct MarkerData {
   int32_t* ell_cell = nullptr;    // [n_shell]
   double* t = nullptr;            // [3][n] per-marker scratch
   double* t2 = nullptr;           // [3][n] per-marker scratch
+  float* t32 = nullptr;           // [3][n] t rounded to FP32 (FP32 Arnoldi cycles)
 };
 
 }  // namespace ibm
@@ -175,11 +177,13 @@ namespace ibm {
 
 // Algorithmic bytes of the marker term of one Schur product (each array read
 // or written once): per marker its tap bases, Roma weights and G-weighted
-// weights (192 B), t written and read back (24 + 24 B); per cell-sorted entry
-// its key and three G^T R coefficients (28 B); per shell cell the input value
-// (sz_in), the cell index and the output read and written (2 sz_out).
-inline double marker_term_bytes(const ibm_ctx* c, int sz_in, int sz_out) {
-  return (double)c->mk.n * 240.0 + (double)c->mk.n_entries * 28.0 +
+// weights (192 B), t written and read back (24 + 24 B; in the FP32 form t is
+// written in FP64 and FP32 and read in FP32, the same 48 B); per cell-sorted
+// entry its key and three G^T R coefficients (entry_bytes: 28 B, or 16 B
+// from the FP32 copies); per shell cell the input value (sz_in), the cell
+// index and the output read and written (2 sz_out).
+inline double marker_term_bytes(const ibm_ctx* c, int sz_in, int sz_out, int entry_bytes = 28) {
+  return (double)c->mk.n * 240.0 + (double)c->mk.n_entries * entry_bytes +
          (double)c->mk.n_shell * (sz_in + 4 + 2 * sz_out);
 }
 
@@ -244,7 +248,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);
 // (on stream st when given, else the context's stream)
 void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t,
                                cudaStream_t st = nullptr);
-void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t,
+void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t, float* t32,
                                    cudaStream_t st = nullptr);
 // out[cell] += scale * (G^T R t)[cell] on the shell cells
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);
@@ -411,6 +415,55 @@ __device__ __forceinline__ double ell_gradt_sum(const int32_t* __restrict__ ekey
     acc = fma(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
   }
   return acc;
+}
+
+// The same sum from the FP32 copies of the coefficients and of t, with FP32
+// FMAs in the same order (the FP32 Arnoldi cycles round the Schur product to
+// FP32; GB300 runs FP64 FMAs at about 1/58 of the FP32 rate).
+__device__ __forceinline__ float ell_gradt_sum_f32(const int32_t* __restrict__ ekey,
+                                                   const float* __restrict__ ecoef,
+                                                   int64_t n_ell, int64_t nmk,
+                                                   const float* __restrict__ t, int64_t idx,
+                                                   int L) {
+  float acc = 0.f;
+  int p = 0;
+  for (; p + 4 <= L; p += 4, idx += 128) {
+    int64_t k[4];
+    float c0[4], c1[4], c2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      k[u] = ekey[idx + 32 * u] >> 6;
+      c0[u] = ecoef[idx + 32 * u];
+      c1[u] = ecoef[n_ell + idx + 32 * u];
+      c2[u] = ecoef[2 * n_ell + idx + 32 * u];
+    }
+    float t0[4], t1[4], t2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      t0[u] = t[k[u]];
+      t1[u] = t[nmk + k[u]];
+      t2[u] = t[2 * nmk + k[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc = fmaf(c0[u], t0[u], acc);
+      acc = fmaf(c1[u], t1[u], acc);
+      acc = fmaf(c2[u], t2[u], acc);
+    }
+  }
+  for (; p < L; ++p, idx += 32) {
+    const int64_t k = ekey[idx] >> 6;
+    acc = fmaf(ecoef[idx], t[k], acc);
+    acc = fmaf(ecoef[n_ell + idx], t[nmk + k], acc);
+    acc = fmaf(ecoef[2 * n_ell + idx], t[2 * nmk + k], acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float ell_combine_f32(float v) {
+#pragma unroll
+  for (int o = 1; o < kEllLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // Programmatic dependent launch: a kernel launched with launch_pdl may be

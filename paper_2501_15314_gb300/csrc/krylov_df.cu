@@ -12,6 +12,7 @@
 // residual b - S~ x that decides convergence (and restarts) is evaluated in
 // native FP64, and dot products are reduced to FP64 per block.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "ds.cuh"
@@ -175,6 +176,27 @@ __global__ void k_shell_gradt_ds(int64_t n_shell, const int32_t* __restrict__ sh
   } else {
     wv[c] = (float)((double)wv[c] + scale * acc);
   }
+}
+
+// The same gather for the FP32 Arnoldi cycles: FP32 coefficients and t, FP32
+// FMAs, the cell's sum added to its FP32 value with one rounding.
+__global__ void k_shell_gradt_f32(int64_t n_shell, const int32_t* __restrict__ shell_cell,
+                                  const int32_t* __restrict__ base,
+                                  const int32_t* __restrict__ len,
+                                  const int32_t* __restrict__ ekey,
+                                  const float* __restrict__ ecoef, int64_t n_ell, int64_t nmk,
+                                  const float* __restrict__ t, float scale,
+                                  float* __restrict__ wv) {
+  const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = tq >> 5;
+  const int lane = (int)(tq & 31);
+  const int64_t q = g * kEllCells + lane / kEllLanes;
+  const bool live = g < ell_groups(n_shell) && q < n_shell;
+  float acc = live ? ell_gradt_sum_f32(ekey, ecoef, n_ell, nmk, t, base[g] + lane, len[g]) : 0.f;
+  acc = ell_combine_f32(acc);
+  if (!live || lane % kEllLanes != 0) return;
+  const int64_t c = shell_cell[q];
+  wv[c] = fmaf(scale, acc, wv[c]);
 }
 
 // Compensated accumulation of products: the running FP32 sum S and an FP32
@@ -562,8 +584,10 @@ ibm_status fetch(ibm_ctx* c, const double* dev, int n) {
 
 bool ds_supported(const ibm_ctx* c) { return c->d.nx % 4 == 0 && c->n_levels > 1; }
 
-// w = S~ z for FP32 z, w as a hi/lo pair: double-single Laplacian, FP64 marker
-// term gathered from z and added on the shell cells.
+// w = S~ z for FP32 z, w as a hi/lo pair (double-single Laplacian, FP64
+// marker term gathered from z and added on the shell cells) or, for the FP32
+// Arnoldi cycles, one FP32 number (the Laplacian formed exactly and rounded
+// once, the scalar-form marker term gathered in FP32).
 template <typename TW>
 ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
   cudaStream_t s = c->stream;
@@ -578,7 +602,8 @@ ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
   if (fork) {
     IBM_CUDA(c, cudaEventRecord(c->ev_fork, s));
     IBM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    launch_marker_grad_interp_f32(c, z, 2.0, m.t, c->side);
+    launch_marker_grad_interp_f32(c, z, 2.0, m.t,
+                                  std::is_same<TW, float>::value ? m.t32 : nullptr, c->side);
     IBM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
   }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
@@ -594,13 +619,23 @@ ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
       IBM_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     } else {
       // +- B^T C^{-1} B z (exact / sign-consistent forms), C^{-1} in FP64
-      launch_marker_grad_interp_f32(c, z, 1.0, m.t);
+      launch_marker_grad_interp_f32(c, z, 1.0, m.t, nullptr);
       const ibm_status st = c_solve(c, m.t, m.t2, c->c_rtol, c->c_maxit, nullptr);
       if (st != IBM_OK) { prof_end(c, ph); return st; }
       t = m.t2;
       sign = c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0;
     }
     count_launch();
+    if constexpr (std::is_same<TW, float>::value) {
+      if (fork) {
+        k_shell_gradt_f32<<<div_up(32 * ell_groups(m.n_shell), 256), 256, 0, s>>>(
+            m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef32, m.n_ell, m.n,
+            m.t32, 1.f, w);
+        prof_end(c, ph, marker_term_bytes(c, 4, (int)sizeof(TW), 16));
+        IBM_LAUNCH_CHECK(c);
+        return IBM_OK;
+      }
+    }
     k_shell_gradt_ds<TW><<<div_up(32 * ell_groups(m.n_shell), 256), 256, 0, s>>>(
         m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_coef, m.n_ell, m.n, t,
         sign, w);

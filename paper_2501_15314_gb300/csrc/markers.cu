@@ -194,7 +194,8 @@ __device__ __forceinline__ double widen(double x) { return x; }
 // order with warp shuffles.
 template <typename TV>
 __global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v,
-                                     double scale, double* __restrict__ t) {
+                                     double scale, double* __restrict__ t,
+                                     float* __restrict__ t32) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = 12 * mk.n;
   double part = 0.0;
@@ -232,7 +233,11 @@ __global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v
   const double p1 = __shfl_sync(0xffffffffu, part, base + 1);
   const double p2 = __shfl_sync(0xffffffffu, part, base + 2);
   const double p3 = __shfl_sync(0xffffffffu, part, base + 3);
-  if (tid < nt && (lane & 3) == 0) t[dc * mk.n + k] = scale * ((p0 + p1) + (p2 + p3));
+  if (tid < nt && (lane & 3) == 0) {
+    const double r = scale * ((p0 + p1) + (p2 + p3));
+    t[dc * mk.n + k] = r;
+    if (t32) t32[dc * mk.n + k] = (float)r;
+  }
 }
 
 // Order of the shell cells in the interleaved layout: each block sorts one
@@ -302,7 +307,7 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
                            const int32_t* __restrict__ key, const int32_t* __restrict__ base,
                            const int32_t* __restrict__ len, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ ell_cell, Dims d, int64_t n_ell,
-                           int32_t* ekey, double* ecoef) {
+                           int32_t* ekey, double* ecoef, float* ecoef32) {
   const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t w = tq >> 5;
   if (w >= ell_groups(n_shell)) return;
@@ -329,11 +334,18 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
       ekey[dst] = kk;
       const int64_t k = kk >> 6;
 #pragma unroll
-      for (int dc = 0; dc < 3; ++dc) ecoef[dc * n_ell + dst] = gtr_coef(mk, k, dc, g);
+      for (int dc = 0; dc < 3; ++dc) {
+        const double cf = gtr_coef(mk, k, dc, g);
+        ecoef[dc * n_ell + dst] = cf;
+        ecoef32[dc * n_ell + dst] = (float)cf;
+      }
     } else {
       ekey[dst] = 0;
 #pragma unroll
-      for (int dc = 0; dc < 3; ++dc) ecoef[dc * n_ell + dst] = 0.0;
+      for (int dc = 0; dc < 3; ++dc) {
+        ecoef[dc * n_ell + dst] = 0.0;
+        ecoef32[dc * n_ell + dst] = 0.f;
+      }
     }
   }
 }
@@ -590,10 +602,12 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
   MarkerData& m = c->mk;
   if (n <= m.cap) return IBM_OK;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
-  cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2); cudaFree(m.dwf); cudaFree(m.dwc);
+  cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2); cudaFree(m.t32); cudaFree(m.dwf);
+  cudaFree(m.dwc);
   cudaFree(m.cg); cudaFree(m.t3);
   m.bf = m.bc = m.org = nullptr;
   m.wf = m.wc = m.cw = m.t = m.t2 = m.dwf = m.dwc = m.cg = m.t3 = nullptr;
+  m.t32 = nullptr;
   m.cap = 0;
   const size_t ni = sizeof(int32_t) * 3 * n, nd = sizeof(double) * 9 * n;
   if (cudaMalloc(&m.bf, ni) != cudaSuccess || cudaMalloc(&m.bc, ni) != cudaSuccess ||
@@ -602,6 +616,7 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
       cudaMalloc(&m.dwc, nd) != cudaSuccess ||
       cudaMalloc(&m.cw, sizeof(double) * 12 * n) != cudaSuccess ||
       cudaMalloc(&m.t, sizeof(double) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&m.t32, sizeof(float) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.t3, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.cg, sizeof(double) * 9 * n) != cudaSuccess) {
@@ -640,12 +655,15 @@ static ibm_status grow_ell(ibm_ctx* c, int64_t n_ell) {
   if (n_ell <= m.ell_cap && m.ell_key) return IBM_OK;
   cudaFree(m.ell_key);
   cudaFree(m.ell_coef);
+  cudaFree(m.ell_coef32);
   m.ell_key = nullptr;
   m.ell_coef = nullptr;
+  m.ell_coef32 = nullptr;
   m.ell_cap = 0;
   const int64_t cap = n_ell > 0 ? n_ell : 1;
   if (cudaMalloc(&m.ell_key, sizeof(int32_t) * cap) != cudaSuccess ||
-      cudaMalloc(&m.ell_coef, sizeof(double) * 3 * cap) != cudaSuccess) {
+      cudaMalloc(&m.ell_coef, sizeof(double) * 3 * cap) != cudaSuccess ||
+      cudaMalloc(&m.ell_coef32, sizeof(float) * 3 * cap) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, IBM_ERR_NOMEM, "marker gather layout allocation failed");
   }
@@ -736,7 +754,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   count_launch();
   k_ell_fill<<<div_up(32 * ng, TPB), TPB, 0, s>>>(mv, ns, m.shell_off, m.entry_key, m.ell_base,
                                              m.ell_len, perm, m.ell_cell, c->d, n_ell, m.ell_key,
-                                             m.ell_coef);
+                                             m.ell_coef, m.ell_coef32);
   IBM_LAUNCH_CHECK(c);
   m.n_ell = n_ell;
   m.n_entries = ne;
@@ -751,16 +769,16 @@ void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double
   if (m.n == 0) return;
   count_launch();
   k_marker_grad_interp<double><<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
-      c->d, view(m), v, scale, t);
+      c->d, view(m), v, scale, t, nullptr);
 }
 
 void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t,
-                                   cudaStream_t st) {
+                                   float* t32, cudaStream_t st) {
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
   k_marker_grad_interp<float><<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
-      c->d, view(m), v, scale, t);
+      c->d, view(m), v, scale, t, t32);
 }
 
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out) {
