@@ -111,10 +111,12 @@ ROOFLINE_CLASSES = {
     "k_axpy_norm_sp4 (Gram-Schmidt axpy+norm on FP32 vectors, float4: V_0..V_j, w in/out)":
         "axpy_norm",
     ("Schur Laplacian class: k_lap_ds<float> (FP32 z in, exact product rounded to FP32 "
-     "out) per iteration and k_laplacian<double> of the FP64 true residuals"):
+     "out) per iteration and k_laplacian_fx (FP64, stencil sum exact in 64-bit integers) "
+     "of the FP64 true residuals"):
         "laplacian_f64",
-    ("Schur marker terms: k_marker_grad_interp (t = 2 R^T G z per marker) and "
-     "k_shell_gradt_ds (B^T t gathered on the shell cells)"): "schur_markers",
+    ("Schur marker terms: k_marker_grad_interp (t = 2 R^T G z per marker) and the B^T t "
+     "gather on the shell cells (k_shell_gradt_f32 in the FP32 Arnoldi cycles, FP64 "
+     "k_shell_gradt in the true residuals)"): "schur_markers",
     "k_first_v4 + k_sweep_v4 (finest V-cycle smoothing)": "mg_smooth_fine",
     "whole V-cycle (every level, the one-block coarse chain and the coarsest solve)": "vcycle",
 }

@@ -45,15 +45,6 @@ __device__ __forceinline__ int64_t fidx(const FaceGeom& g, int c, int i, int j, 
   return g.off[c] + k * g.sz[c] + j * g.sy[c] + i;
 }
 
-// Value of component c at integer point (p[0], p[1], p[2]) of its own grid;
-// wall-normal boundary faces (index 0 or n along c) read as 0.
-__device__ __forceinline__ double face_val(const FaceGeom& g, const double* __restrict__ u,
-                                           int c, int i, int j, int k) {
-  int p[3] = {i, j, k};
-  if (p[c] <= 0 || p[c] >= g.n[c][c] - 1) return 0.0;
-  return __ldg(u + fidx(g, c, i, j, k));
-}
-
 dim3 cell_grid(Dims d) { return dim3(div_up(d.nx, BX), div_up(d.ny, BY), d.nz); }
 dim3 face_grid(Dims d) { return dim3(div_up(d.nx + 1, BX), div_up(d.ny + 1, BY), d.nz + 1); }
 
@@ -184,6 +175,88 @@ __global__ void __launch_bounds__(BX * BY) k_laplacian_fx(Dims d, const double* 
   }
 }
 
+// Scale limits for a fixed-point sum scaled by `scale` (as in lap_fx): the
+// scale 2^(E - 1075 - kLapGuard) * scale is formed by adding E - 1075 -
+// kLapGuard to the exponent field of `scale`, which must stay in [1, 2046];
+// anything else (a non-finite value; a scale that is zero, subnormal or not
+// finite) takes the FP64 formula.
+struct FxLimits {
+  long long bits;
+  int e_min, e_max;
+};
+
+FxLimits fx_limits(double scale) {
+  FxLimits L;
+  std::memcpy(&L.bits, &scale, sizeof(L.bits));
+  const int e_h = (int)((L.bits >> 52) & 0x7ff);
+  L.e_min = std::max(1075 + kLapGuard + 1 - e_h, 1);
+  L.e_max = std::min(2046 + 1075 + kLapGuard - e_h, 2046);
+  if (e_h == 0 || e_h == 0x7ff) L.e_min = 2047;
+  return L;
+}
+
+// alpha ((a0 - a1) + (a2 - a3) + (a4 - a5)) with the sum formed exactly in
+// 64-bit integers as in lap_fx (|S| < 6 2^58)
+__device__ __forceinline__ double div_fx(double a0, double a1, double a2, double a3, double a4,
+                                         double a5, FxLimits L) {
+  const FxVal v0 = fx_unpack(a0), v1 = fx_unpack(a1), v2 = fx_unpack(a2), v3 = fx_unpack(a3),
+              v4 = fx_unpack(a4), v5 = fx_unpack(a5);
+  const int E = max(max(max(v0.e, v1.e), max(v2.e, v3.e)), max(v4.e, v5.e));
+  if (E < L.e_min || E > L.e_max)
+    return __longlong_as_double(L.bits) * (((a0 - a1) + (a2 - a3)) + (a4 - a5));
+  long long S = fx_align(v0.m, v0.e, E) - fx_align(v1.m, v1.e, E);
+  S += fx_align(v2.m, v2.e, E) - fx_align(v3.m, v3.e, E);
+  S += fx_align(v4.m, v4.e, E) - fx_align(v5.m, v5.e, E);
+  const double scale =
+      __longlong_as_double(L.bits + (long long)(E - 1075 - kLapGuard) * (1LL << 52));
+  return __ll2double_rn(S) * scale;
+}
+
+// out = alpha * G^T u + beta * cin (cin may be null), (G^T u)_c = sum_d
+// (u_{c-1/2} - u_{c+1/2}) over interior faces (wall faces read as 0), the
+// sum formed exactly (div_fx).  One cell per thread, blocks of 32 x 8 cells
+// over zc planes: the upper x-face from the next lane, the lower z-face from
+// the march, the y-faces through L1.
+__global__ void __launch_bounds__(BX * BY) k_gradt_fx(Dims d, FaceGeom g,
+                                                      const double* __restrict__ u, FxLimits L,
+                                                      const double* __restrict__ cin,
+                                                      double beta, double* __restrict__ out,
+                                                      int zc) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * BX + lane;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const bool act = i < d.nx && j < d.ny;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz);
+  const double* ux = u + g.off[0];
+  const double* uy = u + g.off[1];
+  const double* uz = u + g.off[2];
+  // interior faces: x-faces 1..nx-1, y-faces 1..ny-1, z-faces 1..nz-1
+  const bool xlo = i > 0, xhi = i + 1 < d.nx, ylo = j > 0, yhi = j + 1 < d.ny;
+  double zlo = (act && z0 > 0) ? __ldg(uz + (int64_t)z0 * g.sz[2] + (int64_t)j * g.sy[2] + i) : 0.0;
+  for (int z = z0; z < z1; ++z) {
+    const int64_t fx = (int64_t)z * g.sz[0] + (int64_t)j * g.sy[0] + i;
+    const int64_t fy = (int64_t)z * g.sz[1] + (int64_t)j * g.sy[1] + i;
+    double a0 = 0.0, a2 = 0.0, a3 = 0.0, zhi = 0.0;
+    if (act) {
+      if (xlo) a0 = __ldg(ux + fx);
+      if (ylo) a2 = __ldg(uy + fy);
+      if (yhi) a3 = __ldg(uy + fy + g.sy[1]);
+      if (z + 1 < d.nz) zhi = __ldg(uz + (int64_t)(z + 1) * g.sz[2] + (int64_t)j * g.sy[2] + i);
+    }
+    // the upper x-face of cell i is the lower one of cell i + 1
+    double a1 = __shfl_down_sync(0xffffffffu, a0, 1);
+    if (lane == 31) a1 = (act && xhi) ? __ldg(ux + fx + 1) : 0.0;
+    if (!xhi) a1 = 0.0;
+    if (act) {
+      const double v = div_fx(a0, a1, a2, a3, zlo, zhi, L);
+      const int64_t c = ((int64_t)z * d.ny + j) * d.nx + i;
+      out[c] = cin ? fma(beta, __ldg(cin + c), v) : v;
+    }
+    zlo = zhi;
+  }
+}
+
 // u = u_in + alpha * G p on interior faces, 0 on wall faces (u_in may be null).
 __global__ void __launch_bounds__(BX * BY) k_grad_axpy(Dims d, FaceGeom g,
                                                        const double* __restrict__ u_in,
@@ -207,24 +280,6 @@ __global__ void __launch_bounds__(BX * BY) k_grad_axpy(Dims d, FaceGeom g,
     }
     u[f] = val;
   }
-}
-
-// out = alpha * G^T u + beta * cin: (G^T u)_c = sum_d (u_{c-1/2} - u_{c+1/2}),
-// interior faces only (alpha carries the 1/h).
-__global__ void __launch_bounds__(BX * BY) k_gradt_axpby(Dims d, FaceGeom g,
-                                                         const double* __restrict__ u,
-                                                         double alpha,
-                                                         const double* __restrict__ cin,
-                                                         double beta, double* __restrict__ out) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= d.nx || j >= d.ny) return;
-  const double s = (face_val(g, u, 0, i, j, k) - face_val(g, u, 0, i + 1, j, k)) +
-                   (face_val(g, u, 1, i, j, k) - face_val(g, u, 1, i, j + 1, k)) +
-                   (face_val(g, u, 2, i, j, k) - face_val(g, u, 2, i, j, k + 1));
-  const int64_t c = ((int64_t)k * d.ny + j) * d.nx + i;
-  out[c] = cin ? fma(alpha, s, beta * __ldg(cin + c)) : alpha * s;
 }
 
 // Predictor Helmholtz operator on the d-faces, A = a I - nu Lap_h with the
@@ -661,25 +716,16 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
 
 }  // namespace
 
+int march_zc(Dims d);
+
 template <typename T>
 void launch_laplacian(Dims d, const T* v, T* out, double inv_h2, cudaStream_t s) {
   count_launch();
   if constexpr (std::is_same<T, double>::value) {
-    // planes per thread: about eight blocks per SM over the grid, at most 4
-    const int64_t bxy = (int64_t)div_up(d.nx, BX) * div_up(d.ny, BY);
-    const int zc = (int)std::min<int64_t>(4, std::max<int64_t>(1, d.nz * bxy / (152 * 8)));
-    long long bits;
-    std::memcpy(&bits, &inv_h2, sizeof(bits));
-    // the scale 2^(E - 1075 - kLapGuard) / h^2 is formed by adding E - 1075 -
-    // kLapGuard to the exponent field e_h of 1/h^2, which must stay in
-    // [1, 2046]; E = 2047 (a non-finite value) always takes the FP64 formula
-    const int e_h = (int)((bits >> 52) & 0x7ff);
-    int e_min = 1075 + kLapGuard + 1 - e_h, e_max = 2046 + 1075 + kLapGuard - e_h;
-    e_min = std::max(e_min, 1);
-    e_max = std::min(e_max, 2046);
-    if (e_h == 0 || e_h == 0x7ff || bits < 0) e_min = 2047;   // 1/h^2 not normal and positive
+    const int zc = march_zc(d);
+    const FxLimits L = fx_limits(inv_h2);
     k_laplacian_fx<<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0,
-                     s>>>(d, v, out, bits, e_min, e_max, zc);
+                     s>>>(d, v, out, L.bits, L.e_min, L.e_max, zc);
   } else {
     k_laplacian<T><<<cell_grid(d), dim3(BX, BY), 0, s>>>(d, v, out, (T)inv_h2);
   }
@@ -698,17 +744,23 @@ void launch_grad_axpy(Dims d, const double* u_in, const double* p, double alpha,
   k_grad_axpy<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u_in, p, alpha, u_out);
 }
 
-void launch_gradient_t(Dims d, const double* u, double* out, double inv_h, cudaStream_t s) {
-  count_launch();
-  k_gradt_axpby<<<cell_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u, inv_h, nullptr,
-                                                       0.0, out);
+// planes per thread of the one-cell z-march kernels: about eight blocks per
+// SM over the grid, at most 4
+int march_zc(Dims d) {
+  const int64_t bxy = (int64_t)div_up(d.nx, BX) * div_up(d.ny, BY);
+  return (int)std::min<int64_t>(4, std::max<int64_t>(1, d.nz * bxy / (152 * 8)));
 }
 
 void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c, double beta,
                         double* out, cudaStream_t s) {
   count_launch();
-  k_gradt_axpby<<<cell_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u, alpha, c, beta,
-                                                       out);
+  const int zc = march_zc(d);
+  k_gradt_fx<<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0, s>>>(
+      d, make_face_geom(d), u, fx_limits(alpha), c, beta, out, zc);
+}
+
+void launch_gradient_t(Dims d, const double* u, double* out, double inv_h, cudaStream_t s) {
+  launch_gradt_axpby(d, u, inv_h, nullptr, 0.0, out, s);
 }
 
 int helm_zchunks(Dims d) { return div_up(d.nz + 1, ZH); }
