@@ -41,12 +41,8 @@ FaceGeom make_face_geom(Dims d) {
   return g;
 }
 
-__device__ __forceinline__ int64_t fidx(const FaceGeom& g, int c, int i, int j, int k) {
-  return g.off[c] + k * g.sz[c] + j * g.sy[c] + i;
-}
 
 dim3 cell_grid(Dims d) { return dim3(div_up(d.nx, BX), div_up(d.ny, BY), d.nz); }
-dim3 face_grid(Dims d) { return dim3(div_up(d.nx + 1, BX), div_up(d.ny + 1, BY), d.nz + 1); }
 
 // ---------------------------------------------------------------------------
 // L v = G^T G v: sum over existing neighbours of (v_c - v_n) / h^2.
@@ -257,28 +253,63 @@ __global__ void __launch_bounds__(BX * BY) k_gradt_fx(Dims d, FaceGeom g,
   }
 }
 
-// u = u_in + alpha * G p on interior faces, 0 on wall faces (u_in may be null).
+// u = u_in + alpha * G p on interior faces, 0 on wall faces (u_in may be
+// null; it may be u).  Thread (i, j) marches over the z-planes 0..nz and
+// writes the x-, y- and z-faces at (i, j, k) that exist: p(i-1) comes from
+// the previous lane, p(k-1) from the march, p(j-1) through L1.
 __global__ void __launch_bounds__(BX * BY) k_grad_axpy(Dims d, FaceGeom g,
                                                        const double* __restrict__ u_in,
                                                        const double* __restrict__ p,
-                                                       double alpha, double* __restrict__ u) {
-  const int i = blockIdx.x * BX + threadIdx.x;
+                                                       double alpha, double* __restrict__ u,
+                                                       int zc) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * BX + lane;
   const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
+  const bool col = i <= d.nx && j <= d.ny;      // some face of this column exists
+  const bool cell = i < d.nx && j < d.ny;       // the cell column exists
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.nz + 1);
   const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
-  const int p3[3] = {i, j, k};
-  const int64_t cs[3] = {1, sy, sz};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (i >= g.n[c][0] || j >= g.n[c][1] || k >= g.n[c][2]) continue;
-    const int64_t f = fidx(g, c, i, j, k);
-    double val = 0.0;
-    if (p3[c] > 0 && p3[c] < g.n[c][c] - 1) {
-      const int64_t cp = k * sz + j * sy + i;   // cell on the + side
-      const double gp = __ldg(p + cp) - __ldg(p + cp - cs[c]);
-      val = u_in ? fma(alpha, gp, __ldg(u_in + f)) : alpha * gp;
+  auto pc_at = [&](int k) { return (int64_t)k * sz + (int64_t)j * sy + i; };
+  double pzm = (cell && z0 > 0 && z0 - 1 < d.nz) ? __ldg(p + pc_at(z0 - 1)) : 0.0;
+  for (int k = z0; k < z1; ++k) {
+    const bool kin = k < d.nz;
+    const double pc = (cell && kin) ? __ldg(p + pc_at(k)) : 0.0;
+    double pxm = __shfl_up_sync(0xffffffffu, pc, 1);
+    if (lane == 0) pxm = (i > 0 && i - 1 < d.nx && j < d.ny && kin) ? __ldg(p + pc_at(k) - 1) : 0.0;
+    if (col) {
+      // x-face (i, j, k): i in 0..nx, j < ny, k < nz
+      if (j < d.ny && kin) {
+        const int64_t f = g.off[0] + (int64_t)k * g.sz[0] + (int64_t)j * g.sy[0] + i;
+        double val = 0.0;
+        if (i > 0 && i < d.nx) {
+          const double gp = pc - pxm;
+          val = u_in ? fma(alpha, gp, __ldg(u_in + f)) : alpha * gp;
+        }
+        u[f] = val;
+      }
+      // y-face (i, j, k): i < nx, j in 0..ny, k < nz
+      if (i < d.nx && kin) {
+        const int64_t f = g.off[1] + (int64_t)k * g.sz[1] + (int64_t)j * g.sy[1] + i;
+        double val = 0.0;
+        if (j > 0 && j < d.ny) {
+          const double gp = pc - __ldg(p + pc_at(k) - sy);
+          val = u_in ? fma(alpha, gp, __ldg(u_in + f)) : alpha * gp;
+        }
+        u[f] = val;
+      }
+      // z-face (i, j, k): i < nx, j < ny, k in 0..nz
+      if (cell) {
+        const int64_t f = g.off[2] + (int64_t)k * g.sz[2] + (int64_t)j * g.sy[2] + i;
+        double val = 0.0;
+        if (k > 0 && k < d.nz) {
+          const double gp = pc - pzm;
+          val = u_in ? fma(alpha, gp, __ldg(u_in + f)) : alpha * gp;
+        }
+        u[f] = val;
+      }
     }
-    u[f] = val;
+    pzm = pc;
   }
 }
 
@@ -733,15 +764,23 @@ void launch_laplacian(Dims d, const T* v, T* out, double inv_h2, cudaStream_t s)
 template void launch_laplacian<float>(Dims, const float*, float*, double, cudaStream_t);
 template void launch_laplacian<double>(Dims, const double*, double*, double, cudaStream_t);
 
+dim3 grad_grid(Dims d, int zc) {
+  return dim3(div_up(d.nx + 1, BX), div_up(d.ny + 1, BY), div_up(d.nz + 1, zc));
+}
+
 void launch_gradient(Dims d, const double* p, double* u, double inv_h, cudaStream_t s) {
   count_launch();
-  k_grad_axpy<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), nullptr, p, inv_h, u);
+  const int zc = march_zc(d);
+  k_grad_axpy<<<grad_grid(d, zc), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), nullptr, p, inv_h,
+                                                         u, zc);
 }
 
 void launch_grad_axpy(Dims d, const double* u_in, const double* p, double alpha, double* u_out,
                       cudaStream_t s) {
   count_launch();
-  k_grad_axpy<<<face_grid(d), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u_in, p, alpha, u_out);
+  const int zc = march_zc(d);
+  k_grad_axpy<<<grad_grid(d, zc), dim3(BX, BY), 0, s>>>(d, make_face_geom(d), u_in, p, alpha,
+                                                         u_out, zc);
 }
 
 // planes per thread of the one-cell z-march kernels: about eight blocks per
