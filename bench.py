@@ -54,15 +54,18 @@ UNIT = "solves/s"
 NCU_TRAFFIC_RATIO = {
     # predictor FP32 Chebyshev step (mode 1): 631.8 + 182.2 MB for 808.5 MB
     "helm_sweep": 1.0067,
-    # finest-level smoothing, one V-cycle: k_first_v4 67.1 + 25.8 MB and the
-    # two k_sweep_v4 134.2 + 39.0 and 134.2 + 36.8 MB, for 134.2 + 2 x 201.3 MB
-    "mg_smooth_fine": 0.8144,
+    # finest-level smoothing, one V-cycle: k_first_v4 67.1 + 26.7 MB and the
+    # two k_sweep_v4 134.2 + 39.4 and 134.2 + 36.5 MB, for 134.2 + 2 x 201.3 MB
+    "mg_smooth_fine": 0.8161,
     # FP32 Gram-Schmidt at basis lengths 6 and 7
     "multidot": 1.0042,
     "axpy_norm": 0.9744,
-    # marker terms of one Schur product: k_marker_grad_interp 13.8 MB and
-    # k_shell_gradt_ds 120.6 + 3.0 MB for 125.0 MB
-    "schur_markers": 1.099,
+    # Schur Laplacian class per step: 14 k_lap_ds (69.8 + 24.6 MB for 134.2 MB)
+    # and 2 k_laplacian_fx (134.2 + 95.8 MB for 268.4 MB)
+    "laplacian_f64": 0.7373,
+    # marker terms of one FP32-cycle Schur product: k_marker_grad_interp
+    # 13.8 MB and k_shell_gradt_f32 70.2 + 0.5 MB, for 78.0 MB
+    "schur_markers": 1.084,
 }
 
 
@@ -384,12 +387,18 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = lib.ibm_kernel_launches()
-    s.profile_enable(True)
     ms_mixed, st_mixed = timed(lambda: step(_lib.IBM_PREC_FP32), args.steps)
-    prof = s.profile_read()
     launches = lib.ibm_kernel_launches() - l0
-    s.profile_enable(False)
     clk = clocks.stop()
+    # Kernel classes: a second timed pass of the same K steps with the
+    # library's CUDA events around each class's launches.  The events sit
+    # between launches in the stream, cost host time at every synchronisation
+    # and break the programmatic-dependent-launch overlap of the kernels they
+    # separate, so the headline pass above runs without them.
+    s.profile_enable(True)
+    ms_prof, _ = timed(lambda: step(_lib.IBM_PREC_FP32), args.steps)
+    prof = s.profile_read()
+    s.profile_enable(False)
     # each form's step result (every timed step repeats the same step), kept
     # on the host for the comparison with the oracle's solution
     to_host = lambda: {kk: v.cpu().numpy().copy() for kk, v in out.items()}  # noqa: E731
@@ -560,6 +569,13 @@ def run_ours(args):
             "helm_iters": st_mixed[-1]["helm_iters"],
             "div_l2": st_mixed[-1]["div_l2"], "slip_l2": st_mixed[-1]["slip_l2"],
             "roofline": roof, "solve_roofline": solve_roof, "kernel_classes": classes,
+            "profiled_pass": {
+                "ms_per_step": ms_prof,
+                "what": ("the kernel classes, the roofline records and the breakdown are "
+                         "timed by CUDA events on the launching streams in a second pass of "
+                         "the same K steps right after the headline pass; the events break "
+                         "the programmatic-dependent-launch overlap and cost host time, so "
+                         "this pass runs slower than the headline")},
             "breakdown": breakdown,
             "adjoint": adjoint, "c_modes": c_modes, "porous": porous, "two_way_fsi": fsi,
             "multistep": multistep,
