@@ -338,7 +338,9 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
   c->nf = c->fd.nfx + c->fd.nfy + c->fd.nfz;
   c->stream = static_cast<cudaStream_t>(stream);
   const int64_t m = c->m, nf = c->nf;
-  const int64_t nscan = (m + 4095) / 4096 + 2;
+  // block sums of the scans: int32 per block, or a pair per block for the
+  // marker lists' shell-cell pass (with the totals after them)
+  const int64_t nscan = 2 * ((m + 4095) / 4096 + 2);
   bool ok = cudaMalloc(&c->cell_count, sizeof(int32_t) * m) == cudaSuccess &&
             cudaMalloc(&c->cell_start, sizeof(int32_t) * (m + 1)) == cudaSuccess &&
             cudaMalloc(&c->cell_flag, sizeof(int32_t) * (m + 1)) == cudaSuccess &&

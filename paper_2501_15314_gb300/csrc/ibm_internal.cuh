@@ -113,7 +113,7 @@ struct ibm_ctx {
   int32_t* cell_count = nullptr;   // [m]
   int32_t* cell_start = nullptr;   // [m + 1]
   int32_t* cell_flag = nullptr;    // [m + 1]
-  int32_t* scan_tmp = nullptr;     // block sums of the scans
+  int32_t* scan_tmp = nullptr;     // block sums of the scans (int32 or int2 per block)
   int32_t* dev_flag = nullptr;     // device error word(s)
   int32_t* host_flag = nullptr;    // mapped pinned mirror (host address)
   int32_t* host_flag_dev = nullptr; // its device address

@@ -120,24 +120,11 @@ __global__ void k_count(Dims d, MkView mk, int32_t* count) {
   atomicAdd(count + cell_of(d, i, j, l), 1);
 }
 
-__global__ void k_flag(const int32_t* __restrict__ count, int64_t m, int32_t* flag) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c < m) flag[c] = count[c] > 0 ? 1 : 0;
-}
-
-__global__ void k_shell_list(const int32_t* __restrict__ count, const int32_t* __restrict__ start,
-                             const int32_t* __restrict__ fpos, int64_t m, int32_t* shell_cell,
-                             int32_t* shell_off) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= m) return;
-  if (count[c] > 0) {
-    const int32_t q = fpos[c];
-    shell_cell[q] = (int32_t)c;
-    shell_off[q] = start[c];
-  }
-}
-
-__global__ void k_fill(Dims d, MkView mk, const int32_t* __restrict__ start, int32_t* fillc,
+// Places each (marker, slot) pair in its cell's segment: the cell's count
+// (left by k_count) is taken down by one per pair, and the value before the
+// decrement gives a free position; the counts end at zero.  The order within
+// a segment depends on the atomics' scheduling until k_sort_segments.
+__global__ void k_fill(Dims d, MkView mk, const int32_t* __restrict__ start, int32_t* count,
                        int32_t* key) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= mk.n * 64) return;
@@ -146,17 +133,37 @@ __global__ void k_fill(Dims d, MkView mk, const int32_t* __restrict__ start, int
   const int i = mk.org[k] + (s & 3), j = mk.org[mk.n + k] + ((s >> 2) & 3),
             l = mk.org[2 * mk.n + k] + (s >> 4);
   const int64_t c = cell_of(d, i, j, l);
-  const int32_t pos = start[c] + atomicAdd(fillc + c, 1);
+  const int32_t pos = start[c] + atomicSub(count + c, 1) - 1;
   key[pos] = (int32_t)(k * 64 + s);
 }
 
-// Insertion sort of each shell cell's segment (segments hold <= a few hundred
-// keys); makes the entry order independent of atomic scheduling.
+// Sorts each shell cell's segment (one warp per segment): the keys are
+// distinct, so a key's place is the number of smaller keys in the segment;
+// segments of up to 64 keys are ranked in registers (two keys per lane),
+// longer ones by an insertion sort in lane 0.  Makes the entry order
+// independent of the atomics' scheduling.
 __global__ void k_sort_segments(int64_t n_shell, const int32_t* __restrict__ off, int32_t* key) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n_shell) return;
-  const int32_t a = off[q], b = off[q + 1];
-  for (int32_t x = a + 1; x < b; ++x) {
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= n_shell) return;   // whole warps leave together
+  const int32_t a = off[q], L = off[q + 1] - off[q];
+  if (L <= 1) return;
+  if (L <= 64) {
+    const int32_t k0 = lane < L ? key[a + lane] : 0x7fffffff;
+    const int32_t k1 = lane + 32 < L ? key[a + 32 + lane] : 0x7fffffff;
+    int r0 = 0, r1 = 0;
+    for (int j = 0; j < L; ++j) {
+      const int32_t kj = __shfl_sync(0xffffffffu, j < 32 ? k0 : k1, j & 31);
+      r0 += kj < k0;
+      r1 += kj < k1;
+    }
+    __syncwarp();
+    if (lane < L) key[a + r0] = k0;
+    if (lane + 32 < L) key[a + r1] = k1;
+    return;
+  }
+  if (lane != 0) return;
+  for (int32_t x = a + 1; x < a + L; ++x) {
     const int32_t v = key[x];
     int32_t y = x - 1;
     while (y >= a && key[y] > v) { key[y + 1] = key[y]; --y; }
@@ -524,6 +531,110 @@ __device__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
   return wprefix + x - v;
 }
 
+// The same for pairs (.x and .y scanned independently).
+__device__ int2 block_excl_scan2(int2 v, int2* sh, int2* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2 x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int yx = __shfl_up_sync(0xffffffffu, x.x, o);
+    const int yy = __shfl_up_sync(0xffffffffu, x.y, o);
+    if (lane >= o) {
+      x.x += yx;
+      x.y += yy;
+    }
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int2 w = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yx = __shfl_up_sync(0xffffffffu, w.x, o);
+      const int yy = __shfl_up_sync(0xffffffffu, w.y, o);
+      if (lane >= o) {
+        w.x += yx;
+        w.y += yy;
+      }
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  const int2 wp = wid > 0 ? sh[wid - 1] : make_int2(0, 0);
+  if (total) *total = sh[31];
+  return make_int2(wp.x + x.x - v.x, wp.y + x.y - v.y);
+}
+
+// Shell cells of the marker lists, in two passes over the cell counts (each
+// block SCAN_T * SCAN_E cells): k_cell_sums writes each block's (entries,
+// shell cells); after the scan of those, k_shell_list writes, for every cell
+// with entries, its segment start and its place in the shell list.
+__global__ void k_cell_sums(const int32_t* __restrict__ count, int64_t n, int2* __restrict__ sums) {
+  __shared__ int2 sh[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_T * SCAN_E + (int64_t)threadIdx.x * SCAN_E;
+  int2 v = make_int2(0, 0);
+#pragma unroll
+  for (int q = 0; q < SCAN_E; ++q) {
+    const int32_t k = (base + q < n) ? count[base + q] : 0;
+    v.x += k;
+    v.y += k > 0;
+  }
+  int2 total;
+  block_excl_scan2(v, sh, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// exclusive scan of the nb block pairs in place (one block); the totals go
+// to sums[nb]
+__global__ void k_scan_sums2(int2* sums, int64_t nb) {
+  __shared__ int2 sh[32];
+  __shared__ int2 carry;
+  if (threadIdx.x == 0) carry = make_int2(0, 0);
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += SCAN_T) {
+    const int64_t i = base + threadIdx.x;
+    const int2 v = i < nb ? sums[i] : make_int2(0, 0);
+    int2 tot;
+    const int2 ex = block_excl_scan2(v, sh, &tot);
+    const int2 c0 = carry;
+    if (i < nb) sums[i] = make_int2(ex.x + c0.x, ex.y + c0.y);
+    __syncthreads();
+    if (threadIdx.x == 0) carry = make_int2(c0.x + tot.x, c0.y + tot.y);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_shell_list(const int32_t* __restrict__ count, int64_t n,
+                             const int2* __restrict__ sums, int32_t* __restrict__ start,
+                             int32_t* __restrict__ shell_cell, int32_t* __restrict__ shell_off,
+                             int64_t nb) {
+  __shared__ int2 sh[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_T * SCAN_E + (int64_t)threadIdx.x * SCAN_E;
+  int32_t k[SCAN_E];
+  int2 v = make_int2(0, 0);
+#pragma unroll
+  for (int q = 0; q < SCAN_E; ++q) {
+    k[q] = (base + q < n) ? count[base + q] : 0;
+    v.x += k[q];
+    v.y += k[q] > 0;
+  }
+  const int2 ex = block_excl_scan2(v, sh, nullptr);
+  const int2 b0 = sums[blockIdx.x];
+  int32_t e = b0.x + ex.x, sidx = b0.y + ex.y;
+#pragma unroll
+  for (int q = 0; q < SCAN_E; ++q) {
+    if (k[q] > 0) {
+      start[base + q] = e;
+      shell_cell[sidx] = (int32_t)(base + q);
+      shell_off[sidx] = e;
+      ++sidx;
+    }
+    e += k[q];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) shell_off[sums[nb].y] = sums[nb].x;
+}
+
 __global__ void k_scan_blocks(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ out,
                               int32_t* __restrict__ block_sums) {
   __shared__ int32_t sh[32];
@@ -697,47 +808,37 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
                    "a marker's delta support touches a wall face or leaves the grid");
   m.n = n;
   const MkView mv = view(m);
-  // counting sort of (marker, slot) pairs by cell
+  // counting sort of (marker, slot) pairs by cell: counts, then one
+  // reduction and one scan-and-list pass over the counts for the segment
+  // starts and the shell-cell list, then the fill (which takes the counts
+  // back to zero) and the per-segment sort
   launch_zero(c->cell_count, sizeof(int32_t) * c->m, s);
   count_launch();
   k_count<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_count);
-  IBM_LAUNCH_CHECK(c);
-  st = exclusive_scan(c, c->cell_count, c->cell_start, c->m);
-  if (st != IBM_OK) return st;
+  const int64_t nb = (c->m + SCAN_T * SCAN_E - 1) / (SCAN_T * SCAN_E);
+  int2* bsum = reinterpret_cast<int2*>(c->scan_tmp);
   count_launch();
-  k_flag<<<div_up(c->m, TPB), TPB, 0, s>>>(c->cell_count, c->m, c->cell_flag);
-  IBM_LAUNCH_CHECK(c);
-  // compact positions of the shell cells (scan of the flags); the cell
-  // temporary c3 (m doubles) holds the m + 1 ints
-  int32_t* fpos = reinterpret_cast<int32_t*>(c->c3);   // m + 1 ints fit in m doubles
-  st = exclusive_scan(c, c->cell_flag, fpos, c->m);
-  if (st != IBM_OK) return st;
-  int32_t tot[2];
-  launch_to_host(c->cell_start + c->m, c->host_flag_dev, sizeof(int32_t), s);
-  launch_to_host(fpos + c->m, c->host_flag_dev + 1, sizeof(int32_t), s);
+  k_cell_sums<<<(unsigned)nb, SCAN_T, 0, s>>>(c->cell_count, c->m, bsum);
+  count_launch();
+  k_scan_sums2<<<1, SCAN_T, 0, s>>>(bsum, nb);
+  launch_to_host(bsum + nb, c->host_flag_dev, sizeof(int2), s);
   IBM_LAUNCH_CHECK(c);
   IBM_CUDA(c, cudaStreamSynchronize(s));
-  tot[0] = c->host_flag[0];
-  tot[1] = c->host_flag[1];
-  const int64_t ne = tot[0], ns = tot[1];
+  const int64_t ne = c->host_flag[0], ns = c->host_flag[1];
   st = grow_entries(c, ne);
   if (st != IBM_OK) return st;
   count_launch();
-  k_shell_list<<<div_up(c->m, TPB), TPB, 0, s>>>(c->cell_count, c->cell_start, fpos, c->m,
-                                                 m.shell_cell, m.shell_off);
-  IBM_LAUNCH_CHECK(c);
-  launch_copy(m.shell_off + ns, c->cell_start + c->m, sizeof(int32_t), s);
-  launch_zero(c->cell_flag, sizeof(int32_t) * c->m, s);
+  k_shell_list<<<(unsigned)nb, SCAN_T, 0, s>>>(c->cell_count, c->m, bsum, c->cell_start,
+                                               m.shell_cell, m.shell_off, nb);
   count_launch();
-  k_fill<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_start, c->cell_flag, m.entry_key);
-  IBM_LAUNCH_CHECK(c);
+  k_fill<<<div_up(n * 64, TPB), TPB, 0, s>>>(c->d, mv, c->cell_start, c->cell_count, m.entry_key);
   count_launch();
-  k_sort_segments<<<div_up(ns, TPB), TPB, 0, s>>>(ns, m.shell_off, m.entry_key);
+  k_sort_segments<<<div_up(32 * ns, TPB), TPB, 0, s>>>(ns, m.shell_off, m.entry_key);
   IBM_LAUNCH_CHECK(c);
   // interleaved layout for the B^T t gather, in the order of ell_cell
   const int64_t ng = ell_groups(ns);
-  int32_t* cnt = c->cell_count;   // free again: reused for the group sizes
-  int32_t* perm = c->cell_flag;   // free again (fill counters): the layout order
+  int32_t* cnt = c->cell_count;   // back at zero after the fill: the group sizes
+  int32_t* perm = c->cell_flag;   // scratch: the layout order
   count_launch();
   k_ell_order<<<div_up(ns, kOrderWin), kOrderWin, 0, s>>>(ns, m.shell_off, m.shell_cell, perm,
                                                           m.ell_cell);
