@@ -61,12 +61,15 @@ MkView view(const MarkerData& m) { return MkView{m.n, m.bf, m.bc, m.org, m.wf, m
 __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __restrict__ X,
                                int32_t* bf, int32_t* bc, int32_t* org, double* wf, double* wc,
                                double* cw, double* dwf, double* dwc, int32_t* err) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int ncell[3] = {d.nx, d.ny, d.nz};
+  // one thread per (axis, marker): the three axes' Roma weights are
+  // independent, and three times the threads hide the FP64 latency better
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int e = (int)(t / n);
+  const int64_t k = t - (int64_t)e * n;
+  const int ncell_e = e == 0 ? d.nx : (e == 1 ? d.ny : d.nz);
   bool bad = false;
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
+  {
     const double s = X[e * n + k] * inv_h;
     const double fs = floor(s + 0.5);
     const double fc = floor(s);
@@ -79,12 +82,13 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
         dwf[(e * 3 + q) * n + k] = 0.0; dwc[(e * 3 + q) * n + k] = 0.0;
       }
       for (int q = 0; q < 4; ++q) cw[(e * 4 + q) * n + k] = 0.0;
-      continue;
+      atomicOr(err, 1);
+      return;
     }
     const int b_f = (int)fs - 1;   // face taps b_f .. b_f+2 at positions i h
     const int b_c = (int)fc - 1;   // centre taps b_c .. b_c+2 at (i+1/2) h
-    if (b_f < 1 || b_f + 2 > ncell[e] - 1) bad = true;
-    if (b_c < 0 || b_c + 2 > ncell[e] - 1) bad = true;
+    if (b_f < 1 || b_f + 2 > ncell_e - 1) bad = true;
+    if (b_c < 0 || b_c + 2 > ncell_e - 1) bad = true;
     bf[e * n + k] = b_f;
     bc[e * n + k] = b_c;
     org[e * n + k] = min(b_f - 1, b_c);
@@ -171,22 +175,25 @@ __global__ void k_sort_segments(int64_t n_shell, const int32_t* __restrict__ off
   }
 }
 
-// Coefficient of G^T R e_{k,d} at global cell g: along d the G^T-weighted
-// face taps cw (cell i lies between faces i and i+1), along the other two
-// axes the centre-tap weights; zero outside the 4 x 3 x 3 footprint.
-__device__ __forceinline__ double gtr_coef(const MkView& mk, int64_t k, int dcomp, const int g[3]) {
-  double c = 1.0;
+// Coefficients of G^T R e_{k,d} (d = 0, 1, 2) at global cell g: along d the
+// G^T-weighted face taps cw (cell i lies between faces i and i+1), along the
+// other two axes the centre-tap weights; zero outside the 4 x 3 x 3
+// footprint.  Each axis's two factors are loaded once; coef_d =
+// (f_0 f_1) f_2 with f_e the cw factor for e = d and the centre weight
+// otherwise.
+__device__ __forceinline__ void gtr_coefs(const MkView& mk, int64_t k, const int g[3],
+                                          double (&coef)[3]) {
+  double fw[3], fc[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    if (e == dcomp) {
-      const int q = g[e] - (mk.bf[e * mk.n + k] - 1);
-      c *= (q >= 0 && q <= 3) ? mk.cw[(e * 4 + q) * mk.n + k] : 0.0;
-    } else {
-      const int q = g[e] - mk.bc[e * mk.n + k];
-      c *= (q >= 0 && q <= 2) ? mk.wc[(e * 3 + q) * mk.n + k] : 0.0;
-    }
+    const int qf = g[e] - (mk.bf[e * mk.n + k] - 1);
+    fc[e] = (qf >= 0 && qf <= 3) ? mk.cw[(e * 4 + qf) * mk.n + k] : 0.0;
+    const int qc = g[e] - mk.bc[e * mk.n + k];
+    fw[e] = (qc >= 0 && qc <= 2) ? mk.wc[(e * 3 + qc) * mk.n + k] : 0.0;
   }
-  return c;
+  coef[0] = (fc[0] * fw[1]) * fw[2];
+  coef[1] = (fw[0] * fc[1]) * fw[2];
+  coef[2] = (fw[0] * fw[1]) * fc[2];
 }
 
 // FP32 values widened to FP64 with integer operations (the conversion
@@ -340,11 +347,12 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
       const int32_t kk = key[a + p];
       ekey[dst] = kk;
       const int64_t k = kk >> 6;
+      double cf[3];
+      gtr_coefs(mk, k, g, cf);
 #pragma unroll
       for (int dc = 0; dc < 3; ++dc) {
-        const double cf = gtr_coef(mk, k, dc, g);
-        ecoef[dc * n_ell + dst] = cf;
-        ecoef32[dc * n_ell + dst] = (float)cf;
+        ecoef[dc * n_ell + dst] = cf[dc];
+        ecoef32[dc * n_ell + dst] = (float)cf[dc];
       }
     } else {
       ekey[dst] = 0;
@@ -797,8 +805,8 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   cudaStream_t s = c->stream;
   launch_zero(c->dev_flag, sizeof(int32_t), s);
   count_launch();
-  k_marker_setup<<<div_up(n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org, m.wf,
-                                                 m.wc, m.cw, m.dwf, m.dwc, c->dev_flag);
+  k_marker_setup<<<div_up(3 * n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org,
+                                                     m.wf, m.wc, m.cw, m.dwf, m.dwc, c->dev_flag);
   IBM_LAUNCH_CHECK(c);
   launch_to_host(c->dev_flag, c->host_flag_dev, sizeof(int32_t), s);
   IBM_LAUNCH_CHECK(c);
