@@ -207,7 +207,7 @@ static void free_all(ibm_ctx* c) {
   cudaFree(m.t3); cudaFree(c->cg_scal);
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_cell);
   cudaFree(m.ell_base); cudaFree(m.ell_len); cudaFree(m.ell_key); cudaFree(m.ell_coef);
-  cudaFree(m.ell_coef32);
+  cudaFree(m.ell_coef32); cudaFree(m.ell_sw); cudaFree(m.ell_any);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -80,6 +80,12 @@ struct MarkerData {
   int32_t* ell_key = nullptr;
   double* ell_coef = nullptr;     // [3][n_ell] G^T R coefficients (0 on padding)
   float* ell_coef32 = nullptr;    // [3][n_ell] the same rounded to FP32 (FP32 Arnoldi cycles)
+  // the spread R F onto the faces through the same layout: per entry and
+  // component d the weight of F_{k,d} at the cell's lower d-face (0 on
+  // padding and outside the support), and per shell cell (layout order) the
+  // bits d of the faces inside some entry's support
+  double* ell_sw = nullptr;       // [3][n_ell]
+  uint8_t* ell_any = nullptr;     // [n_shell]
   int32_t* ell_base = nullptr;    // [n_groups + 1]
   int32_t* ell_len = nullptr;     // [n_groups] rounds (entries per lane)
   int64_t n_shell = 0;

@@ -181,19 +181,34 @@ __global__ void k_sort_segments(int64_t n_shell, const int32_t* __restrict__ off
 // footprint.  Each axis's two factors are loaded once; coef_d =
 // (f_0 f_1) f_2 with f_e the cw factor for e = d and the centre weight
 // otherwise.
+//
+// With them the spread weights of the same entry: the weight of F_{k,d} at
+// the cell's lower d-face, (f_0 f_1) f_2 with the face-tap weight wf along d
+// and the centre weights along the other axes (the product the per-cell
+// spread forms), and in bit d whether that face lies inside the support.
 __device__ __forceinline__ void gtr_coefs(const MkView& mk, int64_t k, const int g[3],
-                                          double (&coef)[3]) {
-  double fw[3], fc[3];
+                                          double (&coef)[3], double (&sw)[3], int& in) {
+  double fw[3], fc[3], ff[3];
+  bool inw[3], inf[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const int qf = g[e] - (mk.bf[e * mk.n + k] - 1);
+    const int b_f = mk.bf[e * mk.n + k];
+    const int qf = g[e] - (b_f - 1);
     fc[e] = (qf >= 0 && qf <= 3) ? mk.cw[(e * 4 + qf) * mk.n + k] : 0.0;
+    inf[e] = qf >= 1 && qf <= 3;   // the face g[e] is face tap qf - 1 of 0..2
+    ff[e] = inf[e] ? mk.wf[(e * 3 + qf - 1) * mk.n + k] : 0.0;
     const int qc = g[e] - mk.bc[e * mk.n + k];
-    fw[e] = (qc >= 0 && qc <= 2) ? mk.wc[(e * 3 + qc) * mk.n + k] : 0.0;
+    inw[e] = qc >= 0 && qc <= 2;
+    fw[e] = inw[e] ? mk.wc[(e * 3 + qc) * mk.n + k] : 0.0;
   }
   coef[0] = (fc[0] * fw[1]) * fw[2];
   coef[1] = (fw[0] * fc[1]) * fw[2];
   coef[2] = (fw[0] * fw[1]) * fc[2];
+  sw[0] = (ff[0] * fw[1]) * fw[2];
+  sw[1] = (fw[0] * ff[1]) * fw[2];
+  sw[2] = (fw[0] * fw[1]) * ff[2];
+  in = (inf[0] && inw[1] && inw[2] ? 1 : 0) | (inw[0] && inf[1] && inw[2] ? 2 : 0) |
+       (inw[0] && inw[1] && inf[2] ? 4 : 0);
 }
 
 // FP32 values widened to FP64 with integer operations (the conversion
@@ -321,7 +336,8 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
                            const int32_t* __restrict__ key, const int32_t* __restrict__ base,
                            const int32_t* __restrict__ len, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ ell_cell, Dims d, int64_t n_ell,
-                           int32_t* ekey, double* ecoef, float* ecoef32) {
+                           int32_t* ekey, double* ecoef, float* ecoef32, double* esw,
+                           uint8_t* eany) {
   const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t w = tq >> 5;
   if (w >= ell_groups(n_shell)) return;
@@ -340,6 +356,7 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
     g[2] = (int)(c / ((int64_t)d.nx * d.ny));
   }
   const int32_t rounds = len[w];
+  int any = 0;
   for (int32_t rr = 0; rr < rounds; ++rr) {
     const int64_t dst = base[w] + (int64_t)rr * 32 + lane;
     const int p = kEllLanes * rr + lane % kEllLanes;
@@ -347,12 +364,15 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
       const int32_t kk = key[a + p];
       ekey[dst] = kk;
       const int64_t k = kk >> 6;
-      double cf[3];
-      gtr_coefs(mk, k, g, cf);
+      double cf[3], sw[3];
+      int in;
+      gtr_coefs(mk, k, g, cf, sw, in);
+      any |= in;
 #pragma unroll
       for (int dc = 0; dc < 3; ++dc) {
         ecoef[dc * n_ell + dst] = cf[dc];
         ecoef32[dc * n_ell + dst] = (float)cf[dc];
+        esw[dc * n_ell + dst] = sw[dc];
       }
     } else {
       ekey[dst] = 0;
@@ -360,8 +380,88 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
       for (int dc = 0; dc < 3; ++dc) {
         ecoef[dc * n_ell + dst] = 0.0;
         ecoef32[dc * n_ell + dst] = 0.f;
+        esw[dc * n_ell + dst] = 0.0;
       }
     }
+  }
+#pragma unroll
+  for (int o = 1; o < kEllLanes; o <<= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
+  if (live && lane % kEllLanes == 0) eany[q] = (uint8_t)any;
+}
+
+// u at the shell cells' lower faces += scale * (R F) (set: = scale * (R F)),
+// faces outside every support left as they are: the spread through the
+// interleaved layout, kEllLanes lanes per cell (each its share of the
+// entries, summed by shuffles in a fixed order), the three components at
+// once.  One warp per group: launch 32 threads per group.
+__global__ void k_shell_spread_ell(Dims d, int64_t n_shell, const int32_t* __restrict__ ell_cell,
+                                   const int32_t* __restrict__ base,
+                                   const int32_t* __restrict__ len,
+                                   const int32_t* __restrict__ ekey,
+                                   const double* __restrict__ esw,
+                                   const uint8_t* __restrict__ eany, int64_t n_ell, int64_t nmk,
+                                   const double* __restrict__ F, double scale, int set,
+                                   double* __restrict__ u) {
+  const int64_t tq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = tq >> 5;
+  const int lane = (int)(tq & 31);
+  const int64_t q = g * kEllCells + lane / kEllLanes;
+  const bool live = g < ell_groups(n_shell) && q < n_shell;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  if (live) {
+    int64_t idx = base[g] + lane;
+    const int L = len[g];
+    int p = 0;
+    for (; p + 4 <= L; p += 4, idx += 128) {
+      int64_t k[4];
+      double w0[4], w1[4], w2[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        k[v] = ekey[idx + 32 * v] >> 6;
+        w0[v] = esw[idx + 32 * v];
+        w1[v] = esw[n_ell + idx + 32 * v];
+        w2[v] = esw[2 * n_ell + idx + 32 * v];
+      }
+      double f0[4], f1[4], f2[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        f0[v] = F[k[v]];
+        f1[v] = F[nmk + k[v]];
+        f2[v] = F[2 * nmk + k[v]];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        a0 = fma(w0[v], f0[v], a0);
+        a1 = fma(w1[v], f1[v], a1);
+        a2 = fma(w2[v], f2[v], a2);
+      }
+    }
+    for (; p < L; ++p, idx += 32) {
+      const int64_t k = ekey[idx] >> 6;
+      a0 = fma(esw[idx], F[k], a0);
+      a1 = fma(esw[n_ell + idx], F[nmk + k], a1);
+      a2 = fma(esw[2 * n_ell + idx], F[2 * nmk + k], a2);
+    }
+  }
+  a0 = ell_combine(a0);
+  a1 = ell_combine(a1);
+  a2 = ell_combine(a2);
+  if (!live || lane % kEllLanes != 0) return;
+  const int64_t c = ell_cell[q];
+  const int ci = (int)(c % d.nx);
+  const int cj = (int)((c / d.nx) % d.ny);
+  const int ck = (int)(c / ((int64_t)d.nx * d.ny));
+  const int any = eany[q];
+  const FaceDims fd = face_dims(d);
+  const double acc[3] = {a0, a1, a2};
+#pragma unroll
+  for (int dc = 0; dc < 3; ++dc) {
+    if (!(any & (1 << dc))) continue;
+    const int64_t foff = dc == 0 ? 0 : (dc == 1 ? fd.nfx : fd.nfx + fd.nfy);
+    const int64_t sy = d.nx + (dc == 0 ? 1 : 0);
+    const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
+    const int64_t f = foff + ck * sz + cj * sy + ci;
+    u[f] = set ? scale * acc[dc] : fma(scale, acc[dc], u[f]);
   }
 }
 
@@ -459,21 +559,6 @@ __device__ __forceinline__ double spread_face(Dims d, const MkView& mk, int64_t 
   const int64_t sz = sy * (d.ny + (dc == 1 ? 1 : 0));
   f = foff + ck * sz + cj * sy + ci;
   return acc;
-}
-
-__global__ void k_shell_spread_faces(Dims d, MkView mk, int64_t n_shell,
-                                     const int32_t* __restrict__ shell_cell,
-                                     const int32_t* __restrict__ off,
-                                     const int32_t* __restrict__ key,
-                                     const double* __restrict__ F, double scale, int set,
-                                     double* __restrict__ u) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= 3 * n_shell) return;
-  bool any;
-  int64_t f;
-  const double acc = spread_face(d, mk, n_shell, shell_cell, off, key, F, tid, any, f);
-  if (!any) return;
-  u[f] = set ? scale * acc : fma(scale, acc, u[f]);
 }
 
 // L1 norms of the spread forces R A and R B over the faces (every face of the
@@ -751,9 +836,9 @@ static ibm_status grow_entries(ibm_ctx* c, int64_t ne) {
   MarkerData& m = c->mk;
   if (ne <= m.entries_cap && m.entry_key) return IBM_OK;
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_base);
-  cudaFree(m.ell_len); cudaFree(m.ell_cell);
+  cudaFree(m.ell_len); cudaFree(m.ell_cell); cudaFree(m.ell_any);
   m.entry_key = nullptr; m.shell_cell = nullptr; m.shell_off = nullptr; m.ell_base = nullptr;
-  m.ell_len = nullptr; m.ell_cell = nullptr;
+  m.ell_len = nullptr; m.ell_cell = nullptr; m.ell_any = nullptr;
   m.entries_cap = 0;
   const int64_t cap = ne > 0 ? ne : 1;
   if (cudaMalloc(&m.entry_key, sizeof(int32_t) * cap) != cudaSuccess ||
@@ -761,6 +846,7 @@ static ibm_status grow_entries(ibm_ctx* c, int64_t ne) {
       cudaMalloc(&m.ell_len, sizeof(int32_t) * (cap / kEllCells + 2)) != cudaSuccess ||
       cudaMalloc(&m.shell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.ell_cell, sizeof(int32_t) * cap) != cudaSuccess ||
+      cudaMalloc(&m.ell_any, cap) != cudaSuccess ||
       cudaMalloc(&m.shell_off, sizeof(int32_t) * (cap + 1)) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, IBM_ERR_NOMEM, "marker entry list allocation failed");
@@ -775,14 +861,17 @@ static ibm_status grow_ell(ibm_ctx* c, int64_t n_ell) {
   cudaFree(m.ell_key);
   cudaFree(m.ell_coef);
   cudaFree(m.ell_coef32);
+  cudaFree(m.ell_sw);
   m.ell_key = nullptr;
   m.ell_coef = nullptr;
   m.ell_coef32 = nullptr;
+  m.ell_sw = nullptr;
   m.ell_cap = 0;
   const int64_t cap = n_ell > 0 ? n_ell : 1;
   if (cudaMalloc(&m.ell_key, sizeof(int32_t) * cap) != cudaSuccess ||
       cudaMalloc(&m.ell_coef, sizeof(double) * 3 * cap) != cudaSuccess ||
-      cudaMalloc(&m.ell_coef32, sizeof(float) * 3 * cap) != cudaSuccess) {
+      cudaMalloc(&m.ell_coef32, sizeof(float) * 3 * cap) != cudaSuccess ||
+      cudaMalloc(&m.ell_sw, sizeof(double) * 3 * cap) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, IBM_ERR_NOMEM, "marker gather layout allocation failed");
   }
@@ -863,7 +952,7 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   count_launch();
   k_ell_fill<<<div_up(32 * ng, TPB), TPB, 0, s>>>(mv, ns, m.shell_off, m.entry_key, m.ell_base,
                                              m.ell_len, perm, m.ell_cell, c->d, n_ell, m.ell_key,
-                                             m.ell_coef, m.ell_coef32);
+                                             m.ell_coef, m.ell_coef32, m.ell_sw, m.ell_any);
   IBM_LAUNCH_CHECK(c);
   m.n_ell = n_ell;
   m.n_entries = ne;
@@ -984,8 +1073,9 @@ void launch_shell_spread_faces(ibm_ctx* c, const double* F, double scale, double
   const MarkerData& m = c->mk;
   if (m.n == 0 || m.n_shell == 0) return;
   count_launch();
-  k_shell_spread_faces<<<div_up(3 * m.n_shell, TPB), TPB, 0, c->stream>>>(
-      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, scale, 0, u);
+  k_shell_spread_ell<<<div_up(32 * ell_groups(m.n_shell), TPB), TPB, 0, c->stream>>>(
+      c->d, m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_sw, m.ell_any, m.n_ell,
+      m.n, F, scale, 0, u);
 }
 
 int launch_shell_spread_asum2(ibm_ctx* c, const double* A, const double* B, double* part) {
@@ -1001,8 +1091,9 @@ void launch_shell_spread_faces_set(ibm_ctx* c, const double* F, double* u) {
   const MarkerData& m = c->mk;
   if (m.n == 0 || m.n_shell == 0) return;
   count_launch();
-  k_shell_spread_faces<<<div_up(3 * m.n_shell, TPB), TPB, 0, c->stream>>>(
-      c->d, view(m), m.n_shell, m.shell_cell, m.shell_off, m.entry_key, F, 1.0, 1, u);
+  k_shell_spread_ell<<<div_up(32 * ell_groups(m.n_shell), TPB), TPB, 0, c->stream>>>(
+      c->d, m.n_shell, m.ell_cell, m.ell_base, m.ell_len, m.ell_key, m.ell_sw, m.ell_any, m.n_ell,
+      m.n, F, 1.0, 1, u);
 }
 
 }  // namespace ibm
