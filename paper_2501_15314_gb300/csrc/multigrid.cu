@@ -359,7 +359,9 @@ bool vec_ok(Dims d) { return d.nx % 4 == 0; }
 // away from the y and z walls (a warp-uniform test) take a path whose
 // weights and neighbour counts are per-thread constants and whose loads
 // need no wall test.
-template <typename TO>
+// ZC > 0: exactly ZC planes per thread (the march unrolled at compile time;
+// the launch's zc equals ZC); ZC = 0: zc planes at run time.
+template <typename TO, int ZC = 0>
 __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __restrict__ x,
                                                       const float* __restrict__ b,
                                                       TO* __restrict__ xo, float w, float h2,
@@ -390,7 +392,11 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
   const bool yin = ny_c == 2;
   float4 xp = (act && z0 > 0) ? ld4(x + c - sz) : Z4;
   float4 xc = act ? ld4(x + c) : Z4;
-  for (int z = z0; z < z1; ++z, c += sz) {
+  constexpr int kUnroll = ZC > 0 ? ZC : 1;
+#pragma unroll kUnroll
+  for (int zz = 0; zz < (ZC > 0 ? ZC : zc); ++zz) {
+    const int z = z0 + zz;
+    if (z >= z1) break;
     const bool inner = yin && z > 0 && z < d.nz - 1;
     float4 xn = Z4, ym = Z4, yp = Z4, bb = Z4;
     if (inner) {
@@ -437,6 +443,7 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
     if (act) st4(xo + c, make_float4(o[0], o[1], o[2], o[3]));
     xp = xc;
     xc = xn;
+    c += sz;
   }
 }
 
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(32 * VY) k_sweep_v4(Dims d, const float* __res
 // thread.  b may be FP64: each value is rounded once; x-neighbours move
 // between lanes by shuffles, the block's rows (and the two y-halo rows) are
 // staged as float4 in shared memory for the y-neighbours, z by the march.
-template <typename TB>
+template <typename TB, int ZC = 0>
 __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __restrict__ b,
                                                       float* __restrict__ bcopy,
                                                       float* __restrict__ xo, float w0h2,
@@ -509,7 +516,11 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
   const bool yin = j >= 2 && j <= d.ny - 3;
   float4 bp = (act && z0 > 0) ? ld4_any(b + c - sz) : Z4;
   float4 bc = act ? ld4_any(b + c) : Z4;
-  for (int z = z0; z < z1; ++z, c += sz) {
+  constexpr int kUnroll = ZC > 0 ? ZC : 1;
+#pragma unroll kUnroll
+  for (int zz = 0; zz < (ZC > 0 ? ZC : zc); ++zz) {
+    const int z = z0 + zz;
+    if (z >= z1) break;
     // rows and planes two cells away from the y and z walls (warp-uniform)
     const bool inner = yin && z >= 2 && z <= d.nz - 3;
     float4 bn = Z4, ym = Z4, yp = Z4;
@@ -594,6 +605,7 @@ __global__ void __launch_bounds__(32 * VY, 4) k_first_v4(Dims d, const TB* __res
     if constexpr (!std::is_same<TB, float>::value) __syncthreads();
     bp = bc;
     bc = bn;
+    c += sz;
   }
 }
 
@@ -1049,8 +1061,9 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
   count_launch();
   if constexpr (std::is_same<T, float>::value) {
     if (vec)
-      launch_pdl(k_first_v4<TB>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, b, bcopy, x,
-                 (float)(w[0] * h2), (float)(two ? w[1] : 0.0), (float)h2, two, zc);
+      launch_pdl(zc == 4 ? k_first_v4<TB, 4> : (zc == 1 ? k_first_v4<TB, 1> : k_first_v4<TB, 0>),
+                 vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, b, bcopy, x, (float)(w[0] * h2),
+                 (float)(two ? w[1] : 0.0), (float)h2, two, zc);
   }
   if constexpr (!std::is_same<TB, float2>::value) {
     if (!vec)
@@ -1066,7 +1079,9 @@ void pre_smooth(ibm_ctx* c, int l, const TB* b, T* bcopy, T* x, T* t, int p, cud
     prof_note(c, (double)L.m * 3 * sizeof(T));
     if constexpr (std::is_same<T, float>::value) {
       if (vec)
-        launch_pdl(k_sweep_v4<float>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d,
+        launch_pdl(zc == 4 ? k_sweep_v4<float, 4>
+                           : (zc == 1 ? k_sweep_v4<float, 1> : k_sweep_v4<float, 0>),
+                   vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d,
                    (const float*)cur, (const float*)bb, nxt, (float)w[q], (float)h2, zc);
     }
     if (!vec)
@@ -1089,7 +1104,8 @@ void sweep_step(ibm_ctx* c, int l, const T* src, const T* b, TO* dst, double w, 
   if constexpr (std::is_same<T, float>::value) {
     if (vec_ok(L.d)) {
       const int zc = vec_zc(L.d);
-      launch_pdl(k_sweep_v4<TO>, vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, (const float*)src,
+      launch_pdl(zc == 4 ? k_sweep_v4<TO, 4> : (zc == 1 ? k_sweep_v4<TO, 1> : k_sweep_v4<TO, 0>),
+                 vec_grid(L.d, zc), dim3(32, VY), 0, s, L.d, (const float*)src,
                  (const float*)b, dst, (float)w, (float)h2, zc);
       return;
     }
