@@ -100,4 +100,38 @@ __device__ __forceinline__ double f2d_exact(float x) {
   return __longlong_as_double((long long)(sign | (e64 << 52) | (ex == 0u ? 0ull : frac)));
 }
 
+// The same transformations on two independent values at once, with the
+// paired FP32 instructions of sm_100 and later (__fadd2_rn, __fmul2_rn,
+// __ffma2_rn: each component rounds exactly as the scalar instruction, so a
+// pair computes bit for bit what two scalar chains would, in half the
+// instructions).  dsf2 holds two double-single values: (hi.x, lo.x) and
+// (hi.y, lo.y).
+struct dsf2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ dsf2 two_sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bb = fsub2(s, a);
+  const float2 e = __fadd2_rn(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dsf2 fast_two_sum2(float2 a, float2 b) {   // |a| >= |b| per component
+  const float2 s = __fadd2_rn(a, b);
+  return {s, fsub2(b, fsub2(s, a))};
+}
+__device__ __forceinline__ dsf2 two_prod2(float2 a, float2 b) {
+  const float2 p = __fmul2_rn(a, b);
+  return {p, __ffma2_rn(a, b, neg2(p))};
+}
+// each component of a times the double-single b (dropping lo*lo), as ds_mul
+__device__ __forceinline__ dsf2 ds_mul2(dsf2 a, dsf b) {
+  const float2 bh = make_float2(b.hi, b.hi), bl = make_float2(b.lo, b.lo);
+  dsf2 p = two_prod2(a.hi, bh);
+  p.lo = __ffma2_rn(a.hi, bl, p.lo);
+  p.lo = __ffma2_rn(a.lo, bh, p.lo);
+  return fast_two_sum2(p.hi, p.lo);
+}
+
 }  // namespace ibm

@@ -78,17 +78,19 @@ __global__ void k_split(const double* __restrict__ x, float2* __restrict__ v,
 // shuffles, z by the march (as the FP32 smoothers).
 constexpr int LVY = 8;
 
-__device__ __forceinline__ dsf lap_cell(float zc, const float (&nb)[6], int nn, dsf ih2) {
-  // exact nn * zc as a pair, then subtract each neighbour exactly
-  dsf acc = two_prod((float)nn, zc);
+// Two cells at once: exact nn * zc as a pair, then each neighbour subtracted
+// exactly (two_sum chain), then the scaling; paired FP32 instructions, bit
+// for bit the two scalar evaluations.
+__device__ __forceinline__ dsf2 lap_cell2(float2 zc, const float2 (&nb)[6], float2 nn, dsf ih2) {
+  dsf2 acc = two_prod2(nn, zc);
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const dsf t = two_sum(acc.hi, -nb[q]);
+    const dsf2 t = two_sum2(acc.hi, neg2(nb[q]));
     acc.hi = t.hi;
-    acc.lo = __fadd_rn(acc.lo, t.lo);
+    acc.lo = __fadd2_rn(acc.lo, t.lo);
   }
-  acc = fast_two_sum(acc.hi, acc.lo);
-  return ds_mul(acc, ih2);
+  acc = fast_two_sum2(acc.hi, acc.lo);
+  return ds_mul2(acc, ih2);
 }
 
 // (TW = float2: the pair; TW = float: rounded once to FP32)
@@ -128,13 +130,19 @@ __global__ void __launch_bounds__(32 * LVY) k_lap_ds(Dims d, const float* __rest
     const float vzp[4] = {zp.x, zp.y, zp.z, zp.w};
     const float vzn[4] = {zn.x, zn.y, zn.z, zn.w};
     float ohi[4], olo[4];
+    // cells (0, 1) and (2, 3) in pairs; missing neighbours contribute 0 and
+    // are not counted
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      // missing neighbours contribute 0 and are not counted
-      const float nb[6] = {xl[q], xr[q], vym[q], vyp[q], vzp[q], vzn[q]};
-      const dsf v = lap_cell(cv[q], nb, nxq[q] + ny_c + zn_c, ih2);
-      ohi[q] = v.hi;
-      olo[q] = v.lo;
+    for (int q = 0; q < 4; q += 2) {
+      const float2 nb[6] = {make_float2(xl[q], xl[q + 1]),   make_float2(xr[q], xr[q + 1]),
+                            make_float2(vym[q], vym[q + 1]), make_float2(vyp[q], vyp[q + 1]),
+                            make_float2(vzp[q], vzp[q + 1]), make_float2(vzn[q], vzn[q + 1])};
+      const float2 nn = make_float2((float)(nxq[q] + ny_c + zn_c), (float)(nxq[q + 1] + ny_c + zn_c));
+      const dsf2 v = lap_cell2(make_float2(cv[q], cv[q + 1]), nb, nn, ih2);
+      ohi[q] = v.hi.x;
+      ohi[q + 1] = v.hi.y;
+      olo[q] = v.lo.x;
+      olo[q + 1] = v.lo.y;
     }
     if (act) {
       if constexpr (std::is_same<TW, float2>::value) {
