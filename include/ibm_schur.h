@@ -134,6 +134,13 @@ typedef struct {
   int32_t c_mode;        /* ibm_cmode                                        */
   double c_rtol;         /* inner CG on C: relative residual target          */
   int32_t c_maxit;       /* inner CG on C: iteration limit per solve         */
+  int32_t cycle_graphs;  /* 1: run each FP32 / double-single Arnoldi cycle as
+                            one CUDA graph replay (Givens rotations and the
+                            stopping test on the device, the next iteration
+                            in a conditional node; scalar C mode, profiling
+                            off); 0 (default): the host-driven loop, which
+                            launches ahead while the residual is far from
+                            the target and measured faster on GB300       */
 } ibm_solve_opts;
 
 #define IBM_HIST_MAX 256
@@ -150,6 +157,9 @@ typedef struct {
   double slip_l2;         /* ||R^T u^{n+1} - U^Gamma||_2  (ibm_step only)    */
   int64_t c_iters;        /* inner CG iterations on C, summed (EXACT and
                              CONSISTENT modes)                               */
+  int32_t graph_cycles;   /* restart cycles run as one CUDA graph replay
+                             (FP32 / double-single Arnoldi, scalar C form,
+                             profiling off): no host round trip inside them */
 } ibm_solve_stats;
 
 /* Fills *opts with defaults: FP32 V-cycle, rtol 1e-8, maxit 200, restart 40,

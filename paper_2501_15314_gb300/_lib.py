@@ -48,14 +48,14 @@ class ibm_solve_opts(C.Structure):
                 ("restart", C.c_int32), ("mg_pre", C.c_int32), ("mg_post", C.c_int32),
                 ("reorth", C.c_int32), ("helm_rtol", C.c_double), ("helm_maxit", C.c_int32),
                 ("with_advection", C.c_int32), ("arnoldi", C.c_int32), ("c_mode", C.c_int32),
-                ("c_rtol", C.c_double), ("c_maxit", C.c_int32)]
+                ("c_rtol", C.c_double), ("c_maxit", C.c_int32), ("cycle_graphs", C.c_int32)]
 
 
 class ibm_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("relres_true", C.c_double),
                 ("relres_hist", C.c_double * HIST_MAX), ("helm_iters", C.c_int32),
                 ("helm_relres", C.c_double), ("div_l2", C.c_double), ("slip_l2", C.c_double),
-                ("c_iters", C.c_int64)]
+                ("c_iters", C.c_int64), ("graph_cycles", C.c_int32)]
 
 
 class ibm_rigid_sphere(C.Structure):

@@ -32,7 +32,7 @@ def _stats_dict(st: _lib.ibm_solve_stats) -> dict:
     return dict(iters=st.iters, restarts=st.restarts, relres_true=st.relres_true,
                 relres_hist=list(st.relres_hist[:n]), helm_iters=st.helm_iters,
                 helm_relres=st.helm_relres, div_l2=st.div_l2, slip_l2=st.slip_l2,
-                c_iters=st.c_iters)
+                c_iters=st.c_iters, graph_cycles=st.graph_cycles)
 
 
 class RigidSpheres:

@@ -25,6 +25,7 @@ ibm_status cuda_err(ibm_ctx* c, cudaError_t e, const char* where) {
 static std::atomic<long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int prof_begin(ibm_ctx* c, int cls) {
   if (!c->prof_on) return -1;
@@ -144,6 +145,8 @@ ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o) {
     return set_err(c, IBM_ERR_ARG, "c_mode must be IBM_CMODE_SCALAR, _EXACT or _CONSISTENT");
   if (o->c_mode != IBM_CMODE_SCALAR && (!(o->c_rtol > 0.0) || o->c_maxit < 1))
     return set_err(c, IBM_ERR_ARG, "need c_rtol > 0 and c_maxit >= 1");
+  if (o->cycle_graphs != 0 && o->cycle_graphs != 1)
+    return set_err(c, IBM_ERR_ARG, "cycle_graphs must be 0 or 1");
   return IBM_OK;
 }
 
@@ -200,6 +203,10 @@ static void free_all(ibm_ctx* c) {
   for (cudaEvent_t& e : c->ev_iter)
     if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->cyc_exec) cudaGraphExecDestroy(c->cyc_exec);
+  if (c->cyc_graph) cudaGraphDestroy(c->cyc_graph);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  cudaFree(c->gstate); cudaFreeHost(c->host_gstate);
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
   cudaFree(m.t); cudaFree(m.t2); cudaFree(m.t32); cudaFree(m.dwf); cudaFree(m.dwc);
@@ -318,6 +325,7 @@ void ibm_default_opts(ibm_solve_opts* o) {
   o->c_mode = IBM_CMODE_SCALAR;
   o->c_rtol = 1e-14;
   o->c_maxit = 500;
+  o->cycle_graphs = 0;
 }
 
 ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
@@ -372,7 +380,12 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_iter[0], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&c->ev_iter[1], cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&c->ev_iter[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&c->gstate, sizeof(double) * GState::kSize) == cudaSuccess &&
+            cudaHostAlloc(&c->host_gstate, sizeof(double) * GState::kSize, cudaHostAllocMapped) ==
+                cudaSuccess &&
+            cudaHostGetDevicePointer(&c->host_gstate_dev, c->host_gstate, 0) == cudaSuccess;
   {
     // partial sums of the fused predictor residual norm (one per block)
     const int64_t nb = (int64_t)div_up(g->nx + 1, 32) * div_up(g->ny + 1, 8) * 3 *

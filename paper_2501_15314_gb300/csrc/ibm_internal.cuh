@@ -113,6 +113,18 @@ struct ibm_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_iter[2] = {nullptr, nullptr};   // ends of Krylov iterations (by parity)
+  // FP32/double-single Arnoldi cycles replayed as one CUDA graph each
+  // (krylov_df.cu): the capture stream, the graph and what it was built for,
+  // the kernels each captured iteration launches, and the Givens state of a
+  // cycle (device, and the mapped pinned copy the host reads after a cycle)
+  cudaStream_t cap = nullptr;
+  cudaGraph_t cyc_graph = nullptr;
+  cudaGraphExec_t cyc_exec = nullptr;
+  unsigned long long cyc_key[16] = {0};
+  int cyc_launches[ibm::kMaxRestart] = {0};
+  double* gstate = nullptr;
+  double* host_gstate = nullptr;
+  double* host_gstate_dev = nullptr;
   std::string err;
 
   // grid-sized scratch (FP64)
@@ -334,6 +346,9 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
 
 // Counts one kernel launch (process-wide counter, ibm_kernel_launches).
 void count_launch();
+// adds n (which may be negative) to the launch counter: kernels captured into
+// a graph are counted when the graph runs them, not when they are captured
+void add_launches(int64_t n);
 
 // Per-body force and torque sums (Eq. (IBM_force)) in one launch of n_bodies
 // blocks: out[6b..6b+5] = h3 (sum F, sum (X - c_b) x F) over the markers with
@@ -508,6 +523,19 @@ struct CoefF64 {
 };
 struct CoefDS {
   float2 v[kMaxRestart + 1];
+};
+
+// Givens state of one FP32 Arnoldi cycle run as a graph (doubles): H
+// [(kMaxRestart + 1) x kMaxRestart, row-major as the host's], cs, sn, g, rn,
+// the residual history of the cycle, and scalars.
+struct GState {
+  static constexpr int R = kMaxRestart;
+  static constexpr int kH = 0, kCS = (R + 1) * R, kSN = kCS + R, kG = kSN + R, kRN = kG + R + 1,
+                       kHist = kRN + R + 1, kSc = kHist + R, kSize = kSc + 16;
+  // scalars: bnorm, rtol, cycle_stop, rmax (iterations allowed), jused,
+  // breakdown flag, non-finite flag
+  static constexpr int sBnorm = 0, sRtol = 1, sStop = 2, sRmax = 3, sJused = 4, sBreak = 5,
+                       sNan = 6;
 };
 
 // Device address of a place in the mapped host mirror host_red (kernels write

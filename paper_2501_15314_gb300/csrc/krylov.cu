@@ -352,7 +352,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   double relres = 0.0;
   if (bnorm == 0.0) {
     launch_zero(x, sizeof(double) * m, s);
-    if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; }
+    if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; st->graph_cycles = 0; }
     return IBM_OK;
   }
   std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart),
@@ -460,6 +460,7 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
   if (st) {
     st->iters = total;
     st->restarts = cycles;
+    st->graph_cycles = 0;
     st->relres_true = relres;
   }
   if (final_status != IBM_OK) return set_err(c, final_status, "FGMRES breakdown");

@@ -11,6 +11,7 @@
 // The marker term of S~ stays FP64 (it touches ~1% of the cells), the true
 // residual b - S~ x that decides convergence (and restarts) is evaluated in
 // native FP64, and dot products are reduced to FP64 per block.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -657,6 +658,203 @@ ibm_status schur_apply_ds(ibm_ctx* c, const float* z, float2* w) {
   return schur_apply_ds_t<float2>(c, z, w);
 }
 
+// ---------------------------------------------------------------------------
+// An Arnoldi cycle as one CUDA graph.  Iteration j's kernels (V-cycle, Schur
+// product, Gram-Schmidt) are captured once, followed by k_givens, which
+// applies the previous Givens rotations to the new Hessenberg column, forms
+// the next rotation and the residual estimate, and decides whether the cycle
+// goes on; iteration j + 1 sits in a conditional IF node whose condition
+// k_givens sets, so the nodes nest as deep as the restart length and a cycle
+// that stops early skips the rest.  The host launches the graph, reads the
+// state once after it (GState layout) and forms the update as in the
+// host-driven loop.  Opt-in (ibm_solve_opts.cycle_graphs): on GB300 the
+// host-driven loop, which launches the next iteration before reading the
+// current column while the residual is far from the target, measured
+// faster (the one-thread Givens kernel and the conditional node add about
+// 9 us per iteration on the critical path).  The host-driven loop also runs
+// while profiling, for the exact and sign-consistent C forms (whose Schur
+// product waits on the host) and when the graph cannot be built.
+
+// g zeroed but g[0] = rn[0] = beta, and the cycle's scalars
+__global__ void k_cycle_init(double* __restrict__ st, double beta, double bnorm, double rtol,
+                             double cycle_stop, int rmax) {
+  for (int i = threadIdx.x; i <= GState::R; i += blockDim.x) st[GState::kG + i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st[GState::kG] = beta;
+    st[GState::kRN] = beta;
+    double* sc = st + GState::kSc;
+    sc[GState::sBnorm] = bnorm;
+    sc[GState::sRtol] = rtol;
+    sc[GState::sStop] = cycle_stop;
+    sc[GState::sRmax] = (double)rmax;
+    sc[GState::sJused] = 0.0;
+    sc[GState::sBreak] = 0.0;
+    sc[GState::sNan] = 0.0;
+  }
+}
+
+// Iteration j's Hessenberg column (raw[i] = <w, V_i>, nrm2[j + 1] = ||w||^2,
+// the basis kept unnormalised with ||V_i|| = rn[i]) into the rotated
+// triangular factor, as the host-driven loop does; one thread.
+__global__ void k_givens(double* __restrict__ st, int j, const double* __restrict__ raw,
+                         const double* __restrict__ nrm2, cudaGraphConditionalHandle next,
+                         int has_next) {
+  if (threadIdx.x != 0) return;
+  constexpr int R = GState::R;
+  double* H = st + GState::kH;
+  double* cs = st + GState::kCS;
+  double* sn = st + GState::kSN;
+  double* g = st + GState::kG;
+  double* rn = st + GState::kRN;
+  double* sc = st + GState::kSc;
+  auto Hm = [&](int i, int q) -> double& { return H[i * R + q]; };
+  for (int i = 0; i <= j; ++i) Hm(i, j) = raw[i] / rn[i];
+  const double hn = sqrt(nrm2[j + 1]);
+  bool stop = true;
+  if (!isfinite(hn)) {
+    sc[GState::sNan] = 1.0;
+  } else {
+    Hm(j + 1, j) = hn;
+    rn[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
+      Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
+      Hm(i, j) = t;
+    }
+    const double den = hypot(Hm(j, j), Hm(j + 1, j));
+    if (den == 0.0) {
+      sc[GState::sBreak] = 1.0;
+    } else {
+      cs[j] = Hm(j, j) / den;
+      sn[j] = Hm(j + 1, j) / den;
+      Hm(j, j) = den;
+      Hm(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      sc[GState::sJused] = (double)(j + 1);
+      const double res = fabs(g[j + 1]);
+      const double bnorm = sc[GState::sBnorm];
+      st[GState::kHist + j] = res / bnorm;
+      stop = res / bnorm <= sc[GState::sRtol] || hn == 0.0 || res <= sc[GState::sStop] ||
+             (double)(j + 1) >= sc[GState::sRmax];
+    }
+  }
+  if (has_next) cudaGraphSetConditional(next, stop ? 0u : 1u);
+}
+
+// The part of the state the host reads after a cycle, copied to the mapped
+// host copy at the same offsets: the scalars, g, the residual history and
+// the upper triangle of the first jused columns of H.
+__global__ void k_cycle_out(const double* __restrict__ st, double* __restrict__ hst) {
+  constexpr int R = GState::R;
+  const int ju = (int)st[GState::kSc + GState::sJused];
+  for (int i = threadIdx.x; i < 16; i += blockDim.x) hst[GState::kSc + i] = st[GState::kSc + i];
+  for (int i = threadIdx.x; i <= R; i += blockDim.x) hst[GState::kG + i] = st[GState::kG + i];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) hst[GState::kHist + i] = st[GState::kHist + i];
+  for (int e = threadIdx.x; e < ju * ju; e += blockDim.x) {
+    const int i = e / ju, q = e - i * ju;
+    if (i <= q) hst[GState::kH + i * R + q] = st[GState::kH + i * R + q];
+  }
+}
+
+// What a cycle graph depends on besides the context's fixed buffers.
+void cycle_key(const ibm_ctx* c, const ibm_solve_opts* o, int restart,
+               unsigned long long (&k)[16]) {
+  const MarkerData& m = c->mk;
+  const unsigned long long v[16] = {
+      (unsigned long long)restart, (unsigned long long)o->mg_pre, (unsigned long long)o->mg_post,
+      (unsigned long long)o->arnoldi, (unsigned long long)c->cmode, (unsigned long long)m.n,
+      (unsigned long long)m.n_shell, (unsigned long long)m.n_ell,
+      (unsigned long long)(uintptr_t)m.bf, (unsigned long long)(uintptr_t)m.ell_key,
+      (unsigned long long)(uintptr_t)m.ell_base, (unsigned long long)c->m, 1ull, 0ull, 0ull, 0ull};
+  for (int i = 0; i < 16; ++i) k[i] = v[i];
+}
+
+void drop_cycle_graph(ibm_ctx* c) {
+  if (c->cyc_exec) cudaGraphExecDestroy(c->cyc_exec);
+  if (c->cyc_graph) cudaGraphDestroy(c->cyc_graph);
+  c->cyc_exec = nullptr;
+  c->cyc_graph = nullptr;
+  for (auto& v : c->cyc_key) v = 0;
+}
+
+// Captures iterations 0..restart-1 (launch_iter(j, true) on the capture
+// stream) with their k_givens and the nested IF nodes; false (and the
+// host-driven loop) if any step fails.  Kernels captured are not counted
+// as launched; cyc_launches[j] holds iteration j's count for the replays.
+template <typename F>
+bool build_cycle_graph(ibm_ctx* c, int restart, F& launch_iter) {
+  drop_cycle_graph(c);
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaStream_t saved = c->stream;
+  c->stream = c->cap;
+  const double* raw = c->red_out;
+  const double* nrm2 = c->red_out + 4 * kOutStride;
+  cudaGraph_t cur = G;
+  bool ok = true;
+  for (int j = 0; j < restart && ok; ++j) {
+    if (cudaStreamBeginCaptureToGraph(c->cap, cur, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    const long long l0 = ibm_kernel_launches();
+    ok = launch_iter(j, true) == IBM_OK;
+    const bool has_next = j + 1 < restart;
+    cudaGraphConditionalHandle h = 0;
+    if (ok && has_next)
+      ok = cudaGraphConditionalHandleCreate(&h, cur, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+      k_givens<<<1, 32, 0, c->cap>>>(c->gstate, j, raw, nrm2, h, has_next ? 1 : 0);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    cudaGraph_t next = nullptr;
+    if (ok && has_next) {
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t capg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      ok = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &capg, &deps, nullptr, &nd) ==
+               cudaSuccess &&
+           cst == cudaStreamCaptureStatusActive;
+      cudaGraphNodeParams p = {};
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = h;
+      p.conditional.type = cudaGraphCondTypeIf;
+      p.conditional.size = 1;
+      cudaGraphNode_t node = nullptr;
+      if (ok) ok = cudaGraphAddNode(&node, capg, deps, nullptr, nd, &p) == cudaSuccess;
+      if (ok)
+        ok = cudaStreamUpdateCaptureDependencies(c->cap, &node, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies) == cudaSuccess;
+      if (ok) next = p.conditional.phGraph_out[0];
+    }
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(c->cap, &out) != cudaSuccess) ok = false;
+    const long long dl = ibm_kernel_launches() - l0;
+    add_launches(-dl);
+    c->cyc_launches[j] = (int)dl + 1;   // and k_givens
+    cur = next;
+  }
+  c->stream = saved;
+  cudaGraphExec_t exec = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&exec, G, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(G);
+    return false;
+  }
+  c->cyc_graph = G;
+  c->cyc_exec = exec;
+  return true;
+}
+
 ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
                            ibm_solve_stats* st, bool x_is_zero) {
   // Same flexible GMRES as fgmres_solve (unnormalised Arnoldi vectors with
@@ -695,11 +893,11 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
   if ((stt = fetch(c, sdev, 1)) != IBM_OK) return stt;
   const double bnorm = std::sqrt(hr[0]);
   if (!std::isfinite(bnorm)) return set_err(c, IBM_ERR_NAN, "non-finite right-hand side");
-  int total = 0, cycles = 0;
+  int total = 0, cycles = 0, graph_cycles = 0;
   double relres = 0.0;
   if (bnorm == 0.0) {
     launch_zero(x, sizeof(double) * m, s);
-    if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; }
+    if (st) { st->iters = 0; st->restarts = 0; st->relres_true = 0.0; st->graph_cycles = 0; }
     return IBM_OK;
   }
   std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart),
@@ -748,7 +946,10 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     // Hessenberg column goes to the host mirror (raw part in one of two
     // buffers by the parity of j, apart from the scalar slot at the mirror's
     // start that other reads use) and an event marks the iteration's end.
-    auto launch_iter = [&](int jj) -> ibm_status {
+    auto launch_iter = [&](int jj, bool graph) -> ibm_status {
+      // graph: captured into a cycle graph (on the capture stream, which
+      // c->stream names meanwhile; no host mirror, no end event)
+      cudaStream_t s = c->stream;
       float* zj = Zf + (int64_t)jj * m;
       float2* w = V2 + (int64_t)(jj + 1) * m;
       float* w1 = V1 + (int64_t)(jj + 1) * m;
@@ -774,7 +975,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       count_launch();
       launch_pdl(k_final_reduce_ds, dim3(nq), dim3(RT), 0, s, (const double*)part, kRedBlocks,
                  raw, (const double*)nrm2, coef, coef_ds,
-                 hmirror(c, hr + (2 + (jj & 1)) * kOutStride));
+                 graph ? nullptr : hmirror(c, hr + (2 + (jj & 1)) * kOutStride));
       prof_end(c, ph, (single ? 4.0 : 8.0) * (nq + 1) * (double)m);
       ph = prof_begin(c, IBM_PROF_AXPY_NORM);
       if (vec4 && nq <= 16)
@@ -787,11 +988,11 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       count_launch();
       launch_pdl(k_final_reduce_ds, dim3(1), dim3(RT), 0, s, (const double*)part, kRedBlocks,
                  nrm2 + jj + 1, (const double*)nullptr, (double*)nullptr, (float2*)nullptr,
-                 hmirror(c, hr + 4 * kOutStride + jj + 1));
+                 graph ? nullptr : hmirror(c, hr + 4 * kOutStride + jj + 1));
       // V_0..V_j and w read, w written (and its leading parts for the pair form)
       prof_end(c, ph, single ? 4.0 * (nq + 2) * (double)m : (8.0 * (nq + 2) + 4.0) * (double)m);
       IBM_LAUNCH_CHECK(c);
-      IBM_CUDA(c, cudaEventRecord(c->ev_iter[jj & 1], s));
+      if (!graph) IBM_CUDA(c, cudaEventRecord(c->ev_iter[jj & 1], s));
       return IBM_OK;
     };
     // The host stays one iteration behind the device where that is safe:
@@ -803,56 +1004,99 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     // iterates and the iteration count do not depend on the guesses.  The
     // exact and sign-consistent forms, whose Schur product waits on the host
     // (inner conjugate gradients), run one iteration at a time.
-    const double thresh = std::max(o->rtol * bnorm, cycle_stop);
-    const bool ahead = c->cmode == IBM_CMODE_SCALAR;
-    double prev = beta, rate = 0.05;   // assumed until a ratio has been seen
-    bool have_rate = false;
-    bool next_launched = false;
-    if (restart > 0 && total < o->maxit) {
-      if ((stt = launch_iter(0)) != IBM_OK) return stt;
-      next_launched = true;
+    // the cycle as one graph replay where it applies
+    const bool graph_form = o->cycle_graphs == 1 && !c->prof_on && c->cmode == IBM_CMODE_SCALAR &&
+                            c->cap != nullptr && restart > 0 && restart <= kMaxRestart &&
+                            total < o->maxit;
+    if (graph_form) {
+      unsigned long long key[16];
+      cycle_key(c, o, restart, key);
+      if (!std::equal(key, key + 16, c->cyc_key)) {
+        // also kept when the build fails: the host-driven loop runs, and the
+        // capture is not tried again for the same key
+        build_cycle_graph(c, restart, launch_iter);
+        std::copy(key, key + 16, c->cyc_key);
+      }
     }
-    for (int j = 0; next_launched; ++j) {
-      const bool can_next = j + 1 < restart && total + 1 < o->maxit;
-      next_launched = false;
-      if (ahead && can_next && prev * rate > 4.0 * thresh) {
-        if ((stt = launch_iter(j + 1)) != IBM_OK) return stt;
+    if (graph_form && c->cyc_exec) {
+      const int rmax = std::min(restart, o->maxit - total);
+      count_launch();
+      k_cycle_init<<<1, RT, 0, s>>>(c->gstate, beta, bnorm, o->rtol, cycle_stop, rmax);
+      IBM_CUDA(c, cudaGraphLaunch(c->cyc_exec, s));
+      count_launch();
+      k_cycle_out<<<1, 256, 0, s>>>(c->gstate, c->host_gstate_dev);
+      IBM_LAUNCH_CHECK(c);
+      IBM_CUDA(c, cudaStreamSynchronize(s));
+      const double* hs = c->host_gstate;
+      const double* sc = hs + GState::kSc;
+      const int ju = (int)sc[GState::sJused];
+      const bool nan_col = sc[GState::sNan] != 0.0;
+      breakdown = sc[GState::sBreak] != 0.0;
+      const int ran = std::min(restart, (nan_col || breakdown) ? ju + 1 : ju);
+      int64_t lsum = 0;
+      for (int q = 0; q < ran; ++q) lsum += c->cyc_launches[q];
+      add_launches(lsum);
+      if (nan_col) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
+      for (int q = 0; q < ju; ++q)
+        for (int i = 0; i <= q; ++i) Hm(i, q) = hs[GState::kH + i * GState::R + q];
+      for (int i = 0; i <= ju; ++i) g[i] = hs[GState::kG + i];
+      for (int q = 0; q < ju; ++q)
+        if (st && total + q < IBM_HIST_MAX) st->relres_hist[total + q] = hs[GState::kHist + q];
+      total += ju;
+      jused = ju;
+      ++graph_cycles;
+    } else {
+      const double thresh = std::max(o->rtol * bnorm, cycle_stop);
+      const bool ahead = c->cmode == IBM_CMODE_SCALAR;
+      double prev = beta, rate = 0.05;   // assumed until a ratio has been seen
+      bool have_rate = false;
+      bool next_launched = false;
+      if (restart > 0 && total < o->maxit) {
+        if ((stt = launch_iter(0, false)) != IBM_OK) return stt;
         next_launched = true;
       }
-      IBM_CUDA(c, cudaEventSynchronize(c->ev_iter[j & 1]));
-      const double* hraw = hr + (2 + (j & 1)) * kOutStride;
-      for (int i = 0; i <= j; ++i) Hm(i, j) = hraw[i] / rn[i];
-      const double hn = std::sqrt(hr[4 * kOutStride + j + 1]);
-      if (!std::isfinite(hn)) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
-      Hm(j + 1, j) = hn;
-      rn[j + 1] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
-        Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
-        Hm(i, j) = t;
-      }
-      const double den = std::hypot(Hm(j, j), Hm(j + 1, j));
-      if (den == 0.0) { breakdown = true; break; }
-      cs[j] = Hm(j, j) / den;
-      sn[j] = Hm(j + 1, j) / den;
-      Hm(j, j) = den;
-      Hm(j + 1, j) = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++total;
-      jused = j + 1;
-      const double res = std::fabs(g[j + 1]);
-      if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = res / bnorm;
-      if (res / bnorm <= o->rtol || hn == 0.0) break;
-      if (res <= cycle_stop) break;   // FP32 basis exhausted
-      if (prev > 0.0) {
-        rate = have_rate ? std::min(rate, res / prev) : res / prev;
-        have_rate = true;
-      }
-      prev = res;
-      if (!next_launched && can_next) {
-        if ((stt = launch_iter(j + 1)) != IBM_OK) return stt;
-        next_launched = true;
+      for (int j = 0; next_launched; ++j) {
+        const bool can_next = j + 1 < restart && total + 1 < o->maxit;
+        next_launched = false;
+        if (ahead && can_next && prev * rate > 4.0 * thresh) {
+          if ((stt = launch_iter(j + 1, false)) != IBM_OK) return stt;
+          next_launched = true;
+        }
+        IBM_CUDA(c, cudaEventSynchronize(c->ev_iter[j & 1]));
+        const double* hraw = hr + (2 + (j & 1)) * kOutStride;
+        for (int i = 0; i <= j; ++i) Hm(i, j) = hraw[i] / rn[i];
+        const double hn = std::sqrt(hr[4 * kOutStride + j + 1]);
+        if (!std::isfinite(hn)) return set_err(c, IBM_ERR_NAN, "non-finite Arnoldi vector");
+        Hm(j + 1, j) = hn;
+        rn[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
+          Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
+          Hm(i, j) = t;
+        }
+        const double den = std::hypot(Hm(j, j), Hm(j + 1, j));
+        if (den == 0.0) { breakdown = true; break; }
+        cs[j] = Hm(j, j) / den;
+        sn[j] = Hm(j + 1, j) / den;
+        Hm(j, j) = den;
+        Hm(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++total;
+        jused = j + 1;
+        const double res = std::fabs(g[j + 1]);
+        if (st && total - 1 < IBM_HIST_MAX) st->relres_hist[total - 1] = res / bnorm;
+        if (res / bnorm <= o->rtol || hn == 0.0) break;
+        if (res <= cycle_stop) break;   // FP32 basis exhausted
+        if (prev > 0.0) {
+          rate = have_rate ? std::min(rate, res / prev) : res / prev;
+          have_rate = true;
+        }
+        prev = res;
+        if (!next_launched && can_next) {
+          if ((stt = launch_iter(j + 1, false)) != IBM_OK) return stt;
+          next_launched = true;
+        }
       }
     }
     if (jused > 0) {
@@ -886,6 +1130,7 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     st->iters = total;
     st->restarts = cycles;
     st->relres_true = relres;
+    st->graph_cycles = graph_cycles;
   }
   if (final_status != IBM_OK) return set_err(c, final_status, "FGMRES breakdown");
   if (!converged) {

@@ -50,6 +50,40 @@ def test_solve_parity(setup, prec, arnoldi):
     assert rel(sysm.apply_S_tilde(ph), b) < 2e-13
 
 
+@pytest.mark.parametrize("arnoldi", [1, 2], ids=["ds_arnoldi", "fp32_arnoldi"])
+def test_cycle_graphs_match_the_host_driven_loop(setup, arnoldi):
+    """With cycle_graphs = 1 the FP32 and double-single Arnoldi cycles run as
+    CUDA graph replays (Givens rotations and the stopping test on the device,
+    the next iteration in a conditional node); by default, and while
+    profiling, the host-driven loop runs.  Both take the same iterations to
+    the same solution, also with a short restart (several cycles) and with a
+    maxit that ends a cycle early."""
+    case, g, s, sysm, b, ref = setup
+    for kw in (dict(rtol=1e-13, maxit=300), dict(rtol=1e-13, restart=5, maxit=300),
+               dict(rtol=1e-10, restart=7, maxit=9)):
+        p_g, st_g = s.solve_schur(dev(b), precond_prec=1, arnoldi=arnoldi, cycle_graphs=1,
+                                  raise_on_error=False, **kw)
+        p_h, st_h = s.solve_schur(dev(b), precond_prec=1, arnoldi=arnoldi,
+                                  raise_on_error=False, **kw)
+        s.profile_enable(True)
+        try:
+            _, st_p = s.solve_schur(dev(b), precond_prec=1, arnoldi=arnoldi, cycle_graphs=1,
+                                    raise_on_error=False, **kw)
+        finally:
+            s.profile_enable(False)
+        assert st_g["graph_cycles"] >= 1 and st_g["graph_cycles"] == st_g["restarts"], st_g
+        assert st_h["graph_cycles"] == 0 and st_p["graph_cycles"] == 0
+        assert st_g["iters"] == st_h["iters"] and st_g["restarts"] == st_h["restarts"], (st_g, st_h)
+        assert rel(host(p_g), host(p_h)) < 1e-12, kw
+        n = min(st_g["iters"], len(st_g["relres_hist"]))
+        # the estimates agree to the rounding of the rotations (the device's
+        # hypot against the host's), far inside the stopping tests
+        np.testing.assert_allclose(st_g["relres_hist"][:n], st_h["relres_hist"][:n], rtol=1e-6,
+                                   atol=1e-13)
+        if kw.get("maxit") == 9:
+            assert st_g["iters"] <= 9
+
+
 @pytest.mark.parametrize("prec,arnoldi", MODES, ids=MODE_IDS)
 def test_solve_throughput_setting(setup, prec, arnoldi):
     case, g, s, sysm, b, ref = setup
