@@ -210,6 +210,7 @@ static void free_all(ibm_ctx* c) {
   MarkerData& m = c->mk;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc); cudaFree(m.cw);
   cudaFree(m.t); cudaFree(m.t2); cudaFree(m.t32); cudaFree(m.dwf); cudaFree(m.dwc);
+  cudaFree(m.wc32); cudaFree(m.cw32);
   cudaFree(m.cg);
   cudaFree(m.t3); cudaFree(c->cg_scal);
   cudaFree(m.entry_key); cudaFree(m.shell_cell); cudaFree(m.shell_off); cudaFree(m.ell_cell);

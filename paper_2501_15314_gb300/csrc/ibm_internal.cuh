@@ -67,6 +67,8 @@ struct MarkerData {
                             // the component's own axis: (w_{a-1} - w_a) / h
   double* dwf = nullptr;    // [3 axes][3 taps][n] phi' at the face taps
   double* dwc = nullptr;    // [3 axes][3 taps][n] phi' at the centre taps
+  float* wc32 = nullptr;    // wc rounded to FP32 (the FP32 Arnoldi cycles' t = 2 B z)
+  float* cw32 = nullptr;    // cw rounded to FP32
   double* cg = nullptr;     // [3][3n] conjugate-gradient work vectors for C^{-1}
   double* t3 = nullptr;     // [3][n] per-marker scratch (RHS_F in the C modes)
   // cell-sorted (marker, slot) list for the atomic-free gathers
@@ -266,7 +268,11 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X);
 // (on stream st when given, else the context's stream)
 void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double* t,
                                cudaStream_t st = nullptr);
-void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t, float* t32,
+void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t,
+                                   cudaStream_t st = nullptr);
+// t32[d][k] = scale * (B v)_{k,d} for FP32 v in FP32 arithmetic (FP32 copies of
+// the weights): the FP32 Arnoldi cycles, whose Schur product is rounded to FP32
+void launch_marker_grad_interp_t32(ibm_ctx* c, const float* v, float scale, float* t32,
                                    cudaStream_t st = nullptr);
 // out[cell] += scale * (G^T R t)[cell] on the shell cells
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out);

@@ -611,8 +611,10 @@ ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
   if (fork) {
     IBM_CUDA(c, cudaEventRecord(c->ev_fork, s));
     IBM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    launch_marker_grad_interp_f32(c, z, 2.0, m.t,
-                                  std::is_same<TW, float>::value ? m.t32 : nullptr, c->side);
+    if constexpr (std::is_same<TW, float>::value)
+      launch_marker_grad_interp_t32(c, z, 2.f, m.t32, c->side);
+    else
+      launch_marker_grad_interp_f32(c, z, 2.0, m.t, c->side);
     IBM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
   }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
@@ -628,7 +630,7 @@ ibm_status schur_apply_ds_t(ibm_ctx* c, const float* z, TW* w) {
       IBM_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     } else {
       // +- B^T C^{-1} B z (exact / sign-consistent forms), C^{-1} in FP64
-      launch_marker_grad_interp_f32(c, z, 1.0, m.t, nullptr);
+      launch_marker_grad_interp_f32(c, z, 1.0, m.t);
       const ibm_status st = c_solve(c, m.t, m.t2, c->c_rtol, c->c_maxit, nullptr);
       if (st != IBM_OK) { prof_end(c, ph); return st; }
       t = m.t2;

@@ -60,7 +60,8 @@ MkView view(const MarkerData& m) { return MkView{m.n, m.bf, m.bc, m.org, m.wf, m
 
 __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __restrict__ X,
                                int32_t* bf, int32_t* bc, int32_t* org, double* wf, double* wc,
-                               double* cw, double* dwf, double* dwc, int32_t* err) {
+                               double* cw, double* dwf, double* dwc, float* wc32, float* cw32,
+                               int32_t* err) {
   // one thread per (axis, marker): the three axes' Roma weights are
   // independent, and three times the threads hide the FP64 latency better
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -82,6 +83,8 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
         dwf[(e * 3 + q) * n + k] = 0.0; dwc[(e * 3 + q) * n + k] = 0.0;
       }
       for (int q = 0; q < 4; ++q) cw[(e * 4 + q) * n + k] = 0.0;
+      for (int q = 0; q < 3; ++q) wc32[(e * 3 + q) * n + k] = 0.f;
+      for (int q = 0; q < 4; ++q) cw32[(e * 4 + q) * n + k] = 0.f;
       atomicOr(err, 1);
       return;
     }
@@ -106,6 +109,10 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
     cw[(e * 4 + 1) * n + k] = (W[0] - W[1]) * inv_h;
     cw[(e * 4 + 2) * n + k] = (W[1] - W[2]) * inv_h;
     cw[(e * 4 + 3) * n + k] = (W[2] - 0.0) * inv_h;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) wc32[(e * 3 + q) * n + k] = (float)wc[(e * 3 + q) * n + k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cw32[(e * 4 + q) * n + k] = (float)cw[(e * 4 + q) * n + k];
   }
   if (bad) atomicOr(err, 1);
 }
@@ -223,8 +230,7 @@ __device__ __forceinline__ double widen(double x) { return x; }
 // order with warp shuffles.
 template <typename TV>
 __global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v,
-                                     double scale, double* __restrict__ t,
-                                     float* __restrict__ t32) {
+                                     double scale, double* __restrict__ t) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = 12 * mk.n;
   double part = 0.0;
@@ -262,11 +268,52 @@ __global__ void k_marker_grad_interp(Dims d, MkView mk, const TV* __restrict__ v
   const double p1 = __shfl_sync(0xffffffffu, part, base + 1);
   const double p2 = __shfl_sync(0xffffffffu, part, base + 2);
   const double p3 = __shfl_sync(0xffffffffu, part, base + 3);
-  if (tid < nt && (lane & 3) == 0) {
-    const double r = scale * ((p0 + p1) + (p2 + p3));
-    t[dc * mk.n + k] = r;
-    if (t32) t32[dc * mk.n + k] = (float)r;
+  if (tid < nt && (lane & 3) == 0) t[dc * mk.n + k] = scale * ((p0 + p1) + (p2 + p3));
+}
+
+// The same for FP32 v with FP32 weights and FP32 FMAs (t32 only).
+__global__ void k_marker_grad_interp_f32(Dims d, MkView mk, const float* __restrict__ wc32,
+                                         const float* __restrict__ cw32,
+                                         const float* __restrict__ v, float scale,
+                                         float* __restrict__ t32) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = 12 * mk.n;
+  float part = 0.f;
+  int dc = 0;
+  int64_t k = 0;
+  if (tid < nt) {
+    const int64_t pk = tid >> 2;
+    const int a = (int)(tid & 3);
+    dc = (int)(pk / mk.n);
+    k = pk - dc * mk.n;
+    const int e1 = dc == 0 ? 1 : 0;
+    const int e2 = dc == 2 ? 1 : 2;
+    int g[3];
+    g[dc] = mk.bf[dc * mk.n + k] - 1 + a;
+    const int b1 = mk.bc[e1 * mk.n + k], b2 = mk.bc[e2 * mk.n + k];
+    const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
+    float acc1 = 0.f;
+#pragma unroll
+    for (int q1 = 0; q1 < 3; ++q1) {
+      g[e1] = b1 + q1;
+      float acc2 = 0.f;
+#pragma unroll
+      for (int q2 = 0; q2 < 3; ++q2) {
+        g[e2] = b2 + q2;
+        const int64_t cell = g[0] + g[1] * sy + (int64_t)g[2] * sz;
+        acc2 = fmaf(wc32[(e2 * 3 + q2) * mk.n + k], __ldg(v + cell), acc2);
+      }
+      acc1 = fmaf(wc32[(e1 * 3 + q1) * mk.n + k], acc2, acc1);
+    }
+    part = cw32[(dc * 4 + a) * mk.n + k] * acc1;
   }
+  const int lane = threadIdx.x & 31;
+  const int base = lane & ~3;
+  const float p0 = __shfl_sync(0xffffffffu, part, base);
+  const float p1 = __shfl_sync(0xffffffffu, part, base + 1);
+  const float p2 = __shfl_sync(0xffffffffu, part, base + 2);
+  const float p3 = __shfl_sync(0xffffffffu, part, base + 3);
+  if (tid < nt && (lane & 3) == 0) t32[dc * mk.n + k] = scale * ((p0 + p1) + (p2 + p3));
 }
 
 // Order of the shell cells in the interleaved layout: each block sorts one
@@ -807,11 +854,12 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
   if (n <= m.cap) return IBM_OK;
   cudaFree(m.bf); cudaFree(m.bc); cudaFree(m.org); cudaFree(m.wf); cudaFree(m.wc);
   cudaFree(m.cw); cudaFree(m.t); cudaFree(m.t2); cudaFree(m.t32); cudaFree(m.dwf);
-  cudaFree(m.dwc);
+  cudaFree(m.dwc); cudaFree(m.wc32); cudaFree(m.cw32);
   cudaFree(m.cg); cudaFree(m.t3);
   m.bf = m.bc = m.org = nullptr;
   m.wf = m.wc = m.cw = m.t = m.t2 = m.dwf = m.dwc = m.cg = m.t3 = nullptr;
   m.t32 = nullptr;
+  m.wc32 = m.cw32 = nullptr;
   m.cap = 0;
   const size_t ni = sizeof(int32_t) * 3 * n, nd = sizeof(double) * 9 * n;
   if (cudaMalloc(&m.bf, ni) != cudaSuccess || cudaMalloc(&m.bc, ni) != cudaSuccess ||
@@ -821,6 +869,8 @@ static ibm_status grow_markers(ibm_ctx* c, int64_t n) {
       cudaMalloc(&m.cw, sizeof(double) * 12 * n) != cudaSuccess ||
       cudaMalloc(&m.t, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.t32, sizeof(float) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&m.wc32, sizeof(float) * 9 * n) != cudaSuccess ||
+      cudaMalloc(&m.cw32, sizeof(float) * 12 * n) != cudaSuccess ||
       cudaMalloc(&m.t2, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.t3, sizeof(double) * 3 * n) != cudaSuccess ||
       cudaMalloc(&m.cg, sizeof(double) * 9 * n) != cudaSuccess) {
@@ -895,7 +945,8 @@ ibm_status markers_build(ibm_ctx* c, int64_t n, const double* X) {
   launch_zero(c->dev_flag, sizeof(int32_t), s);
   count_launch();
   k_marker_setup<<<div_up(3 * n, TPB), TPB, 0, s>>>(c->d, 1.0 / c->h, n, X, m.bf, m.bc, m.org,
-                                                     m.wf, m.wc, m.cw, m.dwf, m.dwc, c->dev_flag);
+                                                     m.wf, m.wc, m.cw, m.dwf, m.dwc, m.wc32,
+                                                     m.cw32, c->dev_flag);
   IBM_LAUNCH_CHECK(c);
   launch_to_host(c->dev_flag, c->host_flag_dev, sizeof(int32_t), s);
   IBM_LAUNCH_CHECK(c);
@@ -967,16 +1018,25 @@ void launch_marker_grad_interp(ibm_ctx* c, const double* v, double scale, double
   if (m.n == 0) return;
   count_launch();
   k_marker_grad_interp<double><<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
-      c->d, view(m), v, scale, t, nullptr);
+      c->d, view(m), v, scale, t);
 }
 
 void launch_marker_grad_interp_f32(ibm_ctx* c, const float* v, double scale, double* t,
-                                   float* t32, cudaStream_t st) {
+                                   cudaStream_t st) {
   const MarkerData& m = c->mk;
   if (m.n == 0) return;
   count_launch();
   k_marker_grad_interp<float><<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
-      c->d, view(m), v, scale, t, t32);
+      c->d, view(m), v, scale, t);
+}
+
+void launch_marker_grad_interp_t32(ibm_ctx* c, const float* v, float scale, float* t32,
+                                   cudaStream_t st) {
+  const MarkerData& m = c->mk;
+  if (m.n == 0) return;
+  count_launch();
+  k_marker_grad_interp_f32<<<div_up(12 * m.n, TPB), TPB, 0, st ? st : c->stream>>>(
+      c->d, view(m), m.wc32, m.cw32, v, scale, t32);
 }
 
 void launch_shell_gradt_spread(ibm_ctx* c, const double* t, double scale, double* out) {
