@@ -237,6 +237,9 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
 // out = scale * L v  (Neumann 7-point, L = G^T G with h folded into scale)
 template <typename T>
 void launch_laplacian(Dims d, const T* v, T* out, double inv_h2, cudaStream_t s);
+// out = b - L v in FP64 (b null: out = L v)
+void launch_laplacian_sub(Dims d, const double* v, const double* b, double* out, double inv_h2,
+                          cudaStream_t s);
 void launch_gradient(Dims d, const double* p, double* u, double inv_h, cudaStream_t s);
 void launch_gradient_t(Dims d, const double* u, double* out, double inv_h, cudaStream_t s);
 // u_out = u_in + alpha * G p   (interior faces; wall faces 0)
@@ -346,6 +349,8 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
 
 // ---- solver (krylov.cu) ----
 ibm_status schur_apply(ibm_ctx* c, const double* v, double* out);
+// out = b - S~ v (the FP64 true residual), in the passes of schur_apply
+ibm_status schur_residual(ibm_ctx* c, const double* b, const double* v, double* out);
 // x_is_zero: the initial guess in x is known to be 0 (skips one S~ product)
 ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_opts* o,
                         ibm_solve_stats* st, bool x_is_zero = false);

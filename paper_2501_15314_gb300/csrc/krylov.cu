@@ -278,8 +278,15 @@ void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale
 
 // ---------------------------------------------------------------------------
 ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
+  return schur_residual(c, nullptr, v, out);
+}
+
+ibm_status schur_residual(ibm_ctx* c, const double* b, const double* v, double* out) {
   // out = L v + 2 B^T (B v): t = 2 R^T G v per marker (on the side stream,
-  // concurrently with out = L v), then the shell cells gather G^T R t.
+  // concurrently with out = L v), then the shell cells gather G^T R t.  With
+  // b: out = b - S~ v, the Laplacian kernel writing b - L v and the gather
+  // subtracting the marker term (no separate pass over the three vectors).
+  const double sgn = b ? -1.0 : 1.0;
   const bool fork = c->cmode == IBM_CMODE_SCALAR && c->mk.n > 0;
   if (fork) {
     IBM_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
@@ -288,18 +295,19 @@ ibm_status schur_apply(ibm_ctx* c, const double* v, double* out) {
     IBM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
   }
   int ph = prof_begin(c, IBM_PROF_LAPLACIAN_F64);
-  launch_laplacian<double>(c->d, v, out, 1.0 / (c->h * c->h), c->stream);
-  prof_end(c, ph, 16.0 * (double)c->m);
+  launch_laplacian_sub(c->d, v, b, out, 1.0 / (c->h * c->h), c->stream);
+  prof_end(c, ph, (b ? 24.0 : 16.0) * (double)c->m);
   ph = prof_begin(c, IBM_PROF_SCHUR_MARKERS);
   if (fork) {
     IBM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-    launch_shell_gradt_spread(c, c->mk.t, 1.0, out);
+    launch_shell_gradt_spread(c, c->mk.t, sgn, out);
   } else if (c->mk.n > 0) {
     // out +- B^T C^{-1} B v (exact / sign-consistent forms)
     launch_marker_grad_interp(c, v, 1.0, c->mk.t);
     const ibm_status s = c_solve(c, c->mk.t, c->mk.t2, c->c_rtol, c->c_maxit, nullptr);
     if (s != IBM_OK) { prof_end(c, ph); return s; }
-    launch_shell_gradt_spread(c, c->mk.t2, c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0, out);
+    launch_shell_gradt_spread(c, c->mk.t2,
+                              sgn * (c->cmode == IBM_CMODE_CONSISTENT ? -1.0 : 1.0), out);
   }
   prof_end(c, ph, c->mk.n > 0 ? marker_term_bytes(c, 8, 8) : 0.0);
   IBM_LAUNCH_CHECK(c);
@@ -372,10 +380,9 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
       prof_note(c, 16.0 * m);
       beta = bnorm;
     } else {
-      if ((stt = schur_apply(c, x, V)) != IBM_OK) return stt;
-      launch_axpby(b, 1.0, V, -1.0, V, m, s);
+      if ((stt = schur_residual(c, b, x, V)) != IBM_OK) return stt;
       launch_dot(V, V, m, part, nrm2, s);
-      prof_note(c, 32.0 * m);
+      prof_note(c, 8.0 * m);
       IBM_LAUNCH_CHECK(c);
       if ((stt = fetch(c, nrm2, 1)) != IBM_OK) return stt;
       beta = std::sqrt(hr[0]);

@@ -915,10 +915,9 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
       launch_copy(nrm2, sdev, sizeof(double), s);
       beta = bnorm;
     } else {
-      if ((stt = schur_apply(c, x, r64)) != IBM_OK) return stt;
-      launch_axpby(b, 1.0, r64, -1.0, r64, m, s);
+      if ((stt = schur_residual(c, b, x, r64)) != IBM_OK) return stt;
       launch_dot(r64, r64, m, part, nrm2, s);
-      prof_note(c, 32.0 * m);
+      prof_note(c, 8.0 * m);
       IBM_LAUNCH_CHECK(c);
       if ((stt = fetch(c, nrm2, 1)) != IBM_OK) return stt;
       beta = std::sqrt(hr[0]);

@@ -136,6 +136,7 @@ __device__ __forceinline__ double lap_fx(double vc, double xm, double xp, double
 // by shuffles (loads at the warp edges), z-neighbours from the registers of
 // the march, y-neighbours through L1.
 __global__ void __launch_bounds__(BX * BY) k_laplacian_fx(Dims d, const double* __restrict__ v,
+                                                          const double* __restrict__ bsub,
                                                           double* __restrict__ out,
                                                           long long inv_h2_bits, int e_min,
                                                           int e_max, int zc) {
@@ -165,7 +166,10 @@ __global__ void __launch_bounds__(BX * BY) k_laplacian_fx(Dims d, const double* 
     if (!hxm) xm = 0.0;
     if (!hxp) xp = 0.0;
     const int nn = nxy + (z > 0) + (z < d.nz - 1);
-    if (act) out[c] = lap_fx(vc, xm, xp, ym, yp, vp, vn, nn, inv_h2_bits, e_min, e_max);
+    if (act) {
+      const double lv = lap_fx(vc, xm, xp, ym, yp, vp, vn, nn, inv_h2_bits, e_min, e_max);
+      out[c] = bsub ? __ldg(bsub + c) - lv : lv;   // b - L v for the true residual
+    }
     vp = vc;
     vc = vn;
   }
@@ -756,11 +760,20 @@ void launch_laplacian(Dims d, const T* v, T* out, double inv_h2, cudaStream_t s)
     const int zc = march_zc(d);
     const FxLimits L = fx_limits(inv_h2);
     k_laplacian_fx<<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0,
-                     s>>>(d, v, out, L.bits, L.e_min, L.e_max, zc);
+                     s>>>(d, v, nullptr, out, L.bits, L.e_min, L.e_max, zc);
   } else {
     k_laplacian<T><<<cell_grid(d), dim3(BX, BY), 0, s>>>(d, v, out, (T)inv_h2);
   }
 }
+void launch_laplacian_sub(Dims d, const double* v, const double* b, double* out, double inv_h2,
+                          cudaStream_t s) {
+  count_launch();
+  const int zc = march_zc(d);
+  const FxLimits L = fx_limits(inv_h2);
+  k_laplacian_fx<<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0,
+                   s>>>(d, v, b, out, L.bits, L.e_min, L.e_max, zc);
+}
+
 template void launch_laplacian<float>(Dims, const float*, float*, double, cudaStream_t);
 template void launch_laplacian<double>(Dims, const double*, double*, double, cudaStream_t);
 
