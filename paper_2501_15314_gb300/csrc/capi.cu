@@ -579,8 +579,7 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   if (s != IBM_OK) return s;
 
   // 2. RHS_p = a G^T u*, RHS_F = a (R^T u* - U), b = RHS_p + 2 B^T RHS_F
-  launch_gradt_axpby(c->d, u_star, a * inv_h, nullptr, 0.0, c->c1, str);
-  launch_copy(c->c2, c->c1, sizeof(double) * c->m, str);
+  launch_gradt_axpby(c->d, u_star, a * inv_h, nullptr, 0.0, c->c2, str);
   if (n > 0) {
     launch_interp(c, u_star, mk.t2);
     count_launch();
@@ -601,13 +600,18 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
   launch_zero(pc, sizeof(double) * c->m, str);
   const double mk0 = prof_mark(c);
   ph = prof_begin(c, IBM_PROF_SOLVE);
+  // p' keeps its constant: only p^{n+1} depends on it, and it is removed
+  // where p^{n+1} is formed (G p' and B p' are blind to it)
+  double* psum = c->red_out + 7 * (kMaxRestart + 2) + 4;
+  c->defer_mean = psum;
   s = fgmres_solve(c, c->c2, pc, o, st, true);
+  c->defer_mean = nullptr;
   prof_end_span(c, ph, mk0);
   if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
   const ibm_status solve_status = s;
 
   // 4.-5. F' = 2 (B p' - RHS_F); updates
-  launch_axpby(p_n, 1.0, pc, 1.0, p_np1, c->m, str);
+  launch_axpy_shift(p_n, pc, psum, -1.0 / (double)c->m, p_np1, c->m, str);
   launch_grad_axpy(c->d, u_star, pc, -(2.0 * c->dt / 3.0) * inv_h, u_np1, str);
   if (n > 0) {
     launch_marker_grad_interp(c, pc, 1.0, mk.t);

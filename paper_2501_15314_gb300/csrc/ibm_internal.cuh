@@ -151,6 +151,10 @@ struct ibm_ctx {
   float* g5 = nullptr;             // low parts of the predictor's residual
   double* red_part = nullptr;      // [kRedBlocks][kMaxRestart + 2] partials
   double* red_out = nullptr;       // [8][kMaxRestart + 2] reduced values
+  // set by the step around its solve: the solver leaves the constant of the
+  // solution in place and writes the sum of its values here (device), which
+  // the step subtracts where it forms p^{n+1} (G and B annihilate constants)
+  double* defer_mean = nullptr;
   double* host_red = nullptr;      // mapped pinned mirror of red_out (host address)
   double* host_red_dev = nullptr;  // its device address
   double* helm_part = nullptr;     // per-block partials of the predictor norm
@@ -328,6 +332,9 @@ void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const doubl
 void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s,
                          double* hout = nullptr);
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s);
+// out = x + (y + scale * (*val)), in the operations of k_add_scalar then k_axpby
+void launch_axpy_shift(const double* x, const double* y, const double* val, double scale,
+                       double* out, int64_t n, cudaStream_t s);
 void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
                            cudaStream_t s);
 

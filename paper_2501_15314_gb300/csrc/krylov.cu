@@ -164,6 +164,17 @@ __global__ void __launch_bounds__(RT) k_gemv_acc(double* __restrict__ x,
   }
 }
 
+__global__ void k_axpy_shift(const double* __restrict__ x, const double* __restrict__ y,
+                             const double* __restrict__ val, double scale,
+                             double* __restrict__ out, int64_t n) {
+  const double v = scale * (*val);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double yi = y[i] + v;
+    out[i] = fma(1.0, x[i], 1.0 * yi);
+  }
+}
+
 __global__ void k_add_scalar(double* __restrict__ x, int64_t n, const double* __restrict__ val,
                              double scale) {
   const double v = scale * (*val);
@@ -268,6 +279,12 @@ void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const doubl
   CoefF64 cy;
   for (int q = 0; q <= kMaxRestart; ++q) cy.v[q] = q < nq ? y[q] : 0.0;
   IBM_NQ_DISPATCH(nq, k_gemv_acc, x, Z, ld, nq, cy, n);
+}
+
+void launch_axpy_shift(const double* x, const double* y, const double* val, double scale,
+                       double* out, int64_t n, cudaStream_t s) {
+  count_launch();
+  k_axpy_shift<<<kRedBlocks, RT, 0, s>>>(x, y, val, scale, out, n);
 }
 
 void launch_add_scalar_dev(double* x, int64_t n, const double* val, double scale,
@@ -460,9 +477,14 @@ ibm_status fgmres_solve(ibm_ctx* c, const double* b, double* x, const ibm_solve_
     if (breakdown && jused == 0) { final_status = IBM_ERR_BREAKDOWN; break; }
   }
   // mean-zero projection (S~ annihilates constants)
-  launch_sum(x, m, part, sdev, s);
-  launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
-  prof_note(c, 24.0 * m);
+  if (c->defer_mean) {
+    launch_sum(x, m, part, c->defer_mean, s);   // the caller removes the mean
+    prof_note(c, 8.0 * m);
+  } else {
+    launch_sum(x, m, part, sdev, s);
+    launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
+    prof_note(c, 24.0 * m);
+  }
   IBM_LAUNCH_CHECK(c);
   if (st) {
     st->iters = total;

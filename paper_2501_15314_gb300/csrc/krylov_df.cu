@@ -1123,9 +1123,14 @@ ibm_status fgmres_solve_ds(ibm_ctx* c, const double* b, double* x, const ibm_sol
     ++cycles;
     if (breakdown && jused == 0) { final_status = IBM_ERR_BREAKDOWN; break; }
   }
-  launch_sum(x, m, part, sdev, s);
-  launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
-  prof_note(c, 24.0 * m);
+  if (c->defer_mean) {
+    launch_sum(x, m, part, c->defer_mean, s);   // the caller removes the mean
+    prof_note(c, 8.0 * m);
+  } else {
+    launch_sum(x, m, part, sdev, s);
+    launch_add_scalar_dev(x, m, sdev, -1.0 / (double)m, s);
+    prof_note(c, 24.0 * m);
+  }
   IBM_LAUNCH_CHECK(c);
   if (st) {
     st->iters = total;
