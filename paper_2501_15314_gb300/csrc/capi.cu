@@ -247,10 +247,12 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   ibm_status st = norm2_host(c, rhs, nf, &rnorm0);
   if (st != IBM_OK) return st;
   if (!std::isfinite(rnorm0)) return set_err(c, IBM_ERR_NAN, "non-finite predictor RHS");
-  launch_zero(u, sizeof(double) * nf, s);
   *iters = 0;
   *relres = 0.0;
-  if (rnorm0 == 0.0) return IBM_OK;
+  if (rnorm0 == 0.0) {
+    launch_zero(u, sizeof(double) * nf, s);
+    return IBM_OK;
+  }
   double* sdev = c->red_out + 7 * (kMaxRestart + 2) + 8;
   float* eK = nullptr;        // the last correction e (input of the next residual)
   double rn = rnorm0;         // ||r|| of the current residual
@@ -275,10 +277,12 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
     if (want < 1e-6) want = 1e-6;
     int K = (int)std::ceil(std::acosh(1.0 / want) / std::acosh(sigma));
     K = K < 2 ? 2 : (K > 60 ? 60 : K);
+    // e_old starts at zero (the first step after the normalisation takes it
+    // as zero without reading it), and the first correction writes u
+    // instead of adding to it
     float* eo = c->g2;
     float* e = c->g3;
     float* en = c->g4;
-    launch_zero(eo, sizeof(float) * helm_fp32_size(c->d), s);
     // r^ = r / ||r||: from the FP64 right-hand side first, then from the pair
     launch_helm_cheb(c->d, nullptr, nullptr, c->g1, c->g5, it == 0 ? rhs : nullptr, 1.0 / qn,
                      (float)a, (float)nu_h2, (float)(1.0 / theta), 0.f, e, nullptr, 0.0, 0, s);
@@ -287,10 +291,12 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
       const int last = q == K - 1;
       const int ph = last ? -1 : prof_begin(c, IBM_PROF_HELM_SWEEP);
+      const int flags = (q == 1 ? 1 : 0) | (last && it == 0 ? 2 : 0);
       launch_helm_cheb(c->d, e, eo, c->g1, nullptr, nullptr, 0.0, (float)a, (float)nu_h2,
                        (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn,
-                       last ? 2 : 1, s);
-      prof_end(c, ph, 16.0 * (double)c->nf);   // e, e_old, r read; e_new written
+                       last ? 2 : 1, s, flags);
+      // e, e_old (not on the first step), r read; e_new written
+      prof_end(c, ph, (q == 1 ? 12.0 : 16.0) * (double)c->nf);
       rho_prev = rho;
       float* t = eo; eo = e; e = en; en = t;
     }

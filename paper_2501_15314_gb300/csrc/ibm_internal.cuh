@@ -262,7 +262,8 @@ int64_t helm_fp32_size(Dims d);
 // one FP32 Chebyshev step of the predictor (see k_helm_cheb_v4)
 void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
                       const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
-                      float* en, double* u, double us, int mode, cudaStream_t s);
+                      float* en, double* u, double us, int mode, cudaStream_t s,
+                      int flags = 0);   // 1: e_old is zero; 2: u is zero (mode 2 writes it)
 // predictor RHS with the convective term of u_n fused in (with_adv != 0),
 // evaluated in double-single arithmetic (see k_predictor_rhs_ds)
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,

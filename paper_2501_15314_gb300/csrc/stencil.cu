@@ -521,9 +521,12 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     FaceGeom g, FaceGeom32 p, int zchunks, const float* __restrict__ e,
     const float* __restrict__ eo, float* __restrict__ r32, float* __restrict__ rlo,
     const double* __restrict__ r64, float rs_hi, float rs_lo, float a, float nu_h2, float alpha,
-    float beta, float* __restrict__ en, double* __restrict__ u, double us) {
+    float beta, float* __restrict__ en, double* __restrict__ u, double us, int flags) {
   pdl_wait();
   pdl_trigger();
+  // flags: 1 = e_old is zero (not read); 2 = the FP64 iterate is zero (mode
+  // 2 writes u = us e_new on every face, 0 on the wall faces, without reading u)
+  const bool eo_zero = flags & 1, u_zero = flags & 2;
   const int c = blockIdx.z / zchunks;
   const int zc = blockIdx.z - c * zchunks;
   const int lane = threadIdx.x;
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     const float4 ym = (act && has_ym) ? *reinterpret_cast<const float4*>(e + f - sy) : Z4;
     const float4 yp = (act && has_yp) ? *reinterpret_cast<const float4*>(e + f + sy) : Z4;
     const float4 rr = act ? *reinterpret_cast<const float4*>(r32 + f) : Z4;
-    const float4 eold = act ? *reinterpret_cast<const float4*>(eo + f) : Z4;
+    const float4 eold = (act && !eo_zero) ? *reinterpret_cast<const float4*>(eo + f) : Z4;
     float left = __shfl_up_sync(kFullMask, ec.w, 1);
     float right = __shfl_down_sync(kFullMask, ec.x, 1);
     if (lane == 0) left = (act && x0 > 0) ? e[f - 1] : 0.f;
@@ -604,7 +607,7 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     if constexpr (mode == 2) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (val[q] && !wallx[q] && !wally && !wallz) uo[q] = u[f64 + q];
+        if (!u_zero && val[q] && !wallx[q] && !wally && !wallz) uo[q] = u[f64 + q];
     }
     const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
     const float evp[4] = {ep.x, ep.y, ep.z, ep.w};
@@ -632,9 +635,12 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     if (act) *reinterpret_cast<float4*>(en + f) = make_float4(out[0], out[1], out[2], out[3]);
     if constexpr (mode == 2) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q) {
         if (val[q] && !wallx[q] && !wally && !wallz)
           u[f64 + q] = fma(us, f2d_exact(out[q]), uo[q]);   // widened without the FP64 pipe
+        else if (u_zero && val[q])
+          u[f64 + q] = 0.0;
+      }
     }
     ep = ec;
     ec = ez;
@@ -831,7 +837,7 @@ dim3 helm_v4_grid(Dims d) {
 
 void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
                       const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
-                      float* en, double* u, double us, int mode, cudaStream_t s) {
+                      float* en, double* u, double us, int mode, cudaStream_t s, int flags) {
   const FaceGeom32 p = make_face_geom32(d);
   const float rs_hi = (float)rs, rs_lo = (float)(rs - (double)rs_hi);
   count_launch();
@@ -839,13 +845,13 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float
   const int zch = helm_zchunks(d);
   if (mode == 0)
     launch_pdl(k_helm_cheb_v4<0>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
-               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us);
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, flags);
   else if (mode == 1)
     launch_pdl(k_helm_cheb_v4<1>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
-               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us);
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, flags);
   else
     launch_pdl(k_helm_cheb_v4<2>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
-               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us);
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, flags);
 }
 
 int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, double a,
