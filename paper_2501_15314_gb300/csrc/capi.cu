@@ -184,6 +184,16 @@ ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out) {
   return IBM_OK;
 }
 
+ibm_status norm2_lead_host(ibm_ctx* c, const double* x, int64_t n, double* out) {
+  launch_norm2_lead(x, n, c->red_part, c->red_out + 7 * (kMaxRestart + 2), c->stream,
+                    c->host_red_dev);
+  IBM_LAUNCH_CHECK(c);
+  IBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = std::sqrt(c->host_red[0]);
+  if (std::isfinite(*out)) return IBM_OK;
+  return norm2_host(c, x, n, out);   // values out of the leading parts' range
+}
+
 static void free_all(ibm_ctx* c) {
   cudaFree(c->cell_count); cudaFree(c->cell_start); cudaFree(c->cell_flag); cudaFree(c->scan_tmp);
   cudaFree(c->dev_flag); cudaFreeHost(c->host_flag);
@@ -244,7 +254,9 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
   const double sigma = theta / delta;
   double rnorm0;
-  ibm_status st = norm2_host(c, rhs, nf, &rnorm0);
+  // the norm is the baseline of the stopping test only: the corrections
+  // scale by the norms their own residual recursion carries
+  ibm_status st = norm2_lead_host(c, rhs, nf, &rnorm0);
   if (st != IBM_OK) return st;
   if (!std::isfinite(rnorm0)) return set_err(c, IBM_ERR_NAN, "non-finite predictor RHS");
   *iters = 0;

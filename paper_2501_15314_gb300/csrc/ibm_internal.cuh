@@ -233,6 +233,11 @@ ibm_status check_ctx(ibm_ctx* c);
 ibm_status check_opts(ibm_ctx* c, const ibm_solve_opts* o);
 ibm_status ensure_krylov(ibm_ctx* c, int restart);
 ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out);
+// the same to about 1e-5 relative without FP64 arithmetic per element (an
+// exact FP64 dot when that is not finite): for stopping baselines
+ibm_status norm2_lead_host(ibm_ctx* c, const double* x, int64_t n, double* out);
+void launch_norm2_lead(const double* x, int64_t n, double* part, double* out, cudaStream_t s,
+                       double* hout);
 // (a - nu Lap) u = rhs of Eq. (ustar) to o->helm_rtol; uses f3 and g1..g4
 ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
                            int* iters, double* relres);

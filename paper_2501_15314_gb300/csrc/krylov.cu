@@ -13,6 +13,7 @@
 #include <cmath>
 #include <vector>
 
+#include "ds.cuh"
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -140,6 +141,21 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
   block_reduce_store<1>(acc, 1, part);
 }
 
+// Sum of squares of an FP64 vector to about 1e-5 relative, for stopping
+// baselines: each value's leading FP32 part (split_exact: sign, exponent and
+// top fraction bits with integer operations) squared and summed in FP32 per
+// thread, the threads' sums in FP64 (an FP64 dot is bound by the FP64 pipe).
+__global__ void __launch_bounds__(RT) k_norm2_lead(const double* __restrict__ x, int64_t n,
+                                                   double* __restrict__ part) {
+  float acc = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    const float h = split_exact(__ldg(x + i)).hi;
+    acc = fmaf(h, h, acc);
+  }
+  double a[1] = {(double)acc};
+  block_reduce_store<1>(a, 1, part);
+}
+
 __global__ void k_axpby(const double* __restrict__ x, double a, const double* __restrict__ y,
                         double b, double* __restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -224,6 +240,14 @@ void launch_dot(const double* a, const double* b, int64_t n, double* part, doubl
                 cudaStream_t s, double* hout) {
   count_launch();
   k_dot<<<kRedBlocks, RT, 0, s>>>(a, b, n, part);
+  count_launch();
+  k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out, nullptr, nullptr, hout);
+}
+
+void launch_norm2_lead(const double* x, int64_t n, double* part, double* out, cudaStream_t s,
+                       double* hout) {
+  count_launch();
+  k_norm2_lead<<<kRedBlocks, RT, 0, s>>>(x, n, part);
   count_launch();
   k_final_reduce<<<1, RT, 0, s>>>(part, kRedBlocks, out, nullptr, nullptr, hout);
 }
