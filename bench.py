@@ -551,8 +551,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 V-cycle + f32 Arnoldi cycles refined by the f64 residual; "
-                     "double-single predictor, f64 markers and true residual",
+            "dtype": "f32 V-cycle + f32 Arnoldi cycles (Schur product, marker terms included, "
+                     "rounded to f32) refined by the f64 true residual; double-single "
+                     "predictor; f64 iterate, residual and update",
             "data": "synthetic",
             "config": workload_config(W),
             "fp64_form": {"value": job_rate(world, ms_fp64), "unit": UNIT, "ms_per_step": ms_fp64,
