@@ -52,20 +52,20 @@ UNIT = "solves/s"
 # null).  Below 1: part of a launch's output is still in the 129 MB L2 when
 # it ends (written back later, often never: the next kernel reads it there).
 NCU_TRAFFIC_RATIO = {
-    # predictor FP32 Chebyshev step (mode 1): 631.8 + 182.2 MB for 808.5 MB
-    "helm_sweep": 1.0067,
-    # finest-level smoothing, one V-cycle: k_first_v4 67.1 + 26.7 MB and the
-    # two k_sweep_v4 134.2 + 39.4 and 134.2 + 36.5 MB, for 134.2 + 2 x 201.3 MB
-    "mg_smooth_fine": 0.8161,
+    # predictor FP32 Chebyshev step (mode 1): 631.7 + 181.4 MB for 808.5 MB
+    "helm_sweep": 1.0058,
+    # finest-level smoothing, one V-cycle: k_first_v4 67.2 + 27.1 MB and the
+    # two k_sweep_v4 134.2 + 38.8 and 134.2 + 37.4 MB, for 134.2 + 2 x 201.3 MB
+    "mg_smooth_fine": 0.8177,
     # FP32 Gram-Schmidt at basis lengths 6 and 7
     "multidot": 1.0042,
     "axpy_norm": 0.9744,
-    # Schur Laplacian class per step: 14 k_lap_ds (69.8 + 24.6 MB for 134.2 MB)
-    # and 2 k_laplacian_fx (134.2 + 95.8 MB for 268.4 MB)
-    "laplacian_f64": 0.7373,
-    # marker terms of one FP32-cycle Schur product: k_marker_grad_interp
-    # 13.8 MB and k_shell_gradt_f32 70.2 + 0.5 MB, for 78.0 MB
-    "schur_markers": 1.084,
+    # Schur Laplacian class per step: 14 k_lap_ds (69.4 + 24.2 MB for 134.2 MB)
+    # and 2 k_laplacian_fx forming b - L x (268.5 + 108.4 MB for 402.7 MB)
+    "laplacian_f64": 0.7691,
+    # marker terms of one FP32-cycle Schur product: k_marker_grad_interp_f32
+    # 8.8 MB and k_shell_gradt_f32 70.2 + 0.8 MB, for 78.0 MB
+    "schur_markers": 1.0219,
 }
 
 
