@@ -199,7 +199,7 @@ static void free_all(ibm_ctx* c) {
   cudaFree(c->dev_flag); cudaFreeHost(c->host_flag);
   cudaFree(c->c1); cudaFree(c->c2); cudaFree(c->c3);
   cudaFree(c->f1); cudaFree(c->f2); cudaFree(c->f3); cudaFree(c->f4);
-  cudaFree(c->g1); cudaFree(c->g2); cudaFree(c->g3); cudaFree(c->g4); cudaFree(c->g5);
+  cudaFree(c->g1); cudaFree(c->g2); cudaFree(c->g3); cudaFree(c->g4); cudaFree(c->g5); cudaFree(c->g6);
   cudaFree(c->red_part); cudaFree(c->red_out); cudaFreeHost(c->host_red); cudaFree(c->helm_part);
   cudaFree(c->V); cudaFree(c->Z);
   for (int l = 0; l < c->n_levels; ++l) {
@@ -269,6 +269,17 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
   float* eK = nullptr;        // the last correction e (input of the next residual)
   double rn = rnorm0;         // ||r|| of the current residual
   double qn = rnorm0;         // norm of the stored (unnormalised) residual pair
+  // The first correction stays in FP32 (g6, scale pend_s) until the last
+  // step of the second writes u = pend_s e_1 + rn e_2 in one pass (the same
+  // products and roundings as adding them one after the other); a later
+  // correction adds into u.  When the first one is the only one, a flush
+  // writes u.
+  const float* pend = nullptr;
+  double pend_s = 0.0;
+  auto flush = [&]() {
+    if (pend) launch_helm_flush(c->d, pend, pend_s, u, s);
+    pend = nullptr;
+  };
   for (int it = 0;; ++it) {
     if (it > 0) {
       // (g1, g5) = r^ - A e_K; ||r_new|| = ||r|| * ||r^ - A e_K||
@@ -282,7 +293,11 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
       if (!std::isfinite(rn)) return set_err(c, IBM_ERR_NAN, "non-finite predictor residual");
     }
     *relres = rn / rnorm0;
-    if (*relres <= o->helm_rtol || rn == 0.0) return IBM_OK;
+    if (*relres <= o->helm_rtol || rn == 0.0) {
+      flush();
+      IBM_LAUNCH_CHECK(c);
+      return IBM_OK;
+    }
     if (it >= o->helm_maxit) break;
     // reduction wanted from this correction (with a 3x margin), FP32-limited
     double want = o->helm_rtol / *relres / 3.0;
@@ -290,8 +305,7 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
     int K = (int)std::ceil(std::acosh(1.0 / want) / std::acosh(sigma));
     K = K < 2 ? 2 : (K > 60 ? 60 : K);
     // e_old starts at zero (the first step after the normalisation takes it
-    // as zero without reading it), and the first correction writes u
-    // instead of adding to it
+    // as zero without reading it)
     float* eo = c->g2;
     float* e = c->g3;
     float* en = c->g4;
@@ -302,20 +316,31 @@ ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_s
     for (int q = 1; q < K; ++q) {
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
       const int last = q == K - 1;
-      const int ph = last ? -1 : prof_begin(c, IBM_PROF_HELM_SWEEP);
-      const int flags = (q == 1 ? 1 : 0) | (last && it == 0 ? 2 : 0);
+      // the first correction's last step keeps its output in g6; the
+      // second's writes u from it and its own output; later ones add to u
+      const bool keep = last && it == 0;
+      const int mode = last && !keep ? 2 : 1;
+      if (keep) en = c->g6;
+      const int ph = mode == 2 ? -1 : prof_begin(c, IBM_PROF_HELM_SWEEP);
+      const int flags = (q == 1 ? 1 : 0) | (mode == 2 && pend ? 2 : 0);
       launch_helm_cheb(c->d, e, eo, c->g1, nullptr, nullptr, 0.0, (float)a, (float)nu_h2,
-                       (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn,
-                       last ? 2 : 1, s, flags);
+                       (float)(2.0 * rho / delta), (float)(rho * rho_prev), en, u, rn, mode, s,
+                       flags, mode == 2 ? pend : nullptr, pend_s);
       // e, e_old (not on the first step), r read; e_new written
       prof_end(c, ph, (q == 1 ? 12.0 : 16.0) * (double)c->nf);
+      if (mode == 2) pend = nullptr;
       rho_prev = rho;
       float* t = eo; eo = e; e = en; en = t;
     }
     eK = e;   // after the rotation the last output is in e
+    if (it == 0) {
+      pend = eK;
+      pend_s = rn;
+    }
     IBM_LAUNCH_CHECK(c);
     *iters = it + 1;
   }
+  flush();
   char buf[160];
   snprintf(buf, sizeof buf, "predictor did not reach helm_rtol %.3g (relres %.3g)", o->helm_rtol,
            *relres);
@@ -388,6 +413,7 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
             cudaMalloc(&c->g3, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->g4, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->g5, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
+            cudaMalloc(&c->g6, sizeof(float) * helm_fp32_size(c->d)) == cudaSuccess &&
             cudaMalloc(&c->red_part, sizeof(double) * kRedBlocks * (kMaxRestart + 2)) ==
                 cudaSuccess &&
             cudaMalloc(&c->red_out, sizeof(double) * 8 * (kMaxRestart + 2)) ==
@@ -409,7 +435,8 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
     // partial sums of the fused predictor residual norm (one per block)
     const int64_t nb = (int64_t)div_up(g->nx + 1, 32) * div_up(g->ny + 1, 8) * 3 *
                        div_up(g->nz + 1, 16);
-    ok = ok && cudaMalloc(&c->helm_part, sizeof(double) * nb * (kMaxRestart + 2)) == cudaSuccess;
+    c->helm_part_n = nb * (kMaxRestart + 2);
+    ok = ok && cudaMalloc(&c->helm_part, sizeof(double) * c->helm_part_n) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -419,7 +446,7 @@ ibm_status ibm_create(const ibm_grid_desc* g, void* stream, ibm_ctx** out) {
   }
   // the predictor's FP32 arrays: wall faces beyond the launched x-range are
   // never written and must read as 0
-  for (float* buf : {c->g1, c->g2, c->g3, c->g4, c->g5})
+  for (float* buf : {c->g1, c->g2, c->g3, c->g4, c->g5, c->g6})
     if (cudaMemset(buf, 0, sizeof(float) * helm_fp32_size(c->d)) != cudaSuccess) ok = false;
   ibm_status st = ok ? mg_setup(c) : IBM_ERR_CUDA;
   if (st == IBM_OK && cudaDeviceSynchronize() != cudaSuccess) st = IBM_ERR_CUDA;
@@ -650,8 +677,14 @@ static ibm_status step_impl(ibm_ctx* c, const double* u_n, const double* u_nm1, 
 
   // 6. diagnostics: both squared norms go to the host mirror, one round trip
   double* dslot = c->red_out + 7 * (kMaxRestart + 2);
-  launch_gradient_t(c->d, u_np1, c->c1, inv_h, str);
-  launch_dot(c->c1, c->c1, c->m, c->red_part, dslot, str, c->host_red_dev);
+  // ||G^T u||^2 from per-block sums of squares (G^T u itself is not stored)
+  if (gradt_norm2_blocks(c->d) <= c->helm_part_n) {
+    const int64_t nb = launch_gradt_norm2(c->d, u_np1, inv_h, c->helm_part, str);
+    launch_final_reduce(c->helm_part, (int)nb, dslot, str, c->host_red_dev, 1);
+  } else {
+    launch_gradient_t(c->d, u_np1, c->c1, inv_h, str);
+    launch_dot(c->c1, c->c1, c->m, c->red_part, dslot, str, c->host_red_dev);
+  }
   if (n > 0) {
     launch_interp(c, u_np1, mk.t2);
     count_launch();

@@ -81,7 +81,7 @@ struct MarkerData {
   int64_t n_ell = 0, ell_cap = 0;
   int32_t* ell_key = nullptr;
   double* ell_coef = nullptr;     // [3][n_ell] G^T R coefficients (0 on padding)
-  float* ell_coef32 = nullptr;    // [3][n_ell] the same rounded to FP32 (FP32 Arnoldi cycles)
+  float* ell_coef32 = nullptr;    // [3][n_ell] their leading FP32 parts (FP32 Arnoldi cycles)
   // the spread R F onto the faces through the same layout: per entry and
   // component d the weight of F_{k,d} at the cell's lower d-face (0 on
   // padding and outside the support), and per shell cell (layout order) the
@@ -149,6 +149,7 @@ struct ibm_ctx {
   float* g3 = nullptr;
   float* g4 = nullptr;
   float* g5 = nullptr;             // low parts of the predictor's residual
+  float* g6 = nullptr;             // the predictor's first correction, kept in FP32
   double* red_part = nullptr;      // [kRedBlocks][kMaxRestart + 2] partials
   double* red_out = nullptr;       // [8][kMaxRestart + 2] reduced values
   // set by the step around its solve: the solver leaves the constant of the
@@ -158,6 +159,7 @@ struct ibm_ctx {
   double* host_red = nullptr;      // mapped pinned mirror of red_out (host address)
   double* host_red_dev = nullptr;  // its device address
   double* helm_part = nullptr;     // per-block partials of the predictor norm
+  int64_t helm_part_n = 0;         // its length (also holds the divergence norm's partials)
 
   // Krylov bases
   double* V = nullptr;             // [(kMaxRestart + 1)][m]
@@ -238,7 +240,7 @@ ibm_status norm2_host(ibm_ctx* c, const double* x, int64_t n, double* out);
 ibm_status norm2_lead_host(ibm_ctx* c, const double* x, int64_t n, double* out);
 void launch_norm2_lead(const double* x, int64_t n, double* part, double* out, cudaStream_t s,
                        double* hout);
-// (a - nu Lap) u = rhs of Eq. (ustar) to o->helm_rtol; uses f3 and g1..g4
+// (a - nu Lap) u = rhs of Eq. (ustar) to o->helm_rtol; uses g1..g6
 ibm_status helmholtz_solve(ibm_ctx* c, const double* rhs, double* u, const ibm_solve_opts* o,
                            int* iters, double* relres);
 
@@ -251,6 +253,10 @@ void launch_laplacian_sub(Dims d, const double* v, const double* b, double* out,
                           cudaStream_t s);
 void launch_gradient(Dims d, const double* p, double* u, double inv_h, cudaStream_t s);
 void launch_gradient_t(Dims d, const double* u, double* out, double inv_h, cudaStream_t s);
+// part[b] = the sums of squares of alpha G^T u over the blocks of one launch
+// (returns their count, gradt_norm2_blocks(d))
+int64_t gradt_norm2_blocks(Dims d);
+int64_t launch_gradt_norm2(Dims d, const double* u, double alpha, double* part, cudaStream_t s);
 // u_out = u_in + alpha * G p   (interior faces; wall faces 0)
 void launch_grad_axpy(Dims d, const double* u_in, const double* p, double alpha,
                       double* u_out, cudaStream_t s);
@@ -268,7 +274,9 @@ int64_t helm_fp32_size(Dims d);
 void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
                       const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
                       float* en, double* u, double us, int mode, cudaStream_t s,
-                      int flags = 0);   // 1: e_old is zero; 2: u is zero (mode 2 writes it)
+                      int flags = 0, const float* pe = nullptr, double ps = 0.0);
+// u = ps pe on the interior faces (pe on the predictor's padded FP32 layout)
+void launch_helm_flush(Dims d, const float* pe, double ps, double* u, cudaStream_t s);   // 1: e_old is zero; 2: u is zero (mode 2 writes it)
 // predictor RHS with the convective term of u_n fused in (with_adv != 0),
 // evaluated in double-single arithmetic (see k_predictor_rhs_ds)
 void launch_predictor_rhs_adv(Dims d, const double* u_n, const double* u_nm1,
@@ -335,8 +343,9 @@ void launch_axpby(const double* x, double a, const double* y, double b, double* 
 void launch_gemv_acc(double* x, const double* Z, int64_t ld, int nq, const double* y,
                      int64_t n, cudaStream_t s);
 // out[0] = sum of part[b * (kMaxRestart + 2)], b < nb (fixed order)
+// out = sum of part[b * stride], b < nb (fixed order)
 void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s,
-                         double* hout = nullptr);
+                         double* hout = nullptr, int stride = kMaxRestart + 2);
 void launch_sum(const double* x, int64_t n, double* part, double* out, cudaStream_t s);
 // out = x + (y + scale * (*val)), in the operations of k_add_scalar then k_axpby
 void launch_axpy_shift(const double* x, const double* y, const double* val, double scale,

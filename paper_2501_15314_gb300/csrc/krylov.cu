@@ -88,17 +88,18 @@ __global__ void __launch_bounds__(RT) k_axpy_norm(double* __restrict__ w,
   block_reduce_store<1>(acc, 1, part);
 }
 
-// out[q] = sum_b part[b][q], fixed-order tree (one block per q); with div
-// != null also quot[q] = out[q] / div[q]; with hout != null also hout[q] =
-// out[q] (the device address of the mapped host mirror)
+// out[q] = sum_b part[b * stride + q], fixed-order tree (one block per q);
+// with div != null also quot[q] = out[q] / div[q]; with hout != null also
+// hout[q] = out[q] (the device address of the mapped host mirror)
 __global__ void __launch_bounds__(RT) k_final_reduce(const double* __restrict__ part, int nb,
                                                      double* __restrict__ out,
                                                      const double* __restrict__ div = nullptr,
                                                      double* __restrict__ quot = nullptr,
-                                                     double* hout = nullptr) {
+                                                     double* hout = nullptr,
+                                                     int stride = kOutStride) {
   const int q = blockIdx.x;
   double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * kOutStride + q];
+  for (int b = threadIdx.x; b < nb; b += RT) s += part[(int64_t)b * stride + q];
   __shared__ double sh[RT / 32];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -231,9 +232,9 @@ void launch_axpy_norm(double* w, const double* V, int64_t ld, int nq, const doub
 }
 
 void launch_final_reduce(const double* part, int nb, double* out, cudaStream_t s,
-                         double* hout) {
+                         double* hout, int stride) {
   count_launch();
-  k_final_reduce<<<1, RT, 0, s>>>(part, nb, out, nullptr, nullptr, hout);
+  k_final_reduce<<<1, RT, 0, s>>>(part, nb, out, nullptr, nullptr, hout, stride);
 }
 
 void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out,

@@ -22,28 +22,31 @@ namespace {
 
 constexpr int TPB = 256;
 
-// Eq. (delta) times the cell width, r in cell widths.
-__device__ __forceinline__ double roma_phi(double r) {
-  r = fabs(r);
-  if (r <= 0.5) return (1.0 + sqrt(fmax(1.0 - 3.0 * r * r, 0.0))) * (1.0 / 3.0);
-  if (r <= 1.5) {
-    const double q = 1.0 - r;
-    return (5.0 - 3.0 * r - sqrt(fmax(1.0 - 3.0 * q * q, 0.0))) * (1.0 / 6.0);
-  }
-  return 0.0;
-}
+// Eq. (delta) times the cell width (phi) and its derivative d phi / dr
+// (differentiated branch by branch; continuous, with value -sign(r) at
+// |r| = 1/2 and 0 at |r| = 3/2), r in cell widths.  Both come from one
+// reciprocal square root R = 1/sqrt(A) of the branch's A = 1 - 3 s^2: the
+// square root is A R and the derivative's quotient s / sqrt(A) is s R (one
+// FP64 rsqrt in place of a square root and a division).
+struct RomaVal {
+  double phi, dphi;
+};
 
-// d phi / dr of Eq. (delta), r in cell widths (differentiated branch by
-// branch; continuous, with value -sign(r) at |r| = 1/2 and 0 at |r| = 3/2).
-__device__ __forceinline__ double roma_dphi(double r) {
+__device__ __forceinline__ RomaVal roma(double r) {
   const double a = fabs(r);
-  if (a <= 0.5) return -r / sqrt(1.0 - 3.0 * r * r);
+  if (a <= 0.5) {
+    const double A = 1.0 - 3.0 * r * r;
+    const double R = rsqrt(A);
+    return {(1.0 + A * R) * (1.0 / 3.0), -r * R};
+  }
   if (a < 1.5) {
     const double q = 1.0 - a;
-    const double v = -0.5 * (1.0 + q / sqrt(1.0 - 3.0 * q * q));
-    return r > 0.0 ? v : -v;
+    const double A = 1.0 - 3.0 * q * q;
+    const double R = rsqrt(A);
+    const double v = -0.5 * (1.0 + q * R);
+    return {(5.0 - 3.0 * a - A * R) * (1.0 / 6.0), r > 0.0 ? v : -v};
   }
-  return 0.0;
+  return {0.0, 0.0};
 }
 
 struct MkView {
@@ -98,21 +101,23 @@ __global__ void k_marker_setup(Dims d, double inv_h, int64_t n, const double* __
     double W[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      W[q] = roma_phi((double)(b_f + q) - s);
-      wf[(e * 3 + q) * n + k] = W[q];
-      wc[(e * 3 + q) * n + k] = roma_phi((double)(b_c + q) + 0.5 - s);
-      dwf[(e * 3 + q) * n + k] = roma_dphi((double)(b_f + q) - s);
-      dwc[(e * 3 + q) * n + k] = roma_dphi((double)(b_c + q) + 0.5 - s);
+      const RomaVal vf = roma((double)(b_f + q) - s);
+      const RomaVal vc = roma((double)(b_c + q) + 0.5 - s);
+      W[q] = vf.phi;
+      wf[(e * 3 + q) * n + k] = vf.phi;
+      wc[(e * 3 + q) * n + k] = vc.phi;
+      dwf[(e * 3 + q) * n + k] = vf.dphi;
+      dwc[(e * 3 + q) * n + k] = vc.dphi;
+      wc32[(e * 3 + q) * n + k] = (float)vc.phi;
     }
     // cell b_f - 1 + q lies between faces b_f - 1 + q and b_f + q
-    cw[(e * 4 + 0) * n + k] = (0.0 - W[0]) * inv_h;
-    cw[(e * 4 + 1) * n + k] = (W[0] - W[1]) * inv_h;
-    cw[(e * 4 + 2) * n + k] = (W[1] - W[2]) * inv_h;
-    cw[(e * 4 + 3) * n + k] = (W[2] - 0.0) * inv_h;
+    const double C[4] = {(0.0 - W[0]) * inv_h, (W[0] - W[1]) * inv_h, (W[1] - W[2]) * inv_h,
+                         (W[2] - 0.0) * inv_h};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) wc32[(e * 3 + q) * n + k] = (float)wc[(e * 3 + q) * n + k];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cw32[(e * 4 + q) * n + k] = (float)cw[(e * 4 + q) * n + k];
+    for (int q = 0; q < 4; ++q) {
+      cw[(e * 4 + q) * n + k] = C[q];
+      cw32[(e * 4 + q) * n + k] = (float)C[q];
+    }
   }
   if (bad) atomicOr(err, 1);
 }
@@ -185,14 +190,15 @@ __global__ void k_sort_segments(int64_t n_shell, const int32_t* __restrict__ off
 // Coefficients of G^T R e_{k,d} (d = 0, 1, 2) at global cell g: along d the
 // G^T-weighted face taps cw (cell i lies between faces i and i+1), along the
 // other two axes the centre-tap weights; zero outside the 4 x 3 x 3
-// footprint.  Each axis's two factors are loaded once; coef_d =
-// (f_0 f_1) f_2 with f_e the cw factor for e = d and the centre weight
-// otherwise.
+// footprint.  Each axis's two factors are loaded once; coef_d = f_d P_d
+// with f_d the cw factor along d and P_d the product of the centre weights
+// along the other two axes (three pair products shared by the six weights:
+// nine FP64 multiplications per entry, the FP64 pipe being this kernel's
+// bound).
 //
 // With them the spread weights of the same entry: the weight of F_{k,d} at
-// the cell's lower d-face, (f_0 f_1) f_2 with the face-tap weight wf along d
-// and the centre weights along the other axes (the product the per-cell
-// spread forms), and in bit d whether that face lies inside the support.
+// the cell's lower d-face, the face-tap weight wf along d times the same
+// P_d, and in bit d whether that face lies inside the support.
 __device__ __forceinline__ void gtr_coefs(const MkView& mk, int64_t k, const int g[3],
                                           double (&coef)[3], double (&sw)[3], int& in) {
   double fw[3], fc[3], ff[3];
@@ -208,12 +214,13 @@ __device__ __forceinline__ void gtr_coefs(const MkView& mk, int64_t k, const int
     inw[e] = qc >= 0 && qc <= 2;
     fw[e] = inw[e] ? mk.wc[(e * 3 + qc) * mk.n + k] : 0.0;
   }
-  coef[0] = (fc[0] * fw[1]) * fw[2];
-  coef[1] = (fw[0] * fc[1]) * fw[2];
-  coef[2] = (fw[0] * fw[1]) * fc[2];
-  sw[0] = (ff[0] * fw[1]) * fw[2];
-  sw[1] = (fw[0] * ff[1]) * fw[2];
-  sw[2] = (fw[0] * fw[1]) * ff[2];
+  const double p12 = fw[1] * fw[2], p02 = fw[0] * fw[2], p01 = fw[0] * fw[1];
+  coef[0] = fc[0] * p12;
+  coef[1] = fc[1] * p02;
+  coef[2] = fc[2] * p01;
+  sw[0] = ff[0] * p12;
+  sw[1] = ff[1] * p02;
+  sw[2] = ff[2] * p01;
   in = (inf[0] && inw[1] && inw[2] ? 1 : 0) | (inw[0] && inf[1] && inw[2] ? 2 : 0) |
        (inw[0] && inw[1] && inf[2] ? 4 : 0);
 }
@@ -418,7 +425,9 @@ __global__ void k_ell_fill(MkView mk, int64_t n_shell, const int32_t* __restrict
 #pragma unroll
       for (int dc = 0; dc < 3; ++dc) {
         ecoef[dc * n_ell + dst] = cf[dc];
-        ecoef32[dc * n_ell + dst] = (float)cf[dc];
+        // the FP32 copy is the leading part (integer operations; a
+        // conversion would run on the FP64 pipe)
+        ecoef32[dc * n_ell + dst] = split_exact(cf[dc]).hi;
         esw[dc * n_ell + dst] = sw[dc];
       }
     } else {

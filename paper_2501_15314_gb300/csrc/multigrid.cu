@@ -810,74 +810,127 @@ __device__ ChainSm chain_layout(float* base, const CoarseChain& ch) {
   return S;
 }
 
-// Copies n 16-byte words from global to shared memory; each thread issues
-// its R loads of a round before its stores, so a round costs one memory
-// latency.
-template <int R>
-__device__ __forceinline__ void copy_words(uint4* dst, const uint4* __restrict__ src, int n) {
-  for (int base = 0; base < n; base += R * (int)blockDim.x) {
-    uint4 v[R];
+// Cells (or 16-byte words) a thread of the chain takes per round: their
+// loads are issued together before their arithmetic or stores, so a round
+// costs about one shared-memory (or L2) latency instead of four.
+constexpr int kChainBatch = 4;
+
+// Copies up to four arrays of 16-byte words from global to shared memory as
+// one sequence: each thread loads its kChainBatch words of a round (from
+// whichever array they fall in) before it stores them.
+struct WordSegs {
+  uint4* dst[4];
+  const uint4* src[4];
+  int end[4];   // running word counts; unused segments repeat the last end
+};
+
+__device__ void copy_segs(const WordSegs& w) {
+  const int n = w.end[3];
+  for (int base = threadIdx.x; base < n; base += kChainBatch * (int)blockDim.x) {
+    uint4 v[kChainBatch];
+    int seg[kChainBatch], off[kChainBatch];
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int e = base + (int)threadIdx.x + q * (int)blockDim.x;
-      if (e < n) v[q] = __ldg(src + e);
+    for (int q = 0; q < kChainBatch; ++q) {
+      const int e = base + q * (int)blockDim.x;
+      const int sg = (e >= w.end[0]) + (e >= w.end[1]) + (e >= w.end[2]);
+      const int first = sg == 0 ? 0 : (sg == 1 ? w.end[0] : (sg == 2 ? w.end[1] : w.end[2]));
+      const uint4* src = sg == 0 ? w.src[0] : (sg == 1 ? w.src[1] : (sg == 2 ? w.src[2] : w.src[3]));
+      seg[q] = sg;
+      off[q] = e - first;
+      if (e < n) v[q] = __ldg(src + off[q]);
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int e = base + (int)threadIdx.x + q * (int)blockDim.x;
-      if (e < n) dst[e] = v[q];
+    for (int q = 0; q < kChainBatch; ++q) {
+      const int e = base + q * (int)blockDim.x;
+      const int sg = seg[q];
+      uint4* dst = sg == 0 ? w.dst[0] : (sg == 1 ? w.dst[1] : (sg == 2 ? w.dst[2] : w.dst[3]));
+      if (e < n) dst[off[q]] = v[q];
     }
   }
 }
 
-// Copies the coordinate and mask tables and the staged pseudo-inverse into
-// shared memory (the caller synchronises before they are used).  The tables
-// are padded to whole 16-byte words at setup.
-__device__ void chain_load(const CoarseChain& ch, const ChainSm& S) {
+// The coordinate and mask tables, the first level's b (m0 floats, a multiple
+// of four) and the staged pseudo-inverse into shared memory in one sequence
+// (the caller synchronises before they are used).  The tables are padded to
+// whole 16-byte words at setup; the pseudo-inverse's last mc^2 mod 4 floats
+// are copied one by one.
+__device__ void chain_load(const CoarseChain& ch, const ChainSm& S, const float* b_in, int m0) {
   const int tot = ch.off[ch.nlev];
-  copy_words<2>(reinterpret_cast<uint4*>(S.pk), reinterpret_cast<const uint4*>(ch.pk),
-                round4(tot) / 4);
-  copy_words<1>(reinterpret_cast<uint4*>(S.nb), reinterpret_cast<const uint4*>(ch.nb),
-                round16(tot) / 16);
-  if (ch.stage_pinv) {
-    const int n = ch.mc * ch.mc;
-    float* pv = const_cast<float*>(S.pinv);
-    copy_words<4>(reinterpret_cast<uint4*>(pv), reinterpret_cast<const uint4*>(ch.pinv), n / 4);
-    for (int q = (n & ~3) + threadIdx.x; q < n; q += blockDim.x) pv[q] = __ldg(ch.pinv + q);
-  }
+  WordSegs w;
+  int e = 0;
+  w.dst[0] = reinterpret_cast<uint4*>(S.pk);
+  w.src[0] = reinterpret_cast<const uint4*>(ch.pk);
+  w.end[0] = e += round4(tot) / 4;
+  w.dst[1] = reinterpret_cast<uint4*>(S.nb);
+  w.src[1] = reinterpret_cast<const uint4*>(ch.nb);
+  w.end[1] = e += round16(tot) / 16;
+  w.dst[2] = reinterpret_cast<uint4*>(S.b);
+  w.src[2] = reinterpret_cast<const uint4*>(b_in);
+  w.end[2] = e += m0 / 4;
+  w.dst[3] = reinterpret_cast<uint4*>(const_cast<float*>(S.pinv));
+  w.src[3] = reinterpret_cast<const uint4*>(ch.pinv);
+  const int np = ch.stage_pinv ? ch.mc * ch.mc : 0;
+  w.end[3] = e += np / 4;
+  copy_segs(w);
+  float* pv = const_cast<float*>(S.pinv);
+  for (int q = (np & ~3) + (int)threadIdx.x; q < np; q += (int)blockDim.x) pv[q] = __ldg(ch.pinv + q);
 }
 
 // p Chebyshev steps on one level in shared memory; from_zero starts at x = 0.
-// Ends with the result in x (t is the ping-pong buffer).
+// The steps alternate between x and t and the result ends in x: from zero
+// the first step writes x or t so that the last one writes x; from x with an
+// odd p the result is copied back.
 __device__ void chain_smooth(const CoarseChain& ch, const ChainSm& S, int l, const float* w,
                              int p, bool from_zero) {
+  if (p <= 0) return;
   const Dims d = ch.d[l];
   const int o = ch.off[l];
   const int m = d.nx * d.ny * d.nz;
   const float h2 = ch.h2[l];
   float* x = S.x + o;
+  float* t = S.t + o;
   const float* b = S.b + o;
   const uint8_t* nb = S.nb + o;
+  const int nt = (int)blockDim.x;
   float* cur = x;
-  float* nxt = S.t + o;
+  float* nxt = t;
   int q = 0;
-  if (from_zero && p > 0) {
-    for (int c = threadIdx.x; c < m; c += blockDim.x)
-      x[c] = w[0] * h2 * b[c] * inv_nn(__popc((uint32_t)nb[c]));
+  if (from_zero) {
+    float* dst = (p & 1) ? x : t;
+    for (int c = threadIdx.x; c < m; c += nt)
+      dst[c] = w[0] * h2 * b[c] * inv_nn(__popc((uint32_t)nb[c]));
     __syncthreads();
+    cur = dst;
+    nxt = (p & 1) ? t : x;
     q = 1;
   }
   for (; q < p; ++q) {
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      int nn;
-      const float s = lap_nb(d, cur, c, nb[c], nn);
-      nxt[c] = fmaf(w[q] * inv_nn(nn), fmaf(h2, b[c], s - (float)nn * cur[c]), cur[c]);
+    const float wq = w[q];
+    for (int base = threadIdx.x; base < m; base += kChainBatch * nt) {
+      float sn[kChainBatch], xv[kChainBatch], bv[kChainBatch];
+      int nn[kChainBatch];
+#pragma unroll
+      for (int k = 0; k < kChainBatch; ++k) {
+        const int c = base + k * nt;
+        sn[k] = 0.f; xv[k] = 0.f; bv[k] = 0.f; nn[k] = 1;
+        if (c < m) {
+          sn[k] = lap_nb(d, cur, c, nb[c], nn[k]);
+          xv[k] = cur[c];
+          bv[k] = b[c];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kChainBatch; ++k) {
+        const int c = base + k * nt;
+        if (c < m)
+          nxt[c] = fmaf(wq * inv_nn(nn[k]), fmaf(h2, bv[k], sn[k] - (float)nn[k] * xv[k]), xv[k]);
+      }
     }
     __syncthreads();
     float* tmp = cur; cur = nxt; nxt = tmp;
   }
   if (cur != x) {
-    for (int c = threadIdx.x; c < m; c += blockDim.x) x[c] = cur[c];
+    for (int c = threadIdx.x; c < m; c += nt) x[c] = cur[c];
     __syncthreads();
   }
 }
@@ -885,6 +938,7 @@ __device__ void chain_smooth(const CoarseChain& ch, const ChainSm& S, int l, con
 // The cycle on the chain's levels: b of its first level in S.b, the tables
 // loaded and synchronised; leaves x of its first level in S.x.
 __device__ void chain_run(const CoarseChain& ch, const ChainSm& S) {
+  const int nt = (int)blockDim.x;
   // descend
   for (int l = 0; l < ch.nlev - 1; ++l) {
     chain_smooth(ch, S, l, ch.wpre, ch.pre, true);
@@ -894,28 +948,41 @@ __device__ void chain_run(const CoarseChain& ch, const ChainSm& S) {
     const float* x = S.x + ch.off[l];
     const float* b = S.b + ch.off[l];
     const uint8_t* nb = S.nb + ch.off[l];
+    const uint32_t* pkc = S.pk + ch.off[l + 1];
     float* bc = S.b + ch.off[l + 1];
-    // eight threads per coarse cell (one child each), summed by shuffles
-    for (int base = 0; base < 8 * mcl; base += blockDim.x) {
-      const int t = base + threadIdx.x;
-      const bool act = t < 8 * mcl;
-      float r = 0.f;
-      if (act) {
-        const int C = t >> 3, q = t & 7;
-        int I, J, K;
-        unpack(S.pk[ch.off[l + 1] + C], I, J, K);
-        const int c = ((2 * K + (q >> 2)) * d.ny + 2 * J + ((q >> 1) & 1)) * d.nx + 2 * I + (q & 1);
-        r = b[c];
-        if (ch.pre > 0) {
-          int nn;
-          const float sn = lap_nb(d, x, c, nb[c], nn);
-          r -= ((float)nn * x[c] - sn) * ih2;
+    // eight threads per coarse cell (one child each), summed by shuffles;
+    // the thread count is a multiple of 8, so a coarse cell's eight threads
+    // are consecutive lanes of one warp in every round
+    for (int base = 0; base < 8 * mcl; base += kChainBatch * nt) {
+      float r[kChainBatch];
+#pragma unroll
+      for (int k = 0; k < kChainBatch; ++k) {
+        const int tq = base + k * nt + (int)threadIdx.x;
+        r[k] = 0.f;
+        if (tq < 8 * mcl) {
+          const int C = tq >> 3, q = tq & 7;
+          int I, J, K;
+          unpack(pkc[C], I, J, K);
+          const int c =
+              ((2 * K + (q >> 2)) * d.ny + 2 * J + ((q >> 1) & 1)) * d.nx + 2 * I + (q & 1);
+          float v = b[c];
+          if (ch.pre > 0) {
+            int nn;
+            const float sn = lap_nb(d, x, c, nb[c], nn);
+            v -= ((float)nn * x[c] - sn) * ih2;
+          }
+          r[k] = v;
         }
       }
-      r += __shfl_xor_sync(0xffffffffu, r, 1);
-      r += __shfl_xor_sync(0xffffffffu, r, 2);
-      r += __shfl_xor_sync(0xffffffffu, r, 4);
-      if (act && (t & 7) == 0) bc[t >> 3] = r * 0.125f;
+#pragma unroll
+      for (int k = 0; k < kChainBatch; ++k) {
+        const int tq = base + k * nt + (int)threadIdx.x;
+        float v = r[k];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        if (tq < 8 * mcl && (tq & 7) == 0) bc[tq >> 3] = v * 0.125f;
+      }
     }
     __syncthreads();
   }
@@ -925,7 +992,7 @@ __device__ void chain_run(const CoarseChain& ch, const ChainSm& S) {
     const int l = ch.nlev - 1;
     float* x = S.x + ch.off[l];
     const float* b = S.b + ch.off[l];
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, nw = nt >> 5;
     for (int r = threadIdx.x >> 5; r < ch.mc; r += nw) {
       float acc = 0.f;
       for (int q = lane; q < ch.mc; q += 32) acc = fmaf(S.pinv[r * ch.mc + q], b[q], acc);
@@ -939,22 +1006,37 @@ __device__ void chain_run(const CoarseChain& ch, const ChainSm& S) {
   for (int l = ch.nlev - 2; l >= 0; --l) {
     float* x = S.x + ch.off[l];
     const float* xc = S.x + ch.off[l + 1];
+    const uint32_t* pkf = S.pk + ch.off[l];
     const Dims d = ch.d[l], dc = ch.d[l + 1];
     const int m = d.nx * d.ny * d.nz;
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      int i, j, k;
-      unpack(S.pk[ch.off[l] + c], i, j, k);
-      const int I = i >> 1, J = j >> 1, K = k >> 1;
-      const int In = (i & 1) ? min(I + 1, dc.nx - 1) : max(I - 1, 0);
-      const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
-      const int Kn = (k & 1) ? min(K + 1, dc.nz - 1) : max(K - 1, 0);
-      auto X = [&](int a, int bb, int cc) { return xc[(cc * dc.ny + bb) * dc.nx + a]; };
-      const float a00 = 0.75f * X(I, J, K) + 0.25f * X(In, J, K);
-      const float a01 = 0.75f * X(I, Jn, K) + 0.25f * X(In, Jn, K);
-      const float a10 = 0.75f * X(I, J, Kn) + 0.25f * X(In, J, Kn);
-      const float a11 = 0.75f * X(I, Jn, Kn) + 0.25f * X(In, Jn, Kn);
-      const float v = 0.75f * (0.75f * a00 + 0.25f * a01) + 0.25f * (0.75f * a10 + 0.25f * a11);
-      x[c] = ch.pre > 0 ? x[c] + v : v;
+    for (int base = threadIdx.x; base < m; base += kChainBatch * nt) {
+      float v[kChainBatch], xo[kChainBatch];
+#pragma unroll
+      for (int k = 0; k < kChainBatch; ++k) {
+        const int c = base + k * nt;
+        v[k] = 0.f;
+        xo[k] = 0.f;
+        if (c < m) {
+          int i, j, kk;
+          unpack(pkf[c], i, j, kk);
+          const int I = i >> 1, J = j >> 1, K = kk >> 1;
+          const int In = (i & 1) ? min(I + 1, dc.nx - 1) : max(I - 1, 0);
+          const int Jn = (j & 1) ? min(J + 1, dc.ny - 1) : max(J - 1, 0);
+          const int Kn = (kk & 1) ? min(K + 1, dc.nz - 1) : max(K - 1, 0);
+          auto X = [&](int a, int bb, int cc) { return xc[(cc * dc.ny + bb) * dc.nx + a]; };
+          const float a00 = 0.75f * X(I, J, K) + 0.25f * X(In, J, K);
+          const float a01 = 0.75f * X(I, Jn, K) + 0.25f * X(In, Jn, K);
+          const float a10 = 0.75f * X(I, J, Kn) + 0.25f * X(In, J, Kn);
+          const float a11 = 0.75f * X(I, Jn, Kn) + 0.25f * X(In, Jn, Kn);
+          v[k] = 0.75f * (0.75f * a00 + 0.25f * a01) + 0.25f * (0.75f * a10 + 0.25f * a11);
+          if (ch.pre > 0) xo[k] = x[c];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kChainBatch; ++k) {
+        const int c = base + k * nt;
+        if (c < m) x[c] = ch.pre > 0 ? xo[k] + v[k] : v[k];
+      }
     }
     __syncthreads();
     chain_smooth(ch, S, l, ch.wpost, ch.post, false);
@@ -968,9 +1050,8 @@ __global__ void __launch_bounds__(kChainThreads) k_coarse_chain(CoarseChain ch,
   pdl_trigger();
   extern __shared__ __align__(16) float sm[];
   const ChainSm S = chain_layout(sm, ch);
-  chain_load(ch, S);
   const int m0 = ch.off[1];   // a multiple of 8 (the level has a level below it)
-  copy_words<1>(reinterpret_cast<uint4*>(S.b), reinterpret_cast<const uint4*>(b_in), m0 / 4);
+  chain_load(ch, S, b_in, m0);
   __syncthreads();
   chain_run(ch, S);
   for (int c = threadIdx.x; c < m0 / 4; c += blockDim.x)

@@ -216,12 +216,14 @@ __device__ __forceinline__ double div_fx(double a0, double a1, double a2, double
 // (u_{c-1/2} - u_{c+1/2}) over interior faces (wall faces read as 0), the
 // sum formed exactly (div_fx).  One cell per thread, blocks of 32 x 8 cells
 // over zc planes: the upper x-face from the next lane, the lower z-face from
-// the march, the y-faces through L1.
+// the march, the y-faces through L1.  NORM: instead of out, the block's sum
+// of the squared values (FP64, fixed order) goes to sq_part[block].
+template <bool NORM>
 __global__ void __launch_bounds__(BX * BY) k_gradt_fx(Dims d, FaceGeom g,
                                                       const double* __restrict__ u, FxLimits L,
                                                       const double* __restrict__ cin,
                                                       double beta, double* __restrict__ out,
-                                                      int zc) {
+                                                      double* __restrict__ sq_part, int zc) {
   const int lane = threadIdx.x;
   const int i = blockIdx.x * BX + lane;
   const int j = blockIdx.y * BY + threadIdx.y;
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(BX * BY) k_gradt_fx(Dims d, FaceGeom g,
   // interior faces: x-faces 1..nx-1, y-faces 1..ny-1, z-faces 1..nz-1
   const bool xlo = i > 0, xhi = i + 1 < d.nx, ylo = j > 0, yhi = j + 1 < d.ny;
   double zlo = (act && z0 > 0) ? __ldg(uz + (int64_t)z0 * g.sz[2] + (int64_t)j * g.sy[2] + i) : 0.0;
+  double sq = 0.0;
   for (int z = z0; z < z1; ++z) {
     const int64_t fx = (int64_t)z * g.sz[0] + (int64_t)j * g.sy[0] + i;
     const int64_t fy = (int64_t)z * g.sz[1] + (int64_t)j * g.sy[1] + i;
@@ -250,10 +253,27 @@ __global__ void __launch_bounds__(BX * BY) k_gradt_fx(Dims d, FaceGeom g,
     if (!xhi) a1 = 0.0;
     if (act) {
       const double v = div_fx(a0, a1, a2, a3, zlo, zhi, L);
-      const int64_t c = ((int64_t)z * d.ny + j) * d.nx + i;
-      out[c] = cin ? fma(beta, __ldg(cin + c), v) : v;
+      if constexpr (NORM) {
+        sq = fma(v, v, sq);
+      } else {
+        const int64_t c = ((int64_t)z * d.ny + j) * d.nx + i;
+        out[c] = cin ? fma(beta, __ldg(cin + c), v) : v;
+      }
     }
     zlo = zhi;
+  }
+  if constexpr (NORM) {
+    __shared__ double sh[BY];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if (lane == 0) sh[threadIdx.y] = sq;
+    __syncthreads();
+    if (lane == 0 && threadIdx.y == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < BY; ++w) t += sh[w];
+      sq_part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
@@ -521,11 +541,13 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     FaceGeom g, FaceGeom32 p, int zchunks, const float* __restrict__ e,
     const float* __restrict__ eo, float* __restrict__ r32, float* __restrict__ rlo,
     const double* __restrict__ r64, float rs_hi, float rs_lo, float a, float nu_h2, float alpha,
-    float beta, float* __restrict__ en, double* __restrict__ u, double us, int flags) {
+    float beta, float* __restrict__ en, double* __restrict__ u, double us,
+    const float* __restrict__ pe, double ps, int flags) {
   pdl_wait();
   pdl_trigger();
-  // flags: 1 = e_old is zero (not read); 2 = the FP64 iterate is zero (mode
-  // 2 writes u = us e_new on every face, 0 on the wall faces, without reading u)
+  // flags: 1 = e_old is zero (not read); 2 = the FP64 iterate is not read
+  // (mode 2 writes u = us e_new + ps pe on every face, ps pe being a
+  // correction not yet added (none when pe is null), 0 on the wall faces)
   const bool eo_zero = flags & 1, u_zero = flags & 2;
   const int c = blockIdx.z / zchunks;
   const int zc = blockIdx.z - c * zchunks;
@@ -604,10 +626,15 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
     const int gz = (c != 2) ? ((z == 0) + (z == n2 - 1)) : 0;
     double uo[4] = {0.0, 0.0, 0.0, 0.0};
+    float4 pv = Z4;
     if constexpr (mode == 2) {
+      if (u_zero) {
+        if (pe && act) pv = *reinterpret_cast<const float4*>(pe + f);
+      } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (!u_zero && val[q] && !wallx[q] && !wally && !wallz) uo[q] = u[f64 + q];
+        for (int q = 0; q < 4; ++q)
+          if (val[q] && !wallx[q] && !wally && !wallz) uo[q] = u[f64 + q];
+      }
     }
     const float ev[4] = {ec.x, ec.y, ec.z, ec.w};
     const float evp[4] = {ep.x, ep.y, ep.z, ep.w};
@@ -634,10 +661,14 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
     }
     if (act) *reinterpret_cast<float4*>(en + f) = make_float4(out[0], out[1], out[2], out[3]);
     if constexpr (mode == 2) {
+      const float pq[4] = {pv.x, pv.y, pv.z, pv.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
+        // (the same products and roundings as adding ps pe first, then us e_new)
+        if (u_zero && pe) uo[q] = ps * f2d_exact(pq[q]);
         if (val[q] && !wallx[q] && !wally && !wallz)
-          u[f64 + q] = fma(us, f2d_exact(out[q]), uo[q]);   // widened without the FP64 pipe
+          u[f64 + q] = u_zero && !pe ? us * f2d_exact(out[q])
+                                     : fma(us, f2d_exact(out[q]), uo[q]);   // widened without the FP64 pipe
         else if (u_zero && val[q])
           u[f64 + q] = 0.0;
       }
@@ -813,8 +844,22 @@ void launch_gradt_axpby(Dims d, const double* u, double alpha, const double* c, 
                         double* out, cudaStream_t s) {
   count_launch();
   const int zc = march_zc(d);
-  k_gradt_fx<<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0, s>>>(
-      d, make_face_geom(d), u, fx_limits(alpha), c, beta, out, zc);
+  k_gradt_fx<false><<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY),
+                      0, s>>>(d, make_face_geom(d), u, fx_limits(alpha), c, beta, out, nullptr, zc);
+}
+
+int64_t gradt_norm2_blocks(Dims d) {
+  const int zc = march_zc(d);
+  return (int64_t)div_up(d.nx, BX) * div_up(d.ny, BY) * div_up(d.nz, zc);
+}
+
+int64_t launch_gradt_norm2(Dims d, const double* u, double alpha, double* part, cudaStream_t s) {
+  count_launch();
+  const int zc = march_zc(d);
+  k_gradt_fx<true><<<dim3(div_up(d.nx, BX), div_up(d.ny, BY), div_up(d.nz, zc)), dim3(BX, BY), 0,
+                     s>>>(d, make_face_geom(d), u, fx_limits(alpha), nullptr, 0.0, nullptr, part,
+                          zc);
+  return gradt_norm2_blocks(d);
 }
 
 void launch_gradient_t(Dims d, const double* u, double* out, double inv_h, cudaStream_t s) {
@@ -837,7 +882,8 @@ dim3 helm_v4_grid(Dims d) {
 
 void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float* rlo,
                       const double* r64, double rs, float a, float nu_h2, float alpha, float beta,
-                      float* en, double* u, double us, int mode, cudaStream_t s, int flags) {
+                      float* en, double* u, double us, int mode, cudaStream_t s, int flags,
+                      const float* pe, double ps) {
   const FaceGeom32 p = make_face_geom32(d);
   const float rs_hi = (float)rs, rs_lo = (float)(rs - (double)rs_hi);
   count_launch();
@@ -845,13 +891,54 @@ void launch_helm_cheb(Dims d, const float* e, const float* eo, float* r32, float
   const int zch = helm_zchunks(d);
   if (mode == 0)
     launch_pdl(k_helm_cheb_v4<0>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
-               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, flags);
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, pe, ps, flags);
   else if (mode == 1)
     launch_pdl(k_helm_cheb_v4<1>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
-               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, flags);
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, pe, ps, flags);
   else
     launch_pdl(k_helm_cheb_v4<2>, helm_v4_grid(d), dim3(32, HVY), 0, s, g, p, zch, e, eo, r32,
-               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, flags);
+               rlo, r64, rs_hi, rs_lo, a, nu_h2, alpha, beta, en, u, us, pe, ps, flags);
+}
+
+// u = ps pe on the interior faces, 0 on the wall faces (a predictor
+// correction kept in FP32 written to the FP64 iterate when no later
+// correction's last step does it)
+__global__ void __launch_bounds__(32 * HVY) k_helm_flush(FaceGeom g, FaceGeom32 p, int zchunks,
+                                                         const float* __restrict__ pe, double ps,
+                                                         double* __restrict__ u) {
+  const int c = blockIdx.z / zchunks;
+  const int zc = blockIdx.z - c * zchunks;
+  const int x0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+  const int j = blockIdx.y * HVY + threadIdx.y;
+  const int n0 = sel3(c, p.n[0][0], p.n[1][0], p.n[2][0]);
+  const int n1 = sel3(c, p.n[0][1], p.n[1][1], p.n[2][1]);
+  const int n2 = sel3(c, p.n[0][2], p.n[1][2], p.n[2][2]);
+  const int z0 = zc * ZH;
+  if (z0 >= n2 || x0 >= n0 || j >= n1) return;
+  const int z1 = min(z0 + ZH, n2);
+  const int64_t sy = sel3(c, p.sy[0], p.sy[1], p.sy[2]), sz = sel3(c, p.sz[0], p.sz[1], p.sz[2]);
+  const int64_t sy64 = sel3(c, g.sy[0], g.sy[1], g.sy[2]);
+  const int64_t sz64 = sel3(c, g.sz[0], g.sz[1], g.sz[2]);
+  int64_t f = sel3(c, p.off[0], p.off[1], p.off[2]) + (int64_t)z0 * sz + (int64_t)j * sy + x0;
+  int64_t f64 = sel3(c, g.off[0], g.off[1], g.off[2]) + (int64_t)z0 * sz64 + (int64_t)j * sy64 + x0;
+  const bool wally = c == 1 && (j == 0 || j == n1 - 1);
+  for (int z = z0; z < z1; ++z, f += sz, f64 += sz64) {
+    const bool wallz = c == 2 && (z == 0 || z == n2 - 1);
+    const float4 v = *reinterpret_cast<const float4*>(pe + f);
+    const float vq[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (x0 + q >= n0) break;
+      const bool wallx = c == 0 && (x0 + q == 0 || x0 + q == n0 - 1);
+      u[f64 + q] = (wallx || wally || wallz) ? 0.0 : ps * f2d_exact(vq[q]);
+    }
+  }
+}
+
+void launch_helm_flush(Dims d, const float* pe, double ps, double* u, cudaStream_t s) {
+  count_launch();
+  k_helm_flush<<<helm_v4_grid(d), dim3(32, HVY), 0, s>>>(make_face_geom(d), make_face_geom32(d),
+                                                          helm_zchunks(d), pe, ps, u);
 }
 
 int64_t launch_helm_resid_ds(Dims d, const float* e, float* rhi, float* rlo, double a,
