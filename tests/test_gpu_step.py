@@ -9,7 +9,7 @@ from gpu_cases import dev, host, rel
 pytestmark = pytest.mark.gpu
 
 
-def _run(case, u_n=None, u_nm1=None, p_n=None, F_n=None, prec=0, rtol=1e-13):
+def _run(case, u_n=None, u_nm1=None, p_n=None, F_n=None, prec=0, rtol=1e-13, helm_rtol=1e-14):
     from oracle import step
     from paper_2501_15314_gb300.api import IBMSolver
     g = case.grid()
@@ -24,7 +24,7 @@ def _run(case, u_n=None, u_nm1=None, p_n=None, F_n=None, prec=0, rtol=1e-13):
                      dev(u_nm1 if u_nm1 is not None else (u_n if u_n is not None else z(g.n_faces))),
                      dev(p_n if p_n is not None else z(g.m)),
                      dev(F_n if F_n is not None else z(3 * case.N)), dev(U), dev(f),
-                     precond_prec=prec, rtol=rtol, helm_rtol=1e-14, helm_maxit=12)
+                     precond_prec=prec, rtol=rtol, helm_rtol=helm_rtol, helm_maxit=12)
     s.close()
     return ref, {k: host(v) for k, v in out.items()}, st
 
@@ -112,6 +112,29 @@ def test_step_with_history_wide_grid(cuda_device):
     for k in ("u", "p", "F"):
         assert rel(out[k], ref[k]) < 1e-10, (k, rel(out[k], ref[k]))
     assert st["helm_iters"] >= 2, st
+
+
+@pytest.mark.parametrize("helm_rtol,n_corr,tol", [(1e-4, 1, 5e-3), (1e-10, 2, 1e-8),
+                                                   (1e-14, 3, 1e-10)])
+def test_predictor_with_one_two_and_three_corrections(cuda_device, helm_rtol, n_corr, tol):
+    """The predictor's first correction stays in FP32 until the second's last
+    step writes u from both; alone, it is written by a pass of its own; a
+    third one adds into u.  Each count gives the oracle's step to the
+    accuracy its tolerance allows (every term of Eq. (ustar) active)."""
+    case = _with_inputs(gc.ragged_multi())
+    g = case.grid()
+    rng = np.random.default_rng(11)
+    mask = g.interior_face_mask_packed()
+    u_n = 0.3 * rng.standard_normal(g.n_faces) * mask
+    u_nm1 = 0.3 * rng.standard_normal(g.n_faces) * mask
+    p_n = rng.standard_normal(g.m)
+    F_n = rng.standard_normal(3 * case.N)
+    ref, out, st = _run(case, u_n, u_nm1, p_n, F_n, helm_rtol=helm_rtol)
+    assert st["helm_iters"] == n_corr if n_corr < 3 else st["helm_iters"] >= 3, st
+    assert st["helm_relres"] <= helm_rtol, st
+    for k in ("u", "p", "F"):
+        assert np.all(np.isfinite(out[k]))
+        assert rel(out[k], ref[k]) < tol, (k, rel(out[k], ref[k]))
 
 
 def test_step_unchanged_by_concurrent_bulk_copies(cuda_device):
