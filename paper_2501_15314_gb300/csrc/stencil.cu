@@ -368,9 +368,9 @@ __device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const double* __r
                                             int x, int y, int z, int q) {
   if (q <= 0 || q >= g.n[E][E] - 1) return dsf{0.f, 0.f};
   const int ax = E == 0 ? q : x, ay = E == 1 ? q : y, az = E == 2 ? q : z;
-  const dsf ue = ds_add(ldu<E>(g, u, ax - (C == 0), ay - (C == 1), az - (C == 2)),
+  const dsf ue = ds_add_d(ldu<E>(g, u, ax - (C == 0), ay - (C == 1), az - (C == 2)),
                         ldu<E>(g, u, ax, ay, az));
-  const dsf uc = ds_add(ldu<C>(g, u, ax - (E == 0), ay - (E == 1), az - (E == 2)),
+  const dsf uc = ds_add_d(ldu<C>(g, u, ax - (E == 0), ay - (E == 1), az - (E == 2)),
                         ldu<C>(g, u, ax, ay, az));
   return ds_mul(ue, uc);
 }
@@ -387,9 +387,11 @@ __device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const double* __r
 // The march runs along z; the flux through the lower z-edge (or, for u_z, the
 // lower cell-centred square) is the previous face's upper one and is reused.
 // The FP64 pipe of GB300 is ~58x slower than its FP32 pipes, so every FP64
-// input is split exactly into an FP32 pair (split_exact, integer operations)
-// and the formula is evaluated in double-single arithmetic (about 2^-46
-// relative); the FP64 result is the exact sum of the pair (one FP64 add).
+// input is split into an FP32 pair (split_exact, integer operations, 2^-46
+// relative) and the formula is evaluated in double-single arithmetic; its
+// sums take Dekker's addition (ds_add_d), whose error, a few units of 2^-46
+// of the operands, is of the order the inputs' splits already carry; the
+// FP64 result is the exact sum of the pair (one FP64 add).
 // Templating on C makes every stride and boundary test a compile-time case.
 template <int C>
 __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
     if (C == 2) {
       const dsf lo = (z0 - 1 >= 1) ? ldu<2>(g, un, i, j, z0 - 1) : Z;
       const dsf mid = (z0 >= 1 && z0 <= n2 - 2) ? ldu<2>(g, un, i, j, z0) : Z;
-      carry = sq(ds_add(lo, mid));
+      carry = sq(ds_add_d(lo, mid));
     } else {
       carry = edge_flux_ds<C, 2>(g, un, i, j, z0, z0);
     }
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
       if (with_adv) {
         const dsf mid = (z >= 1 && z <= n2 - 2) ? ldu<2>(g, un, i, j, z) : Z;
         const dsf hi = (z + 1 <= n2 - 2) ? ldu<2>(g, un, i, j, z + 1) : Z;
-        carry = sq(ds_add(mid, hi));
+        carry = sq(ds_add_d(mid, hi));
       }
       continue;
     }
@@ -461,19 +463,19 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
     const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
     const dsf u0 = split_exact(__ldg(un + f));
     // 4/(2dt) u^n - 1/(2dt) u^{n-1} - (p_+ - p_-)/h (+ f)
-    dsf v = ds_add(ds_mul(c4, u0), ds_neg(ds_mul(c1, split_exact(__ldg(unm1 + f)))));
-    const dsf dp = ds_add(split_exact(__ldg(pn + cp)), ds_neg(split_exact(__ldg(pn + cp - cstr))));
-    v = ds_add(v, ds_neg(ds_mul(cp_h, dp)));
-    if (fb) v = ds_add(v, split_exact(__ldg(fb + f)));
+    dsf v = ds_add_d(ds_mul(c4, u0), ds_neg(ds_mul(c1, split_exact(__ldg(unm1 + f)))));
+    const dsf dp = ds_add_d(split_exact(__ldg(pn + cp)), ds_neg(split_exact(__ldg(pn + cp - cstr))));
+    v = ds_add_d(v, ds_neg(ds_mul(cp_h, dp)));
+    if (fb) v = ds_add_d(v, split_exact(__ldg(fb + f)));
     if (with_adv) {
       dsf acc;
       if (C == 2) {
         const dsf up = (z + 1 <= n2 - 2) ? ldu<2>(g, un, i, j, z + 1) : Z;
-        const dsf up2 = sq(ds_add(u0, up));
-        acc = ds_add(up2, ds_neg(carry));
+        const dsf up2 = sq(ds_add_d(u0, up));
+        acc = ds_add_d(up2, ds_neg(carry));
         carry = up2;
-        acc = ds_add(acc, ds_add(fx_up, ds_neg(fx_lo)));
-        acc = ds_add(acc, ds_add(edge_flux_ds<2, 1>(g, un, i, j, z, j + 1),
+        acc = ds_add_d(acc, ds_add_d(fx_up, ds_neg(fx_lo)));
+        acc = ds_add_d(acc, ds_add_d(edge_flux_ds<2, 1>(g, un, i, j, z, j + 1),
                                  ds_neg(edge_flux_ds<2, 1>(g, un, i, j, z, j))));
       } else {
         // own axis: (u_+ - u_-)(u_+ + 2 u_0 + u_-), wall faces read as 0
@@ -482,18 +484,18 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
         const dsf up = (pc + 1 <= nc - 2) ? ldu<C>(g, un, i + (C == 0), j + (C == 1), z) : Z;
         const dsf um = (pc - 1 >= 1) ? ldu<C>(g, un, i - (C == 0), j - (C == 1), z) : Z;
         const dsf two_u0 = {2.f * u0.hi, 2.f * u0.lo};
-        acc = ds_mul(ds_add(up, ds_neg(um)), ds_add(ds_add(up, um), two_u0));
+        acc = ds_mul(ds_add_d(up, ds_neg(um)), ds_add_d(ds_add_d(up, um), two_u0));
         if (O == 0) {
-          acc = ds_add(acc, ds_add(fx_up, ds_neg(fx_lo)));
+          acc = ds_add_d(acc, ds_add_d(fx_up, ds_neg(fx_lo)));
         } else {
-          acc = ds_add(acc, ds_add(edge_flux_ds<C, O>(g, un, i, j, z, j + 1),
+          acc = ds_add_d(acc, ds_add_d(edge_flux_ds<C, O>(g, un, i, j, z, j + 1),
                                    ds_neg(edge_flux_ds<C, O>(g, un, i, j, z, j))));
         }
         const dsf fz = edge_flux_ds<C, 2>(g, un, i, j, z, z + 1);
-        acc = ds_add(acc, ds_add(fz, ds_neg(carry)));
+        acc = ds_add_d(acc, ds_add_d(fz, ds_neg(carry)));
         carry = fz;
       }
-      v = ds_add(v, ds_neg(ds_mul(ca, acc)));
+      v = ds_add_d(v, ds_neg(ds_mul(ca, acc)));
     }
     rhs[f] = f2d_exact(v.hi) + f2d_exact(v.lo);
   }
