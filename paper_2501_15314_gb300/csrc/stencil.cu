@@ -685,7 +685,8 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_cheb_v4(
 // A e = r^ (r^ = r / ||r|| held as the pair (rhi, rlo)) and added ||r|| e to
 // the FP64 iterate, the new residual is ||r|| (r^ - A e).  This kernel forms
 // q = r^ - A e exactly enough (A e of the FP32 e with error-free sums and
-// products, about 2^-46 relative to r^) and writes it back to (rhi, rlo); the
+// products, the last two sums by Dekker's addition: a few units of 2^-46
+// relative to r^) and writes it back to (rhi, rlo); the
 // block's sum of q.hi^2 goes to part[block * stride] (every block writes
 // one).  The FP64 pipe is not used.
 __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
@@ -759,8 +760,8 @@ __global__ void __launch_bounds__(32 * HVY) k_helm_resid_ds(
       s = ds_add_f(s, evn[q]);
       const int gh = gx[q] + gy + gz;
       const dsf diag = gh == 0 ? D6 : ds_add(A, ds_mul_f(NU, (float)(6 + gh)));
-      const dsf Ae = ds_add(ds_mul_f(diag, ev[q]), ds_neg(ds_mul(NU, s)));
-      dsf qv = ds_add(dsf{vrh[q], vrl[q]}, ds_neg(Ae));
+      const dsf Ae = ds_add_d(ds_mul_f(diag, ev[q]), ds_neg(ds_mul(NU, s)));
+      dsf qv = ds_add_d(dsf{vrh[q], vrl[q]}, ds_neg(Ae));
       const bool live = val[q] && !wallx[q] && !wally && !wallz;
       if (!live) qv = dsf{0.f, 0.f};
       oh[q] = qv.hi;
