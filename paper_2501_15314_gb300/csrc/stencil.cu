@@ -375,6 +375,22 @@ __device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const double* __r
   return ds_mul(ue, uc);
 }
 
+// The same flux in FP64 straight from the FP64 values (no splits): the
+// kernel below forms one pair of fluxes per face this way, on the FP64
+// pipe, which its double-single arithmetic leaves idle.
+template <int C, int E>
+__device__ __forceinline__ double edge_flux_f64(const FaceGeom& g, const double* __restrict__ u,
+                                                int x, int y, int z, int q) {
+  if (q <= 0 || q >= g.n[E][E] - 1) return 0.0;
+  const int ax = E == 0 ? q : x, ay = E == 1 ? q : y, az = E == 2 ? q : z;
+  auto at = [&](int e, int xx, int yy, int zz) {
+    return __ldg(u + g.off[e] + (int64_t)zz * g.sz[e] + (int64_t)yy * g.sy[e] + xx);
+  };
+  const double ue = at(E, ax - (C == 0), ay - (C == 1), az - (C == 2)) + at(E, ax, ay, az);
+  const double uc = at(C, ax - (E == 0), ay - (E == 1), az - (E == 2)) + at(C, ax, ay, az);
+  return ue * uc;
+}
+
 // Right-hand side of the predictor, Eq. (ustar), with the convective term
 // fused in, for the C-faces (one launch per velocity component):
 //   rhs = (4 u^n - u^{n-1}) / (2 dt) - G p^n + f - A(u^n) on interior faces
@@ -386,12 +402,16 @@ __device__ __forceinline__ dsf edge_flux_ds(const FaceGeom& g, const double* __r
 //       + sum over the two other axes of (flux at the upper edge - lower edge).
 // The march runs along z; the flux through the lower z-edge (or, for u_z, the
 // lower cell-centred square) is the previous face's upper one and is reused.
-// The FP64 pipe of GB300 is ~58x slower than its FP32 pipes, so every FP64
-// input is split into an FP32 pair (split_exact, integer operations, 2^-46
+// The FP64 pipe of GB300 is ~58x slower than its FP32 pipes, so the FP64
+// inputs are split into FP32 pairs (split_exact, integer operations, 2^-46
 // relative) and the formula is evaluated in double-single arithmetic; its
 // sums take Dekker's addition (ds_add_d), whose error, a few units of 2^-46
-// of the operands, is of the order the inputs' splits already carry; the
-// FP64 result is the exact sum of the pair (one FP64 add).
+// of the operands, is of the order the inputs' splits already carry.  One
+// pair of edge fluxes per face (the y-edges of u_x and u_z, the x-edges of
+// u_y) is formed in FP64 from the FP64 values instead, which keeps the
+// otherwise idle FP64 pipe busy and saves their splits; their difference
+// joins the sum as a pair.  The FP64 result is the exact sum of the pair
+// (one FP64 add).
 // Templating on C makes every stride and boundary test a compile-time case.
 template <int C>
 __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
@@ -453,11 +473,16 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
       }
       continue;
     }
-    // x-edge fluxes (shared between lanes: every lane takes part)
+    // x-edge fluxes (shared between lanes: every lane takes part); for u_y
+    // in FP64 (its pair of fluxes on the FP64 pipe)
     dsf fx_lo = Z, fx_up = Z;
-    if (with_adv && C != 0) {
-      constexpr int CC = C == 0 ? 1 : C;   // (no x-edge flux for u_x itself)
-      fx_up = xflux_pair([&](int q) { return edge_flux_ds<CC, 0>(g, un, i, j, z, q); }, fx_lo);
+    double fx64_lo = 0.0, fx64_up = 0.0;
+    if (with_adv && C == 2) {
+      fx_up = xflux_pair([&](int q) { return edge_flux_ds<2, 0>(g, un, i, j, z, q); }, fx_lo);
+    } else if (with_adv && C == 1) {
+      fx64_up = act ? edge_flux_f64<1, 0>(g, un, i, j, z, i + 1) : 0.0;
+      fx64_lo = __shfl_up_sync(0xffffffffu, fx64_up, 1);
+      if (lane == 0) fx64_lo = act ? edge_flux_f64<1, 0>(g, un, i, j, z, i) : 0.0;
     }
     if (!act) continue;
     const int64_t cp = (int64_t)z * csz + (int64_t)j * csy + i;   // cell on the + side
@@ -475,8 +500,9 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
         acc = ds_add_d(up2, ds_neg(carry));
         carry = up2;
         acc = ds_add_d(acc, ds_add_d(fx_up, ds_neg(fx_lo)));
-        acc = ds_add_d(acc, ds_add_d(edge_flux_ds<2, 1>(g, un, i, j, z, j + 1),
-                                 ds_neg(edge_flux_ds<2, 1>(g, un, i, j, z, j))));
+        // y-edges in FP64
+        acc = ds_add_d(acc, split_exact(edge_flux_f64<2, 1>(g, un, i, j, z, j + 1) -
+                                        edge_flux_f64<2, 1>(g, un, i, j, z, j)));
       } else {
         // own axis: (u_+ - u_-)(u_+ + 2 u_0 + u_-), wall faces read as 0
         constexpr int O = 1 - C;   // the other in-plane axis
@@ -485,11 +511,12 @@ __global__ void __launch_bounds__(BX * BY) k_predictor_rhs_ds(
         const dsf um = (pc - 1 >= 1) ? ldu<C>(g, un, i - (C == 0), j - (C == 1), z) : Z;
         const dsf two_u0 = {2.f * u0.hi, 2.f * u0.lo};
         acc = ds_mul(ds_add_d(up, ds_neg(um)), ds_add_d(ds_add_d(up, um), two_u0));
+        // the other in-plane axis's pair of fluxes in FP64 (x for u_y, y for u_x)
         if (O == 0) {
-          acc = ds_add_d(acc, ds_add_d(fx_up, ds_neg(fx_lo)));
+          acc = ds_add_d(acc, split_exact(fx64_up - fx64_lo));
         } else {
-          acc = ds_add_d(acc, ds_add_d(edge_flux_ds<C, O>(g, un, i, j, z, j + 1),
-                                   ds_neg(edge_flux_ds<C, O>(g, un, i, j, z, j))));
+          acc = ds_add_d(acc, split_exact(edge_flux_f64<C, O>(g, un, i, j, z, j + 1) -
+                                          edge_flux_f64<C, O>(g, un, i, j, z, j)));
         }
         const dsf fz = edge_flux_ds<C, 2>(g, un, i, j, z, z + 1);
         acc = ds_add_d(acc, ds_add_d(fz, ds_neg(carry)));
